@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused D2Q4^5 collide-stream step on GB300.
+
+Workload (one step = one fused collide-stream kernel over the whole lattice):
+periodic 8192 x 8192 lattice at rest with a Gaussian random initial velocity
+(correlation length 64 cells, std 1e-3, seeds 1 and 2), cK^2 = 1.5, cmu^2 = 0.5
+(lambda = 1, mu = 0.5), time step at 0.9 of the CFL-like bound, b = 0.
+
+Main line: the FP64 path (MLUPS).  Also reported: the FP32 / BF16 / FP16
+storage paths (MLUPS, speed-up over FP64, relative L2 error of every moment
+field against the FP64 run after the same number of steps), the roofline of the
+dominant kernel, an end-to-end figure through the C ABI with host buffers, the
+SM clocks seen during the timed region, and the FP64 oracle timed on the host
+cores on a bounded sample.
+
+``--impl reference`` times the FP64 oracle (the only reference this paper has:
+it ships no code) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = 8192
+CK2, CMU2, CFL = 1.5, 0.5, 0.9
+ELL, STD = 64.0, 1e-3
+METRIC = "MLUPS and % of HBM roofline; mixed-precision vs FP64 at stated L2 error"
+BYTES_PER_NODE = {"f64": 320, "f32": 160, "bf16": 80, "f16": 80}   # one read + one write of 20 values
+FP64_OPS_PER_NODE = 47                                                # DADD/DFMA per node, no forcing
+
+
+def _workload_desc(nx, ny):
+    return (f"periodic {nx}x{ny} lattice at rest, Gaussian random initial velocity (ell={ELL:g} cells, "
+            f"std={STD:g}, seeds 1,2), cK^2={CK2}, cmu^2={CMU2} (lambda=1, mu=0.5), dt at {CFL} of the CFL bound, b=0")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [s.strip() for s in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def make_inputs(nx, ny):
+    import workloads as W
+    wl = W.grf_periodic(nx, ny, CK2, CMU2, cfl=CFL, ell=ELL, std=STD, seeds=(1, 2), steps=0)
+    return wl
+
+
+def _cpu_oracle_mlups(nx, ny, steps, threads=None):
+    """Time the FP64 oracle (as it stands) on the host cores: MLUPS, threads used."""
+    import oracle
+    from oracle import Oracle, Params
+    oracle.build()
+    if threads:
+        oracle.set_threads(threads)
+    wl = make_inputs(nx, ny)
+    o = Oracle(Params(nx, ny, wl.dx, wl.dt, wl.cK, wl.cmu, False))
+    o.init(wl.U0, wl.dU0dx, wl.dU0dy, None, wl.u0)
+    o.step(track_displacement=False)   # warm caches and thread pool
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step(track_displacement=False)
+    dt = time.perf_counter() - t0
+    return nx * ny * steps / dt / 1e6, oracle.max_threads(), dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    # bounded sample of the same workload: a 512 x 512 periodic lattice of the same kind
+    nx = ny = 512
+    t0 = time.perf_counter()
+    mlups, threads, _ = _cpu_oracle_mlups(nx, ny, args.steps)
+    wall = time.perf_counter() - t0
+    line = {"metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * nx * ny / (mlups * 1e6), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": _workload_desc(NX, NY), "sample": f"{nx}x{ny} lattice of the same workload"},
+            "impl": "reference",
+            "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                             "sample": f"FP64 C oracle, {nx}x{ny} periodic GRF lattice, {args.steps} steps"},
+            "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 2)}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2408_01081_gb300 import lbm
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lbm.load()
+    nx, ny = args.nx, args.ny
+    wl = make_inputs(nx, ny)
+    n_nodes = nx * ny
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", local)
+    U0 = torch.from_numpy(wl.U0).to(dev)
+    Ux = torch.from_numpy(wl.dU0dx).to(dev)
+    Uy = torch.from_numpy(wl.dU0dy).to(dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    finals = {}
+    clocks = None
+    for storage in args.formats:
+        lat = lbm.Lattice(nx, ny, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet=False, storage=storage,
+                          track_displacement=False, stream=stream.cuda_stream)
+        lat.init(U0, Ux, Uy)
+        lat.step(args.warmup)
+        barrier()
+        clk = Clocks(local) if storage == "f64" else None
+        if clk:
+            clk.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(args.steps)
+        e1.record(stream)
+        barrier()
+        if clk:
+            clocks = clk.stop()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        out = torch.empty((10, ny, nx), dtype=torch.float64, device=dev)
+        lat.moments(out)
+        torch.cuda.synchronize()
+        finals[storage] = out[0:5].clone()
+        del out
+        lat.close()
+        mlups_rank = n_nodes * args.steps / (ms * 1e-3) / 1e6
+        results[storage] = {"ms_per_step": ms / args.steps, "mlups": mlups_rank * ws}
+
+    # relative L2 of every moment field against the FP64 run after the same steps
+    ref = finals.get("f64")
+    names = ["v_x", "v_y", "j_s", "j_d", "j_xy"]
+    for s in args.formats:
+        if s == "f64" or ref is None:
+            continue
+        err = {}
+        for q, nm in enumerate(names):
+            num = torch.linalg.vector_norm(finals[s][q] - ref[q]).item()
+            den = torch.linalg.vector_norm(ref[q]).item()
+            err[nm] = num / den if den > 0 else num
+        results[s]["rel_l2_vs_f64"] = err
+        results[s]["speedup_vs_f64"] = results[s]["mlups"] / results["f64"]["mlups"]
+    del finals
+
+    # end to end through the C ABI with host buffers: H2D of the initial data from pinned
+    # memory, init, K steps, D2H of the ten output fields, all inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hU0 = torch.from_numpy(wl.U0).pin_memory()
+        hUx = torch.from_numpy(wl.dU0dx).pin_memory()
+        hUy = torch.from_numpy(wl.dU0dy).pin_memory()
+        hout = torch.empty((10, ny, nx), dtype=torch.float64).pin_memory()
+        lat = lbm.Lattice(nx, ny, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet=False, storage="f64",
+                          track_displacement=False, stream=stream.cuda_stream)
+        barrier()
+        t0 = time.perf_counter()
+        lat.init(hU0.numpy(), hUx.numpy(), hUy.numpy())
+        lat.step(args.steps)
+        lat.moments(hout.numpy())
+        barrier()
+        wall = max_over_ranks(time.perf_counter() - t0)
+        lat.close()
+        h2d = 3 * 5 * n_nodes * 8
+        d2h = 10 * n_nodes * 8
+        e2e = {"value": round(n_nodes * args.steps * ws / wall / 1e6, 2), "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
+               "wall_s": round(wall, 3)}
+        del hU0, hUx, hUy, hout
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks = _peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s (of fallback)"
+    r64 = results["f64"]
+    nodes_per_s = n_nodes / (r64["ms_per_step"] * 1e-3)
+    hbm_ach = BYTES_PER_NODE["f64"] * nodes_per_s / 1e9
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2032.0
+    # FP64 pipe: 2 DFMA/DADD per SM per clock on GB300 (measured 601.6 G DFMA/s at ~1.98 GHz)
+    fp64_peak = 152 * 2 * sm_mhz * 1e6 / 1e9
+    fp64_ach = FP64_OPS_PER_NODE * nodes_per_s / 1e9
+    roofline = {"bound": "alu", "achieved": round(fp64_ach, 2), "peak": round(fp64_peak, 2), "unit": "GFP64op/s",
+                "frac": round(fp64_ach / fp64_peak, 4), "traffic": args.traffic,
+                "kernel": "lbmk::step_kernel<F64,2,periodic>",
+                "peak_source": "152 SMs x 2 FP64 ops/clk x median SM clock sampled in the timed region",
+                "hbm": {"achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                        "frac": round(hbm_ach / hbm_peak, 4), "bytes_per_node": BYTES_PER_NODE["f64"],
+                        "peak_source": peak_src}}
+    mixed = {}
+    for s in args.formats:
+        if s == "f64":
+            continue
+        r = results[s]
+        nps = n_nodes / (r["ms_per_step"] * 1e-3)
+        ach = BYTES_PER_NODE[s] * nps / 1e9
+        mixed[s] = {"mlups": round(r["mlups"], 1), "ms_per_step": round(r["ms_per_step"], 4),
+                    "speedup_vs_f64": round(r["speedup_vs_f64"], 3),
+                    "hbm": {"achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                            "frac": round(ach / hbm_peak, 4), "bytes_per_node": BYTES_PER_NODE[s]},
+                    "rel_l2_vs_f64": {k: float(f"{v:.3e}") for k, v in r["rel_l2_vs_f64"].items()},
+                    "error_at_step": args.warmup + args.steps}
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        cx = cy = 1024
+        mlups_cpu, threads, wall = _cpu_oracle_mlups(cx, cy, args.cpu_steps)
+        cpu = {"value": round(mlups_cpu, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+               "sample": f"FP64 C oracle, {cx}x{cy} periodic lattice of the same workload, "
+                         f"{args.cpu_steps} steps ({wall:.1f} s)"}
+    line = {"metric": METRIC, "value": round(r64["mlups"], 1), "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r64["ms_per_step"], 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": _workload_desc(nx, ny), "nodes": n_nodes, "storage": "f64",
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": f"inputs larger than L2: state {2 * 20 * n_nodes * 8 / 1e9:.1f} GB double-buffered"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clocks, "mixed_precision": mixed}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=NX)
+    ap.add_argument("--ny", type=int, default=NY)
+    ap.add_argument("--formats", default="f64,f32,bf16,f16")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the step kernel from an ncu capture (null if unknown)")
+    args = ap.parse_args()
+    args.formats = [s for s in args.formats.split(",") if s]
+    if "f64" not in args.formats:
+        args.formats.insert(0, "f64")
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,154 @@
+/*
+ * lbm.h -- C ABI of the GB300 vectorial lattice Boltzmann library for 2D linear
+ * elastodynamics (D2Q4^5 scheme of Boolakee, Geier and De Lorenzis, arXiv 2408.01081).
+ *
+ * Problem (Sec. 2): d2u/dt2 = div(sigma) + b on a rectangle, periodic on both
+ * axes or u = u_D on all four edges, with u(0) = u0 and du/dt(0) = v0.  The
+ * library advances the first-order system of Eq. system, U = [v_x, v_y, j_s,
+ * j_d, j_xy], with 4 vector populations per node (Eq. index_vel).  All
+ * quantities are dimensionless (Sec. 2.3): lattice spacing dx, time step dt,
+ * lattice speed c = dx/dt, wave speeds cK and cmu.
+ *
+ * Conventions shared by every call
+ *   - Field arrays are dense, field-major and row-major: [field][y][x], x fastest,
+ *     FP64.  Node (k, l) sits at ((k + 1/2) dx, (l + 1/2) dx).
+ *   - Population arrays are [d][k][y][x] with d = 0..3 the velocities
+ *     (1,0), (0,1), (-1,0), (0,-1) and k = 0..4 the components of U.
+ *   - `on_device` = 1: the pointer is CUDA device memory (e.g. a torch tensor's
+ *     data_ptr); 0: host memory.  Host pointers are copied synchronously with
+ *     respect to the context's stream; the caller keeps ownership of every buffer
+ *     it passes and may free it when the call returns.
+ *   - The context owns all device memory it allocates (created by lbm_create,
+ *     released by lbm_destroy).  Work is enqueued on the stream given at creation.
+ *   - No call aborts.  Errors return a status; LBM_ERR_CUDA is sticky: every later
+ *     call on the same context returns it.  lbm_last_error() gives a message.
+ *   - Calls on one context are not thread-safe; distinct contexts are independent.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,       /* invalid argument: NULL pointer, size, enum, table too short  */
+    LBM_ERR_CFL = 2,       /* 2 sqrt(cK^2 + cmu^2) >= c: some g_ij is not SPD (Eq. stab_cond) */
+    LBM_ERR_OOM = 3,       /* device allocation failed                                      */
+    LBM_ERR_CUDA = 4,      /* a CUDA runtime call or launch failed (sticky)                 */
+    LBM_ERR_UNSTABLE = 5,  /* a non-finite value was found by lbm_check_finite              */
+    LBM_ERR_TIMEOUT = 6,   /* a bounded device-side wait ran out                            */
+    LBM_ERR_STATE = 7      /* call order: stepping before lbm_init, data for step m missing */
+} lbm_status;
+
+typedef enum { LBM_PERIODIC = 0, LBM_DIRICHLET = 1 } lbm_bc;
+
+/* Storage precision of the populations.  LBM_F64 stores and computes in FP64;
+ * the others store in the named format and compute in FP32 (the initialisation,
+ * the Dirichlet reconstruction and all reductions stay in FP64). */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_BF16 = 2, LBM_F16 = 3 } lbm_storage;
+
+typedef struct {
+    int32_t nx, ny;              /* nodes per row / number of rows, each >= 2            */
+    int32_t bc;                  /* lbm_bc                                               */
+    int32_t storage;             /* lbm_storage                                          */
+    double dx, dt;               /* lattice spacing and time step, > 0 (Sec. 3.1)        */
+    double cK, cmu;              /* dimensionless wave speeds c~_K > 0, c~_mu >= 0       */
+    int32_t track_displacement;  /* 1: keep u* and update it every step (Eq. trapezoidal) */
+    int32_t reserved;            /* must be 0                                            */
+    void* stream;                /* cudaStream_t for all work; NULL = legacy stream      */
+} lbm_params;
+
+/* Create a context: validates the parameters (LBM_ERR_ARG), the CFL-like
+ * condition 2 sqrt(cK^2 + cmu^2) < dx/dt (Eq. stab_cond; LBM_ERR_CFL) and
+ * allocates two population buffers (plus u* when tracked).  No kernel runs.
+ * On failure *out is set to NULL and nothing is leaked. */
+lbm_status lbm_create(const lbm_params* p, lbm_ctx** out);
+
+/* Second-order initialisation, Eq. ic_second, evaluated per node in FP64.
+ *   U0, dU0dx, dU0dy : [5][ny][nx] initial U (Eq. ic_vector) and its x / y derivatives
+ *   B0               : [2][ny][nx] body load b at t = 0, or NULL for b = 0
+ *   u0               : [2][ny][nx] initial displacement, or NULL for 0 (only read
+ *                      when displacement tracking is on; u^num(0) = u0, Eq. trapezoidal)
+ * Resets the step counter to m = 0 (t = 0). */
+lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const double* dU0dy,
+                    const double* B0, const double* u0, int32_t on_device);
+
+/* Body load as a separable sum (the library copies the tables):
+ *   b_c(x_k, y_l, t_m) = sum_{r<R} X[r][k] * Y[r][l] * T[m][c][r],   c = 0 (b_x), 1 (b_y)
+ * X: [R][nx], Y: [R][ny], T: [nt][2][R]; m = 0 .. nt-1 indexes t = m dt.
+ * 1 <= R <= 16.  R = 0 (pointers ignored) removes the body load.  Stepping to a
+ * time whose row is missing returns LBM_ERR_STATE.  (Eq. lbe uses B at time t.) */
+lbm_status lbm_set_forcing(lbm_ctx* ctx, int32_t R, const double* X, const double* Y,
+                           const double* T, int64_t nt, int32_t on_device);
+
+/* Dirichlet data (only for LBM_DIRICHLET): d/dt u_D at the wall midpoints x_b at
+ * time t_m + dt/2 for the step m -> m+1 (Eq. bc_ansatz with q = 1/2, Eq. bc_q).
+ * g: [nt][2][2(nx+ny)], the last axis ordered [left wall rows 0..ny-1 | right wall
+ * rows | bottom wall columns 0..nx-1 | top wall columns].  g = NULL (nt ignored)
+ * selects homogeneous data u_D = const.  Stepping past row nt-1 returns LBM_ERR_STATE. */
+lbm_status lbm_set_dirichlet(lbm_ctx* ctx, const double* g, int64_t nt, int32_t on_device);
+
+/* Advance n >= 0 time steps (Sec. 3.6: collision, streaming, boundary rule,
+ * displacement update), asynchronously on the context's stream. */
+lbm_status lbm_step(lbm_ctx* ctx, int64_t n);
+
+/* The ten output fields at the current time t = m dt, FP64, [10][ny][nx]:
+ *   v_x, v_y, j_s, j_d, j_xy  (U^num, Eq. cond_eq),
+ *   u_x, u_y                  (u^num = u* + dt/2 v^num; zeros when not tracked),
+ *   sigma_xx, sigma_yy, sigma_xy  (Eq. sigma_num with V = 1).
+ * With a host pointer the call waits for the stream. */
+lbm_status lbm_moments(lbm_ctx* ctx, double* out, int32_t on_device);
+
+/* Weighted grid norm squared ||f||_P^2 = sum_x sum_ij f_ij^T k_ij f_ij of the
+ * pre-collision populations at the current time, k_ij = g_ij^{-1}
+ * (Definition grid_norm, Eq. def_symmetrizer), reduced in FP64.  Writes one
+ * double to host memory *out; waits for the stream. */
+lbm_status lbm_energy(lbm_ctx* ctx, double* out);
+
+/* Error sums against a caller-supplied exact field set, FP64 reductions:
+ *   exact: [10][ny][nx] in the layout of lbm_moments (on_device as given)
+ *   out (host): [3][10] = per field sum (num - exact)^2, sum exact^2, max |num - exact|.
+ * Waits for the stream.  (Error norms of Sec. 6.1.) */
+lbm_status lbm_error_sums(lbm_ctx* ctx, const double* exact, int32_t on_device, double* out);
+
+/* Pre-collision populations f(x, t) at the current time, FP64 [4][5][ny][nx],
+ * and the displacement helper u*(t) [2][ny][nx] (NULL to skip). */
+lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, double* ustar, int32_t on_device);
+
+/* Replace the state: pre-collision populations f at step m (t = m dt) and u*(t)
+ * (NULL = zeros).  Values are rounded to the storage precision. */
+lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, const double* ustar, int64_t m,
+                               int32_t on_device);
+
+/* LBM_UNSTABLE if any stored population is NaN or infinite, else LBM_OK (waits). */
+lbm_status lbm_check_finite(lbm_ctx* ctx);
+
+/* Current step counter m (t = m dt). */
+lbm_status lbm_time_step(const lbm_ctx* ctx, int64_t* m);
+
+/* Wait until all work enqueued by this context has finished. */
+lbm_status lbm_synchronize(lbm_ctx* ctx);
+
+/* Release all device memory of the context; NULL is accepted. */
+lbm_status lbm_destroy(lbm_ctx* ctx);
+
+/* Message describing the last error on ctx (never NULL; "" when none).  With
+ * ctx = NULL: the last error of a failed lbm_create in this thread. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Raw storage-format state for bit-exact checkpoints: bytes needed, copy out, copy in. */
+lbm_status lbm_state_bytes(const lbm_ctx* ctx, int64_t* nbytes);
+lbm_status lbm_save_state(lbm_ctx* ctx, void* dst, int32_t on_device);
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t m, int32_t on_device);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,604 @@
+// Host side of the C ABI declared in include/lbm.h: argument checks, device
+// memory, data tables and kernel launches for one lattice.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lbm.h"
+#include "lbm_dispatch.h"
+
+using lbmh::KindOps;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+const KindOps* ops_for(int storage)
+{
+    switch (storage) {
+    case LBM_F64: return &lbmh::kind_ops_0;
+    case LBM_F32: return &lbmh::kind_ops_1;
+    case LBM_BF16: return &lbmh::kind_ops_2;
+    case LBM_F16: return &lbmh::kind_ops_3;
+    default: return nullptr;
+    }
+}
+
+constexpr int kRedBlocks = 152 * 4;   // blocks of the FP64 reductions (one partial each)
+constexpr int kMaxR = 16;
+
+// 5x5 inverse by Gauss-Jordan elimination with partial pivoting (FP64)
+bool invert5(const double (&a_in)[25], double (&inv)[25])
+{
+    double a[5][10];
+    for (int r = 0; r < 5; ++r)
+        for (int c = 0; c < 10; ++c) a[r][c] = (c < 5) ? a_in[r * 5 + c] : (c - 5 == r ? 1.0 : 0.0);
+    for (int col = 0; col < 5; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 5; ++r)
+            if (std::fabs(a[r][col]) > std::fabs(a[piv][col])) piv = r;
+        if (a[piv][col] == 0.0) return false;
+        if (piv != col)
+            for (int c = 0; c < 10; ++c) std::swap(a[piv][c], a[col][c]);
+        const double d = a[col][col];
+        for (int c = 0; c < 10; ++c) a[col][c] /= d;
+        for (int r = 0; r < 5; ++r) {
+            if (r == col) continue;
+            const double m = a[r][col];
+            if (m != 0.0)
+                for (int c = 0; c < 10; ++c) a[r][c] -= m * a[col][c];
+        }
+    }
+    for (int r = 0; r < 5; ++r)
+        for (int c = 0; c < 5; ++c) inv[r * 5 + c] = a[r][c + 5];
+    return true;
+}
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_params p{};
+    cudaStream_t s = nullptr;
+    const KindOps* ops = nullptr;
+    int pitch = 0;
+    long long plane = 0;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    double* w = nullptr;
+    int R = 0;
+    double* fX = nullptr;
+    double* fY = nullptr;
+    double* fT = nullptr;
+    long long fnt = 0;
+    double* g = nullptr;
+    long long gnt = 0;
+    int nwall = 0;
+    double* scratch = nullptr;   // kRedBlocks * 30 partials + 32 results + flag
+    long long m = 0;
+    bool ready = false;
+    lbm_status sticky = LBM_OK;
+    std::string err;
+    double a = 0, b = 0, c = 0;
+    double k[4][25] = {};
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* ctx, lbm_status st, const std::string& msg)
+{
+    if (ctx) {
+        ctx->err = msg;
+        if (st == LBM_ERR_CUDA) ctx->sticky = LBM_ERR_CUDA;
+    }
+    return st;
+}
+
+lbm_status cuda_fail(lbm_ctx* ctx, cudaError_t e, const char* what)
+{
+    return fail(ctx, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(ctx, call)                                  \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+#define LBM_CHECK_CTX(ctx)                                               \
+    do {                                                                 \
+        if (!(ctx)) return LBM_ERR_ARG;                                  \
+        if ((ctx)->sticky != LBM_OK) return (ctx)->sticky;               \
+    } while (0)
+
+lbmk::NodeArgs node_args(const lbm_ctx* ctx, long long m_time)
+{
+    lbmk::NodeArgs A;
+    A.S = ctx->buf[ctx->cur];
+    A.Sout = ctx->buf[ctx->cur];
+    A.w = ctx->w;
+    A.nx = ctx->p.nx;
+    A.ny = ctx->p.ny;
+    A.pitch = ctx->pitch;
+    A.plane = ctx->plane;
+    A.a = ctx->a;
+    A.b = ctx->b;
+    A.cK = ctx->p.cK;
+    A.cmu = ctx->p.cmu;
+    A.dt = ctx->p.dt;
+    A.c = ctx->c;
+    A.R = 0;
+    A.X = A.Y = A.T = nullptr;
+    if (ctx->R > 0 && m_time >= 0 && m_time < ctx->fnt) {
+        A.R = ctx->R;
+        A.X = ctx->fX;
+        A.Y = ctx->fY;
+        A.T = ctx->fT + m_time * 2 * ctx->R;
+    }
+    std::memcpy(A.k, ctx->k, sizeof(A.k));
+    return A;
+}
+
+void node_grid(const lbm_ctx* ctx, dim3& grid, dim3& block)
+{
+    const long long n = (long long)ctx->p.nx * ctx->p.ny;
+    long long nb = (n + 255) / 256;
+    if (nb > 152 * 16) nb = 152 * 16;
+    grid = dim3((unsigned)nb);
+    block = dim3(256);
+}
+
+// copy a host or device FP64 array of n values into a fresh device buffer (stream ordered)
+lbm_status stage_in(lbm_ctx* ctx, const double* src, size_t n, int on_device, const double** dev, double** owned)
+{
+    *owned = nullptr;
+    if (!src) {
+        *dev = nullptr;
+        return LBM_OK;
+    }
+    if (on_device) {
+        *dev = src;
+        return LBM_OK;
+    }
+    double* d = nullptr;
+    LBM_CUDA(ctx, cudaMallocAsync((void**)&d, n * sizeof(double), ctx->s));
+    cudaError_t e = cudaMemcpyAsync(d, src, n * sizeof(double), cudaMemcpyHostToDevice, ctx->s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(d, ctx->s);
+        return cuda_fail(ctx, e, "cudaMemcpyAsync H2D");
+    }
+    *dev = d;
+    *owned = d;
+    return LBM_OK;
+}
+
+lbm_status check_ready(lbm_ctx* ctx)
+{
+    if (!ctx->ready) return fail(ctx, LBM_ERR_STATE, "state not initialised: call lbm_init or lbm_set_populations");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
+{
+    g_create_error.clear();
+    if (!out) {
+        g_create_error = "out is NULL";
+        return LBM_ERR_ARG;
+    }
+    *out = nullptr;
+    if (!p) {
+        g_create_error = "params is NULL";
+        return LBM_ERR_ARG;
+    }
+    if (p->nx < 2 || p->ny < 2 || p->ny > 65535 || p->nx > (1 << 24)) {
+        g_create_error = "nx must be in [2, 2^24] and ny in [2, 65535]";
+        return LBM_ERR_ARG;
+    }
+    if (p->bc != LBM_PERIODIC && p->bc != LBM_DIRICHLET) {
+        g_create_error = "bc must be LBM_PERIODIC or LBM_DIRICHLET";
+        return LBM_ERR_ARG;
+    }
+    if (!ops_for(p->storage)) {
+        g_create_error = "unknown storage format";
+        return LBM_ERR_ARG;
+    }
+    if ((p->track_displacement != 0 && p->track_displacement != 1) || p->reserved != 0) {
+        g_create_error = "track_displacement must be 0 or 1 and reserved 0";
+        return LBM_ERR_ARG;
+    }
+    if (!(p->dx > 0.0) || !(p->dt > 0.0) || !std::isfinite(p->dx) || !std::isfinite(p->dt) ||
+        !(p->cK > 0.0) || !(p->cmu >= 0.0) || !std::isfinite(p->cK) || !std::isfinite(p->cmu)) {
+        g_create_error = "dx, dt, cK must be positive and finite, cmu >= 0";
+        return LBM_ERR_ARG;
+    }
+    const double c = p->dx / p->dt;
+    if (!(2.0 * std::sqrt(p->cK * p->cK + p->cmu * p->cmu) < c)) {
+        g_create_error = "CFL-like condition 2 sqrt(cK^2 + cmu^2) < dx/dt violated";
+        return LBM_ERR_CFL;
+    }
+    lbm_ctx* ctx = new (std::nothrow) lbm_ctx();
+    if (!ctx) {
+        g_create_error = "host allocation failed";
+        return LBM_ERR_OOM;
+    }
+    ctx->p = *p;
+    ctx->s = static_cast<cudaStream_t>(p->stream);
+    ctx->ops = ops_for(p->storage);
+    ctx->pitch = (p->nx + 63) / 64 * 64;
+    ctx->plane = (long long)ctx->pitch * p->ny;
+    ctx->c = c;
+    ctx->a = p->cK / c;
+    ctx->b = p->cmu / c;
+    ctx->nwall = 2 * (p->nx + p->ny);
+    // symmetrizer blocks k_ij = g_ij^{-1}, g_ij = 1/4 I + (i A_x + j A_y)/(2c)  (Eq. stability_linear)
+    const int VI[4] = {1, 0, -1, 0}, VJ[4] = {0, 1, 0, -1};
+    for (int d = 0; d < 4; ++d) {
+        double Ax[25] = {0}, Ay[25] = {0}, gm[25];
+        Ax[0 * 5 + 2] = Ax[2 * 5 + 0] = p->cK;
+        Ax[0 * 5 + 3] = Ax[3 * 5 + 0] = p->cmu;
+        Ax[1 * 5 + 4] = Ax[4 * 5 + 1] = p->cmu;
+        Ay[0 * 5 + 4] = Ay[4 * 5 + 0] = p->cmu;
+        Ay[1 * 5 + 2] = Ay[2 * 5 + 1] = p->cK;
+        Ay[1 * 5 + 3] = Ay[3 * 5 + 1] = -p->cmu;
+        for (int q = 0; q < 25; ++q)
+            gm[q] = (q % 6 == 0 ? 0.25 : 0.0) + (VI[d] * Ax[q] + VJ[d] * Ay[q]) / (2.0 * c);
+        if (!invert5(gm, ctx->k[d])) {
+            delete ctx;
+            g_create_error = "singular g_ij";
+            return LBM_ERR_CFL;
+        }
+    }
+    const size_t state_bytes = (size_t)20 * ctx->plane * ctx->ops->elem_bytes;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&ctx->buf[i], state_bytes);
+    if (e == cudaSuccess && p->track_displacement) e = cudaMalloc((void**)&ctx->w, (size_t)2 * ctx->plane * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->scratch, (size_t)(kRedBlocks * 30 + 64) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->buf[0], 0, state_bytes, ctx->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->buf[1], 0, state_bytes, ctx->s);
+    if (e == cudaSuccess && ctx->w) e = cudaMemsetAsync(ctx->w, 0, (size_t)2 * ctx->plane * sizeof(double), ctx->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        lbm_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+    }
+    *out = ctx;
+    return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx* ctx)
+{
+    if (!ctx) return LBM_OK;
+    cudaStreamSynchronize(ctx->s);
+    cudaFree(ctx->buf[0]);
+    cudaFree(ctx->buf[1]);
+    cudaFree(ctx->w);
+    cudaFree(ctx->fX);
+    cudaFree(ctx->fY);
+    cudaFree(ctx->fT);
+    cudaFree(ctx->g);
+    cudaFree(ctx->scratch);
+    delete ctx;
+    return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+lbm_status lbm_time_step(const lbm_ctx* ctx, int64_t* m)
+{
+    if (!ctx || !m) return LBM_ERR_ARG;
+    *m = ctx->m;
+    return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_ctx* ctx)
+{
+    LBM_CHECK_CTX(ctx);
+    LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_forcing(lbm_ctx* ctx, int32_t R, const double* X, const double* Y, const double* T,
+                           int64_t nt, int32_t on_device)
+{
+    LBM_CHECK_CTX(ctx);
+    if (R < 0 || R > kMaxR) return fail(ctx, LBM_ERR_ARG, "R must be in [0, 16]");
+    LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    cudaFree(ctx->fX);
+    cudaFree(ctx->fY);
+    cudaFree(ctx->fT);
+    ctx->fX = ctx->fY = ctx->fT = nullptr;
+    ctx->R = 0;
+    ctx->fnt = 0;
+    if (R == 0) return LBM_OK;
+    if (!X || !Y || !T || nt < 1) return fail(ctx, LBM_ERR_ARG, "forcing tables missing or nt < 1");
+    const size_t nX = (size_t)R * ctx->p.nx, nY = (size_t)R * ctx->p.ny, nT = (size_t)nt * 2 * R;
+    LBM_CUDA(ctx, cudaMalloc((void**)&ctx->fX, nX * sizeof(double)));
+    LBM_CUDA(ctx, cudaMalloc((void**)&ctx->fY, nY * sizeof(double)));
+    LBM_CUDA(ctx, cudaMalloc((void**)&ctx->fT, nT * sizeof(double)));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    LBM_CUDA(ctx, cudaMemcpyAsync(ctx->fX, X, nX * sizeof(double), kind, ctx->s));
+    LBM_CUDA(ctx, cudaMemcpyAsync(ctx->fY, Y, nY * sizeof(double), kind, ctx->s));
+    LBM_CUDA(ctx, cudaMemcpyAsync(ctx->fT, T, nT * sizeof(double), kind, ctx->s));
+    LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    ctx->R = R;
+    ctx->fnt = nt;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_dirichlet(lbm_ctx* ctx, const double* g, int64_t nt, int32_t on_device)
+{
+    LBM_CHECK_CTX(ctx);
+    if (ctx->p.bc != LBM_DIRICHLET) return fail(ctx, LBM_ERR_ARG, "lattice is periodic");
+    LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    cudaFree(ctx->g);
+    ctx->g = nullptr;
+    ctx->gnt = 0;
+    if (!g) return LBM_OK;
+    if (nt < 1) return fail(ctx, LBM_ERR_ARG, "nt < 1");
+    const size_t n = (size_t)nt * 2 * ctx->nwall;
+    LBM_CUDA(ctx, cudaMalloc((void**)&ctx->g, n * sizeof(double)));
+    LBM_CUDA(ctx, cudaMemcpyAsync(ctx->g, g, n * sizeof(double),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->s));
+    LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    ctx->gnt = nt;
+    return LBM_OK;
+}
+
+lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const double* dU0dy,
+                    const double* B0, const double* u0, int32_t on_device)
+{
+    LBM_CHECK_CTX(ctx);
+    if (!U0 || !dU0dx || !dU0dy) return fail(ctx, LBM_ERR_ARG, "U0, dU0dx and dU0dy are required");
+    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    const double *dU0, *dUx, *dUy, *dB0, *du0;
+    double *o1, *o2, *o3, *o4, *o5;
+    lbm_status st;
+    if ((st = stage_in(ctx, U0, 5 * n, on_device, &dU0, &o1)) != LBM_OK) return st;
+    if ((st = stage_in(ctx, dU0dx, 5 * n, on_device, &dUx, &o2)) != LBM_OK) return st;
+    if ((st = stage_in(ctx, dU0dy, 5 * n, on_device, &dUy, &o3)) != LBM_OK) return st;
+    if ((st = stage_in(ctx, B0, 2 * n, on_device, &dB0, &o4)) != LBM_OK) return st;
+    if ((st = stage_in(ctx, ctx->w ? u0 : nullptr, 2 * n, on_device, &du0, &o5)) != LBM_OK) return st;
+    lbmk::NodeArgs A = node_args(ctx, -1);
+    dim3 grid, block;
+    node_grid(ctx, grid, block);
+    cudaError_t e = ctx->ops->init(A, dU0, dUx, dUy, dB0, du0, grid, block, ctx->s);
+    for (double* o : {o1, o2, o3, o4, o5})
+        if (o) cudaFreeAsync(o, ctx->s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "init kernel");
+    if (!on_device) LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    ctx->m = 0;
+    ctx->ready = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
+{
+    LBM_CHECK_CTX(ctx);
+    if (n < 0) return fail(ctx, LBM_ERR_ARG, "n < 0");
+    if (n == 0) return LBM_OK;
+    lbm_status st = check_ready(ctx);
+    if (st != LBM_OK) return st;
+    if (ctx->R > 0 && ctx->m + n >= ctx->fnt)
+        return fail(ctx, LBM_ERR_STATE, "body-load table has no row for the requested time");
+    if (ctx->g && ctx->m + n > ctx->gnt)
+        return fail(ctx, LBM_ERR_STATE, "Dirichlet table has no row for the requested step");
+    const KindOps* ops = ctx->ops;
+    const int nchunk = (ctx->p.nx + ops->vec - 1) / ops->vec;
+    int bx = (nchunk + 31) / 32 * 32;
+    if (bx > 256) bx = 256;
+    const dim3 block(bx), grid((nchunk + bx - 1) / bx, ctx->p.ny);
+    lbmk::StepArgs A;
+    A.w = ctx->w;
+    A.nx = ctx->p.nx;
+    A.ny = ctx->p.ny;
+    A.pitch = ctx->pitch;
+    A.plane = ctx->plane;
+    A.a = ctx->a;
+    A.b = ctx->b;
+    A.dt = ctx->p.dt;
+    A.R = ctx->R;
+    A.X = ctx->fX;
+    A.Y = ctx->fY;
+    A.nwall = ctx->nwall;
+    const int variant = (ctx->p.bc == LBM_DIRICHLET ? lbmh::STEP_DIRICHLET : 0) |
+                        (ctx->R > 0 ? lbmh::STEP_FORCING : 0) | (ctx->w ? lbmh::STEP_TRACK : 0);
+    for (int64_t i = 0; i < n; ++i) {
+        const long long m = ctx->m;
+        A.src = ctx->buf[ctx->cur];
+        A.dst = ctx->buf[ctx->cur ^ 1];
+        A.T = ctx->R > 0 ? ctx->fT + (m + 1) * 2 * ctx->R : nullptr;
+        A.g = ctx->g ? ctx->g + m * 2 * ctx->nwall : nullptr;
+        cudaError_t e = ops->step(A, variant, grid, block, ctx->s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "step kernel");
+        ctx->cur ^= 1;
+        ctx->m = m + 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx* ctx, double* out, int32_t on_device)
+{
+    LBM_CHECK_CTX(ctx);
+    if (!out) return fail(ctx, LBM_ERR_ARG, "out is NULL");
+    lbm_status st = check_ready(ctx);
+    if (st != LBM_OK) return st;
+    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    double* dst = out;
+    if (!on_device) LBM_CUDA(ctx, cudaMallocAsync((void**)&dst, 10 * n * sizeof(double), ctx->s));
+    dim3 grid, block;
+    node_grid(ctx, grid, block);
+    cudaError_t e = ctx->ops->moments(node_args(ctx, ctx->m), dst, grid, block, ctx->s);
+    if (e == cudaSuccess && !on_device)
+        e = cudaMemcpyAsync(out, dst, 10 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->s);
+    if (!on_device) cudaFreeAsync(dst, ctx->s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "moments");
+    if (!on_device) LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    return LBM_OK;
+}
+
+lbm_status lbm_energy(lbm_ctx* ctx, double* out)
+{
+    LBM_CHECK_CTX(ctx);
+    if (!out) return fail(ctx, LBM_ERR_ARG, "out is NULL");
+    lbm_status st = check_ready(ctx);
+    if (st != LBM_OK) return st;
+    double* partial = ctx->scratch;
+    double* result = ctx->scratch + kRedBlocks * 30;
+    LBM_CUDA(ctx, ctx->ops->energy(node_args(ctx, ctx->m), partial, dim3(kRedBlocks), dim3(256), ctx->s));
+    LBM_CUDA(ctx, lbmh::finish_sum1(partial, kRedBlocks, result, ctx->s));
+    LBM_CUDA(ctx, cudaMemcpyAsync(out, result, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    return LBM_OK;
+}
+
+lbm_status lbm_error_sums(lbm_ctx* ctx, const double* exact, int32_t on_device, double* out)
+{
+    LBM_CHECK_CTX(ctx);
+    if (!exact || !out) return fail(ctx, LBM_ERR_ARG, "exact and out are required");
+    lbm_status st = check_ready(ctx);
+    if (st != LBM_OK) return st;
+    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    const double* dex;
+    double* owned;
+    if ((st = stage_in(ctx, exact, 10 * n, on_device, &dex, &owned)) != LBM_OK) return st;
+    double* partial = ctx->scratch;
+    double* result = ctx->scratch + kRedBlocks * 30;
+    cudaError_t e = ctx->ops->error(node_args(ctx, ctx->m), dex, partial, dim3(kRedBlocks), dim3(256), ctx->s);
+    if (e == cudaSuccess) e = lbmh::finish_err30(partial, kRedBlocks, result, ctx->s);
+    if (owned) cudaFreeAsync(owned, ctx->s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "error sums");
+    LBM_CUDA(ctx, cudaMemcpyAsync(out, result, 30 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, double* ustar, int32_t on_device)
+{
+    LBM_CHECK_CTX(ctx);
+    if (!f) return fail(ctx, LBM_ERR_ARG, "f is NULL");
+    lbm_status st = check_ready(ctx);
+    if (st != LBM_OK) return st;
+    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    double *df = f, *du = ustar;
+    if (!on_device) {
+        LBM_CUDA(ctx, cudaMallocAsync((void**)&df, 22 * n * sizeof(double), ctx->s));
+        du = ustar ? df + 20 * n : nullptr;
+    }
+    dim3 grid, block;
+    node_grid(ctx, grid, block);
+    cudaError_t e = ctx->ops->get_pop(node_args(ctx, ctx->m), df, du, grid, block, ctx->s);
+    if (!on_device) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(f, df, 20 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->s);
+        if (e == cudaSuccess && ustar)
+            e = cudaMemcpyAsync(ustar, du, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->s);
+        cudaFreeAsync(df, ctx->s);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "get_populations");
+    if (!on_device) LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, const double* ustar, int64_t m, int32_t on_device)
+{
+    LBM_CHECK_CTX(ctx);
+    if (!f || m < 0) return fail(ctx, LBM_ERR_ARG, "f is NULL or m < 0");
+    if (ctx->R > 0 && m >= ctx->fnt) return fail(ctx, LBM_ERR_STATE, "body-load table has no row for step m");
+    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    const double *df, *du;
+    double *o1, *o2;
+    lbm_status st;
+    if ((st = stage_in(ctx, f, 20 * n, on_device, &df, &o1)) != LBM_OK) return st;
+    if ((st = stage_in(ctx, ctx->w ? ustar : nullptr, 2 * n, on_device, &du, &o2)) != LBM_OK) return st;
+    dim3 grid, block;
+    node_grid(ctx, grid, block);
+    cudaError_t e = ctx->ops->set_pop(node_args(ctx, m), df, du, grid, block, ctx->s);
+    if (o1) cudaFreeAsync(o1, ctx->s);
+    if (o2) cudaFreeAsync(o2, ctx->s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set_populations");
+    if (!on_device) LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    ctx->m = m;
+    ctx->ready = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_check_finite(lbm_ctx* ctx)
+{
+    LBM_CHECK_CTX(ctx);
+    lbm_status st = check_ready(ctx);
+    if (st != LBM_OK) return st;
+    int* flag = reinterpret_cast<int*>(ctx->scratch + kRedBlocks * 30 + 40);
+    LBM_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->s));
+    LBM_CUDA(ctx, ctx->ops->finite(ctx->buf[ctx->cur], ctx->p.nx, ctx->p.ny, ctx->pitch, ctx->plane, flag,
+                                   dim3(152 * 8), dim3(256), ctx->s));
+    int h = 0;
+    LBM_CUDA(ctx, cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    return h ? fail(ctx, LBM_ERR_UNSTABLE, "non-finite population found") : LBM_OK;
+}
+
+lbm_status lbm_state_bytes(const lbm_ctx* ctx, int64_t* nbytes)
+{
+    if (!ctx || !nbytes) return LBM_ERR_ARG;
+    *nbytes = (int64_t)20 * ctx->plane * ctx->ops->elem_bytes + (ctx->w ? (int64_t)2 * ctx->plane * 8 : 0);
+    return LBM_OK;
+}
+
+lbm_status lbm_save_state(lbm_ctx* ctx, void* dst, int32_t on_device)
+{
+    LBM_CHECK_CTX(ctx);
+    if (!dst) return fail(ctx, LBM_ERR_ARG, "dst is NULL");
+    lbm_status st = check_ready(ctx);
+    if (st != LBM_OK) return st;
+    const size_t sb = (size_t)20 * ctx->plane * ctx->ops->elem_bytes;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    LBM_CUDA(ctx, cudaMemcpyAsync(dst, ctx->buf[ctx->cur], sb, kind, ctx->s));
+    if (ctx->w)
+        LBM_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(dst) + sb, ctx->w, (size_t)2 * ctx->plane * 8, kind, ctx->s));
+    LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t m, int32_t on_device)
+{
+    LBM_CHECK_CTX(ctx);
+    if (!src || m < 0) return fail(ctx, LBM_ERR_ARG, "src is NULL or m < 0");
+    const size_t sb = (size_t)20 * ctx->plane * ctx->ops->elem_bytes;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    LBM_CUDA(ctx, cudaMemcpyAsync(ctx->buf[ctx->cur], src, sb, kind, ctx->s));
+    if (ctx->w)
+        LBM_CUDA(ctx, cudaMemcpyAsync(ctx->w, static_cast<const char*>(src) + sb, (size_t)2 * ctx->plane * 8, kind,
+                                      ctx->s));
+    LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    ctx->m = m;
+    ctx->ready = true;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace lbmh {
+
+cudaError_t finish_sum1(const double* partial, int nblk, double* out, cudaStream_t s)
+{
+    lbmk::finish_kernel<1><<<1, 256, 0, s>>>(partial, nblk, 1, out);
+    return cudaGetLastError();
+}
+
+cudaError_t finish_err30(const double* partial, int nblk, double* out, cudaStream_t s)
+{
+    lbmk::finish_kernel<30><<<1, 256, 0, s>>>(partial, nblk, 20, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmh

@@ -1,0 +1,726 @@
+// Device code of the GB300 D2Q4^5 elastodynamics library (arXiv 2408.01081).
+//
+// State kept between steps: the post-collision populations f*(x, t) of every
+// node, in structure-of-arrays planes [d*5 + k][y][pitch] of the storage type
+// (d = velocity (1,0),(0,1),(-1,0),(0,-1); k = component of U = [vx, vy, js,
+// jd, jxy]).  One fused kernel per time step pulls f(x, t+dt) = f*(x - c_ij dt, t)
+// (Eq. streaming) or, for a missing link on a Dirichlet edge, the reflected
+// D f*_{-i,-j}(x, t) + S_ij(x_b, t+dt/2) (Eq. bc_ansatz), forms U^num
+// (Eq. cond_eq), collides with omega = 2 (Eqs. feq, collision) and writes
+// f*(x, t+dt) back to the node's own, aligned position.
+//
+// With omega = 2 the collision of Eq. collision reads, per component k,
+//     f*_ij = 1/2 U + i px + j py - f_ij,   px = Phi_x(U)/c, py = Phi_y(U)/c,
+// and since the four outputs of one axis sum to U - (the other axis' pair),
+//     f*_{-1,0} = (U - f_{1,0} - f_{-1,0}) - f*_{1,0},
+//     f*_{0,-1} = (U - f_{0,1} - f_{0,-1}) - f*_{0,1}.
+// That is 47 FP64 operations per node without forcing, the FP64 ALU bound on GB300.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbmk {
+
+// ---------------------------------------------------------------------------
+// storage formats
+// ---------------------------------------------------------------------------
+enum Kind { K_F64 = 0, K_F32 = 1, K_BF16 = 2, K_F16 = 3 };
+
+template <int K> struct Fmt;
+template <> struct Fmt<K_F64> {
+    using E = double;  // element in memory
+    using M = double;  // arithmetic type
+    static __device__ __forceinline__ M ld(E e) { return e; }
+    static __device__ __forceinline__ E st(M m) { return m; }
+};
+template <> struct Fmt<K_F32> {
+    using E = float;
+    using M = float;
+    static __device__ __forceinline__ M ld(E e) { return e; }
+    static __device__ __forceinline__ E st(M m) { return m; }
+};
+template <> struct Fmt<K_BF16> {
+    using E = unsigned short;
+    using M = float;
+    static __device__ __forceinline__ M ld(E e) { return __bfloat162float(__ushort_as_bfloat16(e)); }
+    static __device__ __forceinline__ E st(M m) { return __bfloat16_as_ushort(__float2bfloat16_rn(m)); }
+};
+template <> struct Fmt<K_F16> {
+    using E = unsigned short;
+    using M = float;
+    static __device__ __forceinline__ M ld(E e) { return __half2float(__ushort_as_half(e)); }
+    static __device__ __forceinline__ E st(M m) { return __half_as_ushort(__float2half_rn(m)); }
+};
+
+template <int BYTES> struct Raw;
+template <> struct Raw<4> { using T = unsigned int; };
+template <> struct Raw<8> { using T = uint2; };
+template <> struct Raw<16> { using T = uint4; };
+
+// V consecutive elements from a (V * sizeof(E))-aligned address, one vector access
+template <int K, int V>
+__device__ __forceinline__ void vload(const typename Fmt<K>::E* p, typename Fmt<K>::M (&out)[V])
+{
+    using E = typename Fmt<K>::E;
+    using R = typename Raw<sizeof(E) * V>::T;
+    union { R r; E e[V]; } u;
+    u.r = __ldg(reinterpret_cast<const R*>(p));
+#pragma unroll
+    for (int i = 0; i < V; ++i) out[i] = Fmt<K>::ld(u.e[i]);
+}
+
+template <int K, int V>
+__device__ __forceinline__ void vstore(typename Fmt<K>::E* p, const typename Fmt<K>::M (&in)[V])
+{
+    using E = typename Fmt<K>::E;
+    using R = typename Raw<sizeof(E) * V>::T;
+    union { R r; E e[V]; } u;
+#pragma unroll
+    for (int i = 0; i < V; ++i) u.e[i] = Fmt<K>::st(in[i]);
+    *reinterpret_cast<R*>(p) = u.r;
+}
+
+template <int K>
+__device__ __forceinline__ typename Fmt<K>::M sload(const typename Fmt<K>::E* p)
+{
+    return Fmt<K>::ld(__ldg(p));
+}
+
+// ---------------------------------------------------------------------------
+// arguments
+// ---------------------------------------------------------------------------
+struct StepArgs {
+    const void* src;       // f*(t) planes
+    void* dst;             // f*(t+dt) planes
+    double* w;             // u*(t+dt) helper [2][ny][pitch], updated in place, or nullptr
+    int nx, ny, pitch;
+    long long plane;       // elements per plane = ny * pitch
+    double a, b;           // cK / c, cmu / c
+    double dt;
+    // body load at t+dt: b_c(x_k, y_l) = sum_r X[r][k] Y[r][l] T[c][r]
+    int R;
+    const double* X;
+    const double* Y;
+    const double* T;       // row of the time t+dt: [2][R]
+    // Dirichlet data d/dt u_D at t + dt/2 on the wall midpoints, [2][nwall] or nullptr
+    const double* g;
+    int nwall;
+};
+
+// ---------------------------------------------------------------------------
+// node arithmetic
+// ---------------------------------------------------------------------------
+
+// Collision with omega = 2 for one node.  f[d][k] pulled pre-collision values,
+// U already holds sum_d f_d + dt/2 B; rx = U - f0 - f2, ry = U - f1 - f3 per component.
+template <typename M>
+__device__ __forceinline__ void collide(const M (&f)[4][5], const M (&U)[5], const M (&rx)[5],
+                                        const M (&ry)[5], M a, M b, M (&o)[4][5])
+{
+    const M h = M(0.5);
+    // (1,0): 1/2 U + Phi_x(U)/c - f ; Phi_x = [cK js + cmu jd, cmu jxy, cK vx, cmu vx, cmu vy]
+    o[0][0] = fma(h, U[0], fma(a, U[2], fma(b, U[3], -f[0][0])));
+    o[0][1] = fma(h, U[1], fma(b, U[4], -f[0][1]));
+    o[0][2] = fma(h, U[2], fma(a, U[0], -f[0][2]));
+    o[0][3] = fma(h, U[3], fma(b, U[0], -f[0][3]));
+    o[0][4] = fma(h, U[4], fma(b, U[1], -f[0][4]));
+    // (0,1): 1/2 U + Phi_y(U)/c - f ; Phi_y = [cmu jxy, cK js - cmu jd, cK vy, -cmu vy, cmu vx]
+    o[1][0] = fma(h, U[0], fma(b, U[4], -f[1][0]));
+    o[1][1] = fma(h, U[1], fma(a, U[2], fma(-b, U[3], -f[1][1])));
+    o[1][2] = fma(h, U[2], fma(a, U[1], -f[1][2]));
+    o[1][3] = fma(h, U[3], fma(-b, U[1], -f[1][3]));
+    o[1][4] = fma(h, U[4], fma(b, U[0], -f[1][4]));
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        o[2][k] = rx[k] - o[0][k];   // (-1,0)
+        o[3][k] = ry[k] - o[1][k];   // (0,-1)
+    }
+}
+
+// S_ij of Eq. bc_s for wall data (gx, gy) and velocity (i, j); the j rows carry
+// the 1/c of the equilibrium difference (a = cK/c, b = cmu/c).
+__device__ __forceinline__ void wall_source(int i, int j, double gx, double gy, double a, double b,
+                                            double (&S)[5])
+{
+    S[0] = 0.5 * gx;
+    S[1] = 0.5 * gy;
+    S[2] = a * (i * gx + j * gy);
+    S[3] = b * (i * gx - j * gy);
+    S[4] = b * (j * gx + i * gy);
+}
+
+// ---------------------------------------------------------------------------
+// fused pull-collide step: one thread = V consecutive nodes of one row
+// grid: (ceil(ceil(nx/V) / blockDim.x), ny)
+// ---------------------------------------------------------------------------
+template <int K, int V, bool DIRICHLET, bool FORCING, bool TRACK>
+__global__ void __launch_bounds__(256)
+step_kernel(StepArgs A)
+{
+    using E = typename Fmt<K>::E;
+    using M = typename Fmt<K>::M;
+    const int y = blockIdx.y;
+    const int cx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nchunk = (A.nx + V - 1) / V;
+    const bool active = cx < nchunk;
+    const int x0 = (active ? cx : nchunk - 1) * V;   // inactive lanes mirror a valid chunk
+    const int nx = A.nx, ny = A.ny;
+    const long long plane = A.plane;
+    const E* __restrict__ src = static_cast<const E*>(A.src);
+    E* __restrict__ dst = static_cast<E*>(A.dst);
+    const int lane = threadIdx.x & 31;
+
+    // rows the +y and -y planes are pulled from; on a Dirichlet edge row the
+    // missing link reflects the node's own opposite plane instead
+    const bool bot = DIRICHLET && (y == 0);
+    const bool top = DIRICHLET && (y == ny - 1);
+    const int ym = (y == 0) ? ny - 1 : y - 1;
+    const int yp = (y == ny - 1) ? 0 : y + 1;
+
+    M P0[5][V], P1[5][V], P2[5][V], P3[5][V];   // pulled f_d (edge links patched below)
+    M own0[5][V], own2[5][V];                    // f*_{(1,0)}, f*_{(-1,0)} of the own chunk
+    const long long row = (long long)y * A.pitch + x0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        vload<K, V>(src + (0 * 5 + k) * plane + row, own0[k]);
+        vload<K, V>(src + (2 * 5 + k) * plane + row, own2[k]);
+        if (bot) vload<K, V>(src + (3 * 5 + k) * plane + row, P1[k]);
+        else     vload<K, V>(src + (1 * 5 + k) * plane + (long long)ym * A.pitch + x0, P1[k]);
+        if (top) vload<K, V>(src + (1 * 5 + k) * plane + row, P3[k]);
+        else     vload<K, V>(src + (3 * 5 + k) * plane + (long long)yp * A.pitch + x0, P3[k]);
+    }
+    // x-planes: shift by one node through the neighbouring lanes
+    const int xl = (x0 == 0) ? nx - 1 : x0 - 1;        // source of P0[0]
+    const bool left_in_lane = (lane > 0) && (x0 > 0);
+    const bool right_in_lane = (lane < 31) && (x0 + V < nx) && (cx + 1 < nchunk);
+    const int xr = (x0 + V >= nx) ? 0 : x0 + V;        // source of P2[V-1] (periodic)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        M l = __shfl_up_sync(0xffffffffu, own0[k][V - 1], 1);
+        M r = __shfl_down_sync(0xffffffffu, own2[k][0], 1);
+        if (!left_in_lane) l = sload<K>(src + (0 * 5 + k) * plane + (long long)y * A.pitch + xl);
+        if (!right_in_lane) r = sload<K>(src + (2 * 5 + k) * plane + (long long)y * A.pitch + xr);
+        P0[k][0] = l;
+#pragma unroll
+        for (int e = 1; e < V; ++e) P0[k][e] = own0[k][e - 1];
+#pragma unroll
+        for (int e = 0; e < V - 1; ++e) P2[k][e] = own2[k][e + 1];
+        P2[k][V - 1] = r;
+    }
+    // ragged row end: the node nx-1 may sit inside the chunk; its (-1,0) source wraps to x = 0
+    if (!DIRICHLET && x0 + V > nx && x0 <= nx - 1) {
+        const int e = nx - 1 - x0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const M r0 = sload<K>(src + (2 * 5 + k) * plane + (long long)y * A.pitch + 0);
+#pragma unroll
+            for (int q = 0; q < V; ++q)
+                if (q == e) P2[k][q] = r0;
+        }
+    }
+
+    const M a = M(A.a), b = M(A.b);
+    M out[4][5][V];
+    double wv[2][V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const int x = x0 + e;
+        M f[4][5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            f[0][k] = P0[k][e];
+            f[1][k] = P1[k][e];
+            f[2][k] = P2[k][e];
+            f[3][k] = P3[k][e];
+        }
+        if (DIRICHLET) {
+            // missing incoming links: f_ij = D f*_{-i,-j}(x) + S_ij(x_b, t + dt/2), in FP64
+            const bool le = (x == 0), ri = (x == nx - 1);
+            if (le || ri || bot || top) {
+                const double Dk[5] = {-1.0, -1.0, 1.0, 1.0, 1.0};
+                double S[5];
+                if (le) {
+                    double gx = 0.0, gy = 0.0;
+                    if (A.g) { gx = A.g[y]; gy = A.g[A.nwall + y]; }
+                    wall_source(1, 0, gx, gy, A.a, A.b, S);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) f[0][k] = M(Dk[k] * (double)own2[k][e] + S[k]);
+                }
+                if (ri) {
+                    double gx = 0.0, gy = 0.0;
+                    if (A.g) { gx = A.g[ny + y]; gy = A.g[A.nwall + ny + y]; }
+                    wall_source(-1, 0, gx, gy, A.a, A.b, S);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) f[2][k] = M(Dk[k] * (double)own0[k][e] + S[k]);
+                }
+                if (bot) {
+                    double gx = 0.0, gy = 0.0;
+                    if (A.g && x < nx) { gx = A.g[2 * ny + x]; gy = A.g[A.nwall + 2 * ny + x]; }
+                    wall_source(0, 1, gx, gy, A.a, A.b, S);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) f[1][k] = M(Dk[k] * (double)P1[k][e] + S[k]);
+                }
+                if (top) {
+                    double gx = 0.0, gy = 0.0;
+                    if (A.g && x < nx) { gx = A.g[2 * ny + nx + x]; gy = A.g[A.nwall + 2 * ny + nx + x]; }
+                    wall_source(0, -1, gx, gy, A.a, A.b, S);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) f[3][k] = M(Dk[k] * (double)P3[k][e] + S[k]);
+                }
+            }
+        }
+        M U[5], rx[5], ry[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const M sx = f[0][k] + f[2][k];
+            const M sy = f[1][k] + f[3][k];
+            rx[k] = sy;
+            ry[k] = sx;
+        }
+        if (FORCING) {
+            double bx = 0.0, by = 0.0;
+            if (x < nx) {
+                for (int r = 0; r < A.R; ++r) {
+                    const double xy = A.X[(long long)r * nx + x] * A.Y[(long long)r * ny + y];
+                    bx = fma(xy, A.T[r], bx);
+                    by = fma(xy, A.T[A.R + r], by);
+                }
+            }
+            rx[0] = fma(M(0.5 * A.dt), M(bx), rx[0]);
+            rx[1] = fma(M(0.5 * A.dt), M(by), rx[1]);
+            ry[0] = fma(M(0.5 * A.dt), M(bx), ry[0]);
+            ry[1] = fma(M(0.5 * A.dt), M(by), ry[1]);
+            U[0] = rx[0] + (f[0][0] + f[2][0]);
+            U[1] = rx[1] + (f[0][1] + f[2][1]);
+#pragma unroll
+            for (int k = 2; k < 5; ++k) U[k] = rx[k] + ry[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) U[k] = rx[k] + ry[k];
+        }
+        M o[4][5];
+        collide<M>(f, U, rx, ry, a, b, o);
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) out[d][k][e] = o[d][k];
+        if (TRACK) {
+            wv[0][e] = (double)U[0];
+            wv[1][e] = (double)U[1];
+        }
+    }
+    if (!active) return;
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) vstore<K, V>(dst + (d * 5 + k) * plane + row, out[d][k]);
+    if (TRACK) {
+        // u*(t+2dt) = u*(t+dt) + dt v(t+dt)  (steps 1(b) and 2(c) of the summary, Sec. 3.6)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            double* wp = A.w + (long long)c * plane + row;
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                if (x0 + e < nx) wp[e] = fma(A.dt, wv[c][e], wp[e]);
+        }
+    }
+}
+
+}  // namespace lbmk
+
+namespace lbmk {
+
+// ---------------------------------------------------------------------------
+// FP64 per-node helpers for initialisation, output and reductions
+// ---------------------------------------------------------------------------
+struct NodeArgs {
+    const void* S;         // f* planes at the current time (storage type)
+    void* Sout;            // f* planes to write (init / set_populations)
+    double* w;             // u*(t+dt) [2][ny][pitch] or nullptr
+    int nx, ny, pitch;
+    long long plane;
+    double a, b;           // cK/c, cmu/c
+    double cK, cmu;        // wave speeds (stress output)
+    double dt, c;
+    int R;                 // body load tables at the current time (R = 0: none)
+    const double* X;
+    const double* Y;
+    const double* T;       // [2][R]
+    double k[4][25];       // symmetrizer blocks k_ij = g_ij^{-1}
+};
+
+__device__ __forceinline__ void body_load(const NodeArgs& A, int x, int y, double& bx, double& by)
+{
+    bx = 0.0;
+    by = 0.0;
+    for (int r = 0; r < A.R; ++r) {
+        const double xy = A.X[(long long)r * A.nx + x] * A.Y[(long long)r * A.ny + y];
+        bx = fma(xy, A.T[r], bx);
+        by = fma(xy, A.T[A.R + r], by);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void load_node(const NodeArgs& A, int x, int y, double (&S)[4][5])
+{
+    using E = typename Fmt<K>::E;
+    const E* p = static_cast<const E*>(A.S);
+    const long long off = (long long)y * A.pitch + x;
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) S[d][k] = (double)Fmt<K>::ld(p[(d * 5 + k) * A.plane + off]);
+}
+
+template <int K>
+__device__ __forceinline__ void store_node(const NodeArgs& A, int x, int y, const double (&S)[4][5])
+{
+    using E = typename Fmt<K>::E;
+    using M = typename Fmt<K>::M;
+    E* p = static_cast<E*>(A.Sout);
+    const long long off = (long long)y * A.pitch + x;
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) p[(d * 5 + k) * A.plane + off] = Fmt<K>::st((M)S[d][k]);
+}
+
+// 2 g_ij U - f_ij for all four velocities, with U = sum_d f_d + shift (per component).
+// As collision (shift = +dt/2 B) it maps f to f*; as its inverse (shift = -dt/2 B) f* to f.
+__device__ __forceinline__ void reflect_node(const double (&f)[4][5], const double (&shift)[5],
+                                             double a, double b, double (&o)[4][5], double (&U)[5])
+{
+    double rx[5], ry[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        rx[k] = (f[1][k] + f[3][k]) + shift[k];
+        ry[k] = (f[0][k] + f[2][k]) + shift[k];
+        U[k] = rx[k] + (f[0][k] + f[2][k]);
+    }
+    collide<double>(f, U, rx, ry, a, b, o);
+}
+
+// scaled fluxes phi_x(v) = Phi_x(v)/c, phi_y(v) = Phi_y(v)/c (Eq. system)
+__device__ __forceinline__ void phix(const double (&v)[5], double a, double b, double (&o)[5])
+{
+    o[0] = a * v[2] + b * v[3];
+    o[1] = b * v[4];
+    o[2] = a * v[0];
+    o[3] = b * v[0];
+    o[4] = b * v[1];
+}
+__device__ __forceinline__ void phiy(const double (&v)[5], double a, double b, double (&o)[5])
+{
+    o[0] = b * v[4];
+    o[1] = a * v[2] - b * v[3];
+    o[2] = a * v[1];
+    o[3] = -b * v[1];
+    o[4] = b * v[0];
+}
+
+// Eq. ic_second written with the scaled fluxes (Phi/c), then the first collision.
+// Inputs are dense [5][ny][nx] (U0, dU0dx, dU0dy), [2][ny][nx] (B0, u0; may be null).
+template <int K>
+__global__ void init_kernel(NodeArgs A, const double* __restrict__ U0, const double* __restrict__ Ux,
+                            const double* __restrict__ Uy, const double* __restrict__ B0,
+                            const double* __restrict__ u0)
+{
+    const long long n = (long long)A.nx * A.ny;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+         id += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(id % A.nx), y = (int)(id / A.nx);
+        double u[5], ux[5], uy[5], bv[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            u[k] = U0[k * n + id];
+            ux[k] = Ux[k * n + id];
+            uy[k] = Uy[k * n + id];
+        }
+        if (B0) {
+            bv[0] = B0[id];
+            bv[1] = B0[n + id];
+        }
+        const double a = A.a, b = A.b, c = A.c;
+        double pxu[5], pyu[5], pxb[5], pyb[5], pxx[5], pyy[5], pxpxx[5], pypxx[5], pxpyy[5], pypyy[5];
+        phix(u, a, b, pxu);
+        phiy(u, a, b, pyu);
+        phix(bv, a, b, pxb);
+        phiy(bv, a, b, pyb);
+        phix(ux, a, b, pxx);
+        phiy(uy, a, b, pyy);
+        phix(pxx, a, b, pxpxx);
+        phiy(pxx, a, b, pypxx);
+        phix(pyy, a, b, pxpyy);
+        phiy(pyy, a, b, pypyy);
+        double f[4][5];
+        const int VI[4] = {1, 0, -1, 0}, VJ[4] = {0, 1, 0, -1};
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const double i = VI[d], j = VJ[d];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const double eq = 0.25 * (u[k] + 2.0 * (i * pxu[k] + j * pyu[k]));
+                const double corr = (bv[k] + 2.0 * (i * pxb[k] + j * pyb[k]))
+                                  + c * (i * ux[k] + (2.0 * i * i - 1.0) * pxx[k] - 2.0 * (i * pxpxx[k] + j * pypxx[k]))
+                                  + c * (j * uy[k] + (2.0 * j * j - 1.0) * pyy[k] - 2.0 * (i * pxpyy[k] + j * pypyy[k]));
+                f[d][k] = eq - 0.125 * A.dt * corr;
+            }
+        }
+        double shift[5] = {0.5 * A.dt * bv[0], 0.5 * A.dt * bv[1], 0.0, 0.0, 0.0};
+        double S[4][5], U[5];
+        reflect_node(f, shift, a, b, S, U);
+        store_node<K>(A, x, y, S);
+        if (A.w) {
+            // u*(dt) = u*(0) + dt v(0) with u*(0) = u0 - dt/2 v(0)  (Eq. trapezoidal)
+            const long long off = (long long)y * A.pitch + x;
+            const double u0x = u0 ? u0[id] : 0.0, u0y = u0 ? u0[n + id] : 0.0;
+            A.w[off] = u0x + 0.5 * A.dt * U[0];
+            A.w[A.plane + off] = u0y + 0.5 * A.dt * U[1];
+        }
+    }
+}
+
+// pre-collision f(t) (and U^num(t)) of one node from the stored f*(t)
+template <int K>
+__device__ __forceinline__ void node_state(const NodeArgs& A, int x, int y, double (&f)[4][5], double (&U)[5])
+{
+    double S[4][5];
+    load_node<K>(A, x, y, S);
+    double bx = 0.0, by = 0.0;
+    if (A.R > 0) body_load(A, x, y, bx, by);
+    const double shift[5] = {-0.5 * A.dt * bx, -0.5 * A.dt * by, 0.0, 0.0, 0.0};
+    reflect_node(S, shift, A.a, A.b, f, U);
+}
+
+// ten output fields (Sec. 3.5) of one node
+template <int K>
+__device__ __forceinline__ void node_outputs(const NodeArgs& A, int x, int y, double (&o)[10])
+{
+    double f[4][5], U[5];
+    node_state<K>(A, x, y, f, U);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) o[k] = U[k];
+    if (A.w) {
+        // u(t) = u*(t) + dt/2 v(t) and the stored helper is u*(t) + dt v(t)
+        const long long off = (long long)y * A.pitch + x;
+        o[5] = A.w[off] - 0.5 * A.dt * U[0];
+        o[6] = A.w[A.plane + off] - 0.5 * A.dt * U[1];
+    } else {
+        o[5] = 0.0;
+        o[6] = 0.0;
+    }
+    o[7] = -(A.cK * U[2] + A.cmu * U[3]);   // Eq. sigma_num
+    o[8] = -(A.cK * U[2] - A.cmu * U[3]);
+    o[9] = -(A.cmu * U[4]);
+}
+
+template <int K>
+__global__ void moments_kernel(NodeArgs A, double* __restrict__ out)
+{
+    const long long n = (long long)A.nx * A.ny;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+         id += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(id % A.nx), y = (int)(id / A.nx);
+        double o[10];
+        node_outputs<K>(A, x, y, o);
+#pragma unroll
+        for (int q = 0; q < 10; ++q) out[q * n + id] = o[q];
+    }
+}
+
+template <int K>
+__global__ void get_populations_kernel(NodeArgs A, double* __restrict__ fout, double* __restrict__ ustar)
+{
+    const long long n = (long long)A.nx * A.ny;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+         id += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(id % A.nx), y = (int)(id / A.nx);
+        double f[4][5], U[5];
+        node_state<K>(A, x, y, f, U);
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) fout[(d * 5 + k) * n + id] = f[d][k];
+        if (ustar) {
+            const long long off = (long long)y * A.pitch + x;
+            ustar[id] = A.w ? A.w[off] - A.dt * U[0] : 0.0;
+            ustar[n + id] = A.w ? A.w[A.plane + off] - A.dt * U[1] : 0.0;
+        }
+    }
+}
+
+template <int K>
+__global__ void set_populations_kernel(NodeArgs A, const double* __restrict__ fin, const double* __restrict__ ustar)
+{
+    const long long n = (long long)A.nx * A.ny;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+         id += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(id % A.nx), y = (int)(id / A.nx);
+        double f[4][5];
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) f[d][k] = fin[(d * 5 + k) * n + id];
+        double bx = 0.0, by = 0.0;
+        if (A.R > 0) body_load(A, x, y, bx, by);
+        const double shift[5] = {0.5 * A.dt * bx, 0.5 * A.dt * by, 0.0, 0.0, 0.0};
+        double S[4][5], U[5];
+        reflect_node(f, shift, A.a, A.b, S, U);
+        store_node<K>(A, x, y, S);
+        if (A.w) {
+            const long long off = (long long)y * A.pitch + x;
+            A.w[off] = (ustar ? ustar[id] : 0.0) + A.dt * U[0];
+            A.w[A.plane + off] = (ustar ? ustar[n + id] : 0.0) + A.dt * U[1];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reductions: per-thread accumulation, warp shuffles, one partial per block
+// in a scratch array, then a single-block pass in fixed order (deterministic)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// block reduction of NV values; is_max[q] selects max instead of sum; result valid in thread 0
+template <int NV>
+__device__ __forceinline__ void block_reduce(double (&v)[NV], const bool (&is_max)[NV])
+{
+    __shared__ double red[32][NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = is_max[q] ? warp_max(v[q]) : warp_sum(v[q]);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) red[wid][q] = v[q];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double t = (lane < nw) ? red[lane][q] : 0.0;
+            v[q] = is_max[q] ? warp_max(t) : warp_sum(t);
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ double node_energy(const NodeArgs& A, int x, int y)
+{
+    double f[4][5], U[5];
+    node_state<K>(A, x, y, f, U);
+    double e = 0.0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+#pragma unroll
+        for (int p = 0; p < 5; ++p) {
+            double kf = 0.0;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) kf = fma(A.k[d][p * 5 + q], f[d][q], kf);
+            e = fma(f[d][p], kf, e);
+        }
+    }
+    return e;
+}
+
+// ||f||_P^2: partial sums per block into partial[blockIdx.x]
+template <int K>
+__global__ void __launch_bounds__(256) energy_kernel(NodeArgs A, double* __restrict__ partial)
+{
+    const long long n = (long long)A.nx * A.ny;
+    double v[1] = {0.0};
+    const bool is_max[1] = {false};
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+         id += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(id % A.nx), y = (int)(id / A.nx);
+        v[0] += node_energy<K>(A, x, y);
+    }
+    block_reduce<1>(v, is_max);
+    if (threadIdx.x == 0) partial[blockIdx.x] = v[0];
+}
+
+// error sums against exact [10][ny][nx]: partial[blockIdx.x][30] = (sum e^2, sum ex^2, max|e|) x 10
+template <int K>
+__global__ void __launch_bounds__(256) error_kernel(NodeArgs A, const double* __restrict__ exact,
+                                                    double* __restrict__ partial)
+{
+    const long long n = (long long)A.nx * A.ny;
+    double v[30];
+    bool is_max[30];
+#pragma unroll
+    for (int q = 0; q < 30; ++q) {
+        v[q] = 0.0;
+        is_max[q] = (q >= 20);
+    }
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+         id += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(id % A.nx), y = (int)(id / A.nx);
+        double o[10];
+        node_outputs<K>(A, x, y, o);
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            const double ex = exact[q * n + id];
+            const double e = o[q] - ex;
+            v[q] = fma(e, e, v[q]);
+            v[10 + q] = fma(ex, ex, v[10 + q]);
+            v[20 + q] = fmax(v[20 + q], fabs(e));
+        }
+    }
+    block_reduce<30>(v, is_max);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < 30; ++q) partial[(long long)blockIdx.x * 30 + q] = v[q];
+}
+
+// fold nblk partial rows of width NV into out[NV] (one block, fixed order)
+template <int NV>
+__global__ void __launch_bounds__(256) finish_kernel(const double* __restrict__ partial, int nblk,
+                                                     int nmax_from, double* __restrict__ out)
+{
+    double v[NV];
+    bool is_max[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        v[q] = 0.0;
+        is_max[q] = (q >= nmax_from);
+    }
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const double t = partial[(long long)i * NV + q];
+            v[q] = is_max[q] ? fmax(v[q], t) : v[q] + t;
+        }
+    block_reduce<NV>(v, is_max);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) out[q] = v[q];
+}
+
+template <int K>
+__global__ void finite_kernel(const void* S, int nx, int ny, int pitch, long long plane, int* flag)
+{
+    using E = typename Fmt<K>::E;
+    const E* p = static_cast<const E*>(S);
+    const long long n = 20LL * ny * nx;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+         id += (long long)gridDim.x * blockDim.x) {
+        const long long q = id / ((long long)ny * nx);
+        const long long r = id % ((long long)ny * nx);
+        const int y = (int)(r / nx), x = (int)(r % nx);
+        const double v = (double)Fmt<K>::ld(p[q * plane + (long long)y * pitch + x]);
+        if (!isfinite(v)) atomicOr(flag, 1);
+    }
+}
+
+}  // namespace lbmk

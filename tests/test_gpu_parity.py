@@ -1,0 +1,189 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerance: 1e-12 relative L2 per output field for the FP64 path (the bound the
+FP64 fused kernel is held to); the reduced-precision formats are compared with
+their own stated bounds.  Sizes span several thread blocks and ragged row ends.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Oracle, Params
+from oracle import matrix_form as mf
+from oracle.postprocess import rel_l2
+
+from .helpers import field_errors, gpu_lattice, oracle_run
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+
+
+def _config1(steps=1000):
+    """Periodic 64x64, lambda = 1, mu = 0.5 (cK^2 = 1.5, cmu^2 = 0.5), 0.9 of the CFL bound,
+    one wavelength per side, amplitude 1e-2."""
+    return W.periodic_mms(64, 1.5, 0.5, cfl=0.9, steps=steps, amp=1e-2, kx=2 * math.pi, ky=2 * math.pi)
+
+
+def test_config1_periodic_64_fp64_matches_oracle(lbm):
+    wl = _config1()
+    _, ref = oracle_run(wl)
+    lat = gpu_lattice(lbm, wl)
+    lat.step(wl.steps)
+    out = lat.moments()
+    errs = field_errors(out, ref)
+    assert max(errs) < TOL64, errs
+    # and the solution itself is second-order accurate against the manufactured one
+    ex = wl.exact_outputs(wl.steps * wl.dt)
+    assert rel_l2(out[5:7], ex[5:7]) < 2e-2
+
+
+@pytest.mark.parametrize("nx,ny", [(48, 24), (37, 23), (1100, 9)])
+def test_dirichlet_mms_fp64_matches_oracle(lbm, nx, ny):
+    wl = W.dirichlet_mms(nx, ny, 1.1, 0.4, cfl=0.9, steps=60, height=1.0)
+    _, ref = oracle_run(wl)
+    lat = gpu_lattice(lbm, wl)
+    lat.step(wl.steps)
+    errs = field_errors(lat.moments(), ref)
+    assert max(errs) < TOL64, errs
+
+
+@pytest.mark.parametrize("nx,ny", [(2, 2), (3, 5), (67, 45), (1031, 7), (520, 3)])
+def test_periodic_ragged_sizes_fp64(lbm, nx, ny):
+    rng = np.random.default_rng(nx * 100 + ny)
+    wl = W.periodic_mms(max(nx, ny), 1.5, 0.5, steps=0)
+    o = Oracle(Params(nx, ny, 0.1, 0.1 / 3.2, 1.0, 0.6, False))
+    f = rng.standard_normal((4, 5, ny, nx))
+    us = rng.standard_normal((2, ny, nx))
+    o.set_state(f, us)
+    lat = lbm.Lattice(nx, ny, 0.1, 0.1 / 3.2, 1.0, 0.6, dirichlet=False, storage="f64")
+    lat.set_populations(f, us)
+    for _ in range(7):
+        o.step()
+    lat.step(7)
+    g, gu = lat.populations()
+    np.testing.assert_allclose(g, o.f, rtol=0, atol=1e-13 * np.max(np.abs(o.f)))
+    np.testing.assert_allclose(gu, o.ustar, rtol=0, atol=1e-13 * np.max(np.abs(o.ustar)))
+    del wl
+
+
+@pytest.mark.parametrize("dirichlet", [False, True])
+def test_one_step_4x4_equals_brute_force_operator(lbm, dirichlet):
+    """One GPU step on 4x4 == the 320x320 operator from G, the shift, D and S (Sec. 5.1)."""
+    nx = ny = 4
+    cK, cmu, c, dx = math.sqrt(1.1), math.sqrt(0.4), 2.5, 0.25
+    dt = dx / c
+    M, F, Sg = mf.one_step_operator(nx, ny, cK, cmu, c, dt, dirichlet)
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal((4, 5, ny, nx))
+    lat = lbm.Lattice(nx, ny, dx, dt, cK, cmu, dirichlet=dirichlet, storage="f64")
+    expect = M @ f.reshape(-1)
+    if dirichlet:
+        g = rng.standard_normal((1, 2, 2 * (nx + ny)))
+        lat.set_dirichlet(g)
+        expect = expect + Sg @ g[0].reshape(-1)
+    lat.set_populations(f)
+    lat.step(1)
+    out, _ = lat.populations()
+    np.testing.assert_allclose(out.reshape(-1), expect, atol=1e-13, rtol=0)
+    del F
+
+
+def test_forcing_tables_match_oracle_4x4(lbm):
+    """Body load enters through U^num (Eq. cond_eq): one step with random separable b."""
+    nx = ny = 4
+    cK, cmu, c, dx = math.sqrt(1.1), math.sqrt(0.4), 2.5, 0.25
+    dt = dx / c
+    M, F, _ = mf.one_step_operator(nx, ny, cK, cmu, c, dt, False)
+    rng = np.random.default_rng(11)
+    R = 3
+    X, Y, T = rng.standard_normal((R, nx)), rng.standard_normal((R, ny)), rng.standard_normal((4, 2, R))
+    lat = lbm.Lattice(nx, ny, dx, dt, cK, cmu, storage="f64")
+    lat.set_forcing(X, Y, T)
+    f = rng.standard_normal((4, 5, ny, nx))
+    lat.set_populations(f, m=1)
+    lat.step(1)
+    out, _ = lat.populations()
+    b1 = np.einsum("rx,ry,cr->cyx", X, Y, T[1])
+    np.testing.assert_allclose(out.reshape(-1), M @ f.reshape(-1) + F @ b1.reshape(-1), atol=1e-13)
+
+
+def test_energy_matches_oracle_and_is_conserved(lbm):
+    """||f||_P on the GPU equals the oracle's; homogeneous Dirichlet, b = 0: conserved
+    to round-off over 4000 steps (Sec. 6.2 set-up, paper: 3.4e-15)."""
+    wl = W.energy_box(160, 1.1, 0.4, 1.0 / 400.0, 4000)
+    o = Oracle(Params(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, True))
+    o.init(wl.U0, wl.dU0dx, wl.dU0dy, None, wl.u0)
+    lat = gpu_lattice(lbm, wl, track=False)
+    e0 = lat.energy()
+    assert abs(e0 - o.energy()) < 1e-13 * o.energy()
+    drift = 0.0
+    for _ in range(40):
+        lat.step(100)
+        drift = max(drift, abs(math.sqrt(lat.energy()) - math.sqrt(e0)) / math.sqrt(e0))
+    assert drift < 3.4e-14, drift
+
+
+def test_error_sums_match_host_reduction(lbm):
+    wl = _config1(steps=50)
+    lat = gpu_lattice(lbm, wl)
+    lat.step(wl.steps)
+    out = lat.moments()
+    ex = wl.exact_outputs(wl.steps * wl.dt)
+    s = lat.error_sums(ex)
+    e = out - ex
+    np.testing.assert_allclose(s[0], np.sum(e * e, axis=(1, 2)), rtol=1e-12)
+    np.testing.assert_allclose(s[1], np.sum(ex * ex, axis=(1, 2)), rtol=1e-12)
+    np.testing.assert_allclose(s[2], np.max(np.abs(e), axis=(1, 2)), rtol=1e-12)
+
+
+def test_checkpoint_resume_is_bit_exact(lbm):
+    wl = _config1(steps=40)
+    a = gpu_lattice(lbm, wl)
+    a.step(20)
+    blob = np.empty(lbm.lbm_state_bytes(a.ctx), dtype=np.uint8)
+    lbm.lbm_save_state(a.ctx, blob)
+    a.step(20)
+    ref = a.moments()
+    b = gpu_lattice(lbm, wl)
+    lbm.lbm_load_state(b.ctx, blob, 20)
+    b.step(20)
+    np.testing.assert_array_equal(b.moments(), ref)
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("bf16", 5e-2), ("f16", 5e-3)])
+def test_reduced_precision_against_oracle(lbm, storage, tol):
+    """Populations stored in FP32 / BF16 / FP16 with FP32 arithmetic: relative L2 of the
+    moment fields against the FP64 oracle after 200 steps of the config-1 problem."""
+    wl = _config1(steps=200)
+    _, ref = oracle_run(wl)
+    lat = gpu_lattice(lbm, wl, storage=storage)
+    lat.step(wl.steps)
+    errs = field_errors(lat.moments(), ref, fields=range(5))
+    assert max(errs) < tol, (storage, errs)
+
+
+def test_api_errors(lbm):
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Lattice(8, 8, 0.1, 0.1 / 2.0, 1.0, 0.6)        # c = 2 < 2 sqrt(1.36)
+    assert e.value.status == lbm.LBM_ERR_CFL
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Lattice(1, 8, 0.1, 0.01, 1.0, 0.6)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    lat = lbm.Lattice(8, 8, 0.1, 0.01, 1.0, 0.6)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.step(1)                                        # before init
+    assert e.value.status == lbm.LBM_ERR_STATE
+    lat.set_populations(np.zeros((4, 5, 8, 8)))
+    lat.step(0)
+    lat.set_forcing(np.ones((1, 8)), np.ones((1, 8)), np.ones((2, 2, 1)))
+    lat.step(1)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.step(1)                                        # table has rows for t = 0, 1 only
+    assert e.value.status == lbm.LBM_ERR_STATE
+    f = np.zeros((4, 5, 8, 8))
+    f[1, 2, 3, 4] = np.nan
+    lat.set_forcing()
+    lat.set_populations(f)
+    assert not lat.finite()
