@@ -139,13 +139,40 @@ lbm_status lbm_synchronize(lbm_ctx* ctx);
 lbm_status lbm_destroy(lbm_ctx* ctx);
 
 /* Message describing the last error on ctx (never NULL; "" when none).  With
- * ctx = NULL: the last error of a failed lbm_create in this thread. */
+ * ctx = NULL: the last error of a failed lbm_create or lbm_energy_noalloc in
+ * this thread. */
 const char* lbm_last_error(const lbm_ctx* ctx);
 
 /* Raw storage-format state for bit-exact checkpoints: bytes needed, copy out, copy in. */
 lbm_status lbm_state_bytes(const lbm_ctx* ctx, int64_t* nbytes);
 lbm_status lbm_save_state(lbm_ctx* ctx, void* dst, int32_t on_device);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t m, int32_t on_device);
+
+/* ||f||_P^2 of caller-supplied populations, allocating no device memory.
+ *
+ * Same quantity as lbm_energy, for callers that cannot call cudaMalloc: a host
+ * process whose device memory is entirely owned by another allocator (a caching
+ * allocator that reserved the pool), or a time-critical loop that cannot afford
+ * the implicit device-wide synchronisation of cudaFree.  The paper has no
+ * counterpart; this is a library service.
+ *   f      : device pointer, pre-collision populations [4][5][ny][nx], FP64 (for
+ *            example written by lbm_get_populations with on_device = 1)
+ *   nx, ny : lattice size, nx >= 1 and 1 <= ny <= 16384; larger ny is rejected with
+ *            LBM_ERR_ARG because the scratch holds one partial sum per row
+ *   dx, dt, cK, cmu : as in lbm_params; LBM_ERR_CFL if 2 sqrt(cK^2+cmu^2) >= dx/dt
+ *   out    : one double; device memory when out_on_device = 1 (written in stream
+ *            order, no wait), else host memory (the call waits for the stream)
+ *   stream : cudaStream_t to run on (NULL = legacy stream)
+ * Scratch: a static 128 KB array (16384 + 32 doubles) in the library's device
+ * image, held by every GPU that loads the library until the process exits.  The
+ * first call on each device looks up its device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents; every row
+ * partial is rewritten before it is read, so nothing needs clearing.  Calls
+ * whose work overlaps on the GPU (different streams, or different host threads
+ * on one device) race on the array and must be serialised by the caller. */
+lbm_status lbm_energy_noalloc(const double* f, int32_t nx, int32_t ny, double dx, double dt, double cK,
+                              double cmu, double* out, int32_t out_on_device, void* stream);
 
 #ifdef __cplusplus
 }

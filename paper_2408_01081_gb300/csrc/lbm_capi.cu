@@ -602,3 +602,13 @@ cudaError_t finish_err30(const double* partial, int nblk, double* out, cudaStrea
 }
 
 }  // namespace lbmh
+
+namespace lbmh {
+
+// message for lbm_last_error(NULL) from context-free entry points in other files
+void set_thread_error(const char* msg)
+{
+    g_create_error = msg ? msg : "";
+}
+
+}  // namespace lbmh

@@ -27,7 +27,7 @@ STATUS_NAMES = ["LBM_OK", "LBM_ERR_ARG", "LBM_ERR_CFL", "LBM_ERR_OOM", "LBM_ERR_
 EXPORTS = ["lbm_create", "lbm_init", "lbm_set_forcing", "lbm_set_dirichlet", "lbm_step", "lbm_moments",
            "lbm_energy", "lbm_error_sums", "lbm_get_populations", "lbm_set_populations", "lbm_check_finite",
            "lbm_time_step", "lbm_synchronize", "lbm_destroy", "lbm_last_error", "lbm_state_bytes",
-           "lbm_save_state", "lbm_load_state"]
+           "lbm_save_state", "lbm_load_state", "lbm_energy_noalloc"]
 
 
 class LbmParams(ctypes.Structure):
@@ -79,6 +79,8 @@ def load(path: Optional[str] = None):
         "lbm_state_bytes": ([vp, ctypes.POINTER(i64)], i32),
         "lbm_save_state": ([vp, vp, i32], i32),
         "lbm_load_state": ([vp, vp, i64, i32], i32),
+        "lbm_energy_noalloc": ([dp, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, dp, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -237,6 +239,28 @@ def lbm_load_state(ctx, src, m):
         _check(ctx, load().lbm_load_state(ctx, ctypes.c_void_p(src.data_ptr()), int(m), 1))
     else:
         _check(ctx, load().lbm_load_state(ctx, ctypes.c_void_p(src.ctypes.data), int(m), 0))
+
+
+def lbm_energy_noalloc(f, nx, ny, dx, dt, cK, cmu, out=None, stream=None) -> float:
+    """||f||_P^2 of device populations f [4, 5, ny, nx] without any device allocation.
+
+    ``out``: optional 1-element float64 CUDA tensor to receive the result on the
+    device (no wait); otherwise the value is returned through host memory."""
+    if not _is_torch_cuda(f):
+        raise TypeError("f must be a CUDA tensor (device memory)")
+    p, _, _keep = _arr(f, "f")
+    if out is not None:
+        po, on, _k2 = _arr(out, "out")
+        if on != 1:
+            raise TypeError("out must be a CUDA tensor")
+        _check(None, load().lbm_energy_noalloc(p, int(nx), int(ny), float(dx), float(dt), float(cK), float(cmu),
+                                               po, 1, ctypes.c_void_p(stream or 0)))
+        return None
+    v = ctypes.c_double()
+    _check(None, load().lbm_energy_noalloc(p, int(nx), int(ny), float(dx), float(dt), float(cK), float(cmu),
+                                           ctypes.cast(ctypes.byref(v), ctypes.c_void_p), 0,
+                                           ctypes.c_void_p(stream or 0)))
+    return float(v.value)
 
 
 class Lattice:
