@@ -38,15 +38,19 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(s) <= t for s in _sources())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, out: str = None, defines=()) -> str:
+    """Compile and link the library; ``out``/``defines`` build a tuning variant elsewhere."""
+    lib = out or LIB
+    if not force and out is None and up_to_date():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = os.path.dirname(lib) if out else BUILD
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
-    units = [(os.path.join(CSRC, "lbm_kind.cu"), os.path.join(BUILD, f"lbm_kind{k}.o"), [f"-DLBM_KIND={k}"])
-             for k in range(4)]
+    dflags = [f"-D{d}" for d in defines]
+    units = [(os.path.join(CSRC, "lbm_kind.cu"), os.path.join(build_dir, f"lbm_kind{k}.o"),
+              [f"-DLBM_KIND={k}"] + dflags) for k in range(4)]
     extra = [f for f in sorted(os.listdir(CSRC)) if f.endswith(".cu") and f != "lbm_kind.cu"]
-    units += [(os.path.join(CSRC, f), os.path.join(BUILD, f[:-3] + ".o"), []) for f in extra]
+    units += [(os.path.join(CSRC, f), os.path.join(build_dir, f[:-3] + ".o"), dflags) for f in extra]
     procs = []
     for src, obj, defs in units:
         cmd = [nvcc] + ARCH + FLAGS + defs + ["-c", src, "-o", obj]
@@ -63,13 +67,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         msg = "\n".join(" ".join(c) + "\n" + o for c, o in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     link = [nvcc] + ARCH + ["-shared", "-o", tmp] + [obj for _, obj, _ in units] + ["-lcudart"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

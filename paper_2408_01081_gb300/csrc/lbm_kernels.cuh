@@ -55,6 +55,7 @@ template <> struct Fmt<K_F16> {
 };
 
 template <int BYTES> struct Raw;
+template <> struct Raw<2> { using T = unsigned short; };
 template <> struct Raw<4> { using T = unsigned int; };
 template <> struct Raw<8> { using T = uint2; };
 template <> struct Raw<16> { using T = uint4; };
@@ -155,8 +156,12 @@ __device__ __forceinline__ void wall_source(int i, int j, double gx, double gy, 
 // fused pull-collide step: one thread = V consecutive nodes of one row
 // grid: (ceil(ceil(nx/V) / blockDim.x), ny)
 // ---------------------------------------------------------------------------
+#ifndef LBM_STEP_MIN_BLOCKS
+#define LBM_STEP_MIN_BLOCKS 1
+#endif
+
 template <int K, int V, bool DIRICHLET, bool FORCING, bool TRACK>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS)
 step_kernel(StepArgs A)
 {
     using E = typename Fmt<K>::E;

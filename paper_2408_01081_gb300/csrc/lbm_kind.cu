@@ -8,9 +8,19 @@
 
 namespace {
 
+#ifndef LBM_VEC_F64
+#define LBM_VEC_F64 2
+#endif
+#ifndef LBM_VEC_F32
+#define LBM_VEC_F32 4
+#endif
+#ifndef LBM_VEC_F16
+#define LBM_VEC_F16 4
+#endif
+
 constexpr int K = LBM_KIND;
-// nodes per thread: one 16-byte vector of FP64 / FP32, 8 bytes of 16-bit values
-constexpr int V = (K == lbmk::K_F64) ? 2 : 4;
+// nodes per thread in the step kernel (one vector access per plane and thread)
+constexpr int V = (K == lbmk::K_F64) ? LBM_VEC_F64 : (K == lbmk::K_F32) ? LBM_VEC_F32 : LBM_VEC_F16;
 
 template <bool D, bool F, bool T>
 cudaError_t step_v(const lbmk::StepArgs& a, dim3 g, dim3 b, cudaStream_t s)
