@@ -148,6 +148,73 @@ lbm_status lbm_state_bytes(const lbm_ctx* ctx, int64_t* nbytes);
 lbm_status lbm_save_state(lbm_ctx* ctx, void* dst, int32_t on_device);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t m, int32_t on_device);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent lattices of uneven size and material advanced
+ * together.  Every lattice of a batch has b = 0; a Dirichlet lattice has
+ * homogeneous data (u_D constant in time).  All lattices share one storage
+ * format.  The per-node arithmetic is the single-lattice step's, so a batch
+ * lattice follows exactly the trajectory it would follow alone.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_batch lbm_batch;
+
+typedef struct {
+    int32_t nx, ny;      /* >= 2, ny <= 65535 */
+    int32_t bc;          /* lbm_bc */
+    int32_t reserved;    /* must be 0 */
+    double dx, dt, cK, cmu;
+} lbm_lattice_desc;
+
+/* Lay out `count` lattices (1 <= count <= 65536) in two device arenas and build
+ * the tile work-list with the default tile widths.  Validates every lattice like
+ * lbm_create (LBM_ERR_ARG / LBM_ERR_CFL, message names the lattice index).  All
+ * populations start at zero. */
+lbm_status lbm_batch_create(int32_t count, const lbm_lattice_desc* lattices, int32_t storage, void* stream,
+                            lbm_batch** out);
+
+/* Eq. ic_second for lattice `index` (b = 0, no displacement tracking): U0, dU0dx,
+ * dU0dy are [5][ny][nx] FP64 as in lbm_init. */
+lbm_status lbm_batch_init(lbm_batch* b, int32_t index, const double* U0, const double* dU0dx,
+                          const double* dU0dy, int32_t on_device);
+
+/* Choose the tile width of every size class and the launch mode by timing them
+ * on this GPU, before any lbm_batch_init (tuning steps the zero state; returns
+ * LBM_ERR_STATE afterwards).  cache_path (or NULL): a text file of earlier
+ * results keyed by GPU name, storage format and size class; found entries are
+ * used without timing, new ones are appended. */
+lbm_status lbm_batch_tune(lbm_batch* b, const char* cache_path);
+
+/* Launch mode: 0 = one launch per step; 1 = one persistent launch per
+ * `graph_steps` steps with a grid barrier between steps (cooperative launch).
+ * graph_steps (even, 2..10000): steps captured in one CUDA graph and replayed. */
+lbm_status lbm_batch_set_mode(lbm_batch* b, int32_t mode, int32_t graph_steps);
+
+/* Advance every lattice n >= 0 steps, asynchronously.  Barrier time-outs of the
+ * persistent mode are reported by lbm_batch_synchronize. */
+lbm_status lbm_batch_step(lbm_batch* b, int64_t n);
+
+/* Wait for the batch's stream; LBM_ERR_TIMEOUT if a grid barrier wait ran out
+ * (the flag is cleared; the populations are then undefined until re-initialised). */
+lbm_status lbm_batch_synchronize(lbm_batch* b);
+
+/* Ten output fields of lattice `index` ([10][ny][nx], as lbm_moments; u fields 0). */
+lbm_status lbm_batch_moments(lbm_batch* b, int32_t index, double* out, int32_t on_device);
+
+/* ||f||_P^2 of lattice `index` (as lbm_energy), written to host *out. */
+lbm_status lbm_batch_energy(lbm_batch* b, int32_t index, double* out);
+
+/* Sizes: total nodes, state bytes (both arenas), tiles, and the current tile
+ * width in nodes of lattice `index` (any pointer may be NULL). */
+lbm_status lbm_batch_info(const lbm_batch* b, int32_t index, int64_t* nodes, int64_t* state_bytes,
+                          int32_t* ntiles, int32_t* tile_width);
+
+/* Barrier wait limit of the persistent mode (seconds, > 0; default 2) and a test
+ * hook: extra_arrivals > 0 makes every barrier wait for arrivals that never come,
+ * so the limit expires and lbm_batch_synchronize reports LBM_ERR_TIMEOUT. */
+lbm_status lbm_batch_set_barrier(lbm_batch* b, double timeout_s, int32_t extra_arrivals);
+
+lbm_status lbm_batch_destroy(lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+
 /* ||f||_P^2 of caller-supplied populations, allocating no device memory.
  *
  * Same quantity as lbm_energy, for callers that cannot call cudaMalloc: a host

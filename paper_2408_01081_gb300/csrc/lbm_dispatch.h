@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include "lbm_batch.cuh"
 #include "lbm_kernels.cuh"
 
 namespace lbmh {
@@ -28,6 +29,9 @@ struct KindOps {
                          cudaStream_t s);
     cudaError_t (*finite)(const void* S, int nx, int ny, int pitch, long long plane, int* flag, dim3 grid,
                           dim3 block, cudaStream_t s);
+    // batch: one launch of `grid` blocks x 256 threads; persistent launches are cooperative
+    cudaError_t (*batch_step)(const lbmk::BatchArgs&, bool persistent, int grid, cudaStream_t s);
+    cudaError_t (*batch_occupancy)(int* blocks_per_sm);
 };
 
 extern const KindOps kind_ops_0;  // FP64

@@ -60,14 +60,16 @@ template <> struct Raw<4> { using T = unsigned int; };
 template <> struct Raw<8> { using T = uint2; };
 template <> struct Raw<16> { using T = uint4; };
 
-// V consecutive elements from a (V * sizeof(E))-aligned address, one vector access
-template <int K, int V>
+// V consecutive elements from a (V * sizeof(E))-aligned address, one vector access.
+// COHERENT loads bypass L1 (ld.global.cg): needed when the same launch wrote the
+// data from other blocks (the persistent batch kernel); otherwise the read-only path.
+template <int K, int V, bool COHERENT = false>
 __device__ __forceinline__ void vload(const typename Fmt<K>::E* p, typename Fmt<K>::M (&out)[V])
 {
     using E = typename Fmt<K>::E;
     using R = typename Raw<sizeof(E) * V>::T;
     union { R r; E e[V]; } u;
-    u.r = __ldg(reinterpret_cast<const R*>(p));
+    u.r = COHERENT ? __ldcg(reinterpret_cast<const R*>(p)) : __ldg(reinterpret_cast<const R*>(p));
 #pragma unroll
     for (int i = 0; i < V; ++i) out[i] = Fmt<K>::ld(u.e[i]);
 }
@@ -83,10 +85,10 @@ __device__ __forceinline__ void vstore(typename Fmt<K>::E* p, const typename Fmt
     *reinterpret_cast<R*>(p) = u.r;
 }
 
-template <int K>
+template <int K, bool COHERENT = false>
 __device__ __forceinline__ typename Fmt<K>::M sload(const typename Fmt<K>::E* p)
 {
-    return Fmt<K>::ld(__ldg(p));
+    return Fmt<K>::ld(COHERENT ? __ldcg(p) : __ldg(p));
 }
 
 // ---------------------------------------------------------------------------

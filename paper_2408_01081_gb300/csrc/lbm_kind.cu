@@ -89,6 +89,30 @@ cudaError_t finite(const void* S, int nx, int ny, int pitch, long long plane, in
     return cudaGetLastError();
 }
 
+cudaError_t batch_step(const lbmk::BatchArgs& a, bool persistent, int grid, cudaStream_t s)
+{
+    if (!persistent) {
+        lbmk::batch_step_kernel<K, V, false><<<grid, 256, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, lbmk::batch_step_kernel<K, V, true>, a);
+}
+
+cudaError_t batch_occupancy(int* n)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lbmk::batch_step_kernel<K, V, true>, 256, 0);
+}
+
 }  // namespace
 
 namespace lbmh {
@@ -98,7 +122,7 @@ namespace lbmh {
 
 const KindOps LBM_OPS_NAME(LBM_KIND) = {
     K, V, (int)sizeof(typename lbmk::Fmt<K>::E),
-    step, init, moments, get_pop, set_pop, energy, error, finite,
+    step, init, moments, get_pop, set_pop, energy, error, finite, batch_step, batch_occupancy,
 };
 
 }  // namespace lbmh

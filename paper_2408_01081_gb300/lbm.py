@@ -27,7 +27,10 @@ STATUS_NAMES = ["LBM_OK", "LBM_ERR_ARG", "LBM_ERR_CFL", "LBM_ERR_OOM", "LBM_ERR_
 EXPORTS = ["lbm_create", "lbm_init", "lbm_set_forcing", "lbm_set_dirichlet", "lbm_step", "lbm_moments",
            "lbm_energy", "lbm_error_sums", "lbm_get_populations", "lbm_set_populations", "lbm_check_finite",
            "lbm_time_step", "lbm_synchronize", "lbm_destroy", "lbm_last_error", "lbm_state_bytes",
-           "lbm_save_state", "lbm_load_state", "lbm_energy_noalloc"]
+           "lbm_save_state", "lbm_load_state", "lbm_energy_noalloc", "lbm_batch_create", "lbm_batch_init",
+           "lbm_batch_tune", "lbm_batch_set_mode", "lbm_batch_step", "lbm_batch_synchronize", "lbm_batch_moments",
+           "lbm_batch_energy", "lbm_batch_info", "lbm_batch_set_barrier", "lbm_batch_destroy",
+           "lbm_batch_last_error"]
 
 
 class LbmParams(ctypes.Structure):
@@ -38,6 +41,13 @@ class LbmParams(ctypes.Structure):
         ("cK", ctypes.c_double), ("cmu", ctypes.c_double),
         ("track_displacement", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
+    ]
+
+
+class LatticeDesc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("bc", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("cK", ctypes.c_double), ("cmu", ctypes.c_double),
     ]
 
 
@@ -81,6 +91,19 @@ def load(path: Optional[str] = None):
         "lbm_load_state": ([vp, vp, i64, i32], i32),
         "lbm_energy_noalloc": ([dp, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, dp, i32, vp], i32),
+        "lbm_batch_create": ([i32, ctypes.POINTER(LatticeDesc), i32, vp, ctypes.POINTER(vp)], i32),
+        "lbm_batch_init": ([vp, i32, dp, dp, dp, i32], i32),
+        "lbm_batch_tune": ([vp, ctypes.c_char_p], i32),
+        "lbm_batch_set_mode": ([vp, i32, i32], i32),
+        "lbm_batch_step": ([vp, i64], i32),
+        "lbm_batch_synchronize": ([vp], i32),
+        "lbm_batch_moments": ([vp, i32, dp, i32], i32),
+        "lbm_batch_energy": ([vp, i32, dp], i32),
+        "lbm_batch_info": ([vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                            ctypes.POINTER(i32)], i32),
+        "lbm_batch_set_barrier": ([vp, ctypes.c_double, i32], i32),
+        "lbm_batch_destroy": ([vp], i32),
+        "lbm_batch_last_error": ([vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -261,6 +284,80 @@ def lbm_energy_noalloc(f, nx, ny, dx, dt, cK, cmu, out=None, stream=None) -> flo
                                            ctypes.cast(ctypes.byref(v), ctypes.c_void_p), 0,
                                            ctypes.c_void_p(stream or 0)))
     return float(v.value)
+
+
+# ---------------------------------------------------------------------------
+# batches
+# ---------------------------------------------------------------------------
+
+def _bcheck(b, st):
+    if st != LBM_OK:
+        raise LbmError(st, load().lbm_batch_last_error(b).decode(errors="replace"))
+
+
+def lbm_batch_create(descs, storage=LBM_F64, stream=None):
+    """descs: iterable of (nx, ny, bc, dx, dt, cK, cmu)."""
+    arr = (LatticeDesc * len(descs))()
+    for i, (nx, ny, bc, dx, dt, cK, cmu) in enumerate(descs):
+        arr[i] = LatticeDesc(int(nx), int(ny), int(bc), 0, float(dx), float(dt), float(cK), float(cmu))
+    h = ctypes.c_void_p()
+    st = load().lbm_batch_create(len(descs), arr, int(storage), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+    _bcheck(None, st)
+    return h
+
+
+def lbm_batch_init(b, index, U0, dU0dx, dU0dy):
+    a = [_arr(U0, "U0"), _arr(dU0dx, "dU0dx"), _arr(dU0dy, "dU0dy")]
+    on = _where(*[t[1] for t in a])
+    _bcheck(b, load().lbm_batch_init(b, int(index), a[0][0], a[1][0], a[2][0], on))
+
+
+def lbm_batch_tune(b, cache_path=None):
+    _bcheck(b, load().lbm_batch_tune(b, None if cache_path is None else str(cache_path).encode()))
+
+
+def lbm_batch_set_mode(b, mode, graph_steps=100):
+    _bcheck(b, load().lbm_batch_set_mode(b, int(mode), int(graph_steps)))
+
+
+def lbm_batch_step(b, n=1):
+    _bcheck(b, load().lbm_batch_step(b, int(n)))
+
+
+def lbm_batch_synchronize(b):
+    _bcheck(b, load().lbm_batch_synchronize(b))
+
+
+def lbm_batch_moments(b, index, out):
+    p, on, _keep = _arr(out, "out")
+    _bcheck(b, load().lbm_batch_moments(b, int(index), p, on))
+    return out
+
+
+def lbm_batch_energy(b, index) -> float:
+    v = ctypes.c_double()
+    _bcheck(b, load().lbm_batch_energy(b, int(index), ctypes.cast(ctypes.byref(v), ctypes.c_void_p)))
+    return float(v.value)
+
+
+def lbm_batch_info(b, index=0):
+    n, sb = ctypes.c_int64(), ctypes.c_int64()
+    nt, tw = ctypes.c_int32(), ctypes.c_int32()
+    _bcheck(b, load().lbm_batch_info(b, int(index), ctypes.byref(n), ctypes.byref(sb), ctypes.byref(nt),
+                                     ctypes.byref(tw)))
+    return {"nodes": n.value, "state_bytes": sb.value, "ntiles": nt.value, "tile_width": tw.value}
+
+
+def lbm_batch_set_barrier(b, timeout_s, extra_arrivals=0):
+    _bcheck(b, load().lbm_batch_set_barrier(b, float(timeout_s), int(extra_arrivals)))
+
+
+def lbm_batch_destroy(b):
+    load().lbm_batch_destroy(b)
+
+
+def lbm_batch_last_error(b=None) -> str:
+    return load().lbm_batch_last_error(b).decode(errors="replace")
 
 
 class Lattice:
