@@ -134,3 +134,17 @@ def test_barrier_timeout_is_reported_and_batch_stays_usable(lbm):
     lbm.lbm_batch_moments(b, 1, o)
     assert np.all(np.isfinite(o))
     lbm.lbm_batch_destroy(b)
+
+
+def test_torch_grf_inputs_match_numpy_recipe(lbm):
+    """The GPU generator used for large batches reproduces the numpy GRF recipe."""
+    from workloads.grf import batch_lattice_inputs_torch
+    spec = W.batch_spec(count=4)
+    for sp in spec[:2] + spec[3:4]:
+        dx = 1.0 / max(sp.nx, sp.ny)
+        U0, Ux, Uy = (t.cpu().numpy() for t in batch_lattice_inputs_torch(sp, dx))
+        ref = W.grf_periodic(sp.nx, sp.ny, sp.cK2, sp.cmu2, ell=sp.ell, std=1e-3, seeds=(sp.seed, sp.seed + 7919),
+                             dx=dx, window=sp.dirichlet)
+        np.testing.assert_allclose(U0, ref.U0, atol=1e-15)
+        np.testing.assert_allclose(Ux, ref.dU0dx, atol=1e-12 * np.max(np.abs(ref.dU0dx)))
+        np.testing.assert_allclose(Uy, ref.dU0dy, atol=1e-12 * np.max(np.abs(ref.dU0dy)))

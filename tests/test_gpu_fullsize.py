@@ -1,0 +1,84 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times (periodic, no body load, no displacement tracking):
+
+* periodic 8192^2 GRF, FP64 and FP32: sampled nodes (edges, corners, interior)
+  after 3 steps against the oracle run on a periodic patch around each sample
+  (the domain of dependence of 3 steps is 3 nodes, the patch is 16 wide);
+  properties that hold at any size: sum of U and ||f||_P conserved;
+* Dirichlet 2048x1024 with the moving manufactured solution, FP64 and FP32,
+  displacement tracked: every node after 20 steps against a full oracle run.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Oracle, Params
+from oracle.postprocess import rel_l2
+
+from .helpers import field_errors, gpu_lattice, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def grf8192():
+    return W.grf_periodic(8192, 8192, 1.5, 0.5, cfl=0.9, ell=64.0, std=1e-3, seeds=(1, 2), steps=3)
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_periodic_8192_sampled_against_oracle_patches(lbm, grf8192, storage, tol):
+    import torch
+    wl = grf8192
+    n, k, P = 8192, 3, 16
+    lat = lbm.Lattice(n, n, wl.dx, wl.dt, wl.cK, wl.cmu, storage=storage, track_displacement=False)
+    dev = torch.device("cuda")
+    lat.init(torch.from_numpy(wl.U0).to(dev), torch.from_numpy(wl.dU0dx).to(dev), torch.from_numpy(wl.dU0dy).to(dev))
+    e0 = lat.energy()
+    s0 = None
+    out = torch.empty((10, n, n), dtype=torch.float64, device=dev)
+    lat.moments(out)
+    s0 = out[0:5].sum(dim=(1, 2)).cpu().numpy()
+    lat.step(k)
+    lat.moments(out)
+    s1 = out[0:5].sum(dim=(1, 2)).cpu().numpy()
+    e1 = lat.energy()
+    rng = np.random.default_rng(99)
+    pts = [(0, 0), (n - 1, 0), (0, n - 1), (n - 1, n - 1), (0, 4097), (n - 1, 123), (77, 0), (5000, n - 1),
+           (1, 1), (n - 2, n - 2)] + [tuple(int(v) for v in rng.integers(0, n, 2)) for _ in range(22)]
+    xs = torch.tensor([p[0] for p in pts], device=dev)
+    ys = torch.tensor([p[1] for p in pts], device=dev)
+    got = out[:, ys, xs].cpu().numpy()                 # [10, samples]
+    lat.close()
+    del out
+    ref = np.zeros_like(got)
+    for s, (x, y) in enumerate(pts):
+        ix = (np.arange(P) - P // 2 + x) % n
+        iy = (np.arange(P) - P // 2 + y) % n
+        sub = lambda a: np.ascontiguousarray(a[:, iy][:, :, ix])
+        o = Oracle(Params(P, P, wl.dx, wl.dt, wl.cK, wl.cmu, False))
+        o.init(sub(wl.U0), sub(wl.dU0dx), sub(wl.dU0dy))
+        for _ in range(k):
+            o.step(track_displacement=False)
+        U = o.moments()
+        ref[0:5, s] = U[:, P // 2, P // 2]
+    for q in range(5):
+        assert rel_l2(got[q], ref[q]) < tol, (storage, q, rel_l2(got[q], ref[q]))
+    # properties at full size: sum of U and the weighted norm are invariants (periodic, b = 0)
+    atol = 1e-12 if storage == "f64" else 1e-6
+    assert np.all(np.abs(s1 - s0) <= atol * (np.abs(s0) + np.sqrt(n * n) * 1e-3))
+    assert abs(e1 - e0) <= (1e-13 if storage == "f64" else 1e-5) * e0
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_dirichlet_2048x1024_against_full_oracle(lbm, storage, tol):
+    cK2, cmu2 = W.material.poisson_to_speeds(0.25)
+    wl = W.dirichlet_mms(2048, 1024, cK2, cmu2, cfl=0.9, steps=20, height=1.0, amp=1e-2,
+                         kx=2 * math.pi, ky=2 * math.pi)
+    _, ref = oracle_run(wl)
+    lat = gpu_lattice(lbm, wl, storage=storage)
+    lat.step(wl.steps)
+    errs = field_errors(lat.moments(), ref)
+    lat.close()
+    assert max(errs) < tol, errs
