@@ -1,0 +1,766 @@
+// Kernels of the convolutional surrogate (U-Net neural operator) and their C ABI.
+//
+// Activations are FP32, channels-last [B][H][W][C]; H and W are powers of two
+// and every convolution pads circularly (the lattices are periodic).  Weights
+// are BF16, [Cout][KS][KS][Cin], with FP32 master copies for the optimiser.
+//
+// Convolutions are implicit GEMMs on the tensor cores with mma.sync m16n8k16
+// (BF16 inputs, FP32 accumulation).  An FP32 activation a is split into
+// a_hi = bf16(a) and a_lo = bf16(a - a_hi); products use both halves, so the
+// only rounding of the forward pass is the BF16 weights themselves:
+//   forward / data gradient: W x (a_hi + a_lo)           (2 MMAs per tile)
+//   weight gradient:        dY_hi X_hi + dY_hi X_lo + dY_lo X_hi (3 MMAs)
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_nn.h"
+
+namespace {
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// ---------------------------------------------------------------------------
+// convolution forward (also the data gradient, with flipped/transposed weights)
+// ---------------------------------------------------------------------------
+struct ConvArgs {
+    const float* x1;            // first input, C1 channels
+    const float* x2;            // second input (concatenated after x1), C2 channels, or null
+    int C1, C2;
+    const __nv_bfloat16* w;     // [Cout][KS][KS][C1+C2]
+    const float* bias;          // [Cout] or null
+    float* y1;                  // output channels [0, Co1)
+    float* y2;                  // output channels [Co1, Cout), or null
+    int Co1, Cout;
+    int B, H, W;                // H, W powers of two
+    int relu;                   // apply max(0, .) to the output
+    int beta;                   // 1: add into the output instead of overwriting
+};
+
+constexpr int CBM = 128;        // pixels per CTA tile
+constexpr int CKC = 32;         // K chunk (channels of one tap)
+constexpr int CPAD = 8;
+
+template <int BN, int KS>
+__global__ void __launch_bounds__(256) conv_fwd_kernel(ConvArgs a)
+{
+    __shared__ __align__(16) __nv_bfloat16 As_hi[CBM][CKC + CPAD];
+    __shared__ __align__(16) __nv_bfloat16 As_lo[CBM][CKC + CPAD];
+    __shared__ __align__(16) __nv_bfloat16 Bs[BN][CKC + CPAD];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int wm = warp & 3;                 // 4 warps along M (32 pixels each)
+    const int wn = warp >> 2;                // 2 warps along N
+    constexpr int WN = BN / 2;               // columns per warp
+    constexpr int NT = WN / 8;               // n-tiles per warp
+    const int P = a.B * a.H * a.W;
+    const int p0 = blockIdx.x * CBM;
+    const int co0 = blockIdx.y * BN;
+    const int Cin = a.C1 + a.C2;
+    const int HW = a.H * a.W;
+    const int R = KS / 2;
+
+    float acc[2][NT][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+    // this thread stages half a row of A: pixel p0 + tid/2, channels (tid&1)*16 .. +16
+    const int ap = p0 + (tid >> 1);
+    const int ahalf = (tid & 1) * 16;
+    const bool avalid = ap < P;
+    int an = 0, ay = 0, ax = 0;
+    if (avalid) {
+        an = ap / HW;
+        ay = (ap / a.W) & (a.H - 1);
+        ax = ap & (a.W - 1);
+    }
+
+    for (int tap = 0; tap < KS * KS; ++tap) {
+        const int dy = tap / KS - R, dx = tap % KS - R;
+        const int sy = (ay + dy) & (a.H - 1), sx = (ax + dx) & (a.W - 1);
+        const long long spix = ((long long)an * a.H + sy) * a.W + sx;
+        for (int ci0 = 0; ci0 < Cin; ci0 += CKC) {
+            // --- stage A (FP32 -> bf16 hi / lo) ---
+            {
+                float v[16];
+                if (avalid) {
+                    const float* src;
+                    if (ci0 < a.C1) src = a.x1 + spix * a.C1 + ci0 + ahalf;
+                    else src = a.x2 + spix * a.C2 + (ci0 - a.C1) + ahalf;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 f = *reinterpret_cast<const float4*>(src + 4 * q);
+                        v[4 * q] = f.x;
+                        v[4 * q + 1] = f.y;
+                        v[4 * q + 2] = f.z;
+                        v[4 * q + 3] = f.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] = 0.f;
+                }
+                uint32_t hi[8], lo[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]);
+                    const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * q + 1]);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
+                    hi[q] = pack_bf16(h0, h1);
+                    lo[q] = pack_bf16(l0, l1);
+                }
+                uint4* dh = reinterpret_cast<uint4*>(&As_hi[tid >> 1][ahalf]);
+                uint4* dl = reinterpret_cast<uint4*>(&As_lo[tid >> 1][ahalf]);
+                dh[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                dh[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+                dl[0] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                dl[1] = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+            }
+            // --- stage B: BN output channels x 32 inputs of this tap (64 bytes per row) ---
+            for (int q = tid; q < BN * 4; q += 256) {
+                const int n = q >> 2, part = q & 3;
+                uint4 val = make_uint4(0, 0, 0, 0);
+                if (co0 + n < a.Cout)
+                    val = *reinterpret_cast<const uint4*>(a.w + ((long long)(co0 + n) * KS * KS + tap) * Cin + ci0 +
+                                                          part * 8);
+                *reinterpret_cast<uint4*>(&Bs[n][part * 8]) = val;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < CKC; kk += 16) {
+                uint32_t fh[2][4], fl[2][4];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int r = wm * 32 + i * 16 + g;
+                    fh[i][0] = *reinterpret_cast<const uint32_t*>(&As_hi[r][kk + 2 * t4]);
+                    fh[i][1] = *reinterpret_cast<const uint32_t*>(&As_hi[r + 8][kk + 2 * t4]);
+                    fh[i][2] = *reinterpret_cast<const uint32_t*>(&As_hi[r][kk + 8 + 2 * t4]);
+                    fh[i][3] = *reinterpret_cast<const uint32_t*>(&As_hi[r + 8][kk + 8 + 2 * t4]);
+                    fl[i][0] = *reinterpret_cast<const uint32_t*>(&As_lo[r][kk + 2 * t4]);
+                    fl[i][1] = *reinterpret_cast<const uint32_t*>(&As_lo[r + 8][kk + 2 * t4]);
+                    fl[i][2] = *reinterpret_cast<const uint32_t*>(&As_lo[r][kk + 8 + 2 * t4]);
+                    fl[i][3] = *reinterpret_cast<const uint32_t*>(&As_lo[r + 8][kk + 8 + 2 * t4]);
+                }
+#pragma unroll
+                for (int j = 0; j < NT; ++j) {
+                    const int n = wn * WN + j * 8 + g;
+                    uint32_t fb[2];
+                    fb[0] = *reinterpret_cast<const uint32_t*>(&Bs[n][kk + 2 * t4]);
+                    fb[1] = *reinterpret_cast<const uint32_t*>(&Bs[n][kk + 8 + 2 * t4]);
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        mma_bf16(acc[i][j], fh[i], fb);
+                        mma_bf16(acc[i][j], fl[i], fb);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // --- epilogue: bias, activation, store (optionally accumulate) ---
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int p = p0 + wm * 32 + i * 16 + g + 8 * h;
+            if (p >= P) continue;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const int co = co0 + wn * WN + j * 8 + 2 * t4;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int c = co + e;
+                    if (c >= a.Cout) continue;
+                    float v = acc[i][j][2 * h + e];
+                    if (a.bias) v += a.bias[c];
+                    if (a.relu) v = fmaxf(v, 0.f);
+                    float* dst = (c < a.Co1) ? a.y1 + (long long)p * a.Co1 + c
+                                             : a.y2 + (long long)p * (a.Cout - a.Co1) + (c - a.Co1);
+                    *dst = a.beta ? *dst + v : v;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// weight gradient: dW[co][tap][ci] = sum_p dY[p][co] X[p + tap][ci]
+// CTA tile 64 (co) x 64 (ci of one tap), K = pixels in chunks of 32, split over
+// pixel ranges (gridDim.z); partial[split][co][tap][ci] reduced in fixed order.
+// ---------------------------------------------------------------------------
+struct WgradArgs {
+    const float* dy;          // [P][Cout]
+    const float* x1;          // [P][C1]
+    const float* x2;          // [P][C2] or null
+    int C1, C2, Cout;
+    int B, H, W, KS;
+    int pix_per_split;
+    float* partial;           // [splits][Cout][KS*KS][Cin]
+};
+
+__global__ void __launch_bounds__(256) conv_wgrad_kernel(WgradArgs a)
+{
+    __shared__ __align__(16) __nv_bfloat16 Ah[64][32 + CPAD];
+    __shared__ __align__(16) __nv_bfloat16 Al[64][32 + CPAD];
+    __shared__ __align__(16) __nv_bfloat16 Bh[64][32 + CPAD];
+    __shared__ __align__(16) __nv_bfloat16 Bl[64][32 + CPAD];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int wm = warp & 1;                 // 2 warps along M (32 co each)
+    const int wn = warp >> 1;                // 4 warps along N (16 ci each)
+    const int Cin = a.C1 + a.C2;
+    const int co0 = blockIdx.x * 64;
+    const int ntap = a.KS * a.KS;
+    const int nci = (Cin + 63) / 64;
+    const int tap = blockIdx.y / nci;
+    const int ci0 = (blockIdx.y % nci) * 64;
+    const int R = a.KS / 2;
+    const int dy = tap / a.KS - R, dx = tap % a.KS - R;
+    const int P = a.B * a.H * a.W;
+    const int HW = a.H * a.W;
+    const int pbeg = blockIdx.z * a.pix_per_split;
+    const int pend = min(P, pbeg + a.pix_per_split);
+
+    float acc[2][2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+    // staging: thread -> (pixel k = tid / 8, 8 channels at (tid % 8) * 8)
+    const int sk = tid >> 3, sc = (tid & 7) * 8;
+    for (int pc = pbeg; pc < pend; pc += 32) {
+        const int p = pc + sk;
+        float vy[8], vx[8];
+        if (p < pend) {
+            const int n = p / HW, y = (p / a.W) & (a.H - 1), x = p & (a.W - 1);
+            const long long sp = ((long long)n * a.H + ((y + dy) & (a.H - 1))) * a.W + ((x + dx) & (a.W - 1));
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int co = co0 + sc + q;
+                vy[q] = (co < a.Cout) ? a.dy[(long long)p * a.Cout + co] : 0.f;
+                const int ci = ci0 + sc + q;
+                float xv = 0.f;
+                if (ci < a.C1) xv = a.x1[sp * a.C1 + ci];
+                else if (ci < Cin) xv = a.x2[sp * a.C2 + (ci - a.C1)];
+                vx[q] = xv;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) vy[q] = vx[q] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const __nv_bfloat16 yh = __float2bfloat16_rn(vy[q]);
+            const __nv_bfloat16 xh = __float2bfloat16_rn(vx[q]);
+            Ah[sc + q][sk] = yh;
+            Al[sc + q][sk] = __float2bfloat16_rn(vy[q] - __bfloat162float(yh));
+            Bh[sc + q][sk] = xh;
+            Bl[sc + q][sk] = __float2bfloat16_rn(vx[q] - __bfloat162float(xh));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 32; kk += 16) {
+            uint32_t fah[2][4], fal[2][4];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm * 32 + i * 16 + g;
+                fah[i][0] = *reinterpret_cast<const uint32_t*>(&Ah[r][kk + 2 * t4]);
+                fah[i][1] = *reinterpret_cast<const uint32_t*>(&Ah[r + 8][kk + 2 * t4]);
+                fah[i][2] = *reinterpret_cast<const uint32_t*>(&Ah[r][kk + 8 + 2 * t4]);
+                fah[i][3] = *reinterpret_cast<const uint32_t*>(&Ah[r + 8][kk + 8 + 2 * t4]);
+                fal[i][0] = *reinterpret_cast<const uint32_t*>(&Al[r][kk + 2 * t4]);
+                fal[i][1] = *reinterpret_cast<const uint32_t*>(&Al[r + 8][kk + 2 * t4]);
+                fal[i][2] = *reinterpret_cast<const uint32_t*>(&Al[r][kk + 8 + 2 * t4]);
+                fal[i][3] = *reinterpret_cast<const uint32_t*>(&Al[r + 8][kk + 8 + 2 * t4]);
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int n = wn * 16 + j * 8 + g;
+                uint32_t fbh[2], fbl[2];
+                fbh[0] = *reinterpret_cast<const uint32_t*>(&Bh[n][kk + 2 * t4]);
+                fbh[1] = *reinterpret_cast<const uint32_t*>(&Bh[n][kk + 8 + 2 * t4]);
+                fbl[0] = *reinterpret_cast<const uint32_t*>(&Bl[n][kk + 2 * t4]);
+                fbl[1] = *reinterpret_cast<const uint32_t*>(&Bl[n][kk + 8 + 2 * t4]);
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    mma_bf16(acc[i][j], fah[i], fbh);
+                    mma_bf16(acc[i][j], fah[i], fbl);
+                    mma_bf16(acc[i][j], fal[i], fbh);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    float* out = a.partial + (long long)blockIdx.z * a.Cout * ntap * Cin;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int co = co0 + wm * 32 + i * 16 + g + 8 * h;
+            if (co >= a.Cout) continue;
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int ci = ci0 + wn * 16 + j * 8 + 2 * t4 + e;
+                    if (ci < Cin) out[((long long)co * ntap + tap) * Cin + ci] = acc[i][j][2 * h + e];
+                }
+        }
+}
+
+// sum the split partials in order into dW (FP32)
+__global__ void sum_splits_kernel(const float* __restrict__ partial, int splits, long long n, float* __restrict__ out,
+                                  int beta)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < splits; ++k) s += partial[(long long)k * n + i];
+        out[i] = beta ? out[i] + s : s;
+    }
+}
+
+// db[co] = sum_p dY[p][co]: one block per channel group, fixed order
+__global__ void bias_grad_kernel(const float* __restrict__ dy, int P, int C, float* __restrict__ db)
+{
+    __shared__ float red[256];
+    for (int c = blockIdx.x; c < C; c += gridDim.x) {
+        float s = 0.f;
+        for (int p = threadIdx.x; p < P; p += blockDim.x) s += dy[(long long)p * C + c];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) db[c] = red[0];
+        __syncthreads();
+    }
+}
+
+// Wt[ci][tap'][co] = W[co][KS*KS-1-tap'][ci]: weights of the data-gradient convolution
+__global__ void weight_flip_kernel(const __nv_bfloat16* __restrict__ w, int Cout, int Cin, int KS,
+                                   __nv_bfloat16* __restrict__ wt)
+{
+    const int ntap = KS * KS;
+    const long long n = (long long)Cout * ntap * Cin;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)(i % Cin);
+        const int tap = (int)((i / Cin) % ntap);
+        const int co = (int)(i / ((long long)Cin * ntap));
+        wt[((long long)ci * ntap + (ntap - 1 - tap)) * Cout + co] = w[i];
+    }
+}
+
+__global__ void relu_backward_kernel(float* __restrict__ dy, const float* __restrict__ y, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (!(y[i] > 0.f)) dy[i] = 0.f;
+}
+
+// 2x2 average pooling, [B][H][W][C] -> [B][H/2][W/2][C]
+__global__ void pool_kernel(const float* __restrict__ x, int B, int H, int W, int C, float* __restrict__ y)
+{
+    const int Ho = H / 2, Wo = W / 2;
+    const long long n = (long long)B * Ho * Wo * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long pix = i / C;
+        const int xo = (int)(pix % Wo), yo = (int)((pix / Wo) % Ho), b = (int)(pix / ((long long)Wo * Ho));
+        const long long base = (((long long)b * H + 2 * yo) * W + 2 * xo) * C + c;
+        y[i] = 0.25f * (x[base] + x[base + C] + x[base + (long long)W * C] + x[base + (long long)W * C + C]);
+    }
+}
+
+__global__ void pool_backward_kernel(const float* __restrict__ dy, int B, int H, int W, int C, float* __restrict__ dx,
+                                     int beta)
+{
+    const long long n = (long long)B * H * W * C;
+    const int Ho = H / 2, Wo = W / 2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long pix = i / C;
+        const int x = (int)(pix % W), y = (int)((pix / W) % H), b = (int)(pix / ((long long)W * H));
+        const float v = 0.25f * dy[(((long long)b * Ho + y / 2) * Wo + x / 2) * C + c];
+        dx[i] = beta ? dx[i] + v : v;
+    }
+}
+
+// nearest 2x upsampling, [B][H][W][C] -> [B][2H][2W][C]
+__global__ void upsample_kernel(const float* __restrict__ x, int B, int H, int W, int C, float* __restrict__ y)
+{
+    const int Ho = 2 * H, Wo = 2 * W;
+    const long long n = (long long)B * Ho * Wo * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long pix = i / C;
+        const int xo = (int)(pix % Wo), yo = (int)((pix / Wo) % Ho), b = (int)(pix / ((long long)Wo * Ho));
+        y[i] = x[(((long long)b * H + yo / 2) * W + xo / 2) * C + c];
+    }
+}
+
+__global__ void upsample_backward_kernel(const float* __restrict__ dy, int B, int H, int W, int C,
+                                         float* __restrict__ dx, int beta)
+{
+    const long long n = (long long)B * H * W * C;
+    const int Wo = 2 * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long pix = i / C;
+        const int x = (int)(pix % W), y = (int)((pix / W) % H), b = (int)(pix / ((long long)W * H));
+        const long long base = (((long long)b * 2 * H + 2 * y) * Wo + 2 * x) * C + c;
+        const float v = dy[base] + dy[base + C] + dy[base + (long long)Wo * C] + dy[base + (long long)Wo * C + C];
+        dx[i] = beta ? dx[i] + v : v;
+    }
+}
+
+// loss = sum over pixels and the first `cvalid` channels of (out - tgt)^2; d = 2 (out - tgt) * scale
+__global__ void mse_kernel(const float* __restrict__ out, const float* __restrict__ tgt, long long P, int C, int cvalid,
+                           float scale, float* __restrict__ dout, double* __restrict__ partial)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    const long long n = P * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        float d = 0.f;
+        if (c < cvalid) {
+            d = out[i] - tgt[i];
+            s += (double)d * d;
+        }
+        if (dout) dout[i] = 2.f * d * scale;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void sum_double_kernel(const double* __restrict__ partial, int n, double* __restrict__ out)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// Adam on FP32 master weights, then the BF16 working copy
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ gw, float* __restrict__ m,
+                            float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                            float c2, __nv_bfloat16* __restrict__ wb)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float g = gw[i];
+        const float mi = b1 * m[i] + (1.f - b1) * g;
+        const float vi = b2 * v[i] + (1.f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+        w[i] = wi;
+        if (wb) wb[i] = __float2bfloat16_rn(wi);
+    }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ x, long long n, __nv_bfloat16* __restrict__ y)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// network input: U fields [B][nf][H][W] (FP64, field-major per sample) scaled by 1/scale[c], plus a
+// constant channel per sample, into [B][H][W][C] FP32 with zero padding channels
+__global__ void pack_input_kernel(const double* __restrict__ U, long long sample_stride, int nf, const double* __restrict__ scale,
+                                  const float* __restrict__ extra, int B, int H, int W, int C, float* __restrict__ x)
+{
+    const long long n = (long long)B * H * W * C;
+    const long long HW = (long long)H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long pix = i / C;
+        const int b = (int)(pix / HW);
+        const long long q = pix % HW;
+        float v = 0.f;
+        if (c < nf) v = (float)(U[(long long)b * sample_stride + c * HW + q] / scale[c]);
+        else if (c == nf && extra) v = extra[b];
+        x[i] = v;
+    }
+}
+
+// prediction: U_out[b][c] = U_in[b][c] + scale[c] * net[b][.][.][c] for c < nf (FP64, field-major)
+__global__ void residual_output_kernel(const double* __restrict__ Uin, long long in_stride, const float* __restrict__ net,
+                                       int C, const double* __restrict__ scale, int nf, int B, int H, int W,
+                                       double* __restrict__ Uout, long long out_stride)
+{
+    const long long HW = (long long)H * W;
+    const long long n = (long long)B * nf * HW;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long q = i % HW;
+        const int c = (int)((i / HW) % nf);
+        const int b = (int)(i / (HW * nf));
+        Uout[(long long)b * out_stride + c * HW + q] =
+            Uin[(long long)b * in_stride + c * HW + q] + scale[c] * (double)net[((long long)b * HW + q) * C + c];
+    }
+}
+
+// training target in network units: (U_next - U_now) / scale, [B][H][W][C] (channels >= nf zero)
+__global__ void pack_target_kernel(const double* __restrict__ Unow, const double* __restrict__ Unext, long long stride,
+                                   int nf, const double* __restrict__ scale, int B, int H, int W, int C,
+                                   float* __restrict__ t)
+{
+    const long long HW = (long long)H * W;
+    const long long n = (long long)B * HW * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long pix = i / C;
+        const int b = (int)(pix / HW);
+        const long long q = pix % HW;
+        float v = 0.f;
+        if (c < nf) {
+            const long long o = (long long)b * stride + c * HW + q;
+            v = (float)((Unext[o] - Unow[o]) / scale[c]);
+        }
+        t[i] = v;
+    }
+}
+
+// second-order periodic central differences of [B][nf][H][W] FP64 fields (spacing dx)
+__global__ void gradient_kernel(const double* __restrict__ U, long long stride, int nf, int B, int H, int W, double dx,
+                                double* __restrict__ dUx, double* __restrict__ dUy)
+{
+    const long long HW = (long long)H * W;
+    const long long n = (long long)B * nf * HW;
+    const double s = 0.5 / dx;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % W);
+        const int y = (int)((i / W) % H);
+        const long long fld = i / HW;
+        const int c = (int)(fld % nf), b = (int)(fld / nf);
+        const double* u = U + (long long)b * stride + c * HW;
+        const long long o = (long long)b * stride + c * HW + (long long)y * W + x;
+        dUx[o] = s * (u[(long long)y * W + ((x + 1) % W)] - u[(long long)y * W + ((x + W - 1) % W)]);
+        dUy[o] = s * (u[(long long)((y + 1) % H) * W + x] - u[(long long)((y + H - 1) % H) * W + x]);
+    }
+}
+
+int grid_for(long long n)
+{
+    long long b = (n + 255) / 256;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)(b < 1 ? 1 : b);
+}
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+lbm_status launch_status()
+{
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int32_t C2, const void* w_bf16,
+                               const float* bias, float* y1, int32_t Co1, float* y2, int32_t Cout, int32_t B,
+                               int32_t H, int32_t W, int32_t KS, int32_t relu, int32_t beta, void* stream)
+{
+    if (!x1 || !w_bf16 || !y1 || C1 <= 0 || C1 % 32 || C2 < 0 || C2 % 32 || (C2 > 0 && !x2) || Cout <= 0 ||
+        Cout % 8 || Co1 <= 0 || Co1 > Cout || (Co1 < Cout && !y2) || B <= 0 || !pow2(H) || !pow2(W) ||
+        (KS != 1 && KS != 3))
+        return LBM_ERR_ARG;
+    ConvArgs a{x1, x2, C1, C2, static_cast<const __nv_bfloat16*>(w_bf16), bias, y1, y2, Co1, Cout, B, H, W, relu, beta};
+    const long long P = (long long)B * H * W;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int BN = Cout >= 64 ? 64 : (Cout >= 32 ? 32 : 16);
+    dim3 grid((unsigned)((P + CBM - 1) / CBM), (unsigned)((Cout + BN - 1) / BN));
+    if (KS == 3) {
+        if (BN == 64) conv_fwd_kernel<64, 3><<<grid, 256, 0, s>>>(a);
+        else if (BN == 32) conv_fwd_kernel<32, 3><<<grid, 256, 0, s>>>(a);
+        else conv_fwd_kernel<16, 3><<<grid, 256, 0, s>>>(a);
+    } else {
+        if (BN == 64) conv_fwd_kernel<64, 1><<<grid, 256, 0, s>>>(a);
+        else if (BN == 32) conv_fwd_kernel<32, 1><<<grid, 256, 0, s>>>(a);
+        else conv_fwd_kernel<16, 1><<<grid, 256, 0, s>>>(a);
+    }
+    return launch_status();
+}
+
+int64_t lbm_nn_wgrad_workspace_bytes(int32_t Cin, int32_t Cout, int32_t B, int32_t H, int32_t W, int32_t KS)
+{
+    const long long P = (long long)B * H * W;
+    long long pps = 8192;
+    long long splits = (P + pps - 1) / pps;
+    return splits * (long long)Cout * KS * KS * Cin * (long long)sizeof(float);
+}
+
+lbm_status lbm_nn_conv_backward_weight(const float* dy, int32_t Cout, const float* x1, int32_t C1, const float* x2,
+                                       int32_t C2, int32_t B, int32_t H, int32_t W, int32_t KS, float* dw,
+                                       int32_t beta, void* workspace, int64_t workspace_bytes, void* stream)
+{
+    if (!dy || !x1 || !dw || !workspace || C1 <= 0 || C1 % 32 || C2 < 0 || C2 % 32 || (C2 > 0 && !x2) ||
+        Cout <= 0 || Cout % 8 || B <= 0 || !pow2(H) || !pow2(W) || (KS != 1 && KS != 3))
+        return LBM_ERR_ARG;
+    const int Cin = C1 + C2;
+    if (workspace_bytes < lbm_nn_wgrad_workspace_bytes(Cin, Cout, B, H, W, KS)) return LBM_ERR_ARG;
+    const long long P = (long long)B * H * W;
+    const int pps = 8192;
+    const int splits = (int)((P + pps - 1) / pps);
+    WgradArgs a{dy, x1, x2, C1, C2, Cout, B, H, W, KS, pps, static_cast<float*>(workspace)};
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    dim3 grid((unsigned)((Cout + 63) / 64), (unsigned)(KS * KS * ((Cin + 63) / 64)), (unsigned)splits);
+    conv_wgrad_kernel<<<grid, 256, 0, s>>>(a);
+    const long long n = (long long)Cout * KS * KS * Cin;
+    sum_splits_kernel<<<grid_for(n), 256, 0, s>>>(static_cast<const float*>(workspace), splits, n, dw, beta);
+    return launch_status();
+}
+
+lbm_status lbm_nn_bias_grad(const float* dy, int64_t P, int32_t C, float* db, void* stream)
+{
+    if (!dy || !db || P <= 0 || C <= 0) return LBM_ERR_ARG;
+    bias_grad_kernel<<<C < 1024 ? C : 1024, 256, 0, static_cast<cudaStream_t>(stream)>>>(dy, (int)P, C, db);
+    return launch_status();
+}
+
+lbm_status lbm_nn_weight_flip(const void* w_bf16, int32_t Cout, int32_t Cin, int32_t KS, void* wt_bf16, void* stream)
+{
+    if (!w_bf16 || !wt_bf16 || Cout <= 0 || Cin <= 0 || (KS != 1 && KS != 3)) return LBM_ERR_ARG;
+    const long long n = (long long)Cout * KS * KS * Cin;
+    weight_flip_kernel<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const __nv_bfloat16*>(w_bf16), Cout, Cin, KS, static_cast<__nv_bfloat16*>(wt_bf16));
+    return launch_status();
+}
+
+lbm_status lbm_nn_relu_backward(float* dy, const float* y, int64_t n, void* stream)
+{
+    if (!dy || !y || n < 0) return LBM_ERR_ARG;
+    relu_backward_kernel<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(dy, y, n);
+    return launch_status();
+}
+
+lbm_status lbm_nn_pool(const float* x, int32_t B, int32_t H, int32_t W, int32_t C, float* y, void* stream)
+{
+    if (!x || !y || B <= 0 || H < 2 || W < 2 || (H & 1) || (W & 1) || C <= 0) return LBM_ERR_ARG;
+    pool_kernel<<<grid_for((long long)B * H * W * C / 4), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, B, H, W, C, y);
+    return launch_status();
+}
+
+lbm_status lbm_nn_pool_backward(const float* dy, int32_t B, int32_t H, int32_t W, int32_t C, float* dx, int32_t beta,
+                                void* stream)
+{
+    if (!dy || !dx || B <= 0 || H < 2 || W < 2 || (H & 1) || (W & 1) || C <= 0) return LBM_ERR_ARG;
+    pool_backward_kernel<<<grid_for((long long)B * H * W * C), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        dy, B, H, W, C, dx, beta);
+    return launch_status();
+}
+
+lbm_status lbm_nn_upsample(const float* x, int32_t B, int32_t H, int32_t W, int32_t C, float* y, void* stream)
+{
+    if (!x || !y || B <= 0 || H <= 0 || W <= 0 || C <= 0) return LBM_ERR_ARG;
+    upsample_kernel<<<grid_for((long long)B * H * W * C * 4), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, B, H, W,
+                                                                                                           C, y);
+    return launch_status();
+}
+
+lbm_status lbm_nn_upsample_backward(const float* dy, int32_t B, int32_t H, int32_t W, int32_t C, float* dx,
+                                    int32_t beta, void* stream)
+{
+    if (!dy || !dx || B <= 0 || H <= 0 || W <= 0 || C <= 0) return LBM_ERR_ARG;
+    upsample_backward_kernel<<<grid_for((long long)B * H * W * C), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        dy, B, H, W, C, dx, beta);
+    return launch_status();
+}
+
+lbm_status lbm_nn_mse(const float* out, const float* tgt, int64_t P, int32_t C, int32_t cvalid, float grad_scale,
+                      float* dout, double* workspace, double* loss_out, void* stream)
+{
+    if (!out || !tgt || !workspace || !loss_out || P <= 0 || C <= 0 || cvalid < 0 || cvalid > C) return LBM_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    mse_kernel<<<512, 256, 0, s>>>(out, tgt, P, C, cvalid, grad_scale, dout, workspace);
+    sum_double_kernel<<<1, 256, 0, s>>>(workspace, 512, loss_out);
+    return launch_status();
+}
+
+lbm_status lbm_nn_adam(float* w, const float* g, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
+                       float eps, int64_t step, void* w_bf16, void* stream)
+{
+    if (!w || !g || !m || !v || n <= 0 || step < 1) return LBM_ERR_ARG;
+    const float c1 = 1.f / (1.f - powf(beta1, (float)step));
+    const float c2 = 1.f / (1.f - powf(beta2, (float)step));
+    adam_kernel<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        w, g, m, v, n, lr, beta1, beta2, eps, c1, c2, static_cast<__nv_bfloat16*>(w_bf16));
+    return launch_status();
+}
+
+lbm_status lbm_nn_to_bf16(const float* x, int64_t n, void* y_bf16, void* stream)
+{
+    if (!x || !y_bf16 || n <= 0) return LBM_ERR_ARG;
+    to_bf16_kernel<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, n,
+                                                                               static_cast<__nv_bfloat16*>(y_bf16));
+    return launch_status();
+}
+
+lbm_status lbm_nn_pack_input(const double* U, int64_t sample_stride, int32_t nf, const double* scale,
+                             const float* extra, int32_t B, int32_t H, int32_t W, int32_t C, float* x, void* stream)
+{
+    if (!U || !scale || !x || nf <= 0 || C < nf + (extra ? 1 : 0) || B <= 0 || H <= 0 || W <= 0) return LBM_ERR_ARG;
+    pack_input_kernel<<<grid_for((long long)B * H * W * C), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        U, sample_stride, nf, scale, extra, B, H, W, C, x);
+    return launch_status();
+}
+
+lbm_status lbm_nn_pack_target(const double* Unow, const double* Unext, int64_t sample_stride, int32_t nf,
+                              const double* scale, int32_t B, int32_t H, int32_t W, int32_t C, float* t, void* stream)
+{
+    if (!Unow || !Unext || !scale || !t || nf <= 0 || C < nf || B <= 0 || H <= 0 || W <= 0) return LBM_ERR_ARG;
+    pack_target_kernel<<<grid_for((long long)B * H * W * C), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        Unow, Unext, sample_stride, nf, scale, B, H, W, C, t);
+    return launch_status();
+}
+
+lbm_status lbm_nn_residual_output(const double* Uin, int64_t in_stride, const float* net, int32_t C,
+                                  const double* scale, int32_t nf, int32_t B, int32_t H, int32_t W, double* Uout,
+                                  int64_t out_stride, void* stream)
+{
+    if (!Uin || !net || !scale || !Uout || nf <= 0 || C < nf || B <= 0 || H <= 0 || W <= 0) return LBM_ERR_ARG;
+    residual_output_kernel<<<grid_for((long long)B * nf * H * W), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        Uin, in_stride, net, C, scale, nf, B, H, W, Uout, out_stride);
+    return launch_status();
+}
+
+lbm_status lbm_nn_gradient(const double* U, int64_t sample_stride, int32_t nf, int32_t B, int32_t H, int32_t W,
+                           double dx, double* dUx, double* dUy, void* stream)
+{
+    if (!U || !dUx || !dUy || nf <= 0 || B <= 0 || H < 3 || W < 3 || !(dx > 0)) return LBM_ERR_ARG;
+    gradient_kernel<<<grid_for((long long)B * nf * H * W), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        U, sample_stride, nf, B, H, W, dx, dUx, dUy);
+    return launch_status();
+}
+
+}  // extern "C"

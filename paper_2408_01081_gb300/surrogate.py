@@ -1,0 +1,355 @@
+"""Learned surrogate: a convolutional U-Net neural operator that jumps k steps
+of the lattice Boltzmann solver on periodic lattices, trained on trajectories
+the solver itself generates, with the solver as fallback and as judge.
+
+Model (channels-last, circular padding, ReLU):
+    input  x0 = [U(t) / scale (5 fields), (nu - 0.245) / 0.1415, zero padding] -> 32 channels
+    encoder level l = 0..3: two 3x3 convolutions to c_l channels, 2x2 average pooling between levels
+    decoder level l = 2..0: nearest 2x upsampling, 3x3 convolution of [up | skip_l] to c_l, 3x3 c_l -> c_l
+    output 1x1 convolution c_0 -> 32 (5 used): U(t + k dt) = U(t) + scale * out
+With c = (32, 64, 128, 256) the network has 1.95 M parameters.
+
+Every layer runs in the library's kernels (include/lbm_nn.h): tensor-core
+implicit-GEMM convolutions with BF16 weights and FP32 accumulation, their
+weight and data gradients, pooling, upsampling, the loss and Adam.  This module
+only allocates buffers (torch tensors) and calls them in order.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import lbm as L
+from . import nn as K
+
+NU_MEAN, NU_STD = 0.245, 0.1415
+CIN_PAD = 32          # input channels after padding
+COUT_PAD = 32         # output channels (5 used)
+NF = 5                # predicted fields: v_x, v_y, j_s, j_d, j_xy
+
+
+class Conv:
+    """One convolution: FP32 master weights, BF16 working and flipped copies, Adam state."""
+
+    def __init__(self, cin1, cin2, cout, ks, relu, rng, device, zero=False):
+        import torch
+        self.cin1, self.cin2, self.cout, self.ks, self.relu = cin1, cin2, cout, ks, relu
+        cin = cin1 + cin2
+        std = math.sqrt(2.0 / (cin * ks * ks)) if relu else math.sqrt(1.0 / (cin * ks * ks))
+        w = np.zeros((cout, ks, ks, cin), np.float32) if zero else rng.normal(0.0, std, (cout, ks, ks, cin))
+        self.w = torch.tensor(w, dtype=torch.float32, device=device)
+        self.b = torch.zeros(cout, dtype=torch.float32, device=device)
+        self.wb = torch.empty((cout, ks, ks, cin), dtype=torch.bfloat16, device=device)
+        self.wt = torch.empty((cin, ks, ks, cout), dtype=torch.bfloat16, device=device)
+        self.gw = torch.zeros_like(self.w)
+        self.gb = torch.zeros_like(self.b)
+        self.mw, self.vw = torch.zeros_like(self.w), torch.zeros_like(self.w)
+        self.mb, self.vb = torch.zeros_like(self.b), torch.zeros_like(self.b)
+        K.to_bf16(self.w, self.wb)
+
+    @property
+    def nparams(self):
+        return self.w.numel() + self.b.numel()
+
+    def forward(self, x1, x2, y, B, H, W):
+        K.conv_forward(x1, self.cin1, x2, self.cin2, self.wb, self.b, y, self.cout, None, self.cout, B, H, W,
+                       self.ks, relu=self.relu)
+
+    def backward(self, dy, y, x1, x2, B, H, W, dx1, dx2, workspace, need_dx=True):
+        """dy: gradient w.r.t. this layer's output (overwritten by the ReLU mask)."""
+        if self.relu:
+            K.relu_backward(dy, y)
+        K.conv_backward_weight(dy, self.cout, x1, self.cin1, x2, self.cin2, B, H, W, self.ks, self.gw, workspace)
+        K.bias_grad(dy, B * H * W, self.cout, self.gb)
+        if need_dx:
+            K.weight_flip(self.wb, self.cout, self.cin1 + self.cin2, self.ks, self.wt)
+            K.conv_forward(dy, self.cout, None, 0, self.wt, None, dx1, self.cin1, dx2, self.cin1 + self.cin2,
+                           B, H, W, self.ks, relu=False)
+
+    def adam(self, lr, step, b1=0.9, b2=0.999, eps=1e-8):
+        K.adam(self.w, self.gw, self.mw, self.vw, lr, b1, b2, eps, step, self.wb)
+        K.adam(self.b, self.gb, self.mb, self.vb, lr, b1, b2, eps, step, None)
+
+
+class UNet:
+    def __init__(self, chans: Sequence[int] = (32, 64, 128, 256), seed: int = 0, device="cuda"):
+        import torch
+        self.torch = torch
+        self.dev = torch.device(device)
+        self.c = list(chans)
+        assert len(self.c) == 4
+        rng = np.random.default_rng(seed)
+        c0, c1, c2, c3 = self.c
+        d = self.dev
+        self.enc = [
+            (Conv(CIN_PAD, 0, c0, 3, True, rng, d), Conv(c0, 0, c0, 3, True, rng, d)),
+            (Conv(c0, 0, c1, 3, True, rng, d), Conv(c1, 0, c1, 3, True, rng, d)),
+            (Conv(c1, 0, c2, 3, True, rng, d), Conv(c2, 0, c2, 3, True, rng, d)),
+            (Conv(c2, 0, c3, 3, True, rng, d), Conv(c3, 0, c3, 3, True, rng, d)),
+        ]
+        self.dec = {
+            2: (Conv(c3, c2, c2, 3, True, rng, d), Conv(c2, 0, c2, 3, True, rng, d)),
+            1: (Conv(c2, c1, c1, 3, True, rng, d), Conv(c1, 0, c1, 3, True, rng, d)),
+            0: (Conv(c1, c0, c0, 3, True, rng, d), Conv(c0, 0, c0, 3, True, rng, d)),
+        }
+        # zero-initialised output: the untrained model predicts persistence U(t + k dt) = U(t)
+        self.out = Conv(c0, 0, COUT_PAD, 1, False, rng, d, zero=True)
+        self.layers: List[Conv] = [c for pair in self.enc for c in pair] + \
+            [c for l in (2, 1, 0) for c in self.dec[l]] + [self.out]
+        self.shape = None
+        self.step_count = 0
+
+    @property
+    def nparams(self) -> int:
+        return sum(l.nparams for l in self.layers)
+
+    # -- buffers ---------------------------------------------------------
+    def _alloc(self, B, H, W):
+        if self.shape == (B, H, W):
+            return
+        t = self.torch
+        f32 = dict(dtype=t.float32, device=self.dev)
+        c0, c1, c2, c3 = self.c
+        hw = [(H >> l, W >> l) for l in range(4)]
+        A = {}
+        for l, ch in enumerate(self.c):
+            h, w = hw[l]
+            A[f"ea{l}"] = t.empty((B, h, w, ch), **f32)
+            A[f"e{l}"] = t.empty((B, h, w, ch), **f32)
+            if l > 0:
+                A[f"p{l}"] = t.empty((B, h, w, self.c[l - 1]), **f32)
+        for l in (2, 1, 0):
+            h, w = hw[l]
+            A[f"u{l}"] = t.empty((B, h, w, self.c[l + 1]), **f32)
+            A[f"da{l}"] = t.empty((B, h, w, self.c[l]), **f32)
+            A[f"d{l}"] = t.empty((B, h, w, self.c[l]), **f32)
+        A["x0"] = t.empty((B, H, W, CIN_PAD), **f32)
+        A["out"] = t.empty((B, H, W, COUT_PAD), **f32)
+        A["tgt"] = t.empty((B, H, W, COUT_PAD), **f32)
+        # gradient buffers (same shapes), reused
+        G = {k: t.empty_like(v) for k, v in A.items() if k not in ("x0", "tgt")}
+        ws = max(K.wgrad_workspace_bytes(l.cin1 + l.cin2, l.cout, B, H, W, l.ks) for l in self.layers)
+        self.ws = t.empty(ws // 4 + 1, **f32)
+        self.mse_ws = t.empty(512, dtype=t.float64, device=self.dev)
+        self.loss = t.zeros(1, dtype=t.float64, device=self.dev)
+        self.A, self.G = A, G
+        self.shape = (B, H, W)
+
+    # -- forward / backward ---------------------------------------------
+    def forward(self, B, H, W):
+        """x0 must already hold the packed input; result in self.A['out']."""
+        A = self.A
+        x = A["x0"]
+        for l in range(4):
+            h, w = H >> l, W >> l
+            if l > 0:
+                K.pool(A[f"e{l - 1}"], B, 2 * h, 2 * w, self.c[l - 1], A[f"p{l}"])
+                x = A[f"p{l}"]
+            ca, cb = self.enc[l]
+            ca.forward(x, None, A[f"ea{l}"], B, h, w)
+            cb.forward(A[f"ea{l}"], None, A[f"e{l}"], B, h, w)
+        prev = A["e3"]
+        for l in (2, 1, 0):
+            h, w = H >> l, W >> l
+            K.upsample(prev, B, h // 2, w // 2, self.c[l + 1], A[f"u{l}"])
+            ca, cb = self.dec[l]
+            ca.forward(A[f"u{l}"], A[f"e{l}"], A[f"da{l}"], B, h, w)
+            cb.forward(A[f"da{l}"], None, A[f"d{l}"], B, h, w)
+            prev = A[f"d{l}"]
+        self.out.forward(A["d0"], None, A["out"], B, H, W)
+
+    def backward(self, B, H, W):
+        """G['out'] must hold dLoss/dout; fills every layer's gw, gb."""
+        A, G, ws = self.A, self.G, self.ws
+        self.out.backward(G["out"], A["out"], A["d0"], None, B, H, W, G["d0"], None, ws)
+        for l in (0, 1, 2):
+            h, w = H >> l, W >> l
+            ca, cb = self.dec[l]
+            cb.backward(G[f"d{l}"], A[f"d{l}"], A[f"da{l}"], None, B, h, w, G[f"da{l}"], None, ws)
+            # data gradient of [up | skip]: up part -> G[u], skip part -> G[e] (initialised here)
+            ca.backward(G[f"da{l}"], A[f"da{l}"], A[f"u{l}"], A[f"e{l}"], B, h, w, G[f"u{l}"], G[f"e{l}"], ws)
+            src = G["e3"] if l == 2 else G[f"d{l + 1}"]
+            K.upsample_backward(G[f"u{l}"], B, h // 2, w // 2, self.c[l + 1], src)
+        for l in (3, 2, 1, 0):
+            h, w = H >> l, W >> l
+            ca, cb = self.enc[l]
+            cb.backward(G[f"e{l}"], A[f"e{l}"], A[f"ea{l}"], None, B, h, w, G[f"ea{l}"], None, ws)
+            x = A["x0"] if l == 0 else A[f"p{l}"]
+            ca.backward(G[f"ea{l}"], A[f"ea{l}"], x, None, B, h, w, G[f"p{l}"] if l > 0 else None, None, ws,
+                        need_dx=l > 0)
+            if l > 0:
+                # skip gradient of level l-1 already holds the decoder part; add the pooling path
+                K.pool_backward(G[f"p{l}"], B, 2 * h, 2 * w, self.c[l - 1], G[f"e{l - 1}"], beta=True)
+
+    def adam_step(self, lr):
+        self.step_count += 1
+        for layer in self.layers:
+            layer.adam(lr, self.step_count)
+
+    def train_step(self, B, H, W, lr) -> float:
+        """x0 and tgt packed; one forward, MSE over the 5 used channels, backward, Adam."""
+        A = self.A
+        self.forward(B, H, W)
+        P = B * H * W
+        K.mse(A["out"], A["tgt"], P, COUT_PAD, NF, 1.0 / (P * NF), self.G["out"], self.mse_ws, self.loss)
+        self.backward(B, H, W)
+        self.adam_step(lr)
+        return self.loss  # device scalar (sum of squares), read lazily
+
+    # -- state -------------------------------------------------------------
+    def state_dict(self):
+        return {f"w{i}": l.w.cpu().numpy() for i, l in enumerate(self.layers)} | \
+               {f"b{i}": l.b.cpu().numpy() for i, l in enumerate(self.layers)}
+
+    def load_state_dict(self, sd):
+        t = self.torch
+        for i, l in enumerate(self.layers):
+            l.w.copy_(t.from_numpy(sd[f"w{i}"]))
+            l.b.copy_(t.from_numpy(sd[f"b{i}"]))
+            K.to_bf16(l.w, l.wb)
+
+
+# ---------------------------------------------------------------------------
+# data: trajectories of the batched solver
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Chunk:
+    U: "object"          # [J+1, n, 10, H, W] FP64 snapshots every k steps (moment-field layout)
+    nu: np.ndarray       # [n]
+    nu_norm: "object"    # [n] float32 tensor, (nu - NU_MEAN) / NU_STD
+    n: int
+    J: int
+
+
+def generate_chunk(n, seed, H=256, W=256, k=32, J=4, storage="f64", device="cuda", cfl=0.9,
+                   ell_range=(16.0, 64.0), numax=0.49, std=1e-3):
+    """n periodic H x W lattices, random Poisson ratio and GRF initial velocity, J+1 snapshots
+    of the moment fields every k steps, from the batched lattice Boltzmann solver."""
+    import torch
+    import workloads as Wk
+    from workloads.grf import batch_lattice_inputs_torch
+    rng = np.random.default_rng(seed)
+    nu = rng.uniform(0.0, numax, n)
+    ells = rng.uniform(*ell_range, n)
+    descs, specs = [], []
+    for i in range(n):
+        cK2, cmu2 = Wk.material.poisson_to_speeds(float(nu[i]))
+        c = Wk.material.lattice_speed(cK2, cmu2, cfl)
+        dx = 1.0 / max(H, W)
+        descs.append((W, H, 0, dx, dx / c, math.sqrt(cK2), math.sqrt(cmu2)))
+        specs.append(Wk.LatticeSpec(W, H, cK2, cmu2, float(nu[i]), False, float(ells[i]), int(seed * 100003 + 2 * i)))
+    dev = torch.device(device)
+    stream = torch.cuda.current_stream().cuda_stream
+    b = L.lbm_batch_create(descs, storage=L.STORAGE[storage], stream=stream)
+    try:
+        for i, sp in enumerate(specs):
+            U0, Ux, Uy = batch_lattice_inputs_torch(sp, descs[i][3], std=std, device=dev)
+            L.lbm_batch_init(b, i, U0, Ux, Uy)
+        U = torch.empty((J + 1, n, 10, H, W), dtype=torch.float64, device=dev)
+        for j in range(J + 1):
+            if j:
+                L.lbm_batch_step(b, k)
+            for i in range(n):
+                L.lbm_batch_moments(b, i, U[j, i])
+        L.lbm_batch_synchronize(b)
+    finally:
+        L.lbm_batch_destroy(b)
+    nu_norm = torch.tensor((nu - NU_MEAN) / NU_STD, dtype=torch.float32, device=dev)
+    return Chunk(U, nu, nu_norm, n, J)
+
+
+def field_scales(chunk) -> np.ndarray:
+    """Per-field RMS of the moment fields over a chunk (network units)."""
+    U = chunk.U[1:, :, :NF]
+    return np.sqrt((U * U).mean(dim=(0, 1, 3, 4)).cpu().numpy())
+
+
+class Surrogate:
+    """The trained operator plus the normalisation it was trained with."""
+
+    def __init__(self, net: UNet, scale: np.ndarray, k: int):
+        import torch
+        self.net = net
+        self.k = k
+        self.scale_np = np.asarray(scale, dtype=np.float64)
+        self.scale = torch.tensor(self.scale_np, dtype=torch.float64, device=net.dev)
+
+    def pack(self, U, stride, nu_norm, B, H, W):
+        K.pack_input(U, stride, NF, self.scale, nu_norm, B, H, W, CIN_PAD, self.net.A["x0"])
+
+    def predict(self, U, stride, nu_norm, B, H, W, Uout, out_stride):
+        """Uout = U + scale * net(U): the moment fields k steps later (FP64)."""
+        self.net._alloc(B, H, W)
+        self.pack(U, stride, nu_norm, B, H, W)
+        self.net.forward(B, H, W)
+        K.residual_output(U, stride, self.net.A["out"], COUT_PAD, self.scale, NF, B, H, W, Uout, out_stride)
+
+
+def train(chunks_fn, n_chunks, batch=8, H=256, W=256, lr=1e-3, lr_min=1e-5, epochs_per_chunk=1, seed=0,
+          chans=(32, 64, 128, 256), k=32, log=None, scale=None, time_budget_s=None):
+    """Train on chunks produced by chunks_fn(i) (fresh trajectories per chunk).
+    Cosine learning-rate decay over all iterations.  Returns (Surrogate, history)."""
+    import torch
+    net = UNet(chans, seed=seed)
+    first = chunks_fn(0)
+    scale = field_scales(first) if scale is None else np.asarray(scale)
+    sur = Surrogate(net, scale, k)
+    iters_per_chunk = epochs_per_chunk * (first.n // batch) * first.J
+    total = max(1, n_chunks * iters_per_chunk)
+    net._alloc(batch, H, W)
+    hist = []
+    it = 0
+    t0 = time.time()
+    rng = np.random.default_rng(seed + 1)
+    chunk = first
+    for ci in range(n_chunks):
+        if ci:
+            chunk = chunks_fn(ci)
+        stride = 10 * H * W
+        for _ in range(epochs_per_chunk):
+            blocks = [(j, i0) for j in range(chunk.J) for i0 in range(0, chunk.n - batch + 1, batch)]
+            rng.shuffle(blocks)
+            for j, i0 in blocks:
+                lr_t = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * it / total))
+                Unow = chunk.U[j, i0]
+                Unext = chunk.U[j + 1, i0]
+                sur.pack(Unow, stride, chunk.nu_norm[i0:], batch, H, W)
+                K.pack_target(Unow, Unext, stride, NF, sur.scale, batch, H, W, COUT_PAD, net.A["tgt"])
+                loss = net.train_step(batch, H, W, lr_t)
+                it += 1
+                if it % 20 == 0 or it == total:
+                    lv = float(loss.item()) / (batch * H * W * NF)
+                    hist.append((it, lv, time.time() - t0))
+                    if log:
+                        log(f"iter {it}/{total} loss {lv:.3e} lr {lr_t:.2e} {time.time() - t0:.1f}s")
+                if time_budget_s and time.time() - t0 > time_budget_s:
+                    return sur, hist
+        del chunk
+        torch.cuda.empty_cache()
+    return sur, hist
+
+
+def relative_error(sur, Upred, Uref, stride, B, H, W):
+    """Relative L2 error over the 5 fields in network units (each field divided by its scale),
+    reduced on the GPU; returns one value per sample."""
+    import torch
+    net = sur.net
+    out = torch.empty((1, H, W, COUT_PAD), dtype=torch.float32, device=net.dev)
+    ref = torch.empty_like(out)
+    zero = torch.zeros_like(out)
+    ws = torch.empty(512, dtype=torch.float64, device=net.dev)
+    num = torch.empty(1, dtype=torch.float64, device=net.dev)
+    den = torch.empty(1, dtype=torch.float64, device=net.dev)
+    errs = []
+    for b in range(B):
+        K.pack_input(Upred[b], stride, NF, sur.scale, None, 1, H, W, COUT_PAD, out)
+        K.pack_input(Uref[b], stride, NF, sur.scale, None, 1, H, W, COUT_PAD, ref)
+        K.mse(out, ref, H * W, COUT_PAD, NF, 1.0, None, ws, num)
+        K.mse(ref, zero, H * W, COUT_PAD, NF, 1.0, None, ws, den)
+        errs.append(math.sqrt(float(num.item()) / float(den.item())))
+    return np.array(errs)
