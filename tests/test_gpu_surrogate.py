@@ -1,0 +1,38 @@
+"""The learned surrogate end to end on a small configuration (32x32 lattices,
+jumps of 8 steps, channels 32 at every level): it trains on trajectories the
+batched solver generates, beats the persistence baseline on held-out seeds,
+the fallback driver replaces every prediction whose judged error exceeds the
+tolerance by the solver's result, and the timing report compares the jump
+against the solver on the same GPU."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_surrogate_trains_beats_persistence_and_falls_back(lbm):
+    import torch
+    from paper_2408_01081_gb300 import surrogate as S
+    H = W = 32
+    chunks = lambda i: S.generate_chunk(64, 10_000 + i, H=H, W=W, k=8, J=2, ell_range=(4.0, 8.0))
+    sur, hist = S.train(chunks, 8, batch=8, H=H, W=W, lr=2e-3, chans=(32, 32, 32, 32), k=8, epochs_per_chunk=3)
+    assert len(hist) >= 2 and hist[-1][1] < 0.5 * hist[0][1], hist
+    held = S.generate_chunk(32, 900_000, H=H, W=W, k=8, J=2, ell_range=(4.0, 8.0))
+    errs, pers = S.evaluate(sur, held, batch=16)
+    assert np.median(errs) < 0.6 * np.median(pers), (np.median(errs), np.median(pers))
+    # fallback: with a tolerance below the surrogate's error every checked lattice takes the solver result
+    U = held.U[0, :16].contiguous()
+    drv = S.FallbackDriver(sur, tol=1e-6, check_every=1)
+    out, e = drv.jump(U, held.nu[:16])
+    ref = S.relift_and_step(U, held.nu[:16], 8)
+    assert drv.fallbacks == int(np.sum(e > 1e-6))
+    for i in np.nonzero(e > 1e-6)[0]:
+        torch.testing.assert_close(out[i], ref[i], rtol=0, atol=0)
+    # the judge evaluates exactly the map the training pairs sample (re-lift, then k steps)
+    judge = S.relative_error(sur, ref, held.U[1, :16], 10 * H * W, 16, H, W)
+    assert np.max(judge) < 1e-12
+    drv2 = S.FallbackDriver(sur, tol=10.0, check_every=1)
+    out2, _ = drv2.jump(U, held.nu[:16])
+    assert drv2.fallbacks == 0
+    tm = S.timing(sur, n=8, H=H, W=W, reps=2)
+    assert tm["surrogate_ms_per_lattice"] > 0 and tm["lbm_f64_ms_per_lattice"] > 0
