@@ -37,8 +37,10 @@ NX = NY = 8192
 CK2, CMU2, CFL = 1.5, 0.5, 0.9
 ELL, STD = 64.0, 1e-3
 METRIC = "MLUPS and % of HBM roofline; mixed-precision vs FP64 at stated L2 error"
-BYTES_PER_NODE = {"f64": 320, "f32": 160, "bf16": 80, "f16": 80}   # one read + one write of 20 values
+BYTES_PER_NODE = {"f64": 320, "f32": 160, "bf16": 80, "f16": 80,    # one read + one write of 20 values
+                  "ms_bf16": 100, "ms_f16": 100}                   # 5 FP32 + 15 16-bit moments, read + write
 FP64_OPS_PER_NODE = 47                                                # DADD/DFMA per node, no forcing
+FUSED = {"f32"}      # formats the library advances two steps per pass by default (lbm_set_step_fusion)
 # DRAM bytes per node of one step launch from an ncu capture (profiles/step_kernel_*.md), valid only
 # for the kernel sources with this digest; any change to them reports traffic as null until re-captured
 TRAFFIC_CAPTURE = {"sha256": None, "bytes_per_node": {"f64": 313.19, "f32": 153.77, "bf16": 74.23}}
@@ -221,6 +223,33 @@ def run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws):
                     "bytes_per_node": 160}}
 
 
+def run_surrogate(args):
+    """U-Net jump of 32 steps on 256^2 periodic lattices: train within a time budget on fresh
+    solver trajectories, then held-out error and wall-clock against the solver on this GPU."""
+    import torch
+    from paper_2408_01081_gb300 import surrogate as S
+    t0 = time.perf_counter()
+    chunks = lambda i: S.generate_chunk(256, 10_000 + i, H=256, W=256, k=32, J=4)
+    sur, hist = S.train(chunks, 1000, batch=8, H=256, W=256, lr=1e-3, k=32, time_budget_s=args.surrogate_budget)
+    train_s = time.perf_counter() - t0
+    held = S.generate_chunk(64, 900_000, H=256, W=256, k=32, J=4)
+    errs, pers = S.evaluate(sur, held, batch=16)
+    tm = S.timing(sur, n=16, H=256, W=256)
+    del held
+    torch.cuda.empty_cache()
+    med = float(np.median(errs))
+    return {"workload": "256^2 periodic lattices, GRF v0 (ell 16-64 cells), nu U[0,0.49], jump of 32 steps, "
+                        "4-level U-Net (1.96 M params, BF16 weights, FP32 accumulate)",
+            "train_s": round(train_s, 1), "iterations": sur.net.step_count, "batch": 8,
+            "heldout_rel_l2_median": med, "heldout_rel_l2_max": float(np.max(errs)),
+            "persistence_rel_l2_median": float(np.median(pers)),
+            "fallback_tol": 1e-3, "falls_back": bool(med > 1e-3),
+            "surrogate_ms_per_lattice": round(tm["surrogate_ms_per_lattice"], 4),
+            "lbm_f64_ms_per_lattice": round(tm["lbm_f64_ms_per_lattice"], 4),
+            "lbm_f32_ms_per_lattice": round(tm["lbm_f32_ms_per_lattice"], 4),
+            "gain_vs_f64": round(tm["gain_vs_f64"], 3), "gain_vs_f32": round(tm["gain_vs_f32"], 3)}
+
+
 def _batch_mode(cache):
     """Launch mode the tuner stored for FP32 on this GPU (0 if unknown)."""
     try:
@@ -271,6 +300,8 @@ def run_ours(args):
     for storage in args.formats:
         lat = lbm.Lattice(nx, ny, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet=False, storage=storage,
                           track_displacement=False, stream=stream.cuda_stream)
+        if args.no_fusion:
+            lat.set_step_fusion(1)
         lat.init(U0, Ux, Uy)
         lat.step(args.warmup)
         barrier()
@@ -293,7 +324,10 @@ def run_ours(args):
         del out
         lat.close()
         mlups_rank = n_nodes * args.steps / (ms * 1e-3) / 1e6
-        results[storage] = {"ms_per_step": ms / args.steps, "mlups": mlups_rank * ws}
+        fused = storage in FUSED and not args.no_fusion
+        results[storage] = {"ms_per_step": ms / args.steps, "mlups": mlups_rank * ws,
+                            "steps_per_pass": 2 if fused else 1,
+                            "launches": (args.steps // 2 + args.steps % 2) if fused else args.steps}
 
     # relative L2 of every moment field against the FP64 run after the same steps
     ref = finals.get("f64")
@@ -313,6 +347,10 @@ def run_ours(args):
     batch = None
     if not args.no_batch:
         batch = run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws)
+
+    surrogate = None
+    if not args.no_surrogate and rank == 0:
+        surrogate = run_surrogate(args)
 
     # end to end through the C ABI with host buffers: H2D of the initial data from pinned
     # memory, init, K steps, D2H of the ten output fields, all inside the timed region
@@ -368,12 +406,14 @@ def run_ours(args):
             continue
         r = results[s]
         nps = n_nodes / (r["ms_per_step"] * 1e-3)
-        ach = BYTES_PER_NODE[s] * nps / 1e9
+        bpn = BYTES_PER_NODE[s] / r["steps_per_pass"]      # algorithmic bytes per node and step
+        ach = bpn * nps / 1e9
         mixed[s] = {"mlups": round(r["mlups"], 1), "ms_per_step": round(r["ms_per_step"], 4),
-                    "speedup_vs_f64": round(r["speedup_vs_f64"], 3),
+                    "speedup_vs_f64": round(r["speedup_vs_f64"], 3), "steps_per_pass": r["steps_per_pass"],
+                    "launches": r["launches"],
                     "hbm": {"achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
-                            "frac": round(ach / hbm_peak, 4), "bytes_per_node": BYTES_PER_NODE[s],
-                            "traffic": traffic_per_launch(s, n_nodes)},
+                            "frac": round(ach / hbm_peak, 4), "bytes_per_node_step": bpn,
+                            "traffic": traffic_per_launch(s, n_nodes) if r["steps_per_pass"] == 1 else None},
                     "rel_l2_vs_f64": {k: float(f"{v:.3e}") for k, v in r["rel_l2_vs_f64"].items()},
                     "error_at_step": args.warmup + args.steps}
     cpu = None
@@ -391,7 +431,7 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": f"inputs larger than L2: state {2 * 20 * n_nodes * 8 / 1e9:.1f} GB double-buffered"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-            "clocks": clocks, "mixed_precision": mixed, "batch": batch}
+            "clocks": clocks, "mixed_precision": mixed, "batch": batch, "surrogate": surrogate}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -405,10 +445,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nx", type=int, default=NX)
     ap.add_argument("--ny", type=int, default=NY)
-    ap.add_argument("--formats", default="f64,f32,bf16,f16")
+    ap.add_argument("--formats", default="f64,f32,bf16,f16,ms_bf16,ms_f16")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-fusion", action="store_true", help="one kernel per step for every format")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-budget", type=float, default=60.0, help="surrogate training seconds")
     ap.add_argument("--cpu-steps", type=int, default=100)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the step kernel from an ncu capture (null if unknown)")

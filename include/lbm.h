@@ -48,10 +48,15 @@ typedef enum {
 
 typedef enum { LBM_PERIODIC = 0, LBM_DIRICHLET = 1 } lbm_bc;
 
-/* Storage precision of the populations.  LBM_F64 stores and computes in FP64;
- * the others store in the named format and compute in FP32 (the initialisation,
- * the Dirichlet reconstruction and all reductions stay in FP64). */
-typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_BF16 = 2, LBM_F16 = 3 } lbm_storage;
+/* Storage of the state.  LBM_F64 stores and computes in FP64; LBM_F32 / BF16 /
+ * F16 store the populations in that format and compute in FP32.  LBM_MS_BF16 /
+ * LBM_MS_F16 store per node the zeroth moment U (FP32) and the 15 deviations of
+ * the other moments from their local-equilibrium values (Eq. cond_eq) in BF16 /
+ * FP16, scaled by a power of two chosen at lbm_init / lbm_set_populations
+ * (50 bytes per node instead of 80 for 16-bit populations).  In every reduced
+ * format the initialisation, the Dirichlet reconstruction and all reductions
+ * stay in FP64.  Batches accept formats 0..3. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_BF16 = 2, LBM_F16 = 3, LBM_MS_BF16 = 4, LBM_MS_F16 = 5 } lbm_storage;
 
 typedef struct {
     int32_t nx, ny;              /* nodes per row / number of rows, each >= 2            */
@@ -79,6 +84,26 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out);
 lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const double* dU0dy,
                     const double* B0, const double* u0, int32_t on_device);
 
+/* Steps per pass over memory.  With 2 (the default for LBM_F32; 1 for the other
+ * formats, where the fused kernel is not yet faster) lbm_step advances pairs of
+ * steps with one kernel that keeps the intermediate state on chip (halving the
+ * memory traffic per step) whenever the lattice stores FP32 / BF16 / FP16
+ * populations, omega = 2, there is no body load and no displacement tracking,
+ * and the boundary is periodic or homogeneous Dirichlet; otherwise, and for an
+ * odd last step, one kernel per step runs.  FP32 results are bit-identical to
+ * single steps; 16-bit results skip one rounding per pair and are more accurate.
+ * rows_per_block (default 64) sets the rows each thread block streams through.
+ * steps_per_pass = 1 always uses one kernel per step. */
+lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t rows_per_block);
+
+/* Relaxation rate of the BGK collision (Eq. collision); the paper's scheme is
+ * omega = 2 (the default), the only value with second-order consistency
+ * (Sec. 4.1).  Other values give a first-order, dissipative control scheme whose
+ * forcing weight is W_ij = 1/8 (the value that adds dt B to the zeroth moment
+ * per step).  omega in (0, 1) or (1, 2]; omega = 1 is rejected (LBM_ERR_ARG)
+ * because the pre-collision populations cannot be recovered from f^eq. */
+lbm_status lbm_set_relaxation(lbm_ctx* ctx, double omega);
+
 /* Body load as a separable sum (the library copies the tables):
  *   b_c(x_k, y_l, t_m) = sum_{r<R} X[r][k] * Y[r][l] * T[m][c][r],   c = 0 (b_x), 1 (b_y)
  * X: [R][nx], Y: [R][ny], T: [nt][2][R]; m = 0 .. nt-1 indexes t = m dt.
@@ -93,6 +118,16 @@ lbm_status lbm_set_forcing(lbm_ctx* ctx, int32_t R, const double* X, const doubl
  * rows | bottom wall columns 0..nx-1 | top wall columns].  g = NULL (nt ignored)
  * selects homogeneous data u_D = const.  Stepping past row nt-1 returns LBM_ERR_STATE. */
 lbm_status lbm_set_dirichlet(lbm_ctx* ctx, const double* g, int64_t nt, int32_t on_device);
+
+/* Dirichlet data given as a separable sum, expanded on the device into the
+ * per-step table of lbm_set_dirichlet (which it replaces):
+ *   g_c(x_b, t_m + dt/2) = sum_{r<R} X(x_b)[r] * Y(y_b)[r] * T[m][c][r]
+ * with X evaluated at the node columns Xn [R][nx] (bottom and top walls) and at the
+ * two side walls Xw [R][2] (x = 0, x = nx dx), Y at the node rows Yn [R][ny] (left and
+ * right walls) and at Yw [R][2] (y = 0, y = ny dx); T: [nt][2][R], 1 <= R <= 16.
+ * Device memory of nt * 2 * 2(nx+ny) doubles is allocated for the expanded table. */
+lbm_status lbm_set_dirichlet_separable(lbm_ctx* ctx, int32_t R, const double* Xn, const double* Xw, const double* Yn,
+                                       const double* Yw, const double* T, int64_t nt, int32_t on_device);
 
 /* Advance n >= 0 time steps (Sec. 3.6: collision, streaming, boundary rule,
  * displacement update), asynchronously on the context's stream. */

@@ -268,6 +268,7 @@ lbmk::NodeArgs lattice_node_args(const lbm_batch* b, int i)
     A.c = D.dx / D.dt;
     A.R = 0;
     A.X = A.Y = A.T = nullptr;
+    A.omega = 2.0;
     const int VI[4] = {1, 0, -1, 0}, VJ[4] = {0, 1, 0, -1};
     for (int d = 0; d < 4; ++d) {
         double gm[25] = {0};

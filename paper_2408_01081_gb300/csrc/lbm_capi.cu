@@ -15,6 +15,39 @@ using lbmh::KindOps;
 
 namespace {
 
+__global__ void to_float_kernel(const double* __restrict__ x, long long n, float* __restrict__ y)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+
+// expand separable wall tables into g[m][c][e] for m in [0, nt)
+__global__ void wall_tables_kernel(int R, const double* __restrict__ Xn, const double* __restrict__ Xw,
+                                   const double* __restrict__ Yn, const double* __restrict__ Yw,
+                                   const double* __restrict__ T, long long nt, int nx, int ny, double* __restrict__ g)
+{
+    const int nwall = 2 * (nx + ny);
+    const long long n = nt * nwall;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+         id += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(id % nwall);
+        const long long m = id / nwall;
+        double gx = 0.0, gy = 0.0;
+        for (int r = 0; r < R; ++r) {
+            double xy;
+            if (e < ny) xy = Xw[r * 2 + 0] * Yn[(long long)r * ny + e];                        // left wall
+            else if (e < 2 * ny) xy = Xw[r * 2 + 1] * Yn[(long long)r * ny + (e - ny)];        // right wall
+            else if (e < 2 * ny + nx) xy = Xn[(long long)r * nx + (e - 2 * ny)] * Yw[r * 2 + 0];  // bottom
+            else xy = Xn[(long long)r * nx + (e - 2 * ny - nx)] * Yw[r * 2 + 1];                // top
+            gx = fma(xy, T[(m * 2 + 0) * R + r], gx);
+            gy = fma(xy, T[(m * 2 + 1) * R + r], gy);
+        }
+        g[(m * 2 + 0) * nwall + e] = gx;
+        g[(m * 2 + 1) * nwall + e] = gy;
+    }
+}
+
+
 thread_local std::string g_create_error;
 
 const KindOps* ops_for(int storage)
@@ -24,6 +57,8 @@ const KindOps* ops_for(int storage)
     case LBM_F32: return &lbmh::kind_ops_1;
     case LBM_BF16: return &lbmh::kind_ops_2;
     case LBM_F16: return &lbmh::kind_ops_3;
+    case LBM_MS_BF16: return &lbmh::kind_ops_4;
+    case LBM_MS_F16: return &lbmh::kind_ops_5;
     default: return nullptr;
     }
 }
@@ -73,6 +108,9 @@ struct lbm_ctx {
     double* fX = nullptr;
     double* fY = nullptr;
     double* fT = nullptr;
+    float* fXf = nullptr;        // FP32 copies of the body-load tables for the reduced formats
+    float* fYf = nullptr;
+    float* fTf = nullptr;
     long long fnt = 0;
     double* g = nullptr;
     long long gnt = 0;
@@ -84,6 +122,10 @@ struct lbm_ctx {
     std::string err;
     double a = 0, b = 0, c = 0;
     double k[4][25] = {};
+    double omega = 2.0;
+    double neq_scale = 1.0;      // moment-space storage: scale of the stored deviations
+    int fuse = 1;                // steps per pass over memory when the fused kernel applies
+    int tb_rows = 64;            // rows per block of the fused kernel
 };
 
 namespace {
@@ -139,6 +181,9 @@ lbmk::NodeArgs node_args(const lbm_ctx* ctx, long long m_time)
         A.T = ctx->fT + m_time * 2 * ctx->R;
     }
     std::memcpy(A.k, ctx->k, sizeof(A.k));
+    A.omega = ctx->omega;
+    A.neq_scale = ctx->neq_scale;
+    A.measure = nullptr;
     return A;
 }
 
@@ -182,6 +227,31 @@ lbm_status check_ready(lbm_ctx* ctx)
 }
 
 }  // namespace
+
+// Moment-space storage: pick the power-of-two scale of the stored deviations from the
+// largest deviation the state about to be stored has (run the storing kernel once with
+// `measure` set), so that the 16-bit values use their full precision and stay far from
+// overflow (largest stored value about 2048).
+template <typename Launch>
+lbm_status choose_neq_scale(lbm_ctx* ctx, Launch launch)
+{
+    if (ctx->p.storage < LBM_MS_BF16) return LBM_OK;
+    float* meas = reinterpret_cast<float*>(ctx->scratch + kRedBlocks * 30 + 48);
+    LBM_CUDA(ctx, cudaMemsetAsync(meas, 0, sizeof(float), ctx->s));
+    lbmk::NodeArgs A = node_args(ctx, -1);
+    A.measure = meas;
+    LBM_CUDA(ctx, launch(A));
+    float mx = 0.f;
+    LBM_CUDA(ctx, cudaMemcpyAsync(&mx, meas, sizeof(float), cudaMemcpyDeviceToHost, ctx->s));
+    LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    double s = 1.0;
+    if (mx > 0.f && std::isfinite(mx)) {
+        const int e = (int)std::floor(std::log2(2048.0 / (double)mx));
+        s = std::ldexp(1.0, std::max(-60, std::min(60, e)));
+    }
+    ctx->neq_scale = s;
+    return LBM_OK;
+}
 
 extern "C" {
 
@@ -237,6 +307,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
     ctx->a = p->cK / c;
     ctx->b = p->cmu / c;
     ctx->nwall = 2 * (p->nx + p->ny);
+    ctx->fuse = (p->storage == LBM_F32) ? 2 : 1;   // measured faster than single steps only for FP32
     // symmetrizer blocks k_ij = g_ij^{-1}, g_ij = 1/4 I + (i A_x + j A_y)/(2c)  (Eq. stability_linear)
     const int VI[4] = {1, 0, -1, 0}, VJ[4] = {0, 1, 0, -1};
     for (int d = 0; d < 4; ++d) {
@@ -255,7 +326,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
             return LBM_ERR_CFL;
         }
     }
-    const size_t state_bytes = (size_t)20 * ctx->plane * ctx->ops->elem_bytes;
+    const size_t state_bytes = (size_t)ctx->plane * ctx->ops->state_bytes_per_node;
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&ctx->buf[i], state_bytes);
     if (e == cudaSuccess && p->track_displacement) e = cudaMalloc((void**)&ctx->w, (size_t)2 * ctx->plane * sizeof(double));
@@ -283,6 +354,9 @@ lbm_status lbm_destroy(lbm_ctx* ctx)
     cudaFree(ctx->fX);
     cudaFree(ctx->fY);
     cudaFree(ctx->fT);
+    cudaFree(ctx->fXf);
+    cudaFree(ctx->fYf);
+    cudaFree(ctx->fTf);
     cudaFree(ctx->g);
     cudaFree(ctx->scratch);
     delete ctx;
@@ -308,6 +382,25 @@ lbm_status lbm_synchronize(lbm_ctx* ctx)
     return LBM_OK;
 }
 
+lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t rows_per_block)
+{
+    LBM_CHECK_CTX(ctx);
+    if ((steps_per_pass != 1 && steps_per_pass != 2) || rows_per_block < 1 || rows_per_block > 65535)
+        return fail(ctx, LBM_ERR_ARG, "steps_per_pass must be 1 or 2 and rows_per_block in [1, 65535]");
+    ctx->fuse = steps_per_pass;
+    ctx->tb_rows = rows_per_block;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_relaxation(lbm_ctx* ctx, double omega)
+{
+    LBM_CHECK_CTX(ctx);
+    if (!(omega > 0.0) || omega > 2.0 || omega == 1.0)
+        return fail(ctx, LBM_ERR_ARG, "omega must be in (0, 1) or (1, 2]");
+    ctx->omega = omega;
+    return LBM_OK;
+}
+
 lbm_status lbm_set_forcing(lbm_ctx* ctx, int32_t R, const double* X, const double* Y, const double* T,
                            int64_t nt, int32_t on_device)
 {
@@ -317,7 +410,11 @@ lbm_status lbm_set_forcing(lbm_ctx* ctx, int32_t R, const double* X, const doubl
     cudaFree(ctx->fX);
     cudaFree(ctx->fY);
     cudaFree(ctx->fT);
+    cudaFree(ctx->fXf);
+    cudaFree(ctx->fYf);
+    cudaFree(ctx->fTf);
     ctx->fX = ctx->fY = ctx->fT = nullptr;
+    ctx->fXf = ctx->fYf = ctx->fTf = nullptr;
     ctx->R = 0;
     ctx->fnt = 0;
     if (R == 0) return LBM_OK;
@@ -330,6 +427,15 @@ lbm_status lbm_set_forcing(lbm_ctx* ctx, int32_t R, const double* X, const doubl
     LBM_CUDA(ctx, cudaMemcpyAsync(ctx->fX, X, nX * sizeof(double), kind, ctx->s));
     LBM_CUDA(ctx, cudaMemcpyAsync(ctx->fY, Y, nY * sizeof(double), kind, ctx->s));
     LBM_CUDA(ctx, cudaMemcpyAsync(ctx->fT, T, nT * sizeof(double), kind, ctx->s));
+    if (ctx->p.storage != LBM_F64) {
+        LBM_CUDA(ctx, cudaMalloc((void**)&ctx->fXf, nX * sizeof(float)));
+        LBM_CUDA(ctx, cudaMalloc((void**)&ctx->fYf, nY * sizeof(float)));
+        LBM_CUDA(ctx, cudaMalloc((void**)&ctx->fTf, nT * sizeof(float)));
+        to_float_kernel<<<256, 256, 0, ctx->s>>>(ctx->fX, (long long)nX, ctx->fXf);
+        to_float_kernel<<<256, 256, 0, ctx->s>>>(ctx->fY, (long long)nY, ctx->fYf);
+        to_float_kernel<<<256, 256, 0, ctx->s>>>(ctx->fT, (long long)nT, ctx->fTf);
+        LBM_CUDA(ctx, cudaGetLastError());
+    }
     LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
     ctx->R = R;
     ctx->fnt = nt;
@@ -355,6 +461,40 @@ lbm_status lbm_set_dirichlet(lbm_ctx* ctx, const double* g, int64_t nt, int32_t 
     return LBM_OK;
 }
 
+lbm_status lbm_set_dirichlet_separable(lbm_ctx* ctx, int32_t R, const double* Xn, const double* Xw, const double* Yn,
+                                       const double* Yw, const double* T, int64_t nt, int32_t on_device)
+{
+    LBM_CHECK_CTX(ctx);
+    if (ctx->p.bc != LBM_DIRICHLET) return fail(ctx, LBM_ERR_ARG, "lattice is periodic");
+    if (R < 1 || R > kMaxR || !Xn || !Xw || !Yn || !Yw || !T || nt < 1)
+        return fail(ctx, LBM_ERR_ARG, "R must be in [1, 16], tables non-NULL and nt >= 1");
+    const int nx = ctx->p.nx, ny = ctx->p.ny;
+    const double *dXn, *dXw, *dYn, *dYw, *dT;
+    double *o1, *o2, *o3, *o4, *o5;
+    lbm_status st;
+    if ((st = stage_in(ctx, Xn, (size_t)R * nx, on_device, &dXn, &o1)) != LBM_OK) return st;
+    if ((st = stage_in(ctx, Xw, (size_t)R * 2, on_device, &dXw, &o2)) != LBM_OK) return st;
+    if ((st = stage_in(ctx, Yn, (size_t)R * ny, on_device, &dYn, &o3)) != LBM_OK) return st;
+    if ((st = stage_in(ctx, Yw, (size_t)R * 2, on_device, &dYw, &o4)) != LBM_OK) return st;
+    if ((st = stage_in(ctx, T, (size_t)nt * 2 * R, on_device, &dT, &o5)) != LBM_OK) return st;
+    LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    cudaFree(ctx->g);
+    ctx->g = nullptr;
+    ctx->gnt = 0;
+    const size_t n = (size_t)nt * 2 * ctx->nwall;
+    LBM_CUDA(ctx, cudaMalloc((void**)&ctx->g, n * sizeof(double)));
+    long long nb = ((long long)nt * ctx->nwall + 255) / 256;
+    if (nb > 152 * 32) nb = 152 * 32;
+    wall_tables_kernel<<<(unsigned)nb, 256, 0, ctx->s>>>(R, dXn, dXw, dYn, dYw, dT, nt, nx, ny, ctx->g);
+    cudaError_t e = cudaGetLastError();
+    for (double* o : {o1, o2, o3, o4, o5})
+        if (o) cudaFreeAsync(o, ctx->s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "wall tables kernel");
+    LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    ctx->gnt = nt;
+    return LBM_OK;
+}
+
 lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const double* dU0dy,
                     const double* B0, const double* u0, int32_t on_device)
 {
@@ -369,9 +509,13 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const d
     if ((st = stage_in(ctx, dU0dy, 5 * n, on_device, &dUy, &o3)) != LBM_OK) return st;
     if ((st = stage_in(ctx, B0, 2 * n, on_device, &dB0, &o4)) != LBM_OK) return st;
     if ((st = stage_in(ctx, ctx->w ? u0 : nullptr, 2 * n, on_device, &du0, &o5)) != LBM_OK) return st;
-    lbmk::NodeArgs A = node_args(ctx, -1);
     dim3 grid, block;
     node_grid(ctx, grid, block);
+    st = choose_neq_scale(ctx, [&](const lbmk::NodeArgs& M) {
+        return ctx->ops->init(M, dU0, dUx, dUy, dB0, du0, grid, block, ctx->s);
+    });
+    if (st != LBM_OK) return st;
+    lbmk::NodeArgs A = node_args(ctx, -1);
     cudaError_t e = ctx->ops->init(A, dU0, dUx, dUy, dB0, du0, grid, block, ctx->s);
     for (double* o : {o1, o2, o3, o4, o5})
         if (o) cudaFreeAsync(o, ctx->s);
@@ -410,14 +554,46 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
     A.R = ctx->R;
     A.X = ctx->fX;
     A.Y = ctx->fY;
+    A.Xf = ctx->fXf;
+    A.Yf = ctx->fYf;
     A.nwall = ctx->nwall;
+    A.omega = ctx->omega;
+    A.neq_scale = ctx->neq_scale;
     const int variant = (ctx->p.bc == LBM_DIRICHLET ? lbmh::STEP_DIRICHLET : 0) |
-                        (ctx->R > 0 ? lbmh::STEP_FORCING : 0) | (ctx->w ? lbmh::STEP_TRACK : 0);
+                        (ctx->R > 0 ? lbmh::STEP_FORCING : 0) | (ctx->w ? lbmh::STEP_TRACK : 0) |
+                        (ctx->omega != 2.0 ? lbmh::STEP_OMEGA : 0);
+    // two steps per pass: population formats in FP32 / BF16 / FP16, omega = 2, no body load,
+    // no displacement tracking, periodic or homogeneous Dirichlet
+    const bool fusable = ctx->fuse == 2 &&
+                         (ctx->p.storage == LBM_F32 || ctx->p.storage == LBM_BF16 || ctx->p.storage == LBM_F16) &&
+                         ctx->omega == 2.0 && ctx->R == 0 && !ctx->w && !(ctx->p.bc == LBM_DIRICHLET && ctx->g);
+    if (fusable) {
+        lbmk::TbArgs T;
+        T.nx = ctx->p.nx;
+        T.ny = ctx->p.ny;
+        T.pitch = ctx->pitch;
+        T.plane = ctx->plane;
+        T.a = ctx->a;
+        T.b = ctx->b;
+        T.rows = ctx->tb_rows;
+        const int nstrip = (ctx->p.nx + lbmk::TB_OUT - 1) / lbmk::TB_OUT;
+        const dim3 tblock(128), tgrid((nstrip + 3) / 4, (ctx->p.ny + T.rows - 1) / T.rows);
+        while (n >= 2) {
+            T.src = ctx->buf[ctx->cur];
+            T.dst = ctx->buf[ctx->cur ^ 1];
+            cudaError_t e = ops->tb2_step(T, ctx->p.bc == LBM_DIRICHLET, tgrid, tblock, ctx->s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "fused two-step kernel");
+            ctx->cur ^= 1;
+            ctx->m += 2;
+            n -= 2;
+        }
+    }
     for (int64_t i = 0; i < n; ++i) {
         const long long m = ctx->m;
         A.src = ctx->buf[ctx->cur];
         A.dst = ctx->buf[ctx->cur ^ 1];
         A.T = ctx->R > 0 ? ctx->fT + (m + 1) * 2 * ctx->R : nullptr;
+        A.Tf = (ctx->R > 0 && ctx->fTf) ? ctx->fTf + (m + 1) * 2 * ctx->R : nullptr;
         A.g = ctx->g ? ctx->g + m * 2 * ctx->nwall : nullptr;
         cudaError_t e = ops->step(A, variant, grid, block, ctx->s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step kernel");
@@ -522,6 +698,12 @@ lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, const double* usta
     if ((st = stage_in(ctx, ctx->w ? ustar : nullptr, 2 * n, on_device, &du, &o2)) != LBM_OK) return st;
     dim3 grid, block;
     node_grid(ctx, grid, block);
+    st = choose_neq_scale(ctx, [&](const lbmk::NodeArgs& M0) {
+        lbmk::NodeArgs M = node_args(ctx, m);
+        M.measure = M0.measure;
+        return ctx->ops->set_pop(M, df, du, grid, block, ctx->s);
+    });
+    if (st != LBM_OK) return st;
     cudaError_t e = ctx->ops->set_pop(node_args(ctx, m), df, du, grid, block, ctx->s);
     if (o1) cudaFreeAsync(o1, ctx->s);
     if (o2) cudaFreeAsync(o2, ctx->s);
@@ -539,8 +721,7 @@ lbm_status lbm_check_finite(lbm_ctx* ctx)
     if (st != LBM_OK) return st;
     int* flag = reinterpret_cast<int*>(ctx->scratch + kRedBlocks * 30 + 40);
     LBM_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->s));
-    LBM_CUDA(ctx, ctx->ops->finite(ctx->buf[ctx->cur], ctx->p.nx, ctx->p.ny, ctx->pitch, ctx->plane, flag,
-                                   dim3(152 * 8), dim3(256), ctx->s));
+    LBM_CUDA(ctx, ctx->ops->finite(node_args(ctx, ctx->m), flag, dim3(152 * 8), dim3(256), ctx->s));
     int h = 0;
     LBM_CUDA(ctx, cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
     LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
@@ -550,7 +731,7 @@ lbm_status lbm_check_finite(lbm_ctx* ctx)
 lbm_status lbm_state_bytes(const lbm_ctx* ctx, int64_t* nbytes)
 {
     if (!ctx || !nbytes) return LBM_ERR_ARG;
-    *nbytes = (int64_t)20 * ctx->plane * ctx->ops->elem_bytes + (ctx->w ? (int64_t)2 * ctx->plane * 8 : 0);
+    *nbytes = (int64_t)ctx->plane * ctx->ops->state_bytes_per_node + (ctx->w ? (int64_t)2 * ctx->plane * 8 : 0);
     return LBM_OK;
 }
 
@@ -560,7 +741,7 @@ lbm_status lbm_save_state(lbm_ctx* ctx, void* dst, int32_t on_device)
     if (!dst) return fail(ctx, LBM_ERR_ARG, "dst is NULL");
     lbm_status st = check_ready(ctx);
     if (st != LBM_OK) return st;
-    const size_t sb = (size_t)20 * ctx->plane * ctx->ops->elem_bytes;
+    const size_t sb = (size_t)ctx->plane * ctx->ops->state_bytes_per_node;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     LBM_CUDA(ctx, cudaMemcpyAsync(dst, ctx->buf[ctx->cur], sb, kind, ctx->s));
     if (ctx->w)
@@ -573,7 +754,7 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t m, int32_t on_d
 {
     LBM_CHECK_CTX(ctx);
     if (!src || m < 0) return fail(ctx, LBM_ERR_ARG, "src is NULL or m < 0");
-    const size_t sb = (size_t)20 * ctx->plane * ctx->ops->elem_bytes;
+    const size_t sb = (size_t)ctx->plane * ctx->ops->state_bytes_per_node;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     LBM_CUDA(ctx, cudaMemcpyAsync(ctx->buf[ctx->cur], src, sb, kind, ctx->s));
     if (ctx->w)

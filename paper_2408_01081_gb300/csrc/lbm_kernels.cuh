@@ -107,9 +107,14 @@ struct StepArgs {
     const double* X;
     const double* Y;
     const double* T;       // row of the time t+dt: [2][R]
+    const float* Xf;       // FP32 copies of the tables (reduced-precision formats)
+    const float* Yf;
+    const float* Tf;
     // Dirichlet data d/dt u_D at t + dt/2 on the wall midpoints, [2][nwall] or nullptr
     const double* g;
     int nwall;
+    double omega;          // relaxation rate when the kernel is built for omega != 2
+    double neq_scale;      // moment-space storage: scale of the stored deviations
 };
 
 // ---------------------------------------------------------------------------
@@ -162,7 +167,7 @@ __device__ __forceinline__ void wall_source(int i, int j, double gx, double gy, 
 #define LBM_STEP_MIN_BLOCKS 1
 #endif
 
-template <int K, int V, bool DIRICHLET, bool FORCING, bool TRACK>
+template <int K, int V, bool DIRICHLET, bool FORCING, bool TRACK, bool OMEGA = false>
 __global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS)
 step_kernel(StepArgs A)
 {
@@ -231,9 +236,12 @@ step_kernel(StepArgs A)
     const M a = M(A.a), b = M(A.b);
     M out[4][5][V];
     double wv[2][V];
+    double bxs[V], bys[V];
 #pragma unroll
     for (int e = 0; e < V; ++e) {
         const int x = x0 + e;
+        bxs[e] = 0.0;
+        bys[e] = 0.0;
         M f[4][5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -287,18 +295,29 @@ step_kernel(StepArgs A)
             ry[k] = sx;
         }
         if (FORCING) {
-            double bx = 0.0, by = 0.0;
+            // body load in the arithmetic type (FP32 tables for the reduced formats)
+            M bx = M(0), by = M(0);
             if (x < nx) {
-                for (int r = 0; r < A.R; ++r) {
-                    const double xy = A.X[(long long)r * nx + x] * A.Y[(long long)r * ny + y];
-                    bx = fma(xy, A.T[r], bx);
-                    by = fma(xy, A.T[A.R + r], by);
+                if constexpr (sizeof(M) == 8) {
+                    for (int r = 0; r < A.R; ++r) {
+                        const M xy = A.X[(long long)r * nx + x] * A.Y[(long long)r * ny + y];
+                        bx = fma(xy, A.T[r], bx);
+                        by = fma(xy, A.T[A.R + r], by);
+                    }
+                } else {
+                    for (int r = 0; r < A.R; ++r) {
+                        const M xy = A.Xf[(long long)r * nx + x] * A.Yf[(long long)r * ny + y];
+                        bx = fma(xy, A.Tf[r], bx);
+                        by = fma(xy, A.Tf[A.R + r], by);
+                    }
                 }
             }
-            rx[0] = fma(M(0.5 * A.dt), M(bx), rx[0]);
-            rx[1] = fma(M(0.5 * A.dt), M(by), rx[1]);
-            ry[0] = fma(M(0.5 * A.dt), M(bx), ry[0]);
-            ry[1] = fma(M(0.5 * A.dt), M(by), ry[1]);
+            bxs[e] = (double)bx;
+            bys[e] = (double)by;
+            rx[0] = fma(M(0.5 * A.dt), bx, rx[0]);
+            rx[1] = fma(M(0.5 * A.dt), by, rx[1]);
+            ry[0] = fma(M(0.5 * A.dt), bx, ry[0]);
+            ry[1] = fma(M(0.5 * A.dt), by, ry[1]);
             U[0] = rx[0] + (f[0][0] + f[2][0]);
             U[1] = rx[1] + (f[0][1] + f[2][1]);
 #pragma unroll
@@ -309,6 +328,23 @@ step_kernel(StepArgs A)
         }
         M o[4][5];
         collide<M>(f, U, rx, ry, a, b, o);
+        if (OMEGA) {
+            // omega f^eq + (1 - omega) f + dt (2 - omega) W B  =  (omega/2) o + (1 - omega/2) f + forcing,
+            // with o the omega = 2 result and W = 1/8
+            const M h = M(0.5 * A.omega);
+            const M fw = M(A.dt * (2.0 - A.omega) * 0.125);
+#pragma unroll
+            for (int d = 0; d < 4; ++d)
+#pragma unroll
+                for (int k = 0; k < 5; ++k) o[d][k] = fma(h, o[d][k] - f[d][k], f[d][k]);
+            if (FORCING) {
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    o[d][0] = fma(fw, M(bxs[e]), o[d][0]);
+                    o[d][1] = fma(fw, M(bys[e]), o[d][1]);
+                }
+            }
+        }
 #pragma unroll
         for (int d = 0; d < 4; ++d)
 #pragma unroll
@@ -356,7 +392,14 @@ struct NodeArgs {
     const double* Y;
     const double* T;       // [2][R]
     double k[4][25];       // symmetrizer blocks k_ij = g_ij^{-1}
+    double omega;          // relaxation rate (2 for the paper's scheme; never 1)
+    double neq_scale;      // moment-space storage: scale of the stored deviations
+    float* measure;        // moment-space storage: if set, store_node records max |deviation| instead
 };
+
+// moment-space storage (lbm_ms.cuh)
+template <int K> __device__ void ms_load_node(const NodeArgs& A, int x, int y, double (&S)[4][5]);
+template <int K> __device__ void ms_store_node(const NodeArgs& A, int x, int y, const double (&S)[4][5]);
 
 __device__ __forceinline__ void body_load(const NodeArgs& A, int x, int y, double& bx, double& by)
 {
@@ -372,6 +415,9 @@ __device__ __forceinline__ void body_load(const NodeArgs& A, int x, int y, doubl
 template <int K>
 __device__ __forceinline__ void load_node(const NodeArgs& A, int x, int y, double (&S)[4][5])
 {
+    if constexpr (K >= 4) {
+        ms_load_node<K>(A, x, y, S);
+    } else {
     using E = typename Fmt<K>::E;
     const E* p = static_cast<const E*>(A.S);
     const long long off = (long long)y * A.pitch + x;
@@ -379,11 +425,15 @@ __device__ __forceinline__ void load_node(const NodeArgs& A, int x, int y, doubl
     for (int d = 0; d < 4; ++d)
 #pragma unroll
         for (int k = 0; k < 5; ++k) S[d][k] = (double)Fmt<K>::ld(p[(d * 5 + k) * A.plane + off]);
+    }
 }
 
 template <int K>
 __device__ __forceinline__ void store_node(const NodeArgs& A, int x, int y, const double (&S)[4][5])
 {
+    if constexpr (K >= 4) {
+        ms_store_node<K>(A, x, y, S);
+    } else {
     using E = typename Fmt<K>::E;
     using M = typename Fmt<K>::M;
     E* p = static_cast<E*>(A.Sout);
@@ -392,6 +442,7 @@ __device__ __forceinline__ void store_node(const NodeArgs& A, int x, int y, cons
     for (int d = 0; d < 4; ++d)
 #pragma unroll
         for (int k = 0; k < 5; ++k) p[(d * 5 + k) * A.plane + off] = Fmt<K>::st((M)S[d][k]);
+    }
 }
 
 // 2 g_ij U - f_ij for all four velocities, with U = sum_d f_d + shift (per component).
@@ -407,6 +458,47 @@ __device__ __forceinline__ void reflect_node(const double (&f)[4][5], const doub
         U[k] = rx[k] + (f[0][k] + f[2][k]);
     }
     collide<double>(f, U, rx, ry, a, b, o);
+}
+
+// Collision with relaxation rate omega (Eq. collision): f* = (omega/2)(2 g U - f) + (1 - omega/2) f
+// + dt (2 - omega) W B with W = 1/8 and U = sum f + dt/2 B.
+__device__ __forceinline__ void collide_node(const double (&f)[4][5], double bx, double by, double dt, double omega,
+                                             double a, double b, double (&o)[4][5], double (&U)[5])
+{
+    const double shift[5] = {0.5 * dt * bx, 0.5 * dt * by, 0.0, 0.0, 0.0};
+    reflect_node(f, shift, a, b, o, U);
+    if (omega != 2.0) {
+        const double h = 0.5 * omega, fw = dt * (2.0 - omega) * 0.125;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) o[d][k] = fma(h, o[d][k] - f[d][k], f[d][k]);
+            o[d][0] = fma(fw, bx, o[d][0]);
+            o[d][1] = fma(fw, by, o[d][1]);
+        }
+    }
+}
+
+// Inverse of collide_node: U = sum f* - dt/2 B for every omega; then
+// f = (f* - (omega/2) (2 g U) - dt (2 - omega) W B) / (1 - omega), which for omega = 2 is 2 g U - f*.
+__device__ __forceinline__ void uncollide_node(const double (&S)[4][5], double bx, double by, double dt,
+                                               double omega, double a, double b, double (&f)[4][5], double (&U)[5])
+{
+    const double shift[5] = {-0.5 * dt * bx, -0.5 * dt * by, 0.0, 0.0, 0.0};
+    reflect_node(S, shift, a, b, f, U);       // f = 2 g U - f*
+    if (omega != 2.0) {
+        const double h = 0.5 * omega, fw = dt * (2.0 - omega) * 0.125, inv = 1.0 / (1.0 - omega);
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const double two_gU = f[d][k] + S[d][k];
+                double v = S[d][k] - h * two_gU;
+                if (k == 0) v -= fw * bx;
+                if (k == 1) v -= fw * by;
+                f[d][k] = v * inv;
+            }
+    }
 }
 
 // scaled fluxes phi_x(v) = Phi_x(v)/c, phi_y(v) = Phi_y(v)/c (Eq. system)
@@ -475,9 +567,8 @@ __global__ void init_kernel(NodeArgs A, const double* __restrict__ U0, const dou
                 f[d][k] = eq - 0.125 * A.dt * corr;
             }
         }
-        double shift[5] = {0.5 * A.dt * bv[0], 0.5 * A.dt * bv[1], 0.0, 0.0, 0.0};
         double S[4][5], U[5];
-        reflect_node(f, shift, a, b, S, U);
+        collide_node(f, bv[0], bv[1], A.dt, A.omega, a, b, S, U);
         store_node<K>(A, x, y, S);
         if (A.w) {
             // u*(dt) = u*(0) + dt v(0) with u*(0) = u0 - dt/2 v(0)  (Eq. trapezoidal)
@@ -497,8 +588,7 @@ __device__ __forceinline__ void node_state(const NodeArgs& A, int x, int y, doub
     load_node<K>(A, x, y, S);
     double bx = 0.0, by = 0.0;
     if (A.R > 0) body_load(A, x, y, bx, by);
-    const double shift[5] = {-0.5 * A.dt * bx, -0.5 * A.dt * by, 0.0, 0.0, 0.0};
-    reflect_node(S, shift, A.a, A.b, f, U);
+    uncollide_node(S, bx, by, A.dt, A.omega, A.a, A.b, f, U);
 }
 
 // ten output fields (Sec. 3.5) of one node
@@ -572,9 +662,8 @@ __global__ void set_populations_kernel(NodeArgs A, const double* __restrict__ fi
             for (int k = 0; k < 5; ++k) f[d][k] = fin[(d * 5 + k) * n + id];
         double bx = 0.0, by = 0.0;
         if (A.R > 0) body_load(A, x, y, bx, by);
-        const double shift[5] = {0.5 * A.dt * bx, 0.5 * A.dt * by, 0.0, 0.0, 0.0};
         double S[4][5], U[5];
-        reflect_node(f, shift, A.a, A.b, S, U);
+        collide_node(f, bx, by, A.dt, A.omega, A.a, A.b, S, U);
         store_node<K>(A, x, y, S);
         if (A.w) {
             const long long off = (long long)y * A.pitch + x;
@@ -715,18 +804,19 @@ __global__ void __launch_bounds__(256) finish_kernel(const double* __restrict__ 
 }
 
 template <int K>
-__global__ void finite_kernel(const void* S, int nx, int ny, int pitch, long long plane, int* flag)
+__global__ void finite_kernel(NodeArgs A, int* flag)
 {
-    using E = typename Fmt<K>::E;
-    const E* p = static_cast<const E*>(S);
-    const long long n = 20LL * ny * nx;
+    const long long n = (long long)A.nx * A.ny;
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
          id += (long long)gridDim.x * blockDim.x) {
-        const long long q = id / ((long long)ny * nx);
-        const long long r = id % ((long long)ny * nx);
-        const int y = (int)(r / nx), x = (int)(r % nx);
-        const double v = (double)Fmt<K>::ld(p[q * plane + (long long)y * pitch + x]);
-        if (!isfinite(v)) atomicOr(flag, 1);
+        double S[4][5];
+        load_node<K>(A, (int)(id % A.nx), (int)(id / A.nx), S);
+        bool bad = false;
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) bad |= !isfinite(S[d][k]);
+        if (bad) atomicOr(flag, 1);
     }
 }
 

@@ -19,28 +19,38 @@ namespace {
 #endif
 
 constexpr int K = LBM_KIND;
+constexpr bool MS = (K >= lbmk::K_MSBF16);
 // nodes per thread in the step kernel (one vector access per plane and thread)
-constexpr int V = (K == lbmk::K_F64) ? LBM_VEC_F64 : (K == lbmk::K_F32) ? LBM_VEC_F32 : LBM_VEC_F16;
+constexpr int V = (K == lbmk::K_F64) ? LBM_VEC_F64 : (K == lbmk::K_F32) ? LBM_VEC_F32 : MS ? 4 : LBM_VEC_F16;
+constexpr int ELEM = (K == lbmk::K_F64) ? 8 : (K == lbmk::K_F32) ? 4 : 2;
+constexpr int NODE_BYTES = MS ? 5 * 4 + 15 * 2 : 20 * ELEM;
 
-template <bool D, bool F, bool T>
+template <bool D, bool F, bool T, bool O>
 cudaError_t step_v(const lbmk::StepArgs& a, dim3 g, dim3 b, cudaStream_t s)
 {
-    lbmk::step_kernel<K, V, D, F, T><<<g, b, 0, s>>>(a);
+    if constexpr (MS) lbmk::ms_step_kernel<K, V, D, F, T, O><<<g, b, 0, s>>>(a);
+    else lbmk::step_kernel<K, V, D, F, T, O><<<g, b, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+template <bool O>
+cudaError_t step_o(const lbmk::StepArgs& a, int variant, dim3 g, dim3 b, cudaStream_t s)
+{
+    switch (variant & 7) {
+    case 0: return step_v<false, false, false, O>(a, g, b, s);
+    case 1: return step_v<true, false, false, O>(a, g, b, s);
+    case 2: return step_v<false, true, false, O>(a, g, b, s);
+    case 3: return step_v<true, true, false, O>(a, g, b, s);
+    case 4: return step_v<false, false, true, O>(a, g, b, s);
+    case 5: return step_v<true, false, true, O>(a, g, b, s);
+    case 6: return step_v<false, true, true, O>(a, g, b, s);
+    default: return step_v<true, true, true, O>(a, g, b, s);
+    }
 }
 
 cudaError_t step(const lbmk::StepArgs& a, int variant, dim3 g, dim3 b, cudaStream_t s)
 {
-    switch (variant & 7) {
-    case 0: return step_v<false, false, false>(a, g, b, s);
-    case 1: return step_v<true, false, false>(a, g, b, s);
-    case 2: return step_v<false, true, false>(a, g, b, s);
-    case 3: return step_v<true, true, false>(a, g, b, s);
-    case 4: return step_v<false, false, true>(a, g, b, s);
-    case 5: return step_v<true, false, true>(a, g, b, s);
-    case 6: return step_v<false, true, true>(a, g, b, s);
-    default: return step_v<true, true, true>(a, g, b, s);
-    }
+    return (variant & lbmh::STEP_OMEGA) ? step_o<true>(a, variant, g, b, s) : step_o<false>(a, variant, g, b, s);
 }
 
 cudaError_t init(const lbmk::NodeArgs& a, const double* U0, const double* Ux, const double* Uy,
@@ -82,35 +92,72 @@ cudaError_t error(const lbmk::NodeArgs& a, const double* exact, double* partial,
     return cudaGetLastError();
 }
 
-cudaError_t finite(const void* S, int nx, int ny, int pitch, long long plane, int* flag, dim3 g, dim3 b,
-                   cudaStream_t s)
+cudaError_t finite(const lbmk::NodeArgs& a, int* flag, dim3 g, dim3 b, cudaStream_t s)
 {
-    lbmk::finite_kernel<K><<<g, b, 0, s>>>(S, nx, ny, pitch, plane, flag);
+    lbmk::finite_kernel<K><<<g, b, 0, s>>>(a, flag);
     return cudaGetLastError();
+}
+
+template <int KK>
+cudaError_t batch_step_t(const lbmk::BatchArgs& a, bool persistent, int grid, cudaStream_t s)
+{
+    if constexpr (KK >= lbmk::K_MSBF16) {
+        return cudaErrorNotSupported;        // batches use the population formats only
+    } else {
+        if (!persistent) {
+            lbmk::batch_step_kernel<KK, V, false><<<grid, 256, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, lbmk::batch_step_kernel<KK, V, true>, a);
+    }
+}
+
+template <int KK>
+cudaError_t batch_occupancy_t(int* n)
+{
+    if constexpr (KK >= lbmk::K_MSBF16) {
+        *n = 1;
+        return cudaSuccess;
+    } else {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lbmk::batch_step_kernel<KK, V, true>, 256, 0);
+    }
 }
 
 cudaError_t batch_step(const lbmk::BatchArgs& a, bool persistent, int grid, cudaStream_t s)
 {
-    if (!persistent) {
-        lbmk::batch_step_kernel<K, V, false><<<grid, 256, 0, s>>>(a);
+    return batch_step_t<K>(a, persistent, grid, s);
+}
+
+template <int KK>
+cudaError_t tb2_t(const lbmk::TbArgs& a, bool dirichlet, dim3 g, dim3 b, cudaStream_t s)
+{
+    if constexpr (KK == lbmk::K_F32 || KK == lbmk::K_BF16 || KK == lbmk::K_F16) {
+        if (dirichlet) lbmk::tb2_kernel<KK, true><<<g, b, 0, s>>>(a);
+        else lbmk::tb2_kernel<KK, false><<<g, b, 0, s>>>(a);
         return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, lbmk::batch_step_kernel<K, V, true>, a);
+}
+
+cudaError_t tb2_step(const lbmk::TbArgs& a, bool dirichlet, dim3 g, dim3 b, cudaStream_t s)
+{
+    return tb2_t<K>(a, dirichlet, g, b, s);
 }
 
 cudaError_t batch_occupancy(int* n)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lbmk::batch_step_kernel<K, V, true>, 256, 0);
+    return batch_occupancy_t<K>(n);
 }
 
 }  // namespace
@@ -121,8 +168,8 @@ namespace lbmh {
 #define LBM_OPS_NAME(k) LBM_OPS_NAME2(k)
 
 const KindOps LBM_OPS_NAME(LBM_KIND) = {
-    K, V, (int)sizeof(typename lbmk::Fmt<K>::E),
-    step, init, moments, get_pop, set_pop, energy, error, finite, batch_step, batch_occupancy,
+    K, V, ELEM, NODE_BYTES,
+    step, init, moments, get_pop, set_pop, energy, error, finite, batch_step, batch_occupancy, tb2_step,
 };
 
 }  // namespace lbmh

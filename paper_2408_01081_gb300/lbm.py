@@ -18,13 +18,14 @@ from .build import LIB
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CFL, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LBM_ERR_STATE = range(8)
 LBM_PERIODIC, LBM_DIRICHLET = 0, 1
-LBM_F64, LBM_F32, LBM_BF16, LBM_F16 = 0, 1, 2, 3
-STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "bf16": LBM_BF16, "f16": LBM_F16}
+LBM_F64, LBM_F32, LBM_BF16, LBM_F16, LBM_MS_BF16, LBM_MS_F16 = 0, 1, 2, 3, 4, 5
+STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "bf16": LBM_BF16, "f16": LBM_F16, "ms_bf16": LBM_MS_BF16,
+           "ms_f16": LBM_MS_F16}
 STATUS_NAMES = ["LBM_OK", "LBM_ERR_ARG", "LBM_ERR_CFL", "LBM_ERR_OOM", "LBM_ERR_CUDA", "LBM_ERR_UNSTABLE",
                 "LBM_ERR_TIMEOUT", "LBM_ERR_STATE"]
 
 # every symbol declared in include/lbm.h
-EXPORTS = ["lbm_create", "lbm_init", "lbm_set_forcing", "lbm_set_dirichlet", "lbm_step", "lbm_moments",
+EXPORTS = ["lbm_create", "lbm_init", "lbm_set_relaxation", "lbm_set_step_fusion", "lbm_set_forcing", "lbm_set_dirichlet", "lbm_set_dirichlet_separable", "lbm_step", "lbm_moments",
            "lbm_energy", "lbm_error_sums", "lbm_get_populations", "lbm_set_populations", "lbm_check_finite",
            "lbm_time_step", "lbm_synchronize", "lbm_destroy", "lbm_last_error", "lbm_state_bytes",
            "lbm_save_state", "lbm_load_state", "lbm_energy_noalloc", "lbm_batch_create", "lbm_batch_init",
@@ -74,7 +75,10 @@ def load(path: Optional[str] = None):
         "lbm_create": ([ctypes.POINTER(LbmParams), ctypes.POINTER(vp)], i32),
         "lbm_init": ([vp, dp, dp, dp, dp, dp, i32], i32),
         "lbm_set_forcing": ([vp, i32, dp, dp, dp, i64, i32], i32),
+        "lbm_set_relaxation": ([vp, ctypes.c_double], i32),
+        "lbm_set_step_fusion": ([vp, i32, i32], i32),
         "lbm_set_dirichlet": ([vp, dp, i64, i32], i32),
+        "lbm_set_dirichlet_separable": ([vp, i32, dp, dp, dp, dp, dp, i64, i32], i32),
         "lbm_step": ([vp, i64], i32),
         "lbm_moments": ([vp, dp, i32], i32),
         "lbm_energy": ([vp, dp], i32),
@@ -163,6 +167,14 @@ def lbm_init(ctx, U0, dU0dx, dU0dy, B0=None, u0=None):
     _check(ctx, load().lbm_init(ctx, *[t[0] for t in a], on))
 
 
+def lbm_set_step_fusion(ctx, steps_per_pass=2, rows_per_block=64):
+    _check(ctx, load().lbm_set_step_fusion(ctx, int(steps_per_pass), int(rows_per_block)))
+
+
+def lbm_set_relaxation(ctx, omega):
+    _check(ctx, load().lbm_set_relaxation(ctx, float(omega)))
+
+
 def lbm_set_forcing(ctx, X=None, Y=None, T=None):
     if X is None:
         _check(ctx, load().lbm_set_forcing(ctx, 0, None, None, None, 0, 0))
@@ -179,6 +191,12 @@ def lbm_set_dirichlet(ctx, g=None):
         return
     p, on, _keep = _arr(g, "g")
     _check(ctx, load().lbm_set_dirichlet(ctx, p, int(g.shape[0]), on))
+
+
+def lbm_set_dirichlet_separable(ctx, Xn, Xw, Yn, Yw, T):
+    a = [_arr(v, n) for v, n in ((Xn, "Xn"), (Xw, "Xw"), (Yn, "Yn"), (Yw, "Yw"), (T, "T"))]
+    on = _where(*[t[1] for t in a])
+    _check(ctx, load().lbm_set_dirichlet_separable(ctx, int(Xn.shape[0]), *[t[0] for t in a], int(T.shape[0]), on))
 
 
 def lbm_step(ctx, n=1):
@@ -390,11 +408,20 @@ class Lattice:
     def init(self, U0, dU0dx, dU0dy, B0=None, u0=None):
         lbm_init(self.ctx, U0, dU0dx, dU0dy, B0, u0)
 
+    def set_step_fusion(self, steps_per_pass=2, rows_per_block=64):
+        lbm_set_step_fusion(self.ctx, steps_per_pass, rows_per_block)
+
+    def set_relaxation(self, omega):
+        lbm_set_relaxation(self.ctx, omega)
+
     def set_forcing(self, X=None, Y=None, T=None):
         lbm_set_forcing(self.ctx, X, Y, T)
 
     def set_dirichlet(self, g=None):
         lbm_set_dirichlet(self.ctx, g)
+
+    def set_dirichlet_separable(self, Xn, Xw, Yn, Yw, T):
+        lbm_set_dirichlet_separable(self.ctx, Xn, Xw, Yn, Yw, T)
 
     def step(self, n=1):
         lbm_step(self.ctx, n)

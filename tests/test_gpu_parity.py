@@ -152,7 +152,8 @@ def test_checkpoint_resume_is_bit_exact(lbm):
     np.testing.assert_array_equal(b.moments(), ref)
 
 
-@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("bf16", 5e-2), ("f16", 5e-3)])
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("bf16", 5e-2), ("f16", 5e-3), ("ms_bf16", 1e-2),
+                                         ("ms_f16", 1e-3)])
 def test_reduced_precision_against_oracle(lbm, storage, tol):
     """Populations stored in FP32 / BF16 / FP16 with FP32 arithmetic: relative L2 of the
     moment fields against the FP64 oracle after 200 steps of the config-1 problem."""
@@ -187,3 +188,86 @@ def test_api_errors(lbm):
     lat.set_forcing()
     lat.set_populations(f)
     assert not lat.finite()
+
+
+@pytest.mark.parametrize("dirichlet", [False, True])
+def test_general_omega_matches_oracle(lbm, dirichlet):
+    """omega != 2 (first-order control scheme with W = 1/8) against the oracle, with body load."""
+    from oracle import Oracle, Params
+    if dirichlet:
+        wl = W.dirichlet_mms(40, 24, 1.1, 0.4, cfl=0.9, steps=50)
+    else:
+        wl = W.periodic_mms(48, 1.1, 0.4, cfl=0.9, steps=50)
+    o = Oracle(Params(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, wl.dirichlet, omega=1.7))
+    o.init(wl.U0, wl.dU0dx, wl.dU0dy, wl.body_load(0), wl.u0)
+    for m in range(wl.steps):
+        o.step(wl.body_load(m), wl.wall_data(m))
+    ref = o.outputs(wl.body_load(wl.steps))
+    lat = lbm.Lattice(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet=wl.dirichlet, storage="f64")
+    lat.set_relaxation(1.7)
+    lat.set_forcing(*wl.forcing)
+    if wl.dirichlet:
+        lat.set_dirichlet(wl.wall)
+    lat.init(wl.U0, wl.dU0dx, wl.dU0dy, wl.body_load(0), wl.u0)
+    lat.step(wl.steps)
+    errs = field_errors(lat.moments(), ref)
+    assert max(errs) < TOL64, errs
+    f, _ = lat.populations()
+    np.testing.assert_allclose(f, o.f, atol=1e-12 * np.max(np.abs(o.f)))
+
+
+@pytest.mark.parametrize("storage,tol", [("ms_bf16", 2e-2), ("ms_f16", 2e-3)])
+def test_moment_space_storage_dirichlet_with_forcing(lbm, storage, tol):
+    """Moment-space storage (FP32 U, 16-bit non-equilibrium moments) on the Dirichlet
+    manufactured solution with body load: every output field against the oracle."""
+    wl = W.dirichlet_mms(64, 32, 1.1, 0.4, cfl=0.9, steps=120, amp=1e-2, kx=2 * math.pi, ky=2 * math.pi)
+    _, ref = oracle_run(wl)
+    lat = gpu_lattice(lbm, wl, storage=storage)
+    lat.step(wl.steps)
+    out = lat.moments()
+    errs = field_errors(out, ref)
+    assert max(errs) < tol, errs
+    # the state round-trips through get/set populations and checkpoints
+    blob = np.empty(lbm.lbm_state_bytes(lat.ctx), dtype=np.uint8)
+    lbm.lbm_save_state(lat.ctx, blob)
+    lbm.lbm_load_state(lat.ctx, blob, lat.m)
+    np.testing.assert_array_equal(lat.moments(), out)
+    assert lat.finite()
+
+
+@pytest.mark.parametrize("dirichlet", [False, True])
+@pytest.mark.parametrize("nx,ny", [(5, 3), (67, 45), (1031, 7), (130, 70), (31, 200)])
+def test_two_step_fusion_fp32_is_bit_identical(lbm, dirichlet, nx, ny):
+    """The fused two-step kernel equals two single steps exactly in FP32 (even and odd step counts)."""
+    rng = np.random.default_rng(nx + 1000 * ny)
+    f = rng.standard_normal((4, 5, ny, nx)) * 1e-3
+    outs = []
+    for fuse in (1, 2):
+        lat = lbm.Lattice(nx, ny, 0.1, 0.1 / 3.2, 1.0, 0.6, dirichlet=dirichlet, storage="f32",
+                          track_displacement=False)
+        lat.set_step_fusion(fuse, 16)
+        lat.set_populations(f)
+        lat.step(9)
+        g, _ = lat.populations()
+        outs.append(g)
+        lat.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("storage,tol", [("bf16", 5e-2), ("f16", 5e-3)])
+def test_two_step_fusion_16bit_against_oracle(lbm, storage, tol):
+    wl = W.grf_periodic(96, 64, 1.5, 0.5, ell=8.0, std=1e-3, seeds=(3, 4), steps=200)
+    o = Oracle(Params(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, False))
+    o.init(wl.U0, wl.dU0dx, wl.dU0dy)
+    for _ in range(200):
+        o.step(track_displacement=False)
+    ref = o.moments()
+    errs = {}
+    for fuse in (1, 2):
+        lat = lbm.Lattice(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, storage=storage, track_displacement=False)
+        lat.set_step_fusion(fuse, 64)
+        lat.init(wl.U0, wl.dU0dx, wl.dU0dy)
+        lat.step(200)
+        errs[fuse] = max(field_errors(lat.moments(), ref, fields=range(5)))
+        lat.close()
+    assert errs[2] < tol and errs[2] <= 1.2 * errs[1], errs

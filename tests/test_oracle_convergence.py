@@ -112,3 +112,19 @@ def test_stability_threshold():
         return float(np.max(np.abs(o.f))) / f0
     assert growth(1.1, 0.4, 600) < 3.0
     assert growth(1.2, 0.4, 600) > 1e6
+
+
+def test_omega_below_two_is_first_order():
+    """Sec. 4.1: second-order consistency needs omega = 2; with omega < 2 the scheme is
+    dissipative and the displacement error converges at first order."""
+    def err(n, omega):
+        wl = W.periodic_mms(n, 1.1, 0.4, c=2.5, t_final=0.5)
+        o = Oracle(Params(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, False, omega=omega))
+        o.init(wl.U0, wl.dU0dx, wl.dU0dy, wl.body_load(0), wl.u0)
+        nrm = SpaceTimeNorms(wl.dx, wl.dt)
+        for m in range(wl.steps):
+            o.step(wl.body_load(m), None)
+            nrm.add(o.outputs(wl.body_load(m + 1))[5:7], wl.exact_outputs((m + 1) * wl.dt)[5:7])
+        return nrm.L2rel
+    e = [err(n, 1.6) for n in (40, 80)]
+    assert 0.85 < math.log2(e[0] / e[1]) < 1.2, e

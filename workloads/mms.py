@@ -277,3 +277,34 @@ def separable_tables(fields: List[SepField], nx: int, ny: int, dx: float, times)
 def eval_tables(X, Y, Tm) -> np.ndarray:
     """Dense [2, ny, nx] field from one time slice of separable tables."""
     return np.einsum("rx,ry,cr->cyx", X, Y, Tm)
+
+
+def separable_wall_tables(fields: List[SepField], nx: int, ny: int, dx: float, times):
+    """Separable form on the walls: Xn [R, nx] (node columns), Xw [R, 2] (x = 0, nx dx),
+    Yn [R, ny] (node rows), Yw [R, 2] (y = 0, ny dx), T [len(times), 2, R]."""
+    xs, ys = node_coords(nx, dx), node_coords(ny, dx)
+    xw, yw = np.array([0.0, nx * dx]), np.array([0.0, ny * dx])
+    keys = []
+    for f in fields:
+        for key in f.keys():
+            if key not in keys:
+                keys.append(key)
+    Xn, Xw, Yn, Yw, index = [], [], [], [], []
+    for (kx, ky) in keys:
+        for a in range(2):
+            for b in range(2):
+                fx = np.sin if a == 0 else np.cos
+                fy = np.sin if b == 0 else np.cos
+                Xn.append(fx(kx * xs))
+                Xw.append(fx(kx * xw))
+                Yn.append(fy(ky * ys))
+                Yw.append(fy(ky * yw))
+                index.append(((kx, ky), a, b))
+    T = np.zeros((len(times), len(fields), len(index)))
+    for m, t in enumerate(times):
+        for c, f in enumerate(fields):
+            merged = f.merged(float(t))
+            for r, (key, a, b) in enumerate(index):
+                if key in merged:
+                    T[m, c, r] = merged[key][a, b]
+    return np.stack(Xn), np.stack(Xw), np.stack(Yn), np.stack(Yw), T
