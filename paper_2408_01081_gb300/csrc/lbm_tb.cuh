@@ -30,6 +30,39 @@ struct TbArgs {
 
 constexpr int TB_OUT = 30;   // output columns per 32-lane strip
 
+// S0 inputs of S1(r) at one lane's column: own (1,0) and (-1,0) values of row r (the
+// x-neighbours come from the adjacent lanes), the halo values lanes 0 and 31 need,
+// and the pulled (0,1) / (0,-1) values (own opposite plane on a Dirichlet edge row)
+struct TbRow {
+    float o0[5], o2[5], hl[5], hr[5], fy1[5], fy3[5];
+};
+
+template <int K, bool DIRICHLET>
+__device__ __forceinline__ void tb_load_row(const typename Fmt<K>::E* __restrict__ src, const TbArgs& A, int r, int xc,
+                                            int lane, TbRow& L)
+{
+    const int nx = A.nx, ny = A.ny;
+    const long long plane = A.plane;
+    const bool row_ok = DIRICHLET ? (r >= 0 && r < ny) : true;
+    const int ry = row_ok ? ((r % ny) + ny) % ny : 0;
+    const long long rowoff = (long long)ry * A.pitch;
+    const int rm = (ry == 0) ? ny - 1 : ry - 1, rp = (ry == ny - 1) ? 0 : ry + 1;
+    const bool bot = DIRICHLET && ry == 0, top = DIRICHLET && ry == ny - 1;
+    const int xl = DIRICHLET ? max(xc - 1, 0) : (xc == 0 ? nx - 1 : xc - 1);
+    const int xr = DIRICHLET ? min(xc + 1, nx - 1) : (xc == nx - 1 ? 0 : xc + 1);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        L.o0[k] = sload<K>(src + (0 * 5 + k) * plane + rowoff + xc);
+        L.o2[k] = sload<K>(src + (2 * 5 + k) * plane + rowoff + xc);
+        L.hl[k] = (lane == 0) ? sload<K>(src + (0 * 5 + k) * plane + rowoff + xl) : 0.f;
+        L.hr[k] = (lane == 31) ? sload<K>(src + (2 * 5 + k) * plane + rowoff + xr) : 0.f;
+        L.fy1[k] = bot ? sload<K>(src + (3 * 5 + k) * plane + rowoff + xc)
+                       : sload<K>(src + (1 * 5 + k) * plane + (long long)rm * A.pitch + xc);
+        L.fy3[k] = top ? sload<K>(src + (1 * 5 + k) * plane + rowoff + xc)
+                       : sload<K>(src + (3 * 5 + k) * plane + (long long)rp * A.pitch + xc);
+    }
+}
+
 template <int K, bool DIRICHLET>
 __global__ void __launch_bounds__(128) tb2_kernel(TbArgs A)
 {
@@ -45,7 +78,7 @@ __global__ void __launch_bounds__(128) tb2_kernel(TbArgs A)
     const int xs = strip * TB_OUT - 1 + lane;             // this lane's column (may be -1 or >= nx)
     const bool inside = (xs >= 0) && (xs < nx);
     const int xc = DIRICHLET ? (xs < 0 ? 0 : (xs >= nx ? nx - 1 : xs)) : ((xs % nx) + nx) % nx;
-    const bool out_lane = (lane >= 1) && (lane <= TB_OUT) && (xs < nx);
+    const bool out_lane = (lane >= 1) && (lane <= TB_OUT) && inside;
     const int y0 = blockIdx.y * A.rows;
     const int y1 = min(ny, y0 + A.rows);
     const float fa = (float)A.a, fb = (float)A.b;
@@ -53,43 +86,38 @@ __global__ void __launch_bounds__(128) tb2_kernel(TbArgs A)
 
     float keep_py[5];          // S1(r-2), direction (0,1)
     float prev[4][5];          // S1(r-1), all directions
+#pragma unroll
     for (int k = 0; k < 5; ++k) {
         keep_py[k] = 0.f;
+#pragma unroll
         for (int d = 0; d < 4; ++d) prev[d][k] = 0.f;
     }
+    TbRow cur_in, next_in;
+    tb_load_row<K, DIRICHLET>(src, A, y0 - 1, xc, lane, cur_in);
 
     for (int r = y0 - 1; r <= y1; ++r) {
-        // ---- S1(r) at column xc from S0 ----
+        if (r < y1) tb_load_row<K, DIRICHLET>(src, A, r + 1, xc, lane, next_in);   // in flight during the math
+        // ---- S1(r) at column xc ----
         float cur[4][5];
         const bool row_ok = DIRICHLET ? (r >= 0 && r < ny) : true;
-        const int ry = row_ok ? ((r % ny) + ny) % ny : 0;
         {
-            const long long rowoff = (long long)ry * A.pitch;
-            const int rm = (ry == 0) ? ny - 1 : ry - 1, rp = (ry == ny - 1) ? 0 : ry + 1;
-            const bool bot = DIRICHLET && ry == 0, top = DIRICHLET && ry == ny - 1;
-            const int xl = DIRICHLET ? max(xc - 1, 0) : (xc == 0 ? nx - 1 : xc - 1);
-            const int xr = DIRICHLET ? min(xc + 1, nx - 1) : (xc == nx - 1 ? 0 : xc + 1);
-            float f[4][5], o0[5], o2[5];
+            float f[4][5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
-                o0[k] = sload<K>(src + (0 * 5 + k) * plane + rowoff + xc);
-                o2[k] = sload<K>(src + (2 * 5 + k) * plane + rowoff + xc);
-                float l = __shfl_up_sync(0xffffffffu, o0[k], 1);
-                float rr = __shfl_down_sync(0xffffffffu, o2[k], 1);
-                if (lane == 0) l = sload<K>(src + (0 * 5 + k) * plane + rowoff + xl);
-                if (lane == 31) rr = sload<K>(src + (2 * 5 + k) * plane + rowoff + xr);
-                f[0][k] = l;
-                f[2][k] = rr;
-                f[1][k] = bot ? sload<K>(src + (3 * 5 + k) * plane + rowoff + xc)
-                              : sload<K>(src + (1 * 5 + k) * plane + (long long)rm * A.pitch + xc);
-                f[3][k] = top ? sload<K>(src + (1 * 5 + k) * plane + rowoff + xc)
-                              : sload<K>(src + (3 * 5 + k) * plane + (long long)rp * A.pitch + xc);
+                float l = __shfl_up_sync(0xffffffffu, cur_in.o0[k], 1);
+                float rr = __shfl_down_sync(0xffffffffu, cur_in.o2[k], 1);
+                f[0][k] = (lane == 0) ? cur_in.hl[k] : l;
+                f[2][k] = (lane == 31) ? cur_in.hr[k] : rr;
+                f[1][k] = cur_in.fy1[k];
+                f[3][k] = cur_in.fy3[k];
             }
             if (DIRICHLET) {
+                const int ry = row_ok ? r : 0;
+                const bool bot = ry == 0, top = ry == ny - 1;
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
-                    if (xc == 0) f[0][k] = Dk[k] * o2[k];
-                    if (xc == nx - 1) f[2][k] = Dk[k] * o0[k];
+                    if (xc == 0) f[0][k] = Dk[k] * cur_in.o2[k];
+                    if (xc == nx - 1) f[2][k] = Dk[k] * cur_in.o0[k];
                     if (bot) f[1][k] = Dk[k] * f[1][k];
                     if (top) f[3][k] = Dk[k] * f[3][k];
                 }
@@ -130,7 +158,7 @@ __global__ void __launch_bounds__(128) tb2_kernel(TbArgs A)
                 U[k] = rx[k] + ry2[k];
             }
             collide<float>(f, U, rx, ry2, fa, fb, o);
-            if (out_lane && inside) {
+            if (out_lane) {
                 const long long off = (long long)q * A.pitch + xs;
 #pragma unroll
                 for (int d = 0; d < 4; ++d)
@@ -144,6 +172,7 @@ __global__ void __launch_bounds__(128) tb2_kernel(TbArgs A)
 #pragma unroll
             for (int d = 0; d < 4; ++d) prev[d][k] = cur[d][k];
         }
+        cur_in = next_in;
     }
 }
 
