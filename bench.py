@@ -43,8 +43,13 @@ FP64_OPS_PER_NODE = 47                                                # DADD/DFM
 FUSED = {"f32"}      # formats the library advances two steps per pass by default (lbm_set_step_fusion)
 # DRAM bytes per node of one step launch from an ncu capture (profiles/step_kernel_*.md), valid only
 # for the kernel sources with this digest; any change to them reports traffic as null until re-captured
-TRAFFIC_CAPTURE = {"sha256": None, "bytes_per_node": {"f64": 313.19, "f32": 153.77, "bf16": 74.23}}
-KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_01081_gb300/csrc/lbm_kind.cu"]
+# DRAM bytes per node and launch (dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of
+# 4096x2048, scaled by the node count); valid only while the kernel sources hash to "sha256".
+# "f32_fused" is one launch of the two-step kernel.
+TRAFFIC_CAPTURE = {"sha256": "90564ddc60eae4402cb8ba2dbbac31393e6036126e90556a44b1f7098b27e052", "bytes_per_node": {"f64": 313.31, "f32": 153.35, "f32_fused": 158.99,
+                                                         "bf16": 73.60, "f16": 73.57, "ms_f16": 94.48}}
+KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_01081_gb300/csrc/lbm_kind.cu",
+                  "paper_2408_01081_gb300/csrc/lbm_tb.cuh", "paper_2408_01081_gb300/csrc/lbm_ms.cuh"]
 
 
 def kernel_digest():
@@ -177,7 +182,7 @@ def run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws):
     """512 ragged lattices (config 4 of the workload set), FP32, graph of 100 steps per replay."""
     import workloads as W
     from workloads.grf import batch_lattice_inputs_torch
-    spec = W.batch_spec()
+    spec = W.batch_spec(count=args.batch_count)
     descs = []
     for sp in spec:
         c = W.material.lattice_speed(sp.cK2, sp.cmu2, CFL)
@@ -212,7 +217,7 @@ def run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws):
     peaks = _peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     ach = 160 * nodes / (ms * 1e-3) / 1e9
-    return {"workload": "512 lattices, short side log-uniform [64,1024], aspect U[1,4], nu U[0,0.49], "
+    return {"workload": f"{args.batch_count} lattices, short side log-uniform [64,1024], aspect U[1,4], nu U[0,0.49], "
                         "even periodic / odd homogeneous Dirichlet, GRF v0 (ell = short side/16, std 1e-3), "
                         "FP32 storage, CUDA graph of 100 steps per replay",
             "nodes": nodes, "steps": steps, "ms_per_step": round(ms, 4),
@@ -413,7 +418,7 @@ def run_ours(args):
                     "launches": r["launches"],
                     "hbm": {"achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                             "frac": round(ach / hbm_peak, 4), "bytes_per_node_step": bpn,
-                            "traffic": traffic_per_launch(s, n_nodes) if r["steps_per_pass"] == 1 else None},
+                            "traffic": traffic_per_launch(s if r["steps_per_pass"] == 1 else s + "_fused", n_nodes)},
                     "rel_l2_vs_f64": {k: float(f"{v:.3e}") for k, v in r["rel_l2_vs_f64"].items()},
                     "error_at_step": args.warmup + args.steps}
     cpu = None
@@ -450,6 +455,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-fusion", action="store_true", help="one kernel per step for every format")
+    ap.add_argument("--batch-count", type=int, default=512, help="lattices in the batch leg")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-budget", type=float, default=60.0, help="surrogate training seconds")
     ap.add_argument("--cpu-steps", type=int, default=100)
