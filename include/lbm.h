@@ -96,6 +96,20 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const d
  * steps_per_pass = 1 always uses one kernel per step. */
 lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t rows_per_block);
 
+/* FP64 arithmetic split (LBM_F64 storage only; no counterpart in the paper, whose
+ * scheme this does not change).  The FP64 step needs 35 additions and 12 fused
+ * multiply-adds per node and GB300 issues FP64 operations at 2 per clock per SM,
+ * so the step is bound by the FP64 pipe.  At level > 0 a set of the additions is
+ * computed exactly (IEEE 754 binary64, round to nearest even) on the integer
+ * pipes, in parallel with the FP64 pipe; results are bit-identical to level 0.
+ * Lanes whose operands leave the exact integer path (subnormal, infinite or NaN
+ * results) recompute on the FP64 pipe.  Levels 1..7 select different sets of
+ * additions (level 1: the 10 pair sums and the 5 sums U, the fastest measured
+ * and the default); level 0 runs every operation on the FP64 pipe.  Applies to
+ * steps without body load and with omega = 2; other steps use the FP64 pipe
+ * only.  A level outside [0, 7] returns LBM_ERR_ARG. */
+lbm_status lbm_set_fp64_split(lbm_ctx* ctx, int32_t level);
+
 /* Relaxation rate of the BGK collision (Eq. collision); the paper's scheme is
  * omega = 2 (the default), the only value with second-order consistency
  * (Sec. 4.1).  Other values give a first-order, dissipative control scheme whose

@@ -45,8 +45,15 @@ lbm_status lbm_nn_conv_backward_weight(const float* dy, int32_t Cout, const floa
                                        int32_t C2, int32_t B, int32_t H, int32_t W, int32_t KS, float* dw,
                                        int32_t beta, void* workspace, int64_t workspace_bytes, void* stream);
 
-/* db[c] = sum over P pixels of dy[p][c]. */
-lbm_status lbm_nn_bias_grad(const float* dy, int64_t P, int32_t C, float* db, void* stream);
+/* Workspace (device bytes) lbm_nn_bias_grad needs for P pixels and C channels. */
+int64_t lbm_nn_bias_grad_workspace_bytes(int64_t P, int32_t C);
+
+/* db[c] = sum over P pixels of dy[p][c] (dy: [P][C] FP32, device).  Two passes in a
+ * fixed order (per-block partials in `workspace`, then their sum), so results are
+ * reproducible.  workspace_bytes below lbm_nn_bias_grad_workspace_bytes(P, C), null
+ * pointers or P, C <= 0 return LBM_ERR_ARG. */
+lbm_status lbm_nn_bias_grad(const float* dy, int64_t P, int32_t C, float* db, void* workspace,
+                            int64_t workspace_bytes, void* stream);
 
 /* wt[ci][KS*KS-1-tap][co] = w[co][tap][ci]: with it, lbm_nn_conv_forward of dy gives the data gradient. */
 lbm_status lbm_nn_weight_flip(const void* w_bf16, int32_t Cout, int32_t Cin, int32_t KS, void* wt_bf16, void* stream);

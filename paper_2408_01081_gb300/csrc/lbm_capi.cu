@@ -126,6 +126,7 @@ struct lbm_ctx {
     double neq_scale = 1.0;      // moment-space storage: scale of the stored deviations
     int fuse = 1;                // steps per pass over memory when the fused kernel applies
     int tb_rows = 64;            // rows per block of the fused kernel
+    int split = 1;               // FP64: split level (which additions run on the integer pipes)
 };
 
 namespace {
@@ -392,6 +393,14 @@ lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t row
     return LBM_OK;
 }
 
+lbm_status lbm_set_fp64_split(lbm_ctx* ctx, int32_t level)
+{
+    LBM_CHECK_CTX(ctx);
+    if (level < 0 || level > 7) return fail(ctx, LBM_ERR_ARG, "split level must be in [0, 7]");
+    ctx->split = level;
+    return LBM_OK;
+}
+
 lbm_status lbm_set_relaxation(lbm_ctx* ctx, double omega)
 {
     LBM_CHECK_CTX(ctx);
@@ -538,7 +547,9 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
     if (ctx->g && ctx->m + n > ctx->gnt)
         return fail(ctx, LBM_ERR_STATE, "Dirichlet table has no row for the requested step");
     const KindOps* ops = ctx->ops;
-    const int nchunk = (ctx->p.nx + ops->vec - 1) / ops->vec;
+    const bool split = ctx->p.storage == LBM_F64 && ctx->split > 0 && ctx->R == 0 && ctx->omega == 2.0;
+    const int vec = split ? ops->vec_split : ops->vec;
+    const int nchunk = (ctx->p.nx + vec - 1) / vec;
     int bx = (nchunk + 31) / 32 * 32;
     if (bx > 256) bx = 256;
     const dim3 block(bx), grid((nchunk + bx - 1) / bx, ctx->p.ny);
@@ -561,7 +572,8 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
     A.neq_scale = ctx->neq_scale;
     const int variant = (ctx->p.bc == LBM_DIRICHLET ? lbmh::STEP_DIRICHLET : 0) |
                         (ctx->R > 0 ? lbmh::STEP_FORCING : 0) | (ctx->w ? lbmh::STEP_TRACK : 0) |
-                        (ctx->omega != 2.0 ? lbmh::STEP_OMEGA : 0);
+                        (ctx->omega != 2.0 ? lbmh::STEP_OMEGA : 0) |
+                        (split ? ctx->split << lbmh::STEP_SPLIT_SHIFT : 0);
     // two steps per pass: population formats in FP32 / BF16 / FP16, omega = 2, no body load,
     // no displacement tracking, periodic or homogeneous Dirichlet
     const bool fusable = ctx->fuse == 2 &&

@@ -12,8 +12,32 @@
 
 namespace lbmh {
 
-// step variant bits
-enum { STEP_DIRICHLET = 1, STEP_FORCING = 2, STEP_TRACK = 4, STEP_OMEGA = 8 };
+// step variant bits; bits 4-6 hold the FP64 split level (0 = every addition on the FP64 pipe)
+enum { STEP_DIRICHLET = 1, STEP_FORCING = 2, STEP_TRACK = 4, STEP_OMEGA = 8, STEP_SPLIT_SHIFT = 4 };
+
+// additions moved to the integer pipes at split level 1..7, as bit masks over the
+// node's 35 additions (bit layout of lbmk::collide_split): 0-4 f*_(-1,0), 5-9
+// f*_(0,-1), 10-14 y-pair sums, 15-19 x-pair sums, 20-24 U, 25-29 / 30-34 U/2 + t.
+// On GB300 at 8192^2 (three 256-thread blocks per SM) level 1 ran at 1.36x the
+// FP64-pipe-only step, levels 2-5 at 1.30-1.34x, 6 at 1.12x, 7 at 1.23x.
+constexpr unsigned long long split_mask(int level)
+{
+    return level == 1 ? 0x001FFFC00ull    // 15: the pair sums and U (fastest measured, the default)
+         : level == 2 ? 0x001F07C1Full    // 15: f*_(-1,0), y-pair sums, U
+         : level == 3 ? 0x001F0FC1Full    // 16: f*_(-1,0), y-pair sums, U, x-pair sum 0
+         : level == 4 ? 0x001F003FFull    // 15: f*_(-1,0), f*_(0,-1), U
+         : level == 5 ? 0x000F07C1Full    // 14: f*_(-1,0), y-pair sums, U 0-3
+         : level == 6 ? 0x001FFFC1Full    // 20: f*_(-1,0), pair sums, U
+         : level == 7 ? 0x007F07C1Full    // 17: f*_(-1,0), y-pair sums, U, U/2 + t of (1,0) 0-1
+                      : 0ull;
+}
+
+constexpr int split_adds(int level)
+{
+    int n = 0;
+    for (unsigned long long m = split_mask(level); m; m >>= 1) n += (int)(m & 1);
+    return n;
+}
 
 struct KindOps {
     int kind;
@@ -36,6 +60,7 @@ struct KindOps {
     cudaError_t (*batch_occupancy)(int* blocks_per_sm);
     // two fused steps (FP32 / BF16 / FP16 populations only; others return cudaErrorNotSupported)
     cudaError_t (*tb2_step)(const lbmk::TbArgs&, bool dirichlet, dim3 grid, dim3 block, cudaStream_t s);
+    int vec_split;                 // nodes per thread of the FP64 split-level step kernels
 };
 
 extern const KindOps kind_ops_0;  // FP64

@@ -1,0 +1,120 @@
+// Exact binary64 addition on the integer pipes.
+//
+// GB300 executes FP64 arithmetic at 2 operations per clock per SM, while its
+// integer/logic pipes are nearly idle in the FP64 step kernel.  The step needs
+// 35 additions and 12 fused multiply-adds per node; moving part of the additions
+// to the integer pipes lets both kinds of pipe work at once.
+//
+// emu_add() returns the IEEE 754 binary64 sum of two numbers rounded to nearest,
+// ties to even (the rounding of the hardware add), computed from the bit patterns:
+// align the smaller significand with guard bits and a sticky bit, add or
+// subtract, normalise with a leading-zero count, round, repack.  Zero and
+// subnormal inputs are handled exactly.  Where the result would be subnormal,
+// infinite or NaN (or an input is infinite or NaN) the flag `ok` is cleared and
+// the caller recomputes with the hardware instruction, so whenever `ok` stays
+// set the result is bit-identical to the hardware sum.
+//
+// emu_half_add(u, t) returns round(u/2 + t), the value of fma(0.5, u, t): u/2 is
+// exact for normal u with exponent field >= 2 (its exponent field minus one) and
+// for zero; other u clear `ok`.
+//
+// The header also compiles as plain C++ (host), where its results are checked
+// against the host's hardware addition.
+#pragma once
+
+#ifdef __CUDACC__
+#define EMU_HD __host__ __device__ __forceinline__
+#else
+#define EMU_HD inline
+#endif
+
+namespace lbmemu {
+
+typedef unsigned long long u64;
+
+EMU_HD int clz64(u64 x)
+{
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)x);
+#else
+    return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+EMU_HD u64 emu_add_bits(u64 ua, u64 ub, bool& ok)
+{
+    const u64 SIGN = 0x8000000000000000ull, FRAC = 0x000FFFFFFFFFFFFFull, HID = 0x0010000000000000ull;
+    const u64 xa = ua & ~SIGN, xb = ub & ~SIGN;
+    const bool sw = xb > xa;                        // order by magnitude: |h| >= |l|
+    const u64 h = sw ? ub : ua, l = sw ? ua : ub;
+    const u64 xh = sw ? xb : xa, xl = sw ? xa : xb;
+    const int eh = (int)(xh >> 52), el = (int)(xl >> 52);
+    const bool finite_in = eh < 2047;
+    // significands with the hidden bit (none for zero / subnormal, whose
+    // exponent acts as 1), placed at bits 62..10 to leave guard bits below
+    const u64 mh = ((xh & FRAC) | (eh ? HID : 0ull)) << 10;
+    const u64 ml = ((xl & FRAC) | (el ? HID : 0ull)) << 10;
+    const int e = eh + (eh == 0);
+    int d = e - (el + (el == 0));
+    d = d > 63 ? 63 : d;
+    u64 al = ml >> d;
+    al |= (u64)((al << d) != ml);                   // sticky bit of what was shifted out
+    const bool sub = ((h ^ l) & SIGN) != 0;
+    u64 s = sub ? mh - al : mh + al;
+    const bool zero = (s == 0);
+    const int lz = clz64(s | 1ull);                 // leading one to bit 63
+    s <<= lz;
+    const int er = e + 1 - lz;                      // exponent field of the result
+    const u64 rem = s & 0x7FFull;
+    u64 m = s >> 11;                                // 53-bit significand
+    m += (u64)((rem > 0x400ull) | ((rem == 0x400ull) & (unsigned)(m & 1ull)));
+    const u64 r = ((u64)(er - 1) << 52) + m;        // a carry out of m bumps the exponent
+    ok = ok && finite_in && (zero || (er >= 1 && (r >> 52) < 2047ull));
+    // an exact zero is +0, except -0 + -0
+    return zero ? (ua & ub & SIGN) : (r | (h & SIGN));
+}
+
+EMU_HD u64 emu_half_bits(u64 u, bool& ok)
+{
+    const u64 SIGN = 0x8000000000000000ull;
+    const u64 x = u & ~SIGN;
+    const u64 eu = x >> 52;
+    ok = ok && ((eu >= 2 && eu < 2047) || x == 0);
+    return (x == 0) ? u : u - (1ull << 52);
+}
+
+#ifdef __CUDACC__
+// Bit pattern of a double through inline asm: with a plain reinterpretation the
+// compiler recognises masking / flipping the sign bit as fabs / negation and
+// emits them as FP64 instructions, which is what this path is meant to avoid.
+__device__ __forceinline__ u64 bits_of(double x)
+{
+    u64 u;
+    asm("mov.b64 %0, %1;" : "=l"(u) : "d"(x));
+    return u;
+}
+
+__device__ __forceinline__ double double_of(u64 u)
+{
+    double x;
+    asm("mov.b64 %0, %1;" : "=d"(x) : "l"(u));
+    return x;
+}
+
+__device__ __forceinline__ double emu_add(double a, double b, bool& ok)
+{
+    return double_of(emu_add_bits(bits_of(a), bits_of(b), ok));
+}
+
+__device__ __forceinline__ double emu_sub(double a, double b, bool& ok)
+{
+    return double_of(emu_add_bits(bits_of(a), bits_of(b) ^ 0x8000000000000000ull, ok));
+}
+
+__device__ __forceinline__ double emu_half_add(double u, double t, bool& ok)
+{
+    return double_of(emu_add_bits(emu_half_bits(bits_of(u), ok), bits_of(t), ok));
+}
+#endif
+
+}  // namespace lbmemu

@@ -14,9 +14,12 @@
 // and since the four outputs of one axis sum to U - (the other axis' pair),
 //     f*_{-1,0} = (U - f_{1,0} - f_{-1,0}) - f*_{1,0},
 //     f*_{0,-1} = (U - f_{0,1} - f_{0,-1}) - f*_{0,1}.
-// That is 47 FP64 operations per node without forcing, the FP64 ALU bound on GB300.
+// That is 47 FP64 operations per node without forcing (35 additions, 12 fused
+// multiply-adds), the FP64 ALU bound on GB300; the SPLIT variants compute part of
+// the additions exactly on the integer pipes (collide_split).
 #pragma once
 
+#include "lbm_f64emu.cuh"
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -123,27 +126,133 @@ struct StepArgs {
 
 // Collision with omega = 2 for one node.  f[d][k] pulled pre-collision values,
 // U already holds sum_d f_d + dt/2 B; rx = U - f0 - f2, ry = U - f1 - f3 per component.
+// Phi terms with the population subtracted: t[0][k] = Phi_x(U)_k / c - f_(1,0),k and
+// t[1][k] = Phi_y(U)_k / c - f_(0,1),k, so that f*_(1,0) = U/2 + t[0], f*_(0,1) = U/2 + t[1];
+// Phi_x = [cK js + cmu jd, cmu jxy, cK vx, cmu vx, cmu vy], Phi_y = [cmu jxy, cK js - cmu jd, cK vy, -cmu vy, cmu vx]
+template <typename M>
+__device__ __forceinline__ void collide_terms(const M (&f)[4][5], const M (&U)[5], M a, M b, M (&t)[2][5])
+{
+    t[0][0] = fma(a, U[2], fma(b, U[3], -f[0][0]));
+    t[0][1] = fma(b, U[4], -f[0][1]);
+    t[0][2] = fma(a, U[0], -f[0][2]);
+    t[0][3] = fma(b, U[0], -f[0][3]);
+    t[0][4] = fma(b, U[1], -f[0][4]);
+    t[1][0] = fma(b, U[4], -f[1][0]);
+    t[1][1] = fma(a, U[2], fma(-b, U[3], -f[1][1]));
+    t[1][2] = fma(a, U[1], -f[1][2]);
+    t[1][3] = fma(-b, U[1], -f[1][3]);
+    t[1][4] = fma(b, U[0], -f[1][4]);
+}
+
+// omega = 2 collision (Eqs. feq, collision) in the 47-operation form:
+// f*_(1,0) = U/2 + Phi_x/c - f_(1,0), f*_(0,1) = U/2 + Phi_y/c - f_(0,1), and the
+// opposite directions from the pair sums, f*_(-1,0) = (f_(0,1) + f_(0,-1)) - f*_(1,0)
+// (the pair sums of rx / ry are the other axis' populations), likewise (0,-1).
 template <typename M>
 __device__ __forceinline__ void collide(const M (&f)[4][5], const M (&U)[5], const M (&rx)[5],
                                         const M (&ry)[5], M a, M b, M (&o)[4][5])
 {
     const M h = M(0.5);
-    // (1,0): 1/2 U + Phi_x(U)/c - f ; Phi_x = [cK js + cmu jd, cmu jxy, cK vx, cmu vx, cmu vy]
-    o[0][0] = fma(h, U[0], fma(a, U[2], fma(b, U[3], -f[0][0])));
-    o[0][1] = fma(h, U[1], fma(b, U[4], -f[0][1]));
-    o[0][2] = fma(h, U[2], fma(a, U[0], -f[0][2]));
-    o[0][3] = fma(h, U[3], fma(b, U[0], -f[0][3]));
-    o[0][4] = fma(h, U[4], fma(b, U[1], -f[0][4]));
-    // (0,1): 1/2 U + Phi_y(U)/c - f ; Phi_y = [cmu jxy, cK js - cmu jd, cK vy, -cmu vy, cmu vx]
-    o[1][0] = fma(h, U[0], fma(b, U[4], -f[1][0]));
-    o[1][1] = fma(h, U[1], fma(a, U[2], fma(-b, U[3], -f[1][1])));
-    o[1][2] = fma(h, U[2], fma(a, U[1], -f[1][2]));
-    o[1][3] = fma(h, U[3], fma(-b, U[1], -f[1][3]));
-    o[1][4] = fma(h, U[4], fma(b, U[0], -f[1][4]));
+    M t[2][5];
+    collide_terms<M>(f, U, a, b, t);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        o[0][k] = fma(h, U[k], t[0][k]);
+        o[1][k] = fma(h, U[k], t[1][k]);
+    }
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         o[2][k] = rx[k] - o[0][k];   // (-1,0)
         o[3][k] = ry[k] - o[1][k];   // (0,-1)
+    }
+}
+
+template <bool EMU>
+__device__ __forceinline__ double split_add(double x, double y, bool& ok)
+{
+    if constexpr (EMU) return lbmemu::emu_add(x, y, ok);
+    else return x + y;
+}
+
+template <bool EMU>
+__device__ __forceinline__ double split_sub(double x, double y, bool& ok)
+{
+    if constexpr (EMU) return lbmemu::emu_sub(x, y, ok);
+    else return x - y;
+}
+
+template <bool EMU>
+__device__ __forceinline__ double split_half_add(double u, double t, bool& ok)
+{
+    if constexpr (EMU) return lbmemu::emu_half_add(u, t, ok);
+    else return fma(0.5, u, t);
+}
+
+// component k of the split update (the addition indices are compile-time constants)
+template <unsigned long long M, int k>
+__device__ __forceinline__ void split_sums(const double (&f)[4][5], double (&rx)[5], double (&ry)[5],
+                                           double (&U)[5], bool& ok)
+{
+    rx[k] = split_add<((M >> (10 + k)) & 1) != 0>(f[1][k], f[3][k], ok);
+    ry[k] = split_add<((M >> (15 + k)) & 1) != 0>(f[0][k], f[2][k], ok);
+    U[k] = split_add<((M >> (20 + k)) & 1) != 0>(rx[k], ry[k], ok);
+}
+
+template <unsigned long long M, int k>
+__device__ __forceinline__ void split_outputs(const double (&U)[5], const double (&rx)[5], const double (&ry)[5],
+                                              const double (&t)[2][5], double (&o)[4][5], bool& ok)
+{
+    o[0][k] = split_half_add<((M >> (25 + k)) & 1) != 0>(U[k], t[0][k], ok);
+    o[1][k] = split_half_add<((M >> (30 + k)) & 1) != 0>(U[k], t[1][k], ok);
+    o[2][k] = split_sub<((M >> k) & 1) != 0>(rx[k], o[0][k], ok);
+    o[3][k] = split_sub<((M >> (5 + k)) & 1) != 0>(ry[k], o[1][k], ok);
+}
+
+// The same FP64 node update (pair sums, U, collision; no body load) with the
+// additions selected by the bits of M computed exactly on the integer pipes
+// (lbm_f64emu.cuh) and the rest, with the 12 fused multiply-adds, on the FP64
+// pipe.  Bits: f*_(-1,0) (0-4), f*_(0,-1) (5-9), y-pair sums (10-14), x-pair sums
+// (15-19), U (20-24), U/2 + t for (1,0) (25-29) and (0,1) (30-34), component k at
+// offset k.  Every result is bit-identical to collide<double>; a lane whose
+// operands leave the exact integer path (a subnormal, infinite or NaN result)
+// recomputes on the FP64 pipe.
+template <unsigned long long M>
+__device__ __forceinline__ void collide_split(const double (&f)[4][5], double a, double b, double (&U)[5],
+                                              double (&o)[4][5])
+{
+    bool ok = true;
+    double rx[5], ry[5];
+    split_sums<M, 0>(f, rx, ry, U, ok);
+    split_sums<M, 1>(f, rx, ry, U, ok);
+    split_sums<M, 2>(f, rx, ry, U, ok);
+    split_sums<M, 3>(f, rx, ry, U, ok);
+    split_sums<M, 4>(f, rx, ry, U, ok);
+    double t[2][5];
+    collide_terms<double>(f, U, a, b, t);
+    split_outputs<M, 0>(U, rx, ry, t, o, ok);
+    split_outputs<M, 1>(U, rx, ry, t, o, ok);
+    split_outputs<M, 2>(U, rx, ry, t, o, ok);
+    split_outputs<M, 3>(U, rx, ry, t, o, ok);
+    split_outputs<M, 4>(U, rx, ry, t, o, ok);
+    if (__any_sync(0xffffffffu, !ok)) {
+        if (!ok) {
+            // the copies through volatile asm keep the compiler from computing this
+            // FP64 path speculatively on every lane
+            double g[4][5], ga, gb;
+#pragma unroll
+            for (int d = 0; d < 4; ++d)
+#pragma unroll
+                for (int k = 0; k < 5; ++k) asm volatile("mov.b64 %0, %1;" : "=d"(g[d][k]) : "d"(f[d][k]));
+            asm volatile("mov.b64 %0, %1;" : "=d"(ga) : "d"(a));
+            asm volatile("mov.b64 %0, %1;" : "=d"(gb) : "d"(b));
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                rx[k] = g[1][k] + g[3][k];
+                ry[k] = g[0][k] + g[2][k];
+                U[k] = rx[k] + ry[k];
+            }
+            collide<double>(g, U, rx, ry, ga, gb, o);
+        }
     }
 }
 
@@ -166,9 +275,12 @@ __device__ __forceinline__ void wall_source(int i, int j, double gx, double gy, 
 #ifndef LBM_STEP_MIN_BLOCKS
 #define LBM_STEP_MIN_BLOCKS 1
 #endif
+#ifndef LBM_SPLIT_MIN_BLOCKS
+#define LBM_SPLIT_MIN_BLOCKS 3      // 80 registers: more warps to overlap the two pipes
+#endif
 
-template <int K, int V, bool DIRICHLET, bool FORCING, bool TRACK, bool OMEGA = false>
-__global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS)
+template <int K, int V, bool DIRICHLET, bool FORCING, bool TRACK, bool OMEGA = false, unsigned long long SPLIT = 0>
+__global__ void __launch_bounds__(256, SPLIT > 0 ? LBM_SPLIT_MIN_BLOCKS : LBM_STEP_MIN_BLOCKS)
 step_kernel(StepArgs A)
 {
     using E = typename Fmt<K>::E;
@@ -287,47 +399,51 @@ step_kernel(StepArgs A)
             }
         }
         M U[5], rx[5], ry[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            const M sx = f[0][k] + f[2][k];
-            const M sy = f[1][k] + f[3][k];
-            rx[k] = sy;
-            ry[k] = sx;
-        }
-        if (FORCING) {
-            // body load in the arithmetic type (FP32 tables for the reduced formats)
-            M bx = M(0), by = M(0);
-            if (x < nx) {
-                if constexpr (sizeof(M) == 8) {
-                    for (int r = 0; r < A.R; ++r) {
-                        const M xy = A.X[(long long)r * nx + x] * A.Y[(long long)r * ny + y];
-                        bx = fma(xy, A.T[r], bx);
-                        by = fma(xy, A.T[A.R + r], by);
-                    }
-                } else {
-                    for (int r = 0; r < A.R; ++r) {
-                        const M xy = A.Xf[(long long)r * nx + x] * A.Yf[(long long)r * ny + y];
-                        bx = fma(xy, A.Tf[r], bx);
-                        by = fma(xy, A.Tf[A.R + r], by);
-                    }
-                }
-            }
-            bxs[e] = (double)bx;
-            bys[e] = (double)by;
-            rx[0] = fma(M(0.5 * A.dt), bx, rx[0]);
-            rx[1] = fma(M(0.5 * A.dt), by, rx[1]);
-            ry[0] = fma(M(0.5 * A.dt), bx, ry[0]);
-            ry[1] = fma(M(0.5 * A.dt), by, ry[1]);
-            U[0] = rx[0] + (f[0][0] + f[2][0]);
-            U[1] = rx[1] + (f[0][1] + f[2][1]);
-#pragma unroll
-            for (int k = 2; k < 5; ++k) U[k] = rx[k] + ry[k];
+        M o[4][5];
+        if constexpr (SPLIT > 0 && sizeof(M) == 8 && !FORCING && !OMEGA) {
+            collide_split<SPLIT>(f, a, b, U, o);
         } else {
 #pragma unroll
-            for (int k = 0; k < 5; ++k) U[k] = rx[k] + ry[k];
+            for (int k = 0; k < 5; ++k) {
+                const M sx = f[0][k] + f[2][k];
+                const M sy = f[1][k] + f[3][k];
+                rx[k] = sy;
+                ry[k] = sx;
+            }
+            if (FORCING) {
+                // body load in the arithmetic type (FP32 tables for the reduced formats)
+                M bx = M(0), by = M(0);
+                if (x < nx) {
+                    if constexpr (sizeof(M) == 8) {
+                        for (int r = 0; r < A.R; ++r) {
+                            const M xy = A.X[(long long)r * nx + x] * A.Y[(long long)r * ny + y];
+                            bx = fma(xy, A.T[r], bx);
+                            by = fma(xy, A.T[A.R + r], by);
+                        }
+                    } else {
+                        for (int r = 0; r < A.R; ++r) {
+                            const M xy = A.Xf[(long long)r * nx + x] * A.Yf[(long long)r * ny + y];
+                            bx = fma(xy, A.Tf[r], bx);
+                            by = fma(xy, A.Tf[A.R + r], by);
+                        }
+                    }
+                }
+                bxs[e] = (double)bx;
+                bys[e] = (double)by;
+                rx[0] = fma(M(0.5 * A.dt), bx, rx[0]);
+                rx[1] = fma(M(0.5 * A.dt), by, rx[1]);
+                ry[0] = fma(M(0.5 * A.dt), bx, ry[0]);
+                ry[1] = fma(M(0.5 * A.dt), by, ry[1]);
+                U[0] = rx[0] + (f[0][0] + f[2][0]);
+                U[1] = rx[1] + (f[0][1] + f[2][1]);
+#pragma unroll
+                for (int k = 2; k < 5; ++k) U[k] = rx[k] + ry[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) U[k] = rx[k] + ry[k];
+            }
+            collide<M>(f, U, rx, ry, a, b, o);
         }
-        M o[4][5];
-        collide<M>(f, U, rx, ry, a, b, o);
         if (OMEGA) {
             // omega f^eq + (1 - omega) f + dt (2 - omega) W B  =  (omega/2) o + (1 - omega/2) f + forcing,
             // with o the omega = 2 result and W = 1/8

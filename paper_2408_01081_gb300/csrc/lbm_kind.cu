@@ -17,6 +17,9 @@ namespace {
 #ifndef LBM_VEC_F16
 #define LBM_VEC_F16 4
 #endif
+#ifndef LBM_VEC_SPLIT
+#define LBM_VEC_SPLIT 1
+#endif
 
 constexpr int K = LBM_KIND;
 constexpr bool MS = (K >= lbmk::K_MSBF16);
@@ -25,12 +28,34 @@ constexpr int V = (K == lbmk::K_F64) ? LBM_VEC_F64 : (K == lbmk::K_F32) ? LBM_VE
 constexpr int ELEM = (K == lbmk::K_F64) ? 8 : (K == lbmk::K_F32) ? 4 : 2;
 constexpr int NODE_BYTES = MS ? 5 * 4 + 15 * 2 : 20 * ELEM;
 
-template <bool D, bool F, bool T, bool O>
+template <bool D, bool F, bool T, bool O, unsigned long long SPLIT = 0>
 cudaError_t step_v(const lbmk::StepArgs& a, dim3 g, dim3 b, cudaStream_t s)
 {
     if constexpr (MS) lbmk::ms_step_kernel<K, V, D, F, T, O><<<g, b, 0, s>>>(a);
+    else if constexpr (SPLIT > 0) lbmk::step_kernel<K, LBM_VEC_SPLIT, D, F, T, O, SPLIT><<<g, b, 0, s>>>(a);
     else lbmk::step_kernel<K, V, D, F, T, O><<<g, b, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+// FP64 without body load and with omega = 2: the number of the node's 35
+// additions computed on the integer pipes (lbmh::split_adds of the level)
+template <bool D, bool T>
+cudaError_t step_split(const lbmk::StepArgs& a, int level, dim3 g, dim3 b, cudaStream_t s)
+{
+    if constexpr (K != lbmk::K_F64) {
+        return cudaErrorNotSupported;
+    } else {
+        switch (level) {
+        case 1: return step_v<D, false, T, false, lbmh::split_mask(1)>(a, g, b, s);
+        case 2: return step_v<D, false, T, false, lbmh::split_mask(2)>(a, g, b, s);
+        case 3: return step_v<D, false, T, false, lbmh::split_mask(3)>(a, g, b, s);
+        case 4: return step_v<D, false, T, false, lbmh::split_mask(4)>(a, g, b, s);
+        case 5: return step_v<D, false, T, false, lbmh::split_mask(5)>(a, g, b, s);
+        case 6: return step_v<D, false, T, false, lbmh::split_mask(6)>(a, g, b, s);
+        case 7: return step_v<D, false, T, false, lbmh::split_mask(7)>(a, g, b, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
 }
 
 template <bool O>
@@ -50,6 +75,12 @@ cudaError_t step_o(const lbmk::StepArgs& a, int variant, dim3 g, dim3 b, cudaStr
 
 cudaError_t step(const lbmk::StepArgs& a, int variant, dim3 g, dim3 b, cudaStream_t s)
 {
+    const int level = (variant >> lbmh::STEP_SPLIT_SHIFT) & 7;
+    if (level && !(variant & (lbmh::STEP_FORCING | lbmh::STEP_OMEGA))) {
+        const bool d = variant & lbmh::STEP_DIRICHLET, t = variant & lbmh::STEP_TRACK;
+        return d ? (t ? step_split<true, true>(a, level, g, b, s) : step_split<true, false>(a, level, g, b, s))
+                 : (t ? step_split<false, true>(a, level, g, b, s) : step_split<false, false>(a, level, g, b, s));
+    }
     return (variant & lbmh::STEP_OMEGA) ? step_o<true>(a, variant, g, b, s) : step_o<false>(a, variant, g, b, s);
 }
 
@@ -170,6 +201,7 @@ namespace lbmh {
 const KindOps LBM_OPS_NAME(LBM_KIND) = {
     K, V, ELEM, NODE_BYTES,
     step, init, moments, get_pop, set_pop, energy, error, finite, batch_step, batch_occupancy, tb2_step,
+    LBM_VEC_SPLIT,
 };
 
 }  // namespace lbmh

@@ -200,8 +200,149 @@ __global__ void __launch_bounds__(256) conv_fwd_kernel(ConvArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// 3x3 convolution on an 8 x 16 pixel tile (H >= 8, W >= 16): the input tile with
+// its one-pixel halo (10 x 18 pixels) is staged once per 32-channel chunk as
+// BF16 hi / lo, the weights of all nine taps once per chunk, and every tap reads
+// its A fragments from the halo tile at the tap's offset (ldmatrix).  Same
+// arithmetic as conv_fwd_kernel; warps: 4 along the tile rows (2 rows = 2 m16
+// tiles each) x 2 along the output channels.
+// ---------------------------------------------------------------------------
+constexpr int TH = 8, TW = 16;                  // output tile (pixels)
+constexpr int HH = TH + 2, HW2 = TW + 2;        // halo tile
+constexpr int KROW = CKC + CPAD;                // smem row: 40 bf16 = 80 bytes
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __nv_bfloat16* p)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a)
+                 : "memory");
+}
+
+template <int BN>
+constexpr int conv3_tile_smem_bytes()
+{
+    return (2 * HH * HW2 + 9 * BN) * KROW * (int)sizeof(__nv_bfloat16);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(256) conv3_tile_kernel(ConvArgs a)
+{
+    extern __shared__ __align__(16) __nv_bfloat16 smem[];
+    __nv_bfloat16* Ah = smem;                            // [HH*HW2][KROW]
+    __nv_bfloat16* Al = Ah + HH * HW2 * KROW;            // [HH*HW2][KROW]
+    __nv_bfloat16* Bs = Al + HH * HW2 * KROW;            // [9][BN][KROW]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int wm = warp & 3;                 // tile rows 2 wm, 2 wm + 1
+    const int wn = warp >> 2;                // output-channel half
+    constexpr int WN = BN / 2;
+    constexpr int NT = WN / 8;               // n8 tiles per warp (even)
+    const int tiles_x = a.W / TW, tiles_y = a.H / TH;
+    const int tile = blockIdx.x;
+    const int n = tile / (tiles_x * tiles_y);
+    const int ty0 = ((tile / tiles_x) % tiles_y) * TH, tx0 = (tile % tiles_x) * TW;
+    const int co0 = blockIdx.y * BN;
+    const int Cin = a.C1 + a.C2;
+
+    float acc[2][NT][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+    for (int ci0 = 0; ci0 < Cin; ci0 += CKC) {
+        // --- stage the halo tile: 180 pixels x 32 channels, FP32 -> BF16 hi / lo ---
+        const float* base = (ci0 < a.C1) ? a.x1 : a.x2;
+        const int cstride = (ci0 < a.C1) ? a.C1 : a.C2;
+        const int coff = (ci0 < a.C1) ? ci0 : ci0 - a.C1;
+        for (int q = tid; q < HH * HW2 * (CKC / 4); q += 256) {
+            const int hp = q >> 3, c4 = (q & 7) * 4;
+            const int hy = hp / HW2, hx = hp % HW2;
+            const int sy = (ty0 + hy - 1) & (a.H - 1), sx = (tx0 + hx - 1) & (a.W - 1);
+            const long long spix = ((long long)n * a.H + sy) * a.W + sx;
+            const float4 v = *reinterpret_cast<const float4*>(base + spix * cstride + coff + c4);
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(v.x), h1 = __float2bfloat16_rn(v.y);
+            const __nv_bfloat16 h2 = __float2bfloat16_rn(v.z), h3 = __float2bfloat16_rn(v.w);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(v.x - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(v.y - __bfloat162float(h1));
+            const __nv_bfloat16 l2 = __float2bfloat16_rn(v.z - __bfloat162float(h2));
+            const __nv_bfloat16 l3 = __float2bfloat16_rn(v.w - __bfloat162float(h3));
+            *reinterpret_cast<uint2*>(Ah + hp * KROW + c4) = make_uint2(pack_bf16(h0, h1), pack_bf16(h2, h3));
+            *reinterpret_cast<uint2*>(Al + hp * KROW + c4) = make_uint2(pack_bf16(l0, l1), pack_bf16(l2, l3));
+        }
+        // --- stage the weights of the nine taps: BN x 32 inputs each ---
+        for (int q = tid; q < 9 * BN * 4; q += 256) {
+            const int tap = q / (BN * 4), r = q % (BN * 4);
+            const int nn = r >> 2, part = r & 3;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (co0 + nn < a.Cout)
+                val = *reinterpret_cast<const uint4*>(a.w + ((long long)(co0 + nn) * 9 + tap) * Cin + ci0 + part * 8);
+            *reinterpret_cast<uint4*>(Bs + (tap * BN + nn) * KROW + part * 8) = val;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3;     // halo offsets (0..2)
+#pragma unroll
+            for (int kk = 0; kk < CKC; kk += 16) {
+                uint32_t fh[2][4], fl[2][4];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int hp = (2 * wm + i + dy) * HW2 + (lane & 15) + dx;
+                    const int kc = kk + (lane >> 4) * 8;
+                    ldsm_x4(fh[i], Ah + hp * KROW + kc);
+                    ldsm_x4(fl[i], Al + hp * KROW + kc);
+                }
+#pragma unroll
+                for (int j = 0; j < NT; j += 2) {
+                    uint32_t fb[4];
+                    const int nn = wn * WN + j * 8 + (lane & 7) + ((lane >> 4) << 3);
+                    ldsm_x4(fb, Bs + (tap * BN + nn) * KROW + kk + ((lane >> 3) & 1) * 8);
+                    const uint32_t b0[2] = {fb[0], fb[1]}, b1[2] = {fb[2], fb[3]};
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        mma_bf16(acc[i][j], fh[i], b0);
+                        mma_bf16(acc[i][j], fl[i], b0);
+                        mma_bf16(acc[i][j + 1], fh[i], b1);
+                        mma_bf16(acc[i][j + 1], fl[i], b1);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // --- epilogue: bias, activation, store (optionally accumulate) ---
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int oy = ty0 + 2 * wm + i, ox = tx0 + g + 8 * h;
+            const long long p = ((long long)n * a.H + oy) * a.W + ox;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const int co = co0 + wn * WN + j * 8 + 2 * t4;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int c = co + e;
+                    if (c >= a.Cout) continue;
+                    float v = acc[i][j][2 * h + e];
+                    if (a.bias) v += a.bias[c];
+                    if (a.relu) v = fmaxf(v, 0.f);
+                    float* dst = (c < a.Co1) ? a.y1 + p * a.Co1 + c : a.y2 + p * (a.Cout - a.Co1) + (c - a.Co1);
+                    *dst = a.beta ? *dst + v : v;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // weight gradient: dW[co][tap][ci] = sum_p dY[p][co] X[p + tap][ci]
-// CTA tile 64 (co) x 64 (ci of one tap), K = pixels in chunks of 32, split over
+// CTA tile 64 (co) x 64 (ci of one tap), K = pixels in chunks of 64, split over
 // pixel ranges (gridDim.z); partial[split][co][tap][ci] reduced in fixed order.
 // ---------------------------------------------------------------------------
 struct WgradArgs {
@@ -212,14 +353,30 @@ struct WgradArgs {
     int B, H, W, KS;
     int pix_per_split;
     float* partial;           // [splits][Cout][KS*KS][Cin]
+    int lw, lhw;              // log2(W), log2(H W)
 };
 
+constexpr int WK = 64;                 // pixels per staged chunk
+constexpr int WROW = 64 + 8;           // smem row of 64 channels (+8 pad): 144 bytes
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const __nv_bfloat16* p)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a)
+                 : "memory");
+}
+
+// staging of one 64-pixel chunk: dY[p][co0 .. co0+63] and X[p + tap][ci0 .. ci0+63] as
+// BF16 hi / lo in their natural [pixel][channel] layout (16-byte vector loads); the
+// MMA fragments are read transposed with ldmatrix.trans
 __global__ void __launch_bounds__(256) conv_wgrad_kernel(WgradArgs a)
 {
-    __shared__ __align__(16) __nv_bfloat16 Ah[64][32 + CPAD];
-    __shared__ __align__(16) __nv_bfloat16 Al[64][32 + CPAD];
-    __shared__ __align__(16) __nv_bfloat16 Bh[64][32 + CPAD];
-    __shared__ __align__(16) __nv_bfloat16 Bl[64][32 + CPAD];
+    __shared__ __align__(16) __nv_bfloat16 Yh[WK][WROW];
+    __shared__ __align__(16) __nv_bfloat16 Yl[WK][WROW];
+    __shared__ __align__(16) __nv_bfloat16 Xh[WK][WROW];
+    __shared__ __align__(16) __nv_bfloat16 Xl[WK][WROW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t4 = lane & 3;
     const int wm = warp & 1;                 // 2 warps along M (32 co each)
@@ -233,7 +390,6 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(WgradArgs a)
     const int R = a.KS / 2;
     const int dy = tap / a.KS - R, dx = tap % a.KS - R;
     const int P = a.B * a.H * a.W;
-    const int HW = a.H * a.W;
     const int pbeg = blockIdx.z * a.pix_per_split;
     const int pend = min(P, pbeg + a.pix_per_split);
 
@@ -245,66 +401,85 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(WgradArgs a)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
 
-    // staging: thread -> (pixel k = tid / 8, 8 channels at (tid % 8) * 8)
-    const int sk = tid >> 3, sc = (tid & 7) * 8;
-    for (int pc = pbeg; pc < pend; pc += 32) {
-        const int p = pc + sk;
-        float vy[8], vx[8];
-        if (p < pend) {
-            const int n = p / HW, y = (p / a.W) & (a.H - 1), x = p & (a.W - 1);
-            const long long sp = ((long long)n * a.H + ((y + dy) & (a.H - 1))) * a.W + ((x + dx) & (a.W - 1));
+    // 64 pixels x 16 float4 per tensor per chunk: 4 of each per thread, loaded one
+    // chunk ahead into registers while the tensor cores work on the current one
+    float4 ry[4], rx[4];
+    auto load_chunk = [&](int pc) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int co = co0 + sc + q;
-                vy[q] = (co < a.Cout) ? a.dy[(long long)p * a.Cout + co] : 0.f;
-                const int ci = ci0 + sc + q;
-                float xv = 0.f;
-                if (ci < a.C1) xv = a.x1[sp * a.C1 + ci];
-                else if (ci < Cin) xv = a.x2[sp * a.C2 + (ci - a.C1)];
-                vx[q] = xv;
+        for (int rep = 0; rep < 4; ++rep) {
+            const int q = tid + rep * 256;
+            const int pk = q >> 4, c4 = (q & 15) * 4;
+            const int p = pc + pk;
+            ry[rep] = make_float4(0.f, 0.f, 0.f, 0.f);
+            rx[rep] = ry[rep];
+            if (p < pend) {
+                if (co0 + c4 < a.Cout)
+                    ry[rep] = *reinterpret_cast<const float4*>(a.dy + (long long)p * a.Cout + co0 + c4);
+                const int ci = ci0 + c4;
+                if (ci < Cin) {
+                    const int n = p >> a.lhw, y = (p >> a.lw) & (a.H - 1), x = p & (a.W - 1);
+                    const long long sp =
+                        (((long long)n << a.lhw) | ((long long)((y + dy) & (a.H - 1)) << a.lw)) | ((x + dx) & (a.W - 1));
+                    rx[rep] = (ci < a.C1) ? *reinterpret_cast<const float4*>(a.x1 + sp * a.C1 + ci)
+                                          : *reinterpret_cast<const float4*>(a.x2 + sp * a.C2 + (ci - a.C1));
+                }
             }
-        } else {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) vy[q] = vx[q] = 0.f;
         }
+    };
+    if (pbeg < pend) load_chunk(pbeg);
+    for (int pc = pbeg; pc < pend; pc += WK) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const __nv_bfloat16 yh = __float2bfloat16_rn(vy[q]);
-            const __nv_bfloat16 xh = __float2bfloat16_rn(vx[q]);
-            Ah[sc + q][sk] = yh;
-            Al[sc + q][sk] = __float2bfloat16_rn(vy[q] - __bfloat162float(yh));
-            Bh[sc + q][sk] = xh;
-            Bl[sc + q][sk] = __float2bfloat16_rn(vx[q] - __bfloat162float(xh));
+        for (int rep = 0; rep < 4; ++rep) {
+            const int q = tid + rep * 256;
+            const int pk = q >> 4, c4 = (q & 15) * 4;
+            const float4 vy = ry[rep], vx = rx[rep];
+            const __nv_bfloat16 y0 = __float2bfloat16_rn(vy.x), y1 = __float2bfloat16_rn(vy.y);
+            const __nv_bfloat16 y2 = __float2bfloat16_rn(vy.z), y3 = __float2bfloat16_rn(vy.w);
+            const __nv_bfloat16 x0 = __float2bfloat16_rn(vx.x), x1 = __float2bfloat16_rn(vx.y);
+            const __nv_bfloat16 x2 = __float2bfloat16_rn(vx.z), x3 = __float2bfloat16_rn(vx.w);
+            *reinterpret_cast<uint2*>(&Yh[pk][c4]) = make_uint2(pack_bf16(y0, y1), pack_bf16(y2, y3));
+            *reinterpret_cast<uint2*>(&Yl[pk][c4]) =
+                make_uint2(pack_bf16(__float2bfloat16_rn(vy.x - __bfloat162float(y0)),
+                                     __float2bfloat16_rn(vy.y - __bfloat162float(y1))),
+                           pack_bf16(__float2bfloat16_rn(vy.z - __bfloat162float(y2)),
+                                     __float2bfloat16_rn(vy.w - __bfloat162float(y3))));
+            *reinterpret_cast<uint2*>(&Xh[pk][c4]) = make_uint2(pack_bf16(x0, x1), pack_bf16(x2, x3));
+            *reinterpret_cast<uint2*>(&Xl[pk][c4]) =
+                make_uint2(pack_bf16(__float2bfloat16_rn(vx.x - __bfloat162float(x0)),
+                                     __float2bfloat16_rn(vx.y - __bfloat162float(x1))),
+                           pack_bf16(__float2bfloat16_rn(vx.z - __bfloat162float(x2)),
+                                     __float2bfloat16_rn(vx.w - __bfloat162float(x3))));
         }
+        if (pc + WK < pend) load_chunk(pc + WK);
         __syncthreads();
+        const int mi = lane >> 3, r8 = lane & 7;
 #pragma unroll
-        for (int kk = 0; kk < 32; kk += 16) {
+        for (int kk = 0; kk < WK; kk += 16) {
+            // A = dY^T (co x pixel): matrices (m, k), (m+8, k), (m, k+8), (m+8, k+8)
             uint32_t fah[2][4], fal[2][4];
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
-                const int r = wm * 32 + i * 16 + g;
-                fah[i][0] = *reinterpret_cast<const uint32_t*>(&Ah[r][kk + 2 * t4]);
-                fah[i][1] = *reinterpret_cast<const uint32_t*>(&Ah[r + 8][kk + 2 * t4]);
-                fah[i][2] = *reinterpret_cast<const uint32_t*>(&Ah[r][kk + 8 + 2 * t4]);
-                fah[i][3] = *reinterpret_cast<const uint32_t*>(&Ah[r + 8][kk + 8 + 2 * t4]);
-                fal[i][0] = *reinterpret_cast<const uint32_t*>(&Al[r][kk + 2 * t4]);
-                fal[i][1] = *reinterpret_cast<const uint32_t*>(&Al[r + 8][kk + 2 * t4]);
-                fal[i][2] = *reinterpret_cast<const uint32_t*>(&Al[r][kk + 8 + 2 * t4]);
-                fal[i][3] = *reinterpret_cast<const uint32_t*>(&Al[r + 8][kk + 8 + 2 * t4]);
+                const int m0 = wm * 32 + i * 16 + (mi & 1) * 8;
+                const int k0 = kk + (mi >> 1) * 8 + r8;
+                ldsm_x4_trans(fah[i], &Yh[k0][m0]);
+                ldsm_x4_trans(fal[i], &Yl[k0][m0]);
+            }
+            // B = X (pixel x ci): matrices (k, n), (k+8, n), (k, n+8), (k+8, n+8)
+            uint32_t fbh[4], fbl[4];
+            {
+                const int n0 = wn * 16 + (mi >> 1) * 8;
+                const int k0 = kk + (mi & 1) * 8 + r8;
+                ldsm_x4_trans(fbh, &Xh[k0][n0]);
+                ldsm_x4_trans(fbl, &Xl[k0][n0]);
             }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const int n = wn * 16 + j * 8 + g;
-                uint32_t fbh[2], fbl[2];
-                fbh[0] = *reinterpret_cast<const uint32_t*>(&Bh[n][kk + 2 * t4]);
-                fbh[1] = *reinterpret_cast<const uint32_t*>(&Bh[n][kk + 8 + 2 * t4]);
-                fbl[0] = *reinterpret_cast<const uint32_t*>(&Bl[n][kk + 2 * t4]);
-                fbl[1] = *reinterpret_cast<const uint32_t*>(&Bl[n][kk + 8 + 2 * t4]);
+                const uint32_t bh[2] = {fbh[2 * j], fbh[2 * j + 1]}, bl[2] = {fbl[2 * j], fbl[2 * j + 1]};
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
-                    mma_bf16(acc[i][j], fah[i], fbh);
-                    mma_bf16(acc[i][j], fah[i], fbl);
-                    mma_bf16(acc[i][j], fal[i], fbh);
+                    mma_bf16(acc[i][j], fah[i], bh);
+                    mma_bf16(acc[i][j], fah[i], bl);
+                    mma_bf16(acc[i][j], fal[i], bh);
                 }
             }
         }
@@ -338,22 +513,73 @@ __global__ void sum_splits_kernel(const float* __restrict__ partial, int splits,
     }
 }
 
-// db[co] = sum_p dY[p][co]: one block per channel group, fixed order
-__global__ void bias_grad_kernel(const float* __restrict__ dy, int P, int C, float* __restrict__ db)
+// db[c] = sum_p dY[p][c] in two fixed-order passes.  Pass 1: block b sums the
+// pixels [b ppb, (b+1) ppb); within a block thread t handles channel c0 + t % cc
+// and every (256 / cc)-th pixel (a warp reads consecutive channels of one pixel)
+// into four interleaved partial sums, then the per-thread sums are added in
+// thread order.  Pass 2: one block per channel adds the blocks' partials in a
+// fixed strided order and a fixed tree.
+__global__ void bias_grad_partial_kernel(const float* __restrict__ dy, long long P, int C, long long ppb,
+                                         float* __restrict__ partial)
 {
     __shared__ float red[256];
-    for (int c = blockIdx.x; c < C; c += gridDim.x) {
-        float s = 0.f;
-        for (int p = threadIdx.x; p < P; p += blockDim.x) s += dy[(long long)p * C + c];
-        red[threadIdx.x] = s;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-            __syncthreads();
+    const int t = threadIdx.x;
+    const long long p0 = blockIdx.x * ppb, p1 = min(P, p0 + ppb);
+    for (int c0 = 0; c0 < C; c0 += 256) {
+        const int cc = min(256, C - c0);
+        const int rows = 256 / cc;
+        const int c = t % cc, r = t / cc;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        if (r < rows) {
+            long long p = p0 + r;
+            for (; p + 3 * rows < p1; p += 4 * rows) {
+                s0 += dy[p * C + c0 + c];
+                s1 += dy[(p + rows) * C + c0 + c];
+                s2 += dy[(p + 2 * rows) * C + c0 + c];
+                s3 += dy[(p + 3 * rows) * C + c0 + c];
+            }
+            for (; p < p1; p += rows) s0 += dy[p * C + c0 + c];
         }
-        if (threadIdx.x == 0) db[c] = red[0];
+        red[t] = (s0 + s1) + (s2 + s3);
+        __syncthreads();
+        if (t < cc) {
+            float acc = 0.f;
+            for (int q = 0; q < rows; ++q) acc += red[q * cc + t];
+            partial[(long long)blockIdx.x * C + c0 + t] = acc;
+        }
         __syncthreads();
     }
+}
+
+__global__ void bias_grad_finish_kernel(const float* __restrict__ partial, int nblk, int C, float* __restrict__ db)
+{
+    __shared__ float red[256];
+    const int c = blockIdx.x, t = threadIdx.x;
+    float acc = 0.f;
+    for (int b = t; b < nblk; b += 256) acc += partial[(long long)b * C + c];
+    red[t] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (t < o) red[t] += red[t + o];
+        __syncthreads();
+    }
+    if (t == 0) db[c] = red[0];
+}
+
+// pixels per block: about 32 per thread
+long long bias_grad_ppb(long long P, int C)
+{
+    const int cc = C < 256 ? C : 256;
+    long long ppb = 32LL * (256 / cc);
+    const long long nb = (P + ppb - 1) / ppb;
+    if (nb > 8192) ppb = (P + 8191) / 8192;
+    return ppb;
+}
+
+int bias_grad_blocks(long long P, int C)
+{
+    const long long ppb = bias_grad_ppb(P, C);
+    return (int)((P + ppb - 1) / ppb);
 }
 
 // Wt[ci][tap'][co] = W[co][KS*KS-1-tap'][ci]: weights of the data-gradient convolution
@@ -578,6 +804,26 @@ int grid_for(long long n)
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+int ilog2(long long v)
+{
+    int l = 0;
+    while ((1LL << l) < v) ++l;
+    return l;
+}
+
+// pixels per split of the weight gradient: enough splits for about four blocks per
+// SM (a block walks its pixels serially), at least 1024 pixels (16 chunks) each
+long long wgrad_pixels_per_split(int Cin, int Cout, long long P, int KS)
+{
+    const long long tiles = (long long)((Cout + 63) / 64) * KS * KS * ((Cin + 63) / 64);
+    long long splits = (4 * 152 + tiles - 1) / tiles;
+    const long long max_splits = (P + 1023) / 1024;
+    if (splits > max_splits) splits = max_splits;
+    if (splits < 1) splits = 1;
+    long long pps = (P + splits - 1) / splits;
+    return (pps + 63) / 64 * 64;
+}
+
 lbm_status launch_status()
 {
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
@@ -598,6 +844,20 @@ lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int
     ConvArgs a{x1, x2, C1, C2, static_cast<const __nv_bfloat16*>(w_bf16), bias, y1, y2, Co1, Cout, B, H, W, relu, beta};
     const long long P = (long long)B * H * W;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (KS == 3 && H >= TH && W >= TW && Cout % 32 == 0) {
+        // halo-tiled kernel: BN = 64 when it divides Cout, else 32
+        const long long tiles = (long long)B * (H / TH) * (W / TW);
+        if (Cout % 64 == 0) {
+            constexpr int smem = conv3_tile_smem_bytes<64>();
+            cudaFuncSetAttribute(conv3_tile_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            conv3_tile_kernel<64><<<dim3((unsigned)tiles, (unsigned)(Cout / 64)), 256, smem, s>>>(a);
+        } else {
+            constexpr int smem = conv3_tile_smem_bytes<32>();
+            cudaFuncSetAttribute(conv3_tile_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            conv3_tile_kernel<32><<<dim3((unsigned)tiles, (unsigned)(Cout / 32)), 256, smem, s>>>(a);
+        }
+        return launch_status();
+    }
     const int BN = Cout >= 64 ? 64 : (Cout >= 32 ? 32 : 16);
     dim3 grid((unsigned)((P + CBM - 1) / CBM), (unsigned)((Cout + BN - 1) / BN));
     if (KS == 3) {
@@ -615,8 +875,8 @@ lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int
 int64_t lbm_nn_wgrad_workspace_bytes(int32_t Cin, int32_t Cout, int32_t B, int32_t H, int32_t W, int32_t KS)
 {
     const long long P = (long long)B * H * W;
-    long long pps = 8192;
-    long long splits = (P + pps - 1) / pps;
+    const long long pps = wgrad_pixels_per_split(Cin, Cout, P, KS);
+    const long long splits = (P + pps - 1) / pps;
     return splits * (long long)Cout * KS * KS * Cin * (long long)sizeof(float);
 }
 
@@ -630,9 +890,9 @@ lbm_status lbm_nn_conv_backward_weight(const float* dy, int32_t Cout, const floa
     const int Cin = C1 + C2;
     if (workspace_bytes < lbm_nn_wgrad_workspace_bytes(Cin, Cout, B, H, W, KS)) return LBM_ERR_ARG;
     const long long P = (long long)B * H * W;
-    const int pps = 8192;
+    const int pps = (int)wgrad_pixels_per_split(Cin, Cout, P, KS);
     const int splits = (int)((P + pps - 1) / pps);
-    WgradArgs a{dy, x1, x2, C1, C2, Cout, B, H, W, KS, pps, static_cast<float*>(workspace)};
+    WgradArgs a{dy, x1, x2, C1, C2, Cout, B, H, W, KS, pps, static_cast<float*>(workspace), ilog2(W), ilog2(H * W)};
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     dim3 grid((unsigned)((Cout + 63) / 64), (unsigned)(KS * KS * ((Cin + 63) / 64)), (unsigned)splits);
     conv_wgrad_kernel<<<grid, 256, 0, s>>>(a);
@@ -641,10 +901,23 @@ lbm_status lbm_nn_conv_backward_weight(const float* dy, int32_t Cout, const floa
     return launch_status();
 }
 
-lbm_status lbm_nn_bias_grad(const float* dy, int64_t P, int32_t C, float* db, void* stream)
+int64_t lbm_nn_bias_grad_workspace_bytes(int64_t P, int32_t C)
 {
-    if (!dy || !db || P <= 0 || C <= 0) return LBM_ERR_ARG;
-    bias_grad_kernel<<<C < 1024 ? C : 1024, 256, 0, static_cast<cudaStream_t>(stream)>>>(dy, (int)P, C, db);
+    if (P <= 0 || C <= 0) return 0;
+    return (int64_t)bias_grad_blocks(P, C) * C * (int64_t)sizeof(float);
+}
+
+lbm_status lbm_nn_bias_grad(const float* dy, int64_t P, int32_t C, float* db, void* workspace,
+                            int64_t workspace_bytes, void* stream)
+{
+    if (!dy || !db || !workspace || P <= 0 || C <= 0) return LBM_ERR_ARG;
+    if (workspace_bytes < lbm_nn_bias_grad_workspace_bytes(P, C)) return LBM_ERR_ARG;
+    const int nblk = bias_grad_blocks(P, C);
+    const long long ppb = bias_grad_ppb(P, C);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float* part = static_cast<float*>(workspace);
+    bias_grad_partial_kernel<<<nblk, 256, 0, s>>>(dy, P, C, ppb, part);
+    bias_grad_finish_kernel<<<C, 256, 0, s>>>(part, nblk, C, db);
     return launch_status();
 }
 

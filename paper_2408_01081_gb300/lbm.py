@@ -25,7 +25,7 @@ STATUS_NAMES = ["LBM_OK", "LBM_ERR_ARG", "LBM_ERR_CFL", "LBM_ERR_OOM", "LBM_ERR_
                 "LBM_ERR_TIMEOUT", "LBM_ERR_STATE"]
 
 # every symbol declared in include/lbm.h
-EXPORTS = ["lbm_create", "lbm_init", "lbm_set_relaxation", "lbm_set_step_fusion", "lbm_set_forcing", "lbm_set_dirichlet", "lbm_set_dirichlet_separable", "lbm_step", "lbm_moments",
+EXPORTS = ["lbm_create", "lbm_init", "lbm_set_relaxation", "lbm_set_step_fusion", "lbm_set_fp64_split", "lbm_set_forcing", "lbm_set_dirichlet", "lbm_set_dirichlet_separable", "lbm_step", "lbm_moments",
            "lbm_energy", "lbm_error_sums", "lbm_get_populations", "lbm_set_populations", "lbm_check_finite",
            "lbm_time_step", "lbm_synchronize", "lbm_destroy", "lbm_last_error", "lbm_state_bytes",
            "lbm_save_state", "lbm_load_state", "lbm_energy_noalloc", "lbm_batch_create", "lbm_batch_init",
@@ -77,6 +77,7 @@ def load(path: Optional[str] = None):
         "lbm_set_forcing": ([vp, i32, dp, dp, dp, i64, i32], i32),
         "lbm_set_relaxation": ([vp, ctypes.c_double], i32),
         "lbm_set_step_fusion": ([vp, i32, i32], i32),
+        "lbm_set_fp64_split": ([vp, i32], i32),
         "lbm_set_dirichlet": ([vp, dp, i64, i32], i32),
         "lbm_set_dirichlet_separable": ([vp, i32, dp, dp, dp, dp, dp, i64, i32], i32),
         "lbm_step": ([vp, i64], i32),
@@ -169,6 +170,10 @@ def lbm_init(ctx, U0, dU0dx, dU0dy, B0=None, u0=None):
 
 def lbm_set_step_fusion(ctx, steps_per_pass=2, rows_per_block=64):
     _check(ctx, load().lbm_set_step_fusion(ctx, int(steps_per_pass), int(rows_per_block)))
+
+
+def lbm_set_fp64_split(ctx, level):
+    _check(ctx, load().lbm_set_fp64_split(ctx, int(level)))
 
 
 def lbm_set_relaxation(ctx, omega):
@@ -410,6 +415,9 @@ class Lattice:
 
     def set_step_fusion(self, steps_per_pass=2, rows_per_block=64):
         lbm_set_step_fusion(self.ctx, steps_per_pass, rows_per_block)
+
+    def set_fp64_split(self, level):
+        lbm_set_fp64_split(self.ctx, level)
 
     def set_relaxation(self, omega):
         lbm_set_relaxation(self.ctx, omega)

@@ -9,7 +9,8 @@ import ctypes
 
 from . import lbm as _lbm
 
-EXPORTS = ["lbm_nn_conv_forward", "lbm_nn_wgrad_workspace_bytes", "lbm_nn_conv_backward_weight", "lbm_nn_bias_grad",
+EXPORTS = ["lbm_nn_conv_forward", "lbm_nn_wgrad_workspace_bytes", "lbm_nn_conv_backward_weight",
+           "lbm_nn_bias_grad_workspace_bytes", "lbm_nn_bias_grad",
            "lbm_nn_weight_flip", "lbm_nn_relu_backward", "lbm_nn_pool", "lbm_nn_pool_backward", "lbm_nn_upsample",
            "lbm_nn_upsample_backward", "lbm_nn_mse", "lbm_nn_adam", "lbm_nn_to_bf16", "lbm_nn_pack_input",
            "lbm_nn_pack_target", "lbm_nn_residual_output", "lbm_nn_gradient"]
@@ -26,7 +27,8 @@ def _lib():
             "lbm_nn_conv_forward": [vp, i32, vp, i32, vp, vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, vp],
             "lbm_nn_wgrad_workspace_bytes": [i32, i32, i32, i32, i32, i32],
             "lbm_nn_conv_backward_weight": [vp, i32, vp, i32, vp, i32, i32, i32, i32, i32, vp, i32, vp, i64, vp],
-            "lbm_nn_bias_grad": [vp, i64, i32, vp, vp],
+            "lbm_nn_bias_grad_workspace_bytes": [i64, i32],
+            "lbm_nn_bias_grad": [vp, i64, i32, vp, vp, i64, vp],
             "lbm_nn_weight_flip": [vp, i32, i32, i32, vp, vp],
             "lbm_nn_relu_backward": [vp, vp, i64, vp],
             "lbm_nn_pool": [vp, i32, i32, i32, i32, vp, vp],
@@ -44,7 +46,7 @@ def _lib():
         for name, args in sig.items():
             fn = getattr(lib, name)
             fn.argtypes = args
-            fn.restype = i64 if name == "lbm_nn_wgrad_workspace_bytes" else i32
+            fn.restype = i64 if name.endswith("_workspace_bytes") else i32
         _done = True
     return lib
 
@@ -78,8 +80,13 @@ def conv_backward_weight(dy, Cout, x1, C1, x2, C2, B, H, W, KS, dw, workspace, b
                                            _p(workspace), workspace.numel() * workspace.element_size(), _s()))
 
 
-def bias_grad(dy, P, C, db):
-    _ok("lbm_nn_bias_grad", _lib().lbm_nn_bias_grad(_p(dy), P, C, _p(db), _s()))
+def bias_grad_workspace_bytes(P, C) -> int:
+    return int(_lib().lbm_nn_bias_grad_workspace_bytes(P, C))
+
+
+def bias_grad(dy, P, C, db, workspace):
+    _ok("lbm_nn_bias_grad", _lib().lbm_nn_bias_grad(_p(dy), P, C, _p(db), _p(workspace),
+                                                    workspace.numel() * workspace.element_size(), _s()))
 
 
 def weight_flip(w_bf16, Cout, Cin, KS, wt_bf16):

@@ -64,7 +64,7 @@ class Conv:
         if self.relu:
             K.relu_backward(dy, y)
         K.conv_backward_weight(dy, self.cout, x1, self.cin1, x2, self.cin2, B, H, W, self.ks, self.gw, workspace)
-        K.bias_grad(dy, B * H * W, self.cout, self.gb)
+        K.bias_grad(dy, B * H * W, self.cout, self.gb, workspace)
         if need_dx:
             K.weight_flip(self.wb, self.cout, self.cin1 + self.cin2, self.ks, self.wt)
             K.conv_forward(dy, self.cout, None, 0, self.wt, None, dx1, self.cin1, dx2, self.cin1 + self.cin2,
@@ -132,7 +132,8 @@ class UNet:
         A["tgt"] = t.empty((B, H, W, COUT_PAD), **f32)
         # gradient buffers (same shapes), reused
         G = {k: t.empty_like(v) for k, v in A.items() if k not in ("x0", "tgt")}
-        ws = max(K.wgrad_workspace_bytes(l.cin1 + l.cin2, l.cout, B, H, W, l.ks) for l in self.layers)
+        ws = max(max(K.wgrad_workspace_bytes(l.cin1 + l.cin2, l.cout, B, H, W, l.ks) for l in self.layers),
+                 max(K.bias_grad_workspace_bytes(B * H * W, l.cout) for l in self.layers))
         self.ws = t.empty(ws // 4 + 1, **f32)
         self.mse_ws = t.empty(512, dtype=t.float64, device=self.dev)
         self.loss = t.zeros(1, dtype=t.float64, device=self.dev)

@@ -52,6 +52,42 @@ def test_conv_forward(lbm, KS, C1, C2, Cout, Co1):
     assert np.max(np.abs(got - (ref + prev))) < 1e-4 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("H,W,C1,C2,Cout,Co1", [(8, 16, 32, 0, 32, 32), (16, 32, 32, 32, 32, 32),
+                                               (32, 16, 64, 0, 128, 128), (16, 64, 128, 64, 192, 128),
+                                               (64, 32, 32, 64, 64, 32)])
+def test_conv3_halo_tile_forward(lbm, H, W, C1, C2, Cout, Co1):
+    """The 8x16 halo-tiled 3x3 kernel (H >= 8, W >= 16, Cout a multiple of 32): single tiles
+    whose halo wraps around the image, several tiles per image, two inputs, two outputs."""
+    from paper_2408_01081_gb300 import nn as K
+    B = 2
+    x1 = RNG.standard_normal((B, H, W, C1)).astype(np.float32)
+    x2 = RNG.standard_normal((B, H, W, C2)).astype(np.float32) if C2 else None
+    w = _bf16(RNG.standard_normal((Cout, 3, 3, C1 + C2)) * 0.1)
+    b = RNG.standard_normal(Cout).astype(np.float32)
+    x = x1 if C2 == 0 else np.concatenate([x1, x2], axis=3)
+    ref = R.conv(x.astype(np.float64), w, b)
+    y1 = _t(np.zeros((B, H, W, Co1), np.float32))
+    y2 = _t(np.zeros((B, H, W, Cout - Co1), np.float32)) if Co1 < Cout else None
+    K.conv_forward(_t(x1), C1, _t(x2) if C2 else None, C2, _wb(w), _t(b), y1, Co1, y2, Cout, B, H, W, 3,
+                   relu=False, beta=False)
+    got = y1.cpu().numpy() if y2 is None else np.concatenate([y1.cpu().numpy(), y2.cpu().numpy()], axis=3)
+    assert rel_l2(got, ref) < 2e-5, rel_l2(got, ref)
+    assert np.max(np.abs(got - ref)) < 1e-4 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("P,C", [(1, 5), (100, 32), (70000, 64), (5000, 384), (1 << 21, 32)])
+def test_bias_grad_sizes(lbm, P, C):
+    """Channel counts below, at and above one block's 256 threads; one to many blocks."""
+    import torch
+    from paper_2408_01081_gb300 import nn as K
+    dy = torch.randn((P, C), dtype=torch.float32, device="cuda")
+    db = torch.empty(C, dtype=torch.float32, device="cuda")
+    ws = torch.empty(K.bias_grad_workspace_bytes(P, C) // 4 + 1, dtype=torch.float32, device="cuda")
+    K.bias_grad(dy, P, C, db, ws)
+    ref = dy.double().sum(0)
+    assert torch.max(torch.abs(db.double() - ref)).item() < 1e-5 * max(1.0, P ** 0.5)
+
+
 @pytest.mark.parametrize("KS,C1,C2,Cout", [(3, 32, 0, 32), (3, 64, 32, 48), (1, 32, 0, 32)])
 def test_conv_gradients(lbm, KS, C1, C2, Cout):
     import torch
@@ -69,7 +105,8 @@ def test_conv_gradients(lbm, KS, C1, C2, Cout):
     K.conv_backward_weight(_t(dy), Cout, _t(x1), C1, _t(x2) if C2 else None, C2, B, H, W, KS, dw, ws)
     assert rel_l2(dw.cpu().numpy(), rdw) < 2e-5, rel_l2(dw.cpu().numpy(), rdw)
     db = torch.empty(Cout, dtype=torch.float32, device="cuda")
-    K.bias_grad(_t(dy), B * H * W, Cout, db)
+    wsb = torch.empty(K.bias_grad_workspace_bytes(B * H * W, Cout) // 4 + 1, dtype=torch.float32, device="cuda")
+    K.bias_grad(_t(dy), B * H * W, Cout, db, wsb)
     assert rel_l2(db.cpu().numpy(), rdb) < 1e-5
     wt = torch.empty((C1 + C2, KS, KS, Cout), dtype=torch.bfloat16, device="cuda")
     K.weight_flip(_wb(w), Cout, C1 + C2, KS, wt)

@@ -271,3 +271,69 @@ def test_two_step_fusion_16bit_against_oracle(lbm, storage, tol):
         errs[fuse] = max(field_errors(lat.moments(), ref, fields=range(5)))
         lat.close()
     assert errs[2] < tol and errs[2] <= 1.2 * errs[1], errs
+
+
+def _split_runs(lbm, nx, ny, f, us, steps, levels, dirichlet=False, wall=None, track=False):
+    outs = {}
+    for adds in levels:
+        lat = lbm.Lattice(nx, ny, 0.1, 0.1 / 3.2, 1.0, 0.6, dirichlet=dirichlet, storage="f64",
+                          track_displacement=track)
+        lat.set_fp64_split(adds)
+        if wall is not None:
+            lat.set_dirichlet(wall)
+        lat.set_populations(f, us)
+        lat.step(steps)
+        outs[adds] = lat.populations()
+        lat.close()
+    return outs
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 5), (67, 45), (1031, 7), (130, 70)])
+def test_fp64_split_is_bit_identical_periodic(lbm, nx, ny):
+    """Additions moved to the integer pipes give the hardware FP64 results bit for bit."""
+    rng = np.random.default_rng(7 * nx + ny)
+    f = rng.standard_normal((4, 5, ny, nx))
+    us = rng.standard_normal((2, ny, nx))
+    outs = _split_runs(lbm, nx, ny, f, us, 11, [0, 1, 2, 5, 7], track=True)
+    for adds in (1, 2, 5, 7):
+        np.testing.assert_array_equal(outs[adds][0].view(np.int64), outs[0][0].view(np.int64))
+        np.testing.assert_array_equal(outs[adds][1].view(np.int64), outs[0][1].view(np.int64))
+
+
+def test_fp64_split_is_bit_identical_dirichlet_with_wall_data(lbm):
+    nx, ny, steps = 150, 70, 25
+    rng = np.random.default_rng(11)
+    f = rng.standard_normal((4, 5, ny, nx)) * 1e-2
+    us = rng.standard_normal((2, ny, nx))
+    wall = rng.standard_normal((steps, 2, 2 * (nx + ny))) * 1e-2
+    outs = _split_runs(lbm, nx, ny, f, us, steps, [0, 1, 6], dirichlet=True, wall=wall, track=True)
+    for adds in (1, 6):
+        np.testing.assert_array_equal(outs[adds][0].view(np.int64), outs[0][0].view(np.int64))
+        np.testing.assert_array_equal(outs[adds][1].view(np.int64), outs[0][1].view(np.int64))
+
+
+def test_fp64_split_handles_zeros_subnormals_and_wide_ranges(lbm):
+    """Exact zeros, signed zeros, subnormals and operands 1e300 apart: the integer path
+    either matches the hardware or hands the lane back to the FP64 pipe."""
+    nx, ny = 96, 40
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal((4, 5, ny, nx))
+    pick = rng.integers(0, 6, size=f.shape)
+    f[pick == 0] = 0.0
+    f[pick == 1] = -0.0
+    f[pick == 2] *= 1e-310                   # subnormal
+    f[pick == 3] *= 1e-300
+    f[pick == 4] *= 1e300
+    f[:, :, :, :8] = 0.0                      # whole lanes of zeros (exact cancellations)
+    outs = _split_runs(lbm, nx, ny, f, None, 5, [0, 1, 2, 3, 4, 5, 6, 7])
+    for adds in range(1, 8):
+        np.testing.assert_array_equal(outs[adds][0].view(np.int64), outs[0][0].view(np.int64))
+
+
+def test_fp64_split_rejects_unsupported_counts(lbm):
+    lat = lbm.Lattice(8, 8, 0.1, 0.1 / 3.2, 1.0, 0.6, storage="f64")
+    for bad in (-1, 8, 100):
+        with pytest.raises(lbm.LbmError):
+            lat.set_fp64_split(bad)
+    lat.set_fp64_split(7)
+    lat.close()
