@@ -241,6 +241,7 @@ def run_surrogate(args):
     train_s = time.perf_counter() - t0
     held = S.generate_chunk(64, 900_000, H=256, W=256, k=32, J=4)
     errs, pers = S.evaluate(sur, held, batch=16)
+    errs_fast, _ = S.evaluate(sur, held, batch=16, act_bf16=True)
     tm = S.timing(sur, n=16, H=256, W=256)
     del held
     torch.cuda.empty_cache()
@@ -254,7 +255,11 @@ def run_surrogate(args):
             "surrogate_ms_per_lattice": round(tm["surrogate_ms_per_lattice"], 4),
             "lbm_f64_ms_per_lattice": round(tm["lbm_f64_ms_per_lattice"], 4),
             "lbm_f32_ms_per_lattice": round(tm["lbm_f32_ms_per_lattice"], 4),
-            "gain_vs_f64": round(tm["gain_vs_f64"], 3), "gain_vs_f32": round(tm["gain_vs_f32"], 3)}
+            "gain_vs_f64": round(tm["gain_vs_f64"], 3), "gain_vs_f32": round(tm["gain_vs_f32"], 3),
+            "bf16_activations": {"heldout_rel_l2_median": float(np.median(errs_fast)),
+                                 "surrogate_ms_per_lattice": round(tm["surrogate_bf16_act_ms_per_lattice"], 4),
+                                 "gain_vs_f64": round(tm["gain_bf16_act_vs_f64"], 3),
+                                 "gain_vs_f32": round(tm["gain_bf16_act_vs_f32"], 3)}}
 
 
 def _batch_mode(cache):

@@ -13,8 +13,8 @@
  *     with activations split into two BF16 halves, so the BF16 weights are the
  *     only rounding of the forward pass.
  *   - Two-input convolutions read the channel concatenation [x1 | x2]; two-output
- *     ones write channels [0, Co1) to y1 and [Co1, Cout) to y2.  beta = 1 adds the
- *     result into the destination instead of overwriting it.
+ *     ones write channels [0, Co1) to y1 and [Co1, Cout) to y2.  LBM_NN_ACCUMULATE
+ *     adds the result into the destination instead of overwriting it.
  *   - Channel counts: C1, C2 multiples of 32 (C2 may be 0); Cout a multiple of 8.
  *   - All calls are asynchronous on `stream` (NULL = legacy stream) and return
  *     LBM_ERR_ARG for invalid sizes or NULL pointers, LBM_ERR_CUDA if a launch
@@ -31,19 +31,30 @@
 extern "C" {
 #endif
 
-/* y = act(conv_KS(x, w) + bias), act = ReLU when relu != 0. */
+/* Flags of the convolution calls. */
+enum {
+    LBM_NN_RELU = 1,        /* apply max(0, .) to the output (forward) */
+    LBM_NN_ACCUMULATE = 2,  /* add the result into the destination instead of overwriting it */
+    LBM_NN_X1_HALF = 4,     /* x1 is stored at (H/2, W/2) and read nearest-upsampled to (H, W) */
+    LBM_NN_ACT_BF16 = 8     /* forward: activations as one BF16 value instead of the hi/lo pair
+                               (half the tensor-core work; activations rounded to BF16) */
+};
+
+/* y = act(conv_KS(x, w) + bias), act = ReLU with LBM_NN_RELU; flags as above (any other
+ * bit returns LBM_ERR_ARG). */
 lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int32_t C2, const void* w_bf16,
                                const float* bias, float* y1, int32_t Co1, float* y2, int32_t Cout, int32_t B,
-                               int32_t H, int32_t W, int32_t KS, int32_t relu, int32_t beta, void* stream);
+                               int32_t H, int32_t W, int32_t KS, int32_t flags, void* stream);
 
 /* Workspace bytes lbm_nn_conv_backward_weight needs for these sizes (Cin = C1 + C2). */
 int64_t lbm_nn_wgrad_workspace_bytes(int32_t Cin, int32_t Cout, int32_t B, int32_t H, int32_t W, int32_t KS);
 
 /* dw[co][ky][kx][ci] (+)= sum over pixels of dy[p][co] * x[p + (ky, kx) - KS/2][ci]; FP32 output,
- * reduced over pixel splits in a fixed order (deterministic). */
+ * reduced over pixel splits in a fixed order (deterministic).  flags: LBM_NN_ACCUMULATE,
+ * LBM_NN_X1_HALF (others return LBM_ERR_ARG). */
 lbm_status lbm_nn_conv_backward_weight(const float* dy, int32_t Cout, const float* x1, int32_t C1, const float* x2,
                                        int32_t C2, int32_t B, int32_t H, int32_t W, int32_t KS, float* dw,
-                                       int32_t beta, void* workspace, int64_t workspace_bytes, void* stream);
+                                       int32_t flags, void* workspace, int64_t workspace_bytes, void* stream);
 
 /* Workspace (device bytes) lbm_nn_bias_grad needs for P pixels and C channels. */
 int64_t lbm_nn_bias_grad_workspace_bytes(int64_t P, int32_t C);

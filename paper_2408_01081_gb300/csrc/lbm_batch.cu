@@ -140,7 +140,7 @@ void drop_graph(lbm_batch* b)
 // (re)build the tile list from the tile widths of the size classes
 lbm_status build_tiles(lbm_batch* b)
 {
-    const int V = b->ops->vec;
+    const int V = b->ops->batch_vec;
     int first = 0;
     std::vector<int> tile_lat;
     for (int i = 0; i < b->count; ++i) {
@@ -393,7 +393,7 @@ lbm_status lbm_batch_create(int32_t count, const lbm_lattice_desc* lats, int32_t
         L.b = d.cmu / c;
         off += 20 * L.plane;
         b->nodes += (long long)d.nx * d.ny;
-        b->cls[i] = size_class((d.nx + ops->vec - 1) / ops->vec);
+        b->cls[i] = size_class((d.nx + ops->batch_vec - 1) / ops->batch_vec);
     }
     b->total_elems = off;
     const size_t bytes = (size_t)off * ops->elem_bytes;
@@ -565,7 +565,7 @@ lbm_status lbm_batch_info(const lbm_batch* b, int32_t index, int64_t* nodes, int
     if (ntiles) *ntiles = b->ntiles;
     if (tile_width) {
         if (index < 0 || index >= b->count) return LBM_ERR_ARG;
-        *tile_width = b->lat[index].tpr * b->ops->vec;
+        *tile_width = b->lat[index].tpr * b->ops->batch_vec;
     }
     return LBM_OK;
 }
@@ -611,7 +611,7 @@ lbm_status lbm_batch_tune(lbm_batch* b, const char* cache_path)
         b->mode = cache[key + "mode"];
         return build_tiles(b);
     }
-    const int V = b->ops->vec;
+    const int V = b->ops->batch_vec;
     const int steps = 6;
     const int saved_graph = b->graph_steps;
     b->graph_steps = 2;

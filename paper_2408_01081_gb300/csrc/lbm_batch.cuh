@@ -183,14 +183,19 @@ __device__ __forceinline__ void batch_tile(const LatDesc& L, int local_tile, con
                 for (int k = 0; k < 5; ++k) f[3][k] = M(Dk[k] * (double)P3[k][e]);
         }
         M U[5], rx[5], ry[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            rx[k] = f[1][k] + f[3][k];
-            ry[k] = f[0][k] + f[2][k];
-            U[k] = rx[k] + ry[k];
-        }
         M o[4][5];
-        collide<M>(f, U, rx, ry, a, b, o);
+        if constexpr (K == K_F64) {
+            // FP64: the default split (bit-identical to the FP64-pipe collision)
+            collide_split<kSplitDefaultMask>(f, a, b, U, o);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                rx[k] = f[1][k] + f[3][k];
+                ry[k] = f[0][k] + f[2][k];
+                U[k] = rx[k] + ry[k];
+            }
+            collide<M>(f, U, rx, ry, a, b, o);
+        }
 #pragma unroll
         for (int d = 0; d < 4; ++d)
 #pragma unroll
@@ -204,7 +209,7 @@ __device__ __forceinline__ void batch_tile(const LatDesc& L, int local_tile, con
 }
 
 template <int K, int V, bool PERSISTENT>
-__global__ void __launch_bounds__(256) batch_step_kernel(BatchArgs A)
+__global__ void __launch_bounds__(256, K == K_F64 ? LBM_SPLIT_MIN_BLOCKS : 1) batch_step_kernel(BatchArgs A)
 {
     using E = typename Fmt<K>::E;
     const E* a = static_cast<const E*>(A.arenaA);

@@ -22,7 +22,7 @@ enum { STEP_DIRICHLET = 1, STEP_FORCING = 2, STEP_TRACK = 4, STEP_OMEGA = 8, STE
 // FP64-pipe-only step, levels 2-5 at 1.30-1.34x, 6 at 1.12x, 7 at 1.23x.
 constexpr unsigned long long split_mask(int level)
 {
-    return level == 1 ? 0x001FFFC00ull    // 15: the pair sums and U (fastest measured, the default)
+    return level == 1 ? lbmk::kSplitDefaultMask    // 15: the pair sums and U (fastest measured, the default)
          : level == 2 ? 0x001F07C1Full    // 15: f*_(-1,0), y-pair sums, U
          : level == 3 ? 0x001F0FC1Full    // 16: f*_(-1,0), y-pair sums, U, x-pair sum 0
          : level == 4 ? 0x001F003FFull    // 15: f*_(-1,0), f*_(0,-1), U
@@ -61,6 +61,7 @@ struct KindOps {
     // two fused steps (FP32 / BF16 / FP16 populations only; others return cudaErrorNotSupported)
     cudaError_t (*tb2_step)(const lbmk::TbArgs&, bool dirichlet, dim3 grid, dim3 block, cudaStream_t s);
     int vec_split;                 // nodes per thread of the FP64 split-level step kernels
+    int batch_vec;                 // nodes per thread of the batch kernel
 };
 
 extern const KindOps kind_ops_0;  // FP64

@@ -167,6 +167,9 @@ __device__ __forceinline__ void collide(const M (&f)[4][5], const M (&U)[5], con
     }
 }
 
+// the default split: the 10 pair sums and the 5 sums U on the integer pipes
+constexpr unsigned long long kSplitDefaultMask = 0x001FFFC00ull;
+
 template <bool EMU>
 __device__ __forceinline__ double split_add(double x, double y, bool& ok)
 {

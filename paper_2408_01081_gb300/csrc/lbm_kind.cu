@@ -26,6 +26,8 @@ constexpr bool MS = (K >= lbmk::K_MSBF16);
 // nodes per thread in the step kernel (one vector access per plane and thread)
 constexpr int V = (K == lbmk::K_F64) ? LBM_VEC_F64 : (K == lbmk::K_F32) ? LBM_VEC_F32 : MS ? 4 : LBM_VEC_F16;
 constexpr int ELEM = (K == lbmk::K_F64) ? 8 : (K == lbmk::K_F32) ? 4 : 2;
+// nodes per thread in the batch kernel (FP64 runs the split collision, at its width)
+constexpr int VB = (K == lbmk::K_F64) ? LBM_VEC_SPLIT : V;
 constexpr int NODE_BYTES = MS ? 5 * 4 + 15 * 2 : 20 * ELEM;
 
 template <bool D, bool F, bool T, bool O, unsigned long long SPLIT = 0>
@@ -136,7 +138,7 @@ cudaError_t batch_step_t(const lbmk::BatchArgs& a, bool persistent, int grid, cu
         return cudaErrorNotSupported;        // batches use the population formats only
     } else {
         if (!persistent) {
-            lbmk::batch_step_kernel<KK, V, false><<<grid, 256, 0, s>>>(a);
+            lbmk::batch_step_kernel<KK, VB, false><<<grid, 256, 0, s>>>(a);
             return cudaGetLastError();
         }
         cudaLaunchConfig_t cfg = {};
@@ -149,7 +151,7 @@ cudaError_t batch_step_t(const lbmk::BatchArgs& a, bool persistent, int grid, cu
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, lbmk::batch_step_kernel<KK, V, true>, a);
+        return cudaLaunchKernelEx(&cfg, lbmk::batch_step_kernel<KK, VB, true>, a);
     }
 }
 
@@ -160,7 +162,7 @@ cudaError_t batch_occupancy_t(int* n)
         *n = 1;
         return cudaSuccess;
     } else {
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lbmk::batch_step_kernel<KK, V, true>, 256, 0);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lbmk::batch_step_kernel<KK, VB, true>, 256, 0);
     }
 }
 
@@ -201,7 +203,7 @@ namespace lbmh {
 const KindOps LBM_OPS_NAME(LBM_KIND) = {
     K, V, ELEM, NODE_BYTES,
     step, init, moments, get_pop, set_pop, energy, error, finite, batch_step, batch_occupancy, tb2_step,
-    LBM_VEC_SPLIT,
+    LBM_VEC_SPLIT, VB,
 };
 
 }  // namespace lbmh

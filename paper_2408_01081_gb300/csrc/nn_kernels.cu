@@ -23,6 +23,17 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
+// v -> hi = bf16(v), lo = bf16(v - hi), four values packed in pairs (cvt.rn.bf16x2)
+__device__ __forceinline__ void split_bf16x4(const float4 v, uint2& hi, uint2& lo)
+{
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+    const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+    const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+    hi = make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+    lo = make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+}
+
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
 {
     asm volatile(
@@ -47,6 +58,8 @@ struct ConvArgs {
     int B, H, W;                // H, W powers of two
     int relu;                   // apply max(0, .) to the output
     int beta;                   // 1: add into the output instead of overwriting
+    int x1_half;                // x1 is stored at (H/2, W/2) and read nearest-upsampled
+    int act_bf16;               // activations as one BF16 value (no lo half)
 };
 
 constexpr int CBM = 128;        // pixels per CTA tile
@@ -95,13 +108,14 @@ __global__ void __launch_bounds__(256) conv_fwd_kernel(ConvArgs a)
         const int dy = tap / KS - R, dx = tap % KS - R;
         const int sy = (ay + dy) & (a.H - 1), sx = (ax + dx) & (a.W - 1);
         const long long spix = ((long long)an * a.H + sy) * a.W + sx;
+        const long long spix1 = a.x1_half ? ((long long)an * (a.H >> 1) + (sy >> 1)) * (a.W >> 1) + (sx >> 1) : spix;
         for (int ci0 = 0; ci0 < Cin; ci0 += CKC) {
             // --- stage A (FP32 -> bf16 hi / lo) ---
             {
                 float v[16];
                 if (avalid) {
                     const float* src;
-                    if (ci0 < a.C1) src = a.x1 + spix * a.C1 + ci0 + ahalf;
+                    if (ci0 < a.C1) src = a.x1 + spix1 * a.C1 + ci0 + ahalf;
                     else src = a.x2 + spix * a.C2 + (ci0 - a.C1) + ahalf;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -166,7 +180,7 @@ __global__ void __launch_bounds__(256) conv_fwd_kernel(ConvArgs a)
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
                         mma_bf16(acc[i][j], fh[i], fb);
-                        mma_bf16(acc[i][j], fl[i], fb);
+                        if (!a.act_bf16) mma_bf16(acc[i][j], fl[i], fb);
                     }
                 }
             }
@@ -226,7 +240,7 @@ constexpr int conv3_tile_smem_bytes()
     return (2 * HH * HW2 + 9 * BN) * KROW * (int)sizeof(__nv_bfloat16);
 }
 
-template <int BN>
+template <int BN, bool LO>
 __global__ void __launch_bounds__(256) conv3_tile_kernel(ConvArgs a)
 {
     extern __shared__ __align__(16) __nv_bfloat16 smem[];
@@ -256,23 +270,27 @@ __global__ void __launch_bounds__(256) conv3_tile_kernel(ConvArgs a)
 
     for (int ci0 = 0; ci0 < Cin; ci0 += CKC) {
         // --- stage the halo tile: 180 pixels x 32 channels, FP32 -> BF16 hi / lo ---
-        const float* base = (ci0 < a.C1) ? a.x1 : a.x2;
-        const int cstride = (ci0 < a.C1) ? a.C1 : a.C2;
-        const int coff = (ci0 < a.C1) ? ci0 : ci0 - a.C1;
+        const bool from1 = ci0 < a.C1;
+        const float* base = from1 ? a.x1 : a.x2;
+        const int cstride = from1 ? a.C1 : a.C2;
+        const int coff = from1 ? ci0 : ci0 - a.C1;
+        const int half = (from1 && a.x1_half) ? 1 : 0;     // nearest upsampling of a half-size x1
         for (int q = tid; q < HH * HW2 * (CKC / 4); q += 256) {
             const int hp = q >> 3, c4 = (q & 7) * 4;
             const int hy = hp / HW2, hx = hp % HW2;
             const int sy = (ty0 + hy - 1) & (a.H - 1), sx = (tx0 + hx - 1) & (a.W - 1);
-            const long long spix = ((long long)n * a.H + sy) * a.W + sx;
+            const long long spix = ((long long)n * (a.H >> half) + (sy >> half)) * (a.W >> half) + (sx >> half);
             const float4 v = *reinterpret_cast<const float4*>(base + spix * cstride + coff + c4);
-            const __nv_bfloat16 h0 = __float2bfloat16_rn(v.x), h1 = __float2bfloat16_rn(v.y);
-            const __nv_bfloat16 h2 = __float2bfloat16_rn(v.z), h3 = __float2bfloat16_rn(v.w);
-            const __nv_bfloat16 l0 = __float2bfloat16_rn(v.x - __bfloat162float(h0));
-            const __nv_bfloat16 l1 = __float2bfloat16_rn(v.y - __bfloat162float(h1));
-            const __nv_bfloat16 l2 = __float2bfloat16_rn(v.z - __bfloat162float(h2));
-            const __nv_bfloat16 l3 = __float2bfloat16_rn(v.w - __bfloat162float(h3));
-            *reinterpret_cast<uint2*>(Ah + hp * KROW + c4) = make_uint2(pack_bf16(h0, h1), pack_bf16(h2, h3));
-            *reinterpret_cast<uint2*>(Al + hp * KROW + c4) = make_uint2(pack_bf16(l0, l1), pack_bf16(l2, l3));
+            if constexpr (LO) {
+                uint2 hi, lo;
+                split_bf16x4(v, hi, lo);
+                *reinterpret_cast<uint2*>(Ah + hp * KROW + c4) = hi;
+                *reinterpret_cast<uint2*>(Al + hp * KROW + c4) = lo;
+            } else {
+                const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+                *reinterpret_cast<uint2*>(Ah + hp * KROW + c4) =
+                    make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+            }
         }
         // --- stage the weights of the nine taps: BN x 32 inputs each ---
         for (int q = tid; q < 9 * BN * 4; q += 256) {
@@ -295,7 +313,7 @@ __global__ void __launch_bounds__(256) conv3_tile_kernel(ConvArgs a)
                     const int hp = (2 * wm + i + dy) * HW2 + (lane & 15) + dx;
                     const int kc = kk + (lane >> 4) * 8;
                     ldsm_x4(fh[i], Ah + hp * KROW + kc);
-                    ldsm_x4(fl[i], Al + hp * KROW + kc);
+                    if constexpr (LO) ldsm_x4(fl[i], Al + hp * KROW + kc);
                 }
 #pragma unroll
                 for (int j = 0; j < NT; j += 2) {
@@ -306,9 +324,11 @@ __global__ void __launch_bounds__(256) conv3_tile_kernel(ConvArgs a)
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
                         mma_bf16(acc[i][j], fh[i], b0);
-                        mma_bf16(acc[i][j], fl[i], b0);
                         mma_bf16(acc[i][j + 1], fh[i], b1);
-                        mma_bf16(acc[i][j + 1], fl[i], b1);
+                        if constexpr (LO) {
+                            mma_bf16(acc[i][j], fl[i], b0);
+                            mma_bf16(acc[i][j + 1], fl[i], b1);
+                        }
                     }
                 }
             }
@@ -354,6 +374,7 @@ struct WgradArgs {
     int pix_per_split;
     float* partial;           // [splits][Cout][KS*KS][Cin]
     int lw, lhw;              // log2(W), log2(H W)
+    int x1_half;              // x1 stored at (H/2, W/2), read nearest-upsampled
 };
 
 constexpr int WK = 64;                 // pixels per staged chunk
@@ -420,8 +441,15 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(WgradArgs a)
                     const int n = p >> a.lhw, y = (p >> a.lw) & (a.H - 1), x = p & (a.W - 1);
                     const long long sp =
                         (((long long)n << a.lhw) | ((long long)((y + dy) & (a.H - 1)) << a.lw)) | ((x + dx) & (a.W - 1));
-                    rx[rep] = (ci < a.C1) ? *reinterpret_cast<const float4*>(a.x1 + sp * a.C1 + ci)
-                                          : *reinterpret_cast<const float4*>(a.x2 + sp * a.C2 + (ci - a.C1));
+                    if (ci < a.C1) {
+                        const long long s1 = a.x1_half ? (((long long)n << (a.lhw - 2)) |
+                                                          ((long long)(((y + dy) & (a.H - 1)) >> 1) << (a.lw - 1)) |
+                                                          (((x + dx) & (a.W - 1)) >> 1))
+                                                       : sp;
+                        rx[rep] = *reinterpret_cast<const float4*>(a.x1 + s1 * a.C1 + ci);
+                    } else {
+                        rx[rep] = *reinterpret_cast<const float4*>(a.x2 + sp * a.C2 + (ci - a.C1));
+                    }
                 }
             }
         }
@@ -432,23 +460,13 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(WgradArgs a)
         for (int rep = 0; rep < 4; ++rep) {
             const int q = tid + rep * 256;
             const int pk = q >> 4, c4 = (q & 15) * 4;
-            const float4 vy = ry[rep], vx = rx[rep];
-            const __nv_bfloat16 y0 = __float2bfloat16_rn(vy.x), y1 = __float2bfloat16_rn(vy.y);
-            const __nv_bfloat16 y2 = __float2bfloat16_rn(vy.z), y3 = __float2bfloat16_rn(vy.w);
-            const __nv_bfloat16 x0 = __float2bfloat16_rn(vx.x), x1 = __float2bfloat16_rn(vx.y);
-            const __nv_bfloat16 x2 = __float2bfloat16_rn(vx.z), x3 = __float2bfloat16_rn(vx.w);
-            *reinterpret_cast<uint2*>(&Yh[pk][c4]) = make_uint2(pack_bf16(y0, y1), pack_bf16(y2, y3));
-            *reinterpret_cast<uint2*>(&Yl[pk][c4]) =
-                make_uint2(pack_bf16(__float2bfloat16_rn(vy.x - __bfloat162float(y0)),
-                                     __float2bfloat16_rn(vy.y - __bfloat162float(y1))),
-                           pack_bf16(__float2bfloat16_rn(vy.z - __bfloat162float(y2)),
-                                     __float2bfloat16_rn(vy.w - __bfloat162float(y3))));
-            *reinterpret_cast<uint2*>(&Xh[pk][c4]) = make_uint2(pack_bf16(x0, x1), pack_bf16(x2, x3));
-            *reinterpret_cast<uint2*>(&Xl[pk][c4]) =
-                make_uint2(pack_bf16(__float2bfloat16_rn(vx.x - __bfloat162float(x0)),
-                                     __float2bfloat16_rn(vx.y - __bfloat162float(x1))),
-                           pack_bf16(__float2bfloat16_rn(vx.z - __bfloat162float(x2)),
-                                     __float2bfloat16_rn(vx.w - __bfloat162float(x3))));
+            uint2 yh, yl, xh, xl;
+            split_bf16x4(ry[rep], yh, yl);
+            split_bf16x4(rx[rep], xh, xl);
+            *reinterpret_cast<uint2*>(&Yh[pk][c4]) = yh;
+            *reinterpret_cast<uint2*>(&Yl[pk][c4]) = yl;
+            *reinterpret_cast<uint2*>(&Xh[pk][c4]) = xh;
+            *reinterpret_cast<uint2*>(&Xl[pk][c4]) = xl;
         }
         if (pc + WK < pend) load_chunk(pc + WK);
         __syncthreads();
@@ -630,6 +648,38 @@ __global__ void pool_backward_kernel(const float* __restrict__ dy, int B, int H,
     }
 }
 
+// Fast paths of pooling and upsampling for power-of-two H, W and C / 4: one thread
+// per output pixel and 4 channels (16-byte accesses), index arithmetic by shifts.
+__global__ void pool4_kernel(const float4* __restrict__ x, int lho, int lwo, int lc4, long long n,
+                             float4* __restrict__ y)
+{
+    const int C4 = 1 << lc4, Wo = 1 << lwo, Ho = 1 << lho;
+    const long long rowin = 2LL * Wo * C4;           // one input row
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i & (C4 - 1));
+        const long long pix = i >> lc4;
+        const int xo = (int)(pix & (Wo - 1)), yo = (int)((pix >> lwo) & (Ho - 1));
+        const long long b = pix >> (lwo + lho);
+        const long long base = ((b * 2 * Ho + 2 * yo) * 2 * Wo + 2 * xo) * C4 + c;
+        const float4 a0 = x[base], a1 = x[base + C4], a2 = x[base + rowin], a3 = x[base + rowin + C4];
+        y[i] = make_float4(0.25f * (a0.x + a1.x + a2.x + a3.x), 0.25f * (a0.y + a1.y + a2.y + a3.y),
+                           0.25f * (a0.z + a1.z + a2.z + a3.z), 0.25f * (a0.w + a1.w + a2.w + a3.w));
+    }
+}
+
+__global__ void upsample4_kernel(const float4* __restrict__ x, int lho, int lwo, int lc4, long long n,
+                                 float4* __restrict__ y)
+{
+    const int C4 = 1 << lc4, Wo = 1 << lwo, Ho = 1 << lho;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i & (C4 - 1));
+        const long long pix = i >> lc4;
+        const int xo = (int)(pix & (Wo - 1)), yo = (int)((pix >> lwo) & (Ho - 1));
+        const long long b = pix >> (lwo + lho);
+        y[i] = x[((b * (Ho >> 1) + (yo >> 1)) * (Wo >> 1) + (xo >> 1)) * C4 + c];
+    }
+}
+
 // nearest 2x upsampling, [B][H][W][C] -> [B][2H][2W][C]
 __global__ void upsample_kernel(const float* __restrict__ x, int B, int H, int W, int C, float* __restrict__ y)
 {
@@ -725,17 +775,30 @@ __global__ void to_bf16_kernel(const float* __restrict__ x, long long n, __nv_bf
 __global__ void pack_input_kernel(const double* __restrict__ U, long long sample_stride, int nf, const double* __restrict__ scale,
                                   const float* __restrict__ extra, int B, int H, int W, int C, float* __restrict__ x)
 {
-    const long long n = (long long)B * H * W * C;
+    // one thread per pixel: the nf fields (coalesced across the warp), the extra
+    // channel, zeros up to C; 16-byte stores when C is a multiple of 4
     const long long HW = (long long)H * W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const long long pix = i / C;
-        const int b = (int)(pix / HW);
-        const long long q = pix % HW;
-        float v = 0.f;
-        if (c < nf) v = (float)(U[(long long)b * sample_stride + c * HW + q] / scale[c]);
-        else if (c == nf && extra) v = extra[b];
-        x[i] = v;
+    const long long npix = (long long)B * HW;
+    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix;
+         pix += (long long)gridDim.x * blockDim.x) {
+        const long long b = pix / HW, q = pix - b * HW;
+        float* dst = x + pix * C;
+        if ((C & 3) == 0) {
+            for (int c0 = 0; c0 < C; c0 += 4) {
+                float v[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = c0 + e;
+                    v[e] = c < nf ? (float)(U[b * sample_stride + c * HW + q] / scale[c])
+                                  : (c == nf && extra) ? extra[b] : 0.f;
+                }
+                *reinterpret_cast<float4*>(dst + c0) = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        } else {
+            for (int c = 0; c < C; ++c)
+                dst[c] = c < nf ? (float)(U[b * sample_stride + c * HW + q] / scale[c])
+                                : (c == nf && extra) ? extra[b] : 0.f;
+        }
     }
 }
 
@@ -760,19 +823,21 @@ __global__ void pack_target_kernel(const double* __restrict__ Unow, const double
                                    int nf, const double* __restrict__ scale, int B, int H, int W, int C,
                                    float* __restrict__ t)
 {
+    // one thread per pixel (field reads coalesced across the warp), zeros up to C
     const long long HW = (long long)H * W;
-    const long long n = (long long)B * HW * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const long long pix = i / C;
-        const int b = (int)(pix / HW);
-        const long long q = pix % HW;
-        float v = 0.f;
-        if (c < nf) {
-            const long long o = (long long)b * stride + c * HW + q;
-            v = (float)((Unext[o] - Unow[o]) / scale[c]);
+    const long long npix = (long long)B * HW;
+    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix;
+         pix += (long long)gridDim.x * blockDim.x) {
+        const long long b = pix / HW, q = pix - b * HW;
+        float* dst = t + pix * C;
+        for (int c = 0; c < C; ++c) {
+            float v = 0.f;
+            if (c < nf) {
+                const long long o = b * stride + c * HW + q;
+                v = (float)((Unext[o] - Unow[o]) / scale[c]);
+            }
+            dst[c] = v;
         }
-        t[i] = v;
     }
 }
 
@@ -835,26 +900,31 @@ extern "C" {
 
 lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int32_t C2, const void* w_bf16,
                                const float* bias, float* y1, int32_t Co1, float* y2, int32_t Cout, int32_t B,
-                               int32_t H, int32_t W, int32_t KS, int32_t relu, int32_t beta, void* stream)
+                               int32_t H, int32_t W, int32_t KS, int32_t flags, void* stream)
 {
     if (!x1 || !w_bf16 || !y1 || C1 <= 0 || C1 % 32 || C2 < 0 || C2 % 32 || (C2 > 0 && !x2) || Cout <= 0 ||
         Cout % 8 || Co1 <= 0 || Co1 > Cout || (Co1 < Cout && !y2) || B <= 0 || !pow2(H) || !pow2(W) ||
-        (KS != 1 && KS != 3))
+        (KS != 1 && KS != 3) || (flags & ~15) || ((flags & LBM_NN_X1_HALF) && (H < 2 || W < 2)))
         return LBM_ERR_ARG;
-    ConvArgs a{x1, x2, C1, C2, static_cast<const __nv_bfloat16*>(w_bf16), bias, y1, y2, Co1, Cout, B, H, W, relu, beta};
+    ConvArgs a{x1, x2, C1, C2, static_cast<const __nv_bfloat16*>(w_bf16), bias, y1, y2, Co1, Cout, B, H, W,
+               (flags & LBM_NN_RELU) ? 1 : 0, (flags & LBM_NN_ACCUMULATE) ? 1 : 0, (flags & LBM_NN_X1_HALF) ? 1 : 0,
+               (flags & LBM_NN_ACT_BF16) ? 1 : 0};
     const long long P = (long long)B * H * W;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (KS == 3 && H >= TH && W >= TW && Cout % 32 == 0) {
         // halo-tiled kernel: BN = 64 when it divides Cout, else 32
         const long long tiles = (long long)B * (H / TH) * (W / TW);
+        const bool lo = !a.act_bf16;
         if (Cout % 64 == 0) {
             constexpr int smem = conv3_tile_smem_bytes<64>();
-            cudaFuncSetAttribute(conv3_tile_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            conv3_tile_kernel<64><<<dim3((unsigned)tiles, (unsigned)(Cout / 64)), 256, smem, s>>>(a);
+            auto k = lo ? conv3_tile_kernel<64, true> : conv3_tile_kernel<64, false>;
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k<<<dim3((unsigned)tiles, (unsigned)(Cout / 64)), 256, smem, s>>>(a);
         } else {
             constexpr int smem = conv3_tile_smem_bytes<32>();
-            cudaFuncSetAttribute(conv3_tile_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            conv3_tile_kernel<32><<<dim3((unsigned)tiles, (unsigned)(Cout / 32)), 256, smem, s>>>(a);
+            auto k = lo ? conv3_tile_kernel<32, true> : conv3_tile_kernel<32, false>;
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k<<<dim3((unsigned)tiles, (unsigned)(Cout / 32)), 256, smem, s>>>(a);
         }
         return launch_status();
     }
@@ -882,17 +952,20 @@ int64_t lbm_nn_wgrad_workspace_bytes(int32_t Cin, int32_t Cout, int32_t B, int32
 
 lbm_status lbm_nn_conv_backward_weight(const float* dy, int32_t Cout, const float* x1, int32_t C1, const float* x2,
                                        int32_t C2, int32_t B, int32_t H, int32_t W, int32_t KS, float* dw,
-                                       int32_t beta, void* workspace, int64_t workspace_bytes, void* stream)
+                                       int32_t flags, void* workspace, int64_t workspace_bytes, void* stream)
 {
     if (!dy || !x1 || !dw || !workspace || C1 <= 0 || C1 % 32 || C2 < 0 || C2 % 32 || (C2 > 0 && !x2) ||
-        Cout <= 0 || Cout % 8 || B <= 0 || !pow2(H) || !pow2(W) || (KS != 1 && KS != 3))
+        Cout <= 0 || Cout % 8 || B <= 0 || !pow2(H) || !pow2(W) || (KS != 1 && KS != 3) ||
+        (flags & ~(LBM_NN_ACCUMULATE | LBM_NN_X1_HALF)) || ((flags & LBM_NN_X1_HALF) && (H < 2 || W < 2)))
         return LBM_ERR_ARG;
+    const int beta = (flags & LBM_NN_ACCUMULATE) ? 1 : 0;
     const int Cin = C1 + C2;
     if (workspace_bytes < lbm_nn_wgrad_workspace_bytes(Cin, Cout, B, H, W, KS)) return LBM_ERR_ARG;
     const long long P = (long long)B * H * W;
     const int pps = (int)wgrad_pixels_per_split(Cin, Cout, P, KS);
     const int splits = (int)((P + pps - 1) / pps);
-    WgradArgs a{dy, x1, x2, C1, C2, Cout, B, H, W, KS, pps, static_cast<float*>(workspace), ilog2(W), ilog2(H * W)};
+    WgradArgs a{dy, x1, x2, C1, C2, Cout, B, H, W, KS, pps, static_cast<float*>(workspace), ilog2(W), ilog2(H * W),
+                (flags & LBM_NN_X1_HALF) ? 1 : 0};
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     dim3 grid((unsigned)((Cout + 63) / 64), (unsigned)(KS * KS * ((Cin + 63) / 64)), (unsigned)splits);
     conv_wgrad_kernel<<<grid, 256, 0, s>>>(a);
@@ -940,6 +1013,12 @@ lbm_status lbm_nn_relu_backward(float* dy, const float* y, int64_t n, void* stre
 lbm_status lbm_nn_pool(const float* x, int32_t B, int32_t H, int32_t W, int32_t C, float* y, void* stream)
 {
     if (!x || !y || B <= 0 || H < 2 || W < 2 || (H & 1) || (W & 1) || C <= 0) return LBM_ERR_ARG;
+    if (pow2(H) && pow2(W) && C % 4 == 0 && pow2(C / 4)) {
+        const long long n = (long long)B * (H / 2) * (W / 2) * (C / 4);
+        pool4_kernel<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+            reinterpret_cast<const float4*>(x), ilog2(H / 2), ilog2(W / 2), ilog2(C / 4), n, reinterpret_cast<float4*>(y));
+        return launch_status();
+    }
     pool_kernel<<<grid_for((long long)B * H * W * C / 4), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, B, H, W, C, y);
     return launch_status();
 }
@@ -956,6 +1035,12 @@ lbm_status lbm_nn_pool_backward(const float* dy, int32_t B, int32_t H, int32_t W
 lbm_status lbm_nn_upsample(const float* x, int32_t B, int32_t H, int32_t W, int32_t C, float* y, void* stream)
 {
     if (!x || !y || B <= 0 || H <= 0 || W <= 0 || C <= 0) return LBM_ERR_ARG;
+    if (pow2(H) && pow2(W) && C % 4 == 0 && pow2(C / 4)) {
+        const long long n = (long long)B * (2 * H) * (2 * W) * (C / 4);
+        upsample4_kernel<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+            reinterpret_cast<const float4*>(x), ilog2(2 * H), ilog2(2 * W), ilog2(C / 4), n, reinterpret_cast<float4*>(y));
+        return launch_status();
+    }
     upsample_kernel<<<grid_for((long long)B * H * W * C * 4), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, B, H, W,
                                                                                                            C, y);
     return launch_status();
@@ -1003,7 +1088,7 @@ lbm_status lbm_nn_pack_input(const double* U, int64_t sample_stride, int32_t nf,
                              const float* extra, int32_t B, int32_t H, int32_t W, int32_t C, float* x, void* stream)
 {
     if (!U || !scale || !x || nf <= 0 || C < nf + (extra ? 1 : 0) || B <= 0 || H <= 0 || W <= 0) return LBM_ERR_ARG;
-    pack_input_kernel<<<grid_for((long long)B * H * W * C), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+    pack_input_kernel<<<grid_for((long long)B * H * W), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         U, sample_stride, nf, scale, extra, B, H, W, C, x);
     return launch_status();
 }
@@ -1012,7 +1097,7 @@ lbm_status lbm_nn_pack_target(const double* Unow, const double* Unext, int64_t s
                               const double* scale, int32_t B, int32_t H, int32_t W, int32_t C, float* t, void* stream)
 {
     if (!Unow || !Unext || !scale || !t || nf <= 0 || C < nf || B <= 0 || H <= 0 || W <= 0) return LBM_ERR_ARG;
-    pack_target_kernel<<<grid_for((long long)B * H * W * C), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+    pack_target_kernel<<<grid_for((long long)B * H * W), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         Unow, Unext, sample_stride, nf, scale, B, H, W, C, t);
     return launch_status();
 }

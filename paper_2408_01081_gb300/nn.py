@@ -24,7 +24,7 @@ def _lib():
     if not _done:
         vp, i32, i64, f32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
         sig = {
-            "lbm_nn_conv_forward": [vp, i32, vp, i32, vp, vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, vp],
+            "lbm_nn_conv_forward": [vp, i32, vp, i32, vp, vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, vp],
             "lbm_nn_wgrad_workspace_bytes": [i32, i32, i32, i32, i32, i32],
             "lbm_nn_conv_backward_weight": [vp, i32, vp, i32, vp, i32, i32, i32, i32, i32, vp, i32, vp, i64, vp],
             "lbm_nn_bias_grad_workspace_bytes": [i64, i32],
@@ -65,18 +65,25 @@ def _ok(name, st):
         raise _lbm.LbmError(st, f"{name} failed")
 
 
-def conv_forward(x1, C1, x2, C2, w_bf16, bias, y1, Co1, y2, Cout, B, H, W, KS, relu=False, beta=False):
+RELU, ACCUMULATE, X1_HALF, ACT_BF16 = 1, 2, 4, 8     # flags of include/lbm_nn.h
+
+
+def conv_forward(x1, C1, x2, C2, w_bf16, bias, y1, Co1, y2, Cout, B, H, W, KS, relu=False, beta=False,
+                 x1_half=False, act_bf16=False):
+    flags = (RELU if relu else 0) | (ACCUMULATE if beta else 0) | (X1_HALF if x1_half else 0) | \
+        (ACT_BF16 if act_bf16 else 0)
     _ok("lbm_nn_conv_forward", _lib().lbm_nn_conv_forward(_p(x1), C1, _p(x2), C2, _p(w_bf16), _p(bias), _p(y1), Co1,
-                                                          _p(y2), Cout, B, H, W, KS, int(relu), int(beta), _s()))
+                                                          _p(y2), Cout, B, H, W, KS, flags, _s()))
 
 
 def wgrad_workspace_bytes(Cin, Cout, B, H, W, KS) -> int:
     return int(_lib().lbm_nn_wgrad_workspace_bytes(Cin, Cout, B, H, W, KS))
 
 
-def conv_backward_weight(dy, Cout, x1, C1, x2, C2, B, H, W, KS, dw, workspace, beta=False):
+def conv_backward_weight(dy, Cout, x1, C1, x2, C2, B, H, W, KS, dw, workspace, beta=False, x1_half=False):
+    flags = (ACCUMULATE if beta else 0) | (X1_HALF if x1_half else 0)
     _ok("lbm_nn_conv_backward_weight",
-        _lib().lbm_nn_conv_backward_weight(_p(dy), Cout, _p(x1), C1, _p(x2), C2, B, H, W, KS, _p(dw), int(beta),
+        _lib().lbm_nn_conv_backward_weight(_p(dy), Cout, _p(x1), C1, _p(x2), C2, B, H, W, KS, _p(dw), flags,
                                            _p(workspace), workspace.numel() * workspace.element_size(), _s()))
 
 

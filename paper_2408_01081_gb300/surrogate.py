@@ -55,15 +55,18 @@ class Conv:
     def nparams(self):
         return self.w.numel() + self.b.numel()
 
-    def forward(self, x1, x2, y, B, H, W):
+    def forward(self, x1, x2, y, B, H, W, x1_half=False, act_bf16=False):
+        """x1_half: x1 is at (H/2, W/2), read nearest-upsampled (the decoder's upsampling)."""
         K.conv_forward(x1, self.cin1, x2, self.cin2, self.wb, self.b, y, self.cout, None, self.cout, B, H, W,
-                       self.ks, relu=self.relu)
+                       self.ks, relu=self.relu, x1_half=x1_half, act_bf16=act_bf16)
 
-    def backward(self, dy, y, x1, x2, B, H, W, dx1, dx2, workspace, need_dx=True):
-        """dy: gradient w.r.t. this layer's output (overwritten by the ReLU mask)."""
+    def backward(self, dy, y, x1, x2, B, H, W, dx1, dx2, workspace, need_dx=True, x1_half=False):
+        """dy: gradient w.r.t. this layer's output (overwritten by the ReLU mask); with x1_half
+        the data gradient dx1 is at full resolution (the caller folds it back to (H/2, W/2))."""
         if self.relu:
             K.relu_backward(dy, y)
-        K.conv_backward_weight(dy, self.cout, x1, self.cin1, x2, self.cin2, B, H, W, self.ks, self.gw, workspace)
+        K.conv_backward_weight(dy, self.cout, x1, self.cin1, x2, self.cin2, B, H, W, self.ks, self.gw, workspace,
+                               x1_half=x1_half)
         K.bias_grad(dy, B * H * W, self.cout, self.gb, workspace)
         if need_dx:
             K.weight_flip(self.wb, self.cout, self.cin1 + self.cin2, self.ks, self.wt)
@@ -124,7 +127,7 @@ class UNet:
                 A[f"p{l}"] = t.empty((B, h, w, self.c[l - 1]), **f32)
         for l in (2, 1, 0):
             h, w = hw[l]
-            A[f"u{l}"] = t.empty((B, h, w, self.c[l + 1]), **f32)
+            A[f"u{l}"] = t.empty((B, h, w, self.c[l + 1]), **f32)     # shape only: G[u] is the upsampled gradient
             A[f"da{l}"] = t.empty((B, h, w, self.c[l]), **f32)
             A[f"d{l}"] = t.empty((B, h, w, self.c[l]), **f32)
         A["x0"] = t.empty((B, H, W, CIN_PAD), **f32)
@@ -141,8 +144,10 @@ class UNet:
         self.shape = (B, H, W)
 
     # -- forward / backward ---------------------------------------------
-    def forward(self, B, H, W):
-        """x0 must already hold the packed input; result in self.A['out']."""
+    def forward(self, B, H, W, act_bf16=False):
+        """x0 must already hold the packed input; result in self.A['out'].  The decoder's
+        nearest upsampling is folded into the next convolution (it reads the coarse tensor).
+        act_bf16: activations as one BF16 value (inference only; training uses the hi/lo pair)."""
         A = self.A
         x = A["x0"]
         for l in range(4):
@@ -151,17 +156,16 @@ class UNet:
                 K.pool(A[f"e{l - 1}"], B, 2 * h, 2 * w, self.c[l - 1], A[f"p{l}"])
                 x = A[f"p{l}"]
             ca, cb = self.enc[l]
-            ca.forward(x, None, A[f"ea{l}"], B, h, w)
-            cb.forward(A[f"ea{l}"], None, A[f"e{l}"], B, h, w)
+            ca.forward(x, None, A[f"ea{l}"], B, h, w, act_bf16=act_bf16)
+            cb.forward(A[f"ea{l}"], None, A[f"e{l}"], B, h, w, act_bf16=act_bf16)
         prev = A["e3"]
         for l in (2, 1, 0):
             h, w = H >> l, W >> l
-            K.upsample(prev, B, h // 2, w // 2, self.c[l + 1], A[f"u{l}"])
             ca, cb = self.dec[l]
-            ca.forward(A[f"u{l}"], A[f"e{l}"], A[f"da{l}"], B, h, w)
-            cb.forward(A[f"da{l}"], None, A[f"d{l}"], B, h, w)
+            ca.forward(prev, A[f"e{l}"], A[f"da{l}"], B, h, w, x1_half=True, act_bf16=act_bf16)
+            cb.forward(A[f"da{l}"], None, A[f"d{l}"], B, h, w, act_bf16=act_bf16)
             prev = A[f"d{l}"]
-        self.out.forward(A["d0"], None, A["out"], B, H, W)
+        self.out.forward(A["d0"], None, A["out"], B, H, W, act_bf16=act_bf16)
 
     def backward(self, B, H, W):
         """G['out'] must hold dLoss/dout; fills every layer's gw, gb."""
@@ -172,7 +176,9 @@ class UNet:
             ca, cb = self.dec[l]
             cb.backward(G[f"d{l}"], A[f"d{l}"], A[f"da{l}"], None, B, h, w, G[f"da{l}"], None, ws)
             # data gradient of [up | skip]: up part -> G[u], skip part -> G[e] (initialised here)
-            ca.backward(G[f"da{l}"], A[f"da{l}"], A[f"u{l}"], A[f"e{l}"], B, h, w, G[f"u{l}"], G[f"e{l}"], ws)
+            coarse = A["e3"] if l == 2 else A[f"d{l + 1}"]
+            ca.backward(G[f"da{l}"], A[f"da{l}"], coarse, A[f"e{l}"], B, h, w, G[f"u{l}"], G[f"e{l}"], ws,
+                        x1_half=True)
             src = G["e3"] if l == 2 else G[f"d{l + 1}"]
             K.upsample_backward(G[f"u{l}"], B, h // 2, w // 2, self.c[l + 1], src)
         for l in (3, 2, 1, 0):
@@ -298,11 +304,12 @@ class Surrogate:
     def pack(self, U, stride, nu_norm, B, H, W):
         K.pack_input(U, stride, NF, self.scale, nu_norm, B, H, W, CIN_PAD, self.net.A["x0"])
 
-    def predict(self, U, stride, nu_norm, B, H, W, Uout, out_stride):
-        """Uout = U + scale * net(U): the moment fields k steps later (FP64)."""
+    def predict(self, U, stride, nu_norm, B, H, W, Uout, out_stride, act_bf16=False):
+        """Uout = U + scale * net(U): the moment fields k steps later (FP64).  act_bf16 runs
+        the network with single-BF16 activations (half the tensor-core work)."""
         self.net._alloc(B, H, W)
         self.pack(U, stride, nu_norm, B, H, W)
-        self.net.forward(B, H, W)
+        self.net.forward(B, H, W, act_bf16=act_bf16)
         K.residual_output(U, stride, self.net.A["out"], COUT_PAD, self.scale, NF, B, H, W, Uout, out_stride)
 
 
@@ -375,7 +382,7 @@ def relative_error(sur, Upred, Uref, stride, B, H, W):
 # evaluation, timing and the fallback driver
 # ---------------------------------------------------------------------------
 
-def evaluate(sur, chunk, batch=16):
+def evaluate(sur, chunk, batch=16, act_bf16=False):
     """One-jump relative errors on a chunk: surrogate vs the solver's own next snapshot,
     and the persistence baseline U(t + k dt) ~ U(t)."""
     import torch
@@ -385,7 +392,7 @@ def evaluate(sur, chunk, batch=16):
     errs, pers = [], []
     for j in range(chunk.J):
         for i0 in range(0, chunk.n - batch + 1, batch):
-            sur.predict(chunk.U[j, i0], stride, chunk.nu_norm[i0:], batch, H, W, pred, stride)
+            sur.predict(chunk.U[j, i0], stride, chunk.nu_norm[i0:], batch, H, W, pred, stride, act_bf16=act_bf16)
             errs.extend(relative_error(sur, pred, chunk.U[j + 1, i0:i0 + batch], stride, batch, H, W))
             pers.extend(relative_error(sur, chunk.U[j, i0:i0 + batch], chunk.U[j + 1, i0:i0 + batch], stride, batch,
                                        H, W))
@@ -462,8 +469,8 @@ class FallbackDriver:
 
 
 def timing(sur, n=16, H=256, W=256, reps=5):
-    """ms per lattice for one jump: surrogate inference (batch n) vs k solver steps on a batch
-    of n lattices (FP64 and FP32 storage)."""
+    """ms per lattice for one jump: surrogate inference (batch n; hi/lo activations and
+    single-BF16 activations) vs k solver steps on a batch of n lattices (FP64, FP32 storage)."""
     import torch
     k = sur.k
     stride = 10 * H * W
@@ -474,15 +481,19 @@ def timing(sur, n=16, H=256, W=256, reps=5):
     nu_norm = torch.tensor((nu - NU_MEAN) / NU_STD, dtype=torch.float32, device=sur.net.dev)
     out = torch.empty_like(U)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sur.predict(U[0], stride, nu_norm, n, H, W, out[0], stride)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(reps):
-        sur.predict(U[0], stride, nu_norm, n, H, W, out[0], stride)
-    e1.record()
-    torch.cuda.synchronize()
-    t_sur = e0.elapsed_time(e1) / reps / n
-    res = {"surrogate_ms_per_lattice": t_sur, "batch": n, "H": H, "W": W, "k": k}
+    t = {}
+    for fast in (False, True):
+        sur.predict(U[0], stride, nu_norm, n, H, W, out[0], stride, act_bf16=fast)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            sur.predict(U[0], stride, nu_norm, n, H, W, out[0], stride, act_bf16=fast)
+        e1.record()
+        torch.cuda.synchronize()
+        t[fast] = e0.elapsed_time(e1) / reps / n
+    t_sur = t[False]
+    res = {"surrogate_ms_per_lattice": t_sur, "surrogate_bf16_act_ms_per_lattice": t[True], "batch": n, "H": H,
+           "W": W, "k": k}
     for storage in ("f64", "f32"):
         b = L.lbm_batch_create(_descs_for(nu, H, W), storage=L.STORAGE[storage],
                                stream=torch.cuda.current_stream().cuda_stream)
@@ -496,6 +507,7 @@ def timing(sur, n=16, H=256, W=256, reps=5):
         res[f"lbm_{storage}_ms_per_lattice"] = e0.elapsed_time(e1) / reps / n
         L.lbm_batch_destroy(b)
         res[f"gain_vs_{storage}"] = res[f"lbm_{storage}_ms_per_lattice"] / t_sur
+        res[f"gain_bf16_act_vs_{storage}"] = res[f"lbm_{storage}_ms_per_lattice"] / t[True]
     return res
 
 
@@ -513,6 +525,7 @@ def run(out_dir, n_chunks=20, lattices=256, H=256, W=256, k=32, J=4, batch=8, lr
     t_train = time.time() - t0
     held = generate_chunk(eval_lattices, 900_000, H=H, W=W, k=k, J=J)
     errs, pers = evaluate(sur, held, batch=16)
+    errs_fast, _ = evaluate(sur, held, batch=16, act_bf16=True)
     tm = timing(sur, n=16, H=H, W=W)
     drv = FallbackDriver(sur, tol=1e-3, check_every=1)
     _, derr = drv.jump(held.U[0, :16].contiguous(), held.nu[:16])
@@ -521,6 +534,7 @@ def run(out_dir, n_chunks=20, lattices=256, H=256, W=256, k=32, J=4, batch=8, lr
         "pairs_seen": sur.net.step_count * batch, "iterations": sur.net.step_count, "train_s": round(t_train, 1),
         "final_loss": hist[-1][1] if hist else None,
         "heldout_rel_l2": {"median": float(np.median(errs)), "mean": float(np.mean(errs)), "max": float(np.max(errs))},
+        "heldout_rel_l2_bf16_activations": {"median": float(np.median(errs_fast)), "max": float(np.max(errs_fast))},
         "persistence_rel_l2": {"median": float(np.median(pers)), "mean": float(np.mean(pers))},
         "fallback_tol": 1e-3, "fallback_fraction": drv.fallbacks / max(1, drv.checked),
         "judge_errors_after_relift": [float(e) for e in derr],

@@ -213,3 +213,34 @@ def test_unet_output_and_gradients_match_reference(lbm):
         e_w = rel_l2(layer.gw.cpu().numpy(), grads[i][0])
         e_b = rel_l2(layer.gb.cpu().numpy(), grads[i][1])
         assert e_w < 1e-3 and e_b < 1e-3, (i, e_w, e_b)
+
+
+@pytest.mark.parametrize("H,W,KS", [(16, 32, 3), (8, 8, 3), (16, 16, 1)])
+def test_conv_half_resolution_input_and_bf16_activations(lbm, H, W, KS):
+    """x1 read nearest-upsampled from (H/2, W/2) equals the convolution of the materialised
+    upsampled tensor; single-BF16 activations stay within BF16 rounding of the exact result."""
+    import torch
+    from paper_2408_01081_gb300 import nn as K
+    B, C1, C2, Cout = 2, 64, 32, 64
+    xc = RNG.standard_normal((B, H // 2, W // 2, C1)).astype(np.float32)
+    xu = np.repeat(np.repeat(xc, 2, axis=1), 2, axis=2)
+    x2 = RNG.standard_normal((B, H, W, C2)).astype(np.float32)
+    w = _bf16(RNG.standard_normal((Cout, KS, KS, C1 + C2)) * 0.1)
+    b = RNG.standard_normal(Cout).astype(np.float32)
+    ref = R.conv(np.concatenate([xu, x2], axis=3).astype(np.float64), w, b)
+    y = _t(np.zeros((B, H, W, Cout), np.float32))
+    K.conv_forward(_t(xc), C1, _t(x2), C2, _wb(w), _t(b), y, Cout, None, Cout, B, H, W, KS, x1_half=True)
+    assert rel_l2(y.cpu().numpy(), ref) < 2e-5, rel_l2(y.cpu().numpy(), ref)
+    y2 = _t(np.zeros((B, H, W, Cout), np.float32))
+    K.conv_forward(_t(xu), C1, _t(x2), C2, _wb(w), _t(b), y2, Cout, None, Cout, B, H, W, KS, act_bf16=True)
+    e = rel_l2(y2.cpu().numpy(), ref)
+    assert 1e-5 < e < 1e-2, e           # BF16 rounding of the activations, and only that
+    # weight gradient with the half-resolution x1 equals the one of the upsampled tensor
+    dy = RNG.standard_normal((B, H, W, Cout)).astype(np.float32)
+    ws = torch.empty(K.wgrad_workspace_bytes(C1 + C2, Cout, B, H, W, KS) // 4 + 1, dtype=torch.float32,
+                     device="cuda")
+    dwh = torch.empty((Cout, KS, KS, C1 + C2), dtype=torch.float32, device="cuda")
+    dwf = torch.empty_like(dwh)
+    K.conv_backward_weight(_t(dy), Cout, _t(xc), C1, _t(x2), C2, B, H, W, KS, dwh, ws, x1_half=True)
+    K.conv_backward_weight(_t(dy), Cout, _t(xu), C1, _t(x2), C2, B, H, W, KS, dwf, ws)
+    torch.testing.assert_close(dwh, dwf, rtol=0, atol=0)
