@@ -221,8 +221,8 @@ __global__ void __launch_bounds__(256) conv_fwd_kernel(ConvArgs a)
 // arithmetic as conv_fwd_kernel; warps: 4 along the tile rows (2 rows = 2 m16
 // tiles each) x 2 along the output channels.
 // ---------------------------------------------------------------------------
-constexpr int TH = 8, TW = 16;                  // output tile (pixels)
-constexpr int HH = TH + 2, HW2 = TW + 2;        // halo tile
+constexpr int TW = 16;                          // output tile width (pixels); height TH is 8 or 16
+constexpr int HW2 = TW + 2;                     // halo tile width
 constexpr int KROW = CKC + CPAD;                // smem row: 40 bf16 = 80 bytes
 
 __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __nv_bfloat16* p)
@@ -234,24 +234,28 @@ __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __nv_bfloat16* p
                  : "memory");
 }
 
-template <int BN>
+template <int BN, int TH>
 constexpr int conv3_tile_smem_bytes()
 {
-    return (2 * HH * HW2 + 9 * BN) * KROW * (int)sizeof(__nv_bfloat16);
+    return (2 * (TH + 2) * HW2 + 9 * BN) * KROW * (int)sizeof(__nv_bfloat16);
 }
 
-template <int BN, bool LO>
+// TH = 8: warps 4 (row pairs) x 2 (channel halves); TH = 16: 8 row pairs x all BN channels
+template <int BN, bool LO, int TH>
 __global__ void __launch_bounds__(256) conv3_tile_kernel(ConvArgs a)
 {
+    constexpr int HH = TH + 2;               // halo tile height
+    constexpr int WR = TH / 2;               // warps along the tile rows (2 rows each)
+    constexpr int WC = 8 / WR;               // warps along the output channels
     extern __shared__ __align__(16) __nv_bfloat16 smem[];
     __nv_bfloat16* Ah = smem;                            // [HH*HW2][KROW]
     __nv_bfloat16* Al = Ah + HH * HW2 * KROW;            // [HH*HW2][KROW]
     __nv_bfloat16* Bs = Al + HH * HW2 * KROW;            // [9][BN][KROW]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t4 = lane & 3;
-    const int wm = warp & 3;                 // tile rows 2 wm, 2 wm + 1
-    const int wn = warp >> 2;                // output-channel half
-    constexpr int WN = BN / 2;
+    const int wm = warp % WR;                // tile rows 2 wm, 2 wm + 1
+    const int wn = warp / WR;                // output-channel group
+    constexpr int WN = BN / WC;
     constexpr int NT = WN / 8;               // n8 tiles per warp (even)
     const int tiles_x = a.W / TW, tiles_y = a.H / TH;
     const int tile = blockIdx.x;
@@ -911,21 +915,27 @@ lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int
                (flags & LBM_NN_ACT_BF16) ? 1 : 0};
     const long long P = (long long)B * H * W;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (KS == 3 && H >= TH && W >= TW && Cout % 32 == 0) {
-        // halo-tiled kernel: BN = 64 when it divides Cout, else 32
-        const long long tiles = (long long)B * (H / TH) * (W / TW);
+    if (KS == 3 && H >= 8 && W >= TW && Cout % 32 == 0) {
+        // halo-tiled kernel: BN = 64 when it divides Cout, else 32; 16-row tiles when H allows
         const bool lo = !a.act_bf16;
-        if (Cout % 64 == 0) {
-            constexpr int smem = conv3_tile_smem_bytes<64>();
-            auto k = lo ? conv3_tile_kernel<64, true> : conv3_tile_kernel<64, false>;
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            k<<<dim3((unsigned)tiles, (unsigned)(Cout / 64)), 256, smem, s>>>(a);
+        const int th = H >= 16 ? 16 : 8;
+        const long long tiles = (long long)B * (H / th) * (W / TW);
+        const int bn = (Cout % 64 == 0) ? 64 : 32;
+        const dim3 grid((unsigned)tiles, (unsigned)(Cout / bn));
+#define LBM_CONV3(BNV, LOV, THV)                                                                     \
+    do {                                                                                             \
+        constexpr int smem = conv3_tile_smem_bytes<BNV, THV>();                                      \
+        cudaFuncSetAttribute(conv3_tile_kernel<BNV, LOV, THV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+        conv3_tile_kernel<BNV, LOV, THV><<<grid, 256, smem, s>>>(a);                                 \
+    } while (0)
+        if (bn == 64) {
+            if (th == 16) { if (lo) LBM_CONV3(64, true, 16); else LBM_CONV3(64, false, 16); }
+            else { if (lo) LBM_CONV3(64, true, 8); else LBM_CONV3(64, false, 8); }
         } else {
-            constexpr int smem = conv3_tile_smem_bytes<32>();
-            auto k = lo ? conv3_tile_kernel<32, true> : conv3_tile_kernel<32, false>;
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            k<<<dim3((unsigned)tiles, (unsigned)(Cout / 32)), 256, smem, s>>>(a);
+            if (th == 16) { if (lo) LBM_CONV3(32, true, 16); else LBM_CONV3(32, false, 16); }
+            else { if (lo) LBM_CONV3(32, true, 8); else LBM_CONV3(32, false, 8); }
         }
+#undef LBM_CONV3
         return launch_status();
     }
     const int BN = Cout >= 64 ? 64 : (Cout >= 32 ? 32 : 16);
