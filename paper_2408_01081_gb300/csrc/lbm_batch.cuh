@@ -209,7 +209,7 @@ __device__ __forceinline__ void batch_tile(const LatDesc& L, int local_tile, con
 }
 
 template <int K, int V, bool PERSISTENT>
-__global__ void __launch_bounds__(256, K == K_F64 ? LBM_SPLIT_MIN_BLOCKS : 1) batch_step_kernel(BatchArgs A)
+__global__ void __launch_bounds__(256, K == K_F64 ? LBM_SPLIT_MIN_BLOCKS : 2) batch_step_kernel(BatchArgs A)
 {
     using E = typename Fmt<K>::E;
     const E* a = static_cast<const E*>(A.arenaA);

@@ -672,19 +672,27 @@ __global__ void init_kernel(NodeArgs A, const double* __restrict__ U0, const dou
         phiy(pxx, a, b, pypxx);
         phix(pyy, a, b, pxpyy);
         phiy(pyy, a, b, pypyy);
+        // per velocity (i, j), with the zero and unit factors of i, j written out:
+        //   f = 1/4 (u + 2 (i px u + j py u)) - dt/8 [ b + 2 (i px b + j py b)
+        //       + c (i u_x + (2 i^2 - 1) px u_x - 2 (i px + j py) px u_x)
+        //       + c (j u_y + (2 j^2 - 1) py u_y - 2 (i px + j py) py u_y) ]
         double f[4][5];
-        const int VI[4] = {1, 0, -1, 0}, VJ[4] = {0, 1, 0, -1};
+        const double h = 0.125 * A.dt;
 #pragma unroll
-        for (int d = 0; d < 4; ++d) {
-            const double i = VI[d], j = VJ[d];
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                const double eq = 0.25 * (u[k] + 2.0 * (i * pxu[k] + j * pyu[k]));
-                const double corr = (bv[k] + 2.0 * (i * pxb[k] + j * pyb[k]))
-                                  + c * (i * ux[k] + (2.0 * i * i - 1.0) * pxx[k] - 2.0 * (i * pxpxx[k] + j * pypxx[k]))
-                                  + c * (j * uy[k] + (2.0 * j * j - 1.0) * pyy[k] - 2.0 * (i * pxpyy[k] + j * pypyy[k]));
-                f[d][k] = eq - 0.125 * A.dt * corr;
-            }
+        for (int k = 0; k < 5; ++k) {
+            const double q = bv[k];
+            // (1,0) and (-1,0)
+            const double ex = 0.5 * pxu[k], bx2 = 2.0 * pxb[k];
+            const double sx = c * (pxx[k] - pyy[k]);                     // parts common to +/- x
+            const double dxp = c * (ux[k] - 2.0 * pxpxx[k] - 2.0 * pxpyy[k]);
+            f[0][k] = (0.25 * u[k] + ex) - h * ((q + bx2) + (sx + dxp));
+            f[2][k] = (0.25 * u[k] - ex) - h * ((q - bx2) + (sx - dxp));
+            // (0,1) and (0,-1)
+            const double ey = 0.5 * pyu[k], by2 = 2.0 * pyb[k];
+            const double sy = c * (pyy[k] - pxx[k]);
+            const double dyp = c * (uy[k] - 2.0 * pypxx[k] - 2.0 * pypyy[k]);
+            f[1][k] = (0.25 * u[k] + ey) - h * ((q + by2) + (sy + dyp));
+            f[3][k] = (0.25 * u[k] - ey) - h * ((q - by2) + (sy - dyp));
         }
         double S[4][5], U[5];
         collide_node(f, bv[0], bv[1], A.dt, A.omega, a, b, S, U);

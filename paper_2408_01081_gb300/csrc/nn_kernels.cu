@@ -225,6 +225,13 @@ constexpr int TW = 16;                          // output tile width (pixels); h
 constexpr int HW2 = TW + 2;                     // halo tile width
 constexpr int KROW = CKC + CPAD;                // smem row: 40 bf16 = 80 bytes
 
+// 16-byte global -> shared copy that bypasses the registers (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(__nv_bfloat16* smem_dst, const __nv_bfloat16* gmem_src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
 __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __nv_bfloat16* p)
 {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
@@ -296,15 +303,15 @@ __global__ void __launch_bounds__(256) conv3_tile_kernel(ConvArgs a)
                     make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
             }
         }
-        // --- stage the weights of the nine taps: BN x 32 inputs each ---
+        // --- stage the weights of the nine taps: BN x 32 inputs each (asynchronous copies;
+        //     the launcher guarantees co0 + BN <= Cout) ---
         for (int q = tid; q < 9 * BN * 4; q += 256) {
             const int tap = q / (BN * 4), r = q % (BN * 4);
             const int nn = r >> 2, part = r & 3;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (co0 + nn < a.Cout)
-                val = *reinterpret_cast<const uint4*>(a.w + ((long long)(co0 + nn) * 9 + tap) * Cin + ci0 + part * 8);
-            *reinterpret_cast<uint4*>(Bs + (tap * BN + nn) * KROW + part * 8) = val;
+            cp_async16(Bs + (tap * BN + nn) * KROW + part * 8,
+                       a.w + ((long long)(co0 + nn) * 9 + tap) * Cin + ci0 + part * 8);
         }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
 #pragma unroll 1
         for (int tap = 0; tap < 9; ++tap) {

@@ -6,6 +6,10 @@
   observed orders between successive lattices.
 * :func:`long_run` -- homogeneous Dirichlet, b = 0, the initial data of the
   energy test (Sec. 6.2) on a 2:1 rectangle; relative drift of ||f||_P.
+* :func:`precision_errors` -- periodic lattice with a Gaussian-random initial
+  velocity, every storage format run for the same number of steps; relative L2
+  of each moment field against the FP64 run (which matches the CPU oracle to
+  1e-12), and the step rate of each format.
 
 Inputs come from :mod:`workloads` (exact separable tables for b and the wall
 data, so nothing per step is built on the host); every step runs in the
@@ -137,10 +141,50 @@ def long_run(steps=100_000, nx=512, ny=256, cK2=1.1, cmu2=0.4, cfl=None, dt=None
             "wall_s": wall}
 
 
+def precision_errors(n=8192, steps=5000, formats=("f32", "bf16", "f16", "ms_bf16", "ms_f16"), seeds=(1, 2),
+                     ell=64.0, std=1e-3, cK2=1.5, cmu2=0.5, cfl=0.9, device="cuda"):
+    """Relative L2 of v_x, v_y, j_s, j_d, j_xy after `steps` steps, each format vs FP64."""
+    import torch
+    import workloads as W
+    wl = W.grf_periodic(n, n, cK2, cmu2, cfl=cfl, ell=ell, std=std, seeds=seeds, steps=0)
+    dev = torch.device(device)
+    U0 = torch.from_numpy(wl.U0).to(dev)
+    Ux = torch.from_numpy(wl.dU0dx).to(dev)
+    Uy = torch.from_numpy(wl.dU0dy).to(dev)
+    st = torch.cuda.current_stream()
+    out = torch.empty((10, n, n), dtype=torch.float64, device=dev)
+    res, ref = {}, None
+    for storage in ("f64",) + tuple(formats):
+        lat = L.Lattice(n, n, wl.dx, wl.dt, wl.cK, wl.cmu, storage=storage, track_displacement=False,
+                        stream=st.cuda_stream)
+        lat.init(U0, Ux, Uy)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.step(steps)
+        lat.synchronize()
+        wall = time.perf_counter() - t0
+        lat.moments(out)
+        torch.cuda.synchronize()
+        lat.close()
+        fields = out[0:5].clone()
+        row = {"mlups": n * n * steps / wall / 1e6}
+        if ref is None:
+            ref = fields
+        else:
+            names = ["v_x", "v_y", "j_s", "j_d", "j_xy"]
+            row["rel_l2_vs_f64"] = {nm: float(torch.linalg.vector_norm(fields[q] - ref[q]) /
+                                              torch.linalg.vector_norm(ref[q])) for q, nm in enumerate(names)}
+        res[storage] = row
+        del fields
+    return {"n": n, "steps": steps, "ell": ell, "std": std, "formats": res}
+
+
 if __name__ == "__main__":
     import argparse
     ap = argparse.ArgumentParser(description="convergence sweep and long run on the GPU")
-    ap.add_argument("--what", default="all", choices=["all", "convergence", "longrun"])
+    ap.add_argument("--what", default="all", choices=["all", "convergence", "longrun", "precision"])
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--storage", default="f64")
     ap.add_argument("--max-ny", type=int, default=4096)
     ap.add_argument("--out", default=None)
@@ -151,6 +195,8 @@ if __name__ == "__main__":
         res["convergence"] = dirichlet_convergence(nys, storage=a.storage)
     if a.what in ("all", "longrun"):
         res["longrun"] = [long_run(storage=a.storage)]
+    if a.what == "precision":
+        res["precision"] = precision_errors(n=a.n, steps=a.steps)
     txt = json.dumps(res, indent=1)
     if a.out:
         open(a.out, "w").write(txt)

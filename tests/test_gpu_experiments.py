@@ -41,3 +41,13 @@ def test_dirichlet_separable_wall_tables_match_dense(lbm):
 def test_long_run_energy_fp64(lbm):
     r = X.long_run(steps=100_000, nx=512, ny=256, every=10_000)
     assert r["finite"] and r["max_rel_energy_drift"] < 1e-12, r
+
+
+def test_precision_errors_ordering(lbm):
+    """Storage formats against the FP64 run on a small lattice: FP32 within its 1e-5 bar,
+    FP16 and moment-space formats below BF16 (more mantissa bits or fewer rounded values)."""
+    r = X.precision_errors(n=256, steps=300, ell=16.0)["formats"]
+    worst = {s: max(v["rel_l2_vs_f64"].values()) for s, v in r.items() if s != "f64"}
+    assert worst["f32"] < 1e-5, worst
+    assert worst["ms_f16"] < worst["f16"] < worst["bf16"], worst
+    assert worst["ms_bf16"] < worst["bf16"], worst
