@@ -63,8 +63,12 @@ __device__ __forceinline__ void tb_load_row(const typename Fmt<K>::E* __restrict
     }
 }
 
+#ifndef LBM_TB_MIN_BLOCKS
+#define LBM_TB_MIN_BLOCKS 1
+#endif
+
 template <int K, bool DIRICHLET>
-__global__ void __launch_bounds__(128) tb2_kernel(TbArgs A)
+__global__ void __launch_bounds__(128, LBM_TB_MIN_BLOCKS) tb2_kernel(TbArgs A)
 {
     using E = typename Fmt<K>::E;
     const E* __restrict__ src = static_cast<const E*>(A.src);

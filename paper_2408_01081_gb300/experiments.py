@@ -142,8 +142,9 @@ def long_run(steps=100_000, nx=512, ny=256, cK2=1.1, cmu2=0.4, cfl=None, dt=None
 
 
 def precision_errors(n=8192, steps=5000, formats=("f32", "bf16", "f16", "ms_bf16", "ms_f16"), seeds=(1, 2),
-                     ell=64.0, std=1e-3, cK2=1.5, cmu2=0.5, cfl=0.9, device="cuda"):
-    """Relative L2 of v_x, v_y, j_s, j_d, j_xy after `steps` steps, each format vs FP64."""
+                     ell=64.0, std=1e-3, cK2=1.5, cmu2=0.5, cfl=0.9, every=1000, device="cuda"):
+    """Relative L2 of v_x, v_y, j_s, j_d, j_xy at steps every, 2 every, ..., steps: each
+    storage format against the FP64 run (kept as snapshots on the device)."""
     import torch
     import workloads as W
     wl = W.grf_periodic(n, n, cK2, cmu2, cfl=cfl, ell=ell, std=std, seeds=seeds, steps=0)
@@ -153,30 +154,36 @@ def precision_errors(n=8192, steps=5000, formats=("f32", "bf16", "f16", "ms_bf16
     Uy = torch.from_numpy(wl.dU0dy).to(dev)
     st = torch.cuda.current_stream()
     out = torch.empty((10, n, n), dtype=torch.float64, device=dev)
-    res, ref = {}, None
+    checkpoints = list(range(every, steps + 1, every)) or [steps]
+    names = ["v_x", "v_y", "j_s", "j_d", "j_xy"]
+    res, ref = {}, {}
     for storage in ("f64",) + tuple(formats):
         lat = L.Lattice(n, n, wl.dx, wl.dt, wl.cK, wl.cmu, storage=storage, track_displacement=False,
                         stream=st.cuda_stream)
         lat.init(U0, Ux, Uy)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        lat.step(steps)
-        lat.synchronize()
-        wall = time.perf_counter() - t0
-        lat.moments(out)
-        torch.cuda.synchronize()
+        row = {"rel_l2_vs_f64": {}}
+        done, wall = 0, 0.0
+        for cp in checkpoints:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lat.step(cp - done)
+            lat.synchronize()
+            wall += time.perf_counter() - t0
+            done = cp
+            lat.moments(out)
+            torch.cuda.synchronize()
+            if storage == "f64":
+                ref[cp] = out[0:5].clone()
+            else:
+                row["rel_l2_vs_f64"][cp] = {nm: float(torch.linalg.vector_norm(out[q] - ref[cp][q]) /
+                                                      torch.linalg.vector_norm(ref[cp][q]))
+                                            for q, nm in enumerate(names)}
         lat.close()
-        fields = out[0:5].clone()
-        row = {"mlups": n * n * steps / wall / 1e6}
-        if ref is None:
-            ref = fields
-        else:
-            names = ["v_x", "v_y", "j_s", "j_d", "j_xy"]
-            row["rel_l2_vs_f64"] = {nm: float(torch.linalg.vector_norm(fields[q] - ref[q]) /
-                                              torch.linalg.vector_norm(ref[q])) for q, nm in enumerate(names)}
+        row["mlups"] = n * n * done / wall / 1e6
+        if storage == "f64":
+            del row["rel_l2_vs_f64"]
         res[storage] = row
-        del fields
-    return {"n": n, "steps": steps, "ell": ell, "std": std, "formats": res}
+    return {"n": n, "steps": steps, "ell": ell, "std": std, "checkpoints": checkpoints, "formats": res}
 
 
 if __name__ == "__main__":
@@ -185,6 +192,7 @@ if __name__ == "__main__":
     ap.add_argument("--what", default="all", choices=["all", "convergence", "longrun", "precision"])
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--every", type=int, default=1000)
     ap.add_argument("--storage", default="f64")
     ap.add_argument("--max-ny", type=int, default=4096)
     ap.add_argument("--out", default=None)
@@ -196,7 +204,7 @@ if __name__ == "__main__":
     if a.what in ("all", "longrun"):
         res["longrun"] = [long_run(storage=a.storage)]
     if a.what == "precision":
-        res["precision"] = precision_errors(n=a.n, steps=a.steps)
+        res["precision"] = precision_errors(n=a.n, steps=a.steps, every=a.every)
     txt = json.dumps(res, indent=1)
     if a.out:
         open(a.out, "w").write(txt)
