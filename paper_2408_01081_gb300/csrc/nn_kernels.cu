@@ -887,6 +887,11 @@ int ilog2(long long v)
     return l;
 }
 
+// dynamic shared-memory opt-in of the tile convolution, set once per device and variant
+// (setting it twice from racing threads is harmless)
+constexpr int kMaxDevices = 64;
+bool g_conv3_attr[kMaxDevices][8] = {};
+
 // pixels per split of the weight gradient: enough splits for about four blocks per
 // SM (a block walks its pixels serially), at least 1024 pixels (16 chunks) each
 long long wgrad_pixels_per_split(int Cin, int Cout, long long P, int KS)
@@ -929,10 +934,17 @@ lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int
         const long long tiles = (long long)B * (H / th) * (W / TW);
         const int bn = (Cout % 64 == 0) ? 64 : 32;
         const dim3 grid((unsigned)tiles, (unsigned)(Cout / bn));
+        int dev = 0;
+        cudaGetDevice(&dev);
 #define LBM_CONV3(BNV, LOV, THV)                                                                     \
     do {                                                                                             \
         constexpr int smem = conv3_tile_smem_bytes<BNV, THV>();                                      \
-        cudaFuncSetAttribute(conv3_tile_kernel<BNV, LOV, THV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+        constexpr int slot = (BNV == 64 ? 4 : 0) + (LOV ? 2 : 0) + (THV == 16 ? 1 : 0);              \
+        if (dev >= 0 && dev < kMaxDevices && !g_conv3_attr[dev][slot]) {                             \
+            cudaFuncSetAttribute(conv3_tile_kernel<BNV, LOV, THV>,                                   \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);                 \
+            g_conv3_attr[dev][slot] = true;                                                          \
+        }                                                                                            \
         conv3_tile_kernel<BNV, LOV, THV><<<grid, 256, smem, s>>>(a);                                 \
     } while (0)
         if (bn == 64) {

@@ -545,6 +545,32 @@ def run(out_dir, n_chunks=20, lattices=256, H=256, W=256, k=32, J=4, batch=8, lr
     return sur, report
 
 
+def kernel_workload(what, batch=16, H=256, W=256, repeats=3, act_bf16=False):
+    """A fixed launch sequence for profiling the layer kernels with an untrained network:
+    what = "infer" runs `repeats` inferences of `batch` lattices, "train" runs `repeats` + 1
+    training steps of `batch` lattices on random inputs and targets."""
+    import torch
+    net = UNet((32, 64, 128, 256), seed=0)
+    if what == "infer":
+        sur = Surrogate(net, np.ones(NF), 32)
+        stride = 10 * H * W
+        U = torch.zeros((batch, 10, H, W), dtype=torch.float64, device=net.dev)
+        U[:, :NF].normal_(0.0, 1e-3)
+        nu = torch.zeros(batch, dtype=torch.float32, device=net.dev)
+        out = torch.empty_like(U)
+        for _ in range(repeats):
+            sur.predict(U[0], stride, nu, batch, H, W, out[0], stride, act_bf16=act_bf16)
+    elif what == "train":
+        net._alloc(batch, H, W)
+        net.A["x0"].normal_()
+        net.A["tgt"].normal_()
+        for _ in range(repeats + 1):
+            net.train_step(batch, H, W, 1e-4)
+    else:
+        raise ValueError(what)
+    torch.cuda.synchronize()
+
+
 if __name__ == "__main__":
     import argparse
     ap = argparse.ArgumentParser(description="train and evaluate the surrogate on solver trajectories")
@@ -556,7 +582,14 @@ if __name__ == "__main__":
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--budget", type=float, default=None, help="training time budget in seconds")
+    ap.add_argument("--kernels", choices=["infer", "train"], default=None,
+                    help="only run a fixed launch sequence of the layer kernels (for profiling)")
     a = ap.parse_args()
-    _, rep = run(a.out, a.chunks, a.lattices, a.size, a.size, a.k, batch=a.batch, lr=a.lr, time_budget_s=a.budget)
-    import json
-    print(json.dumps({k: v for k, v in rep.items() if k != "history"}, indent=1))
+    if a.kernels:
+        kernel_workload(a.kernels, batch=a.batch, H=a.size, W=a.size)
+        print("done")
+    else:
+        _, rep = run(a.out, a.chunks, a.lattices, a.size, a.size, a.k, batch=a.batch, lr=a.lr,
+                     time_budget_s=a.budget)
+        import json
+        print(json.dumps({k: v for k, v in rep.items() if k != "history"}, indent=1))
