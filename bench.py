@@ -48,8 +48,8 @@ FUSED = {"f32"}      # formats the library advances two steps per pass by defaul
 # DRAM bytes per node and launch (dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of
 # 4096x2048, scaled by the node count); valid only while the kernel sources hash to "sha256".
 # "f32_fused" is one launch of the two-step kernel.
-TRAFFIC_CAPTURE = {"sha256": "234088bb59db89aa38d520a181b5a9c15ff2c7c6ae84fe1a1c900c2f8d96d58e",
-                   "bytes_per_node": {"f64": 317.16, "f32": 153.35, "f32_fused": 159.02, "bf16": 73.60, "f16": 73.58,
+TRAFFIC_CAPTURE = {"sha256": "3ff2bbd854885dd12f21f0ac036110fbd2f88577f9ca33ace2f84632dc725188",
+                   "bytes_per_node": {"f64": 317.16, "f32": 153.34, "f32_fused": 157.36, "bf16": 73.59, "f16": 73.58,
                                       "ms_f16": 94.50}}
 KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_01081_gb300/csrc/lbm_kind.cu",
                   "paper_2408_01081_gb300/csrc/lbm_tb.cuh", "paper_2408_01081_gb300/csrc/lbm_ms.cuh"]
@@ -80,6 +80,22 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def reduce_max(v, dist=None, device="cpu"):
+    """Largest value over the ranks of the process group (v itself without one)."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, seconds_per_rank, dist=None, device="cpu"):
+    """Units all ranks processed divided by the slowest rank's time (the job's wall time)."""
+    ws = dist.get_world_size() if dist is not None else 1
+    return units_per_rank * ws / reduce_max(seconds_per_rank, dist, device)
 
 
 class Clocks:
@@ -302,11 +318,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, dist, dev)
 
     results = {}
     finals = {}
