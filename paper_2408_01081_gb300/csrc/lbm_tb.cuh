@@ -44,7 +44,7 @@ __device__ __forceinline__ void tb_load_row(const typename Fmt<K>::E* __restrict
     const int nx = A.nx, ny = A.ny;
     const long long plane = A.plane;
     const bool row_ok = DIRICHLET ? (r >= 0 && r < ny) : true;
-    const int ry = row_ok ? ((r % ny) + ny) % ny : 0;
+    const int ry = row_ok ? (r < 0 ? r + ny : (r >= ny ? r - ny : r)) : 0;   // r in [-1, ny]
     const long long rowoff = (long long)ry * A.pitch;
     const int rm = (ry == 0) ? ny - 1 : ry - 1, rp = (ry == ny - 1) ? 0 : ry + 1;
     const bool bot = DIRICHLET && ry == 0, top = DIRICHLET && ry == ny - 1;
