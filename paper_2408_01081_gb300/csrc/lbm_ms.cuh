@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(256) ms_step_kernel(StepArgs A)
     const long long plane = A.plane;
     const int lane = threadIdx.x & 31;
     const float fa = (float)A.a, fb = (float)A.b;
-    const float inv_s = (float)(1.0 / A.neq_scale), sc = (float)A.neq_scale;
+    // the scale is a power of two: its FP32 reciprocal is exact (no FP64 division in the kernel)
+    const float sc = (float)A.neq_scale, inv_s = 1.0f / sc;
     const bool bot = DIRICHLET && (y == 0);
     const bool top = DIRICHLET && (y == ny - 1);
     const int ym = (y == 0) ? ny - 1 : y - 1;
@@ -344,7 +345,7 @@ __device__ void ms_load_node(const NodeArgs& A, int x, int y, double (&S)[4][5])
     const float* m0p = static_cast<const float*>(A.S);
     const unsigned short* dv = reinterpret_cast<const unsigned short*>(m0p + 5 * A.plane);
     const long long off = (long long)y * A.pitch + x;
-    const float inv_s = (float)(1.0 / A.neq_scale);
+    const float inv_s = 1.0f / (float)A.neq_scale;     // exact: the scale is a power of two
     float m0[5], gx[5], gy[5], dd[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
