@@ -1,6 +1,6 @@
 """Learned surrogate: a convolutional U-Net neural operator that jumps k steps
 of the lattice Boltzmann solver on periodic lattices, trained on trajectories
-the solver itself generates, with the solver as fallback and as judge.
+the solver itself generates, with the solver as fallback and as the check of its error.
 
 Model (channels-last, circular padding, ReLU):
     input  x0 = [U(t) / scale (5 fields), (nu - 0.245) / 0.1415, zero padding] -> 32 channels
@@ -240,7 +240,7 @@ def generate_chunk(n, seed, H=256, W=256, k=32, J=4, storage="f64", device="cuda
 
     relift=True: before each k-step segment the populations are re-initialised from the
     moment fields (Eq. ic_second, periodic central differences), so every pair
-    (U_j, U_{j+1}) is the same function of U_j that the fallback driver's judge evaluates.
+    (U_j, U_{j+1}) is the same function of U_j that the fallback driver's check evaluates.
     A continuing run also carries non-equilibrium populations that U does not determine,
     so its k-step map is not a function of U alone."""
     import torch
@@ -411,7 +411,7 @@ def _descs_for(nu, H, W, cfl=0.9):
 
 
 def relift_and_step(U, nu, k, storage="f64"):
-    """The solver as judge: re-initialise populations from U (Eq. ic_second with periodic
+    """The solver as reference: re-initialise populations from U (Eq. ic_second with periodic
     central-difference derivatives) and run k steps.  U: [n, 10, H, W] FP64 device tensor."""
     import torch
     n, _, H, W = U.shape
@@ -437,7 +437,7 @@ def relift_and_step(U, nu, k, storage="f64"):
 
 class FallbackDriver:
     """Advances lattices by surrogate jumps of k steps.  Every `check_every`-th jump the
-    solver re-runs the jump from the same state and judges the surrogate: a lattice whose
+    solver re-runs the jump from the same state and checks the surrogate: a lattice whose
     relative error exceeds `tol` takes the solver's result instead (fallback)."""
 
     def __init__(self, sur, tol=1e-3, check_every=1, storage="f64"):
@@ -537,7 +537,7 @@ def run(out_dir, n_chunks=20, lattices=256, H=256, W=256, k=32, J=4, batch=8, lr
         "heldout_rel_l2_bf16_activations": {"median": float(np.median(errs_fast)), "max": float(np.max(errs_fast))},
         "persistence_rel_l2": {"median": float(np.median(pers)), "mean": float(np.mean(pers))},
         "fallback_tol": 1e-3, "fallback_fraction": drv.fallbacks / max(1, drv.checked),
-        "judge_errors_after_relift": [float(e) for e in derr],
+        "check_errors_after_relift": [float(e) for e in derr],
         "timing": tm, "scale": sur.scale_np.tolist(), "history": hist[-50:],
     }
     json.dump(report, open(os.path.join(out_dir, "report.json"), "w"), indent=1)

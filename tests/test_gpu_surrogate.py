@@ -1,7 +1,7 @@
 """The learned surrogate end to end on a small configuration (32x32 lattices,
 jumps of 8 steps, channels 32 at every level): it trains on trajectories the
 batched solver generates, beats the persistence baseline on held-out seeds,
-the fallback driver replaces every prediction whose judged error exceeds the
+the fallback driver replaces every prediction whose checked error exceeds the
 tolerance by the solver's result, and the timing report compares the jump
 against the solver on the same GPU."""
 import numpy as np
@@ -28,9 +28,9 @@ def test_surrogate_trains_beats_persistence_and_falls_back(lbm):
     assert drv.fallbacks == int(np.sum(e > 1e-6))
     for i in np.nonzero(e > 1e-6)[0]:
         torch.testing.assert_close(out[i], ref[i], rtol=0, atol=0)
-    # the judge evaluates exactly the map the training pairs sample (re-lift, then k steps)
-    judge = S.relative_error(sur, ref, held.U[1, :16], 10 * H * W, 16, H, W)
-    assert np.max(judge) < 1e-12
+    # the solver's check evaluates exactly the map the training pairs sample (re-lift, then k steps)
+    check = S.relative_error(sur, ref, held.U[1, :16], 10 * H * W, 16, H, W)
+    assert np.max(check) < 1e-12
     drv2 = S.FallbackDriver(sur, tol=10.0, check_every=1)
     out2, _ = drv2.jump(U, held.nu[:16])
     assert drv2.fallbacks == 0
