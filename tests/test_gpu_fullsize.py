@@ -6,7 +6,9 @@ times (periodic, no body load, no displacement tracking):
   (the domain of dependence of 3 steps is 3 nodes, the patch is 16 wide);
   properties that hold at any size: sum of U and ||f||_P conserved;
 * Dirichlet 2048x1024 with the moving manufactured solution, FP64 and FP32,
-  displacement tracked: every node after 20 steps against a full oracle run.
+  displacement tracked: every node after 20 steps against a full oracle run;
+* the benchmark's batch of 512 ragged lattices (233 M nodes, FP32, tuned launch
+  mode, 100-step graphs): sampled lattices bit-identical to single-lattice runs.
 """
 import math
 
@@ -82,3 +84,46 @@ def test_dirichlet_2048x1024_against_full_oracle(lbm, storage, tol):
     errs = field_errors(lat.moments(), ref)
     lat.close()
     assert max(errs) < tol, errs
+
+
+def test_batch_512_lattices_sampled_against_single_lattices(lbm, tmp_path):
+    """The benchmark's batch workload at full size and in its launch configuration (autotuned
+    tiles and mode, graphs of 100 steps): the smallest, the largest and a spread of other
+    lattices, periodic and Dirichlet, equal single-lattice runs bit for bit after 200 steps."""
+    import torch
+    from workloads.grf import batch_lattice_inputs_torch
+    spec = W.batch_spec(count=512)
+    descs = []
+    for sp in spec:
+        c = W.material.lattice_speed(sp.cK2, sp.cmu2, 0.9)
+        dx = 1.0 / max(sp.nx, sp.ny)
+        descs.append((sp.nx, sp.ny, int(sp.dirichlet), dx, dx / c, sp.cK2 ** 0.5, sp.cmu2 ** 0.5))
+    b = lbm.lbm_batch_create(descs, storage=lbm.LBM_F32)
+    lbm.lbm_batch_tune(b, str(tmp_path / "tune.txt"))
+    for i, (sp, d) in enumerate(zip(spec, descs)):
+        lbm.lbm_batch_init(b, i, *batch_lattice_inputs_torch(sp, d[3], device="cuda"))
+    mode = 0
+    for line in open(tmp_path / "tune.txt"):
+        if "|f32|mode|" in line:
+            mode = int(line.rsplit("|", 1)[1])
+    lbm.lbm_batch_set_mode(b, mode, 100)
+    lbm.lbm_batch_step(b, 200)
+    lbm.lbm_batch_synchronize(b)
+    nodes = [d[0] * d[1] for d in descs]
+    pick = {int(np.argmin(nodes)), int(np.argmax(nodes))} | set(range(0, 512, 73)) | {1, 511}
+    for i in sorted(pick):
+        sp, d = spec[i], descs[i]
+        nx, ny, bc, dx, dt, cK, cmu = d
+        got = torch.empty((10, ny, nx), dtype=torch.float64, device="cuda")
+        lbm.lbm_batch_moments(b, i, got)
+        lbm.lbm_batch_synchronize(b)
+        lat = lbm.Lattice(nx, ny, dx, dt, cK, cmu, dirichlet=bool(bc), storage="f32", track_displacement=False)
+        lat.init(*batch_lattice_inputs_torch(sp, dx, device="cuda"))
+        lat.step(200)
+        ref = torch.empty_like(got)
+        lat.moments(ref)
+        lat.synchronize()
+        torch.cuda.synchronize()
+        lat.close()
+        assert torch.equal(got[0:5], ref[0:5]), (i, nx, ny, bc)
+    lbm.lbm_batch_destroy(b)
