@@ -280,12 +280,22 @@ __global__ void __launch_bounds__(256) conv3_tile_kernel(ConvArgs a)
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
 
     for (int ci0 = 0; ci0 < Cin; ci0 += CKC) {
-        // --- stage the halo tile: 180 pixels x 32 channels, FP32 -> BF16 hi / lo ---
+        // --- stage the weights of the nine taps: BN x 32 inputs each (asynchronous copies,
+        //     issued first so that they overlap the halo staging; the launcher guarantees
+        //     co0 + BN <= Cout) ---
+        for (int q = tid; q < 9 * BN * 4; q += 256) {
+            const int tap = q / (BN * 4), r = q % (BN * 4);
+            const int nn = r >> 2, part = r & 3;
+            cp_async16(Bs + (tap * BN + nn) * KROW + part * 8,
+                       a.w + ((long long)(co0 + nn) * 9 + tap) * Cin + ci0 + part * 8);
+        }
+        // --- stage the halo tile: (TH + 2) x 18 pixels x 32 channels, FP32 -> BF16 hi / lo ---
         const bool from1 = ci0 < a.C1;
         const float* base = from1 ? a.x1 : a.x2;
         const int cstride = from1 ? a.C1 : a.C2;
         const int coff = from1 ? ci0 : ci0 - a.C1;
         const int half = (from1 && a.x1_half) ? 1 : 0;     // nearest upsampling of a half-size x1
+#pragma unroll 4
         for (int q = tid; q < HH * HW2 * (CKC / 4); q += 256) {
             const int hp = q >> 3, c4 = (q & 7) * 4;
             const int hy = hp / HW2, hx = hp % HW2;
@@ -302,14 +312,6 @@ __global__ void __launch_bounds__(256) conv3_tile_kernel(ConvArgs a)
                 *reinterpret_cast<uint2*>(Ah + hp * KROW + c4) =
                     make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
             }
-        }
-        // --- stage the weights of the nine taps: BN x 32 inputs each (asynchronous copies;
-        //     the launcher guarantees co0 + BN <= Cout) ---
-        for (int q = tid; q < 9 * BN * 4; q += 256) {
-            const int tap = q / (BN * 4), r = q % (BN * 4);
-            const int nn = r >> 2, part = r & 3;
-            cp_async16(Bs + (tap * BN + nn) * KROW + part * 8,
-                       a.w + ((long long)(co0 + nn) * 9 + tap) * Cin + ci0 + part * 8);
         }
         asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
