@@ -337,3 +337,39 @@ def test_fp64_split_rejects_unsupported_counts(lbm):
             lat.set_fp64_split(bad)
     lat.set_fp64_split(7)
     lat.close()
+
+
+@pytest.mark.parametrize("dirichlet", [False, True])
+def test_degenerate_material_without_shear_speed(lbm, dirichlet):
+    """c_mu = 0 (no shear waves, the j_d / j_xy couplings vanish): still the oracle's result."""
+    nx, ny, steps = 40, 24, 20
+    rng = np.random.default_rng(17)
+    f = rng.standard_normal((4, 5, ny, nx)) * 1e-2
+    o = Oracle(Params(nx, ny, 0.1, 0.1 / 2.5, 1.0, 0.0, dirichlet))
+    o.set_state(f, np.zeros((2, ny, nx)))
+    for _ in range(steps):
+        o.step(track_displacement=False)
+    lat = lbm.Lattice(nx, ny, 0.1, 0.1 / 2.5, 1.0, 0.0, dirichlet=dirichlet, storage="f64", track_displacement=False)
+    lat.set_populations(f)
+    lat.step(steps)
+    g, _ = lat.populations()
+    lat.close()
+    np.testing.assert_allclose(g, o.f, rtol=0, atol=1e-13 * np.max(np.abs(o.f)))
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-13), ("f32", 2e-6)])
+def test_largest_row_count(lbm, storage, tol):
+    """ny = 65535, the largest row count the library accepts, with a ragged 3-node row."""
+    nx, ny, steps = 3, 65535, 4
+    rng = np.random.default_rng(23)
+    f = rng.standard_normal((4, 5, ny, nx)) * 1e-2
+    o = Oracle(Params(nx, ny, 0.1, 0.1 / 3.2, 1.0, 0.6, False))
+    o.set_state(f, np.zeros((2, ny, nx)))
+    for _ in range(steps):
+        o.step(track_displacement=False)
+    lat = lbm.Lattice(nx, ny, 0.1, 0.1 / 3.2, 1.0, 0.6, storage=storage, track_displacement=False)
+    lat.set_populations(f)
+    lat.step(steps)
+    g, _ = lat.populations()
+    lat.close()
+    np.testing.assert_allclose(g, o.f, rtol=0, atol=tol * np.max(np.abs(o.f)))

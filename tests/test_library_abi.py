@@ -46,3 +46,13 @@ def test_create_validates_arguments_before_touching_the_gpu(lib):
         lib.lbm_create(8, 8, 0.1, 0.1 / 2.5, 1.0, 0.8)          # 2 sqrt(1.64) = 2.56 >= 2.5
     assert e.value.status == lib.LBM_ERR_CFL
     assert "CFL" in lib.lbm_last_error(None)
+
+
+def test_create_rejects_sizes_beyond_the_limits(lib):
+    for nx, ny in [(8, 65536), ((1 << 24) + 1, 8), (8, 1), (0, 8)]:
+        with pytest.raises(lib.LbmError) as e:
+            lib.lbm_create(nx, ny, 0.1, 0.01, 1.0, 0.5)
+        assert e.value.status == lib.LBM_ERR_ARG, (nx, ny)
+    with pytest.raises(lib.LbmError) as e:
+        lib.lbm_create(8, 8, 0.1, 0.01, 1.0, -0.1)           # negative shear speed
+    assert e.value.status == lib.LBM_ERR_ARG
