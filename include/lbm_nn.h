@@ -9,9 +9,11 @@
  *     powers of two; every convolution pads circularly (periodic lattices).
  *   - Weights: BF16 (stored as 16-bit words) [Cout][KS][KS][Cin], KS in {1, 3};
  *     biases FP32 [Cout].  FP32 master weights live with the optimiser.
- *   - Convolutions run on the tensor cores (mma.sync BF16, FP32 accumulation)
- *     with activations split into two BF16 halves, so the BF16 weights are the
- *     only rounding of the forward pass.
+ *   - Convolutions run on the tensor cores (BF16 inputs, FP32 accumulation) with
+ *     activations split into two BF16 halves, so the BF16 weights are the only
+ *     rounding of the forward pass.  3x3 convolutions with H >= 16, W >= 8 and
+ *     Cout a multiple of 32 use tcgen05.mma with the accumulator in tensor
+ *     memory; other sizes (and LBM_NN_MMA_SYNC) use mma.sync kernels.
  *   - Two-input convolutions read the channel concatenation [x1 | x2]; two-output
  *     ones write channels [0, Co1) to y1 and [Co1, Cout) to y2.  LBM_NN_ACCUMULATE
  *     adds the result into the destination instead of overwriting it.
@@ -36,8 +38,10 @@ enum {
     LBM_NN_RELU = 1,        /* apply max(0, .) to the output (forward) */
     LBM_NN_ACCUMULATE = 2,  /* add the result into the destination instead of overwriting it */
     LBM_NN_X1_HALF = 4,     /* x1 is stored at (H/2, W/2) and read nearest-upsampled to (H, W) */
-    LBM_NN_ACT_BF16 = 8     /* forward: activations as one BF16 value instead of the hi/lo pair
+    LBM_NN_ACT_BF16 = 8,    /* forward: activations as one BF16 value instead of the hi/lo pair
                                (half the tensor-core work; activations rounded to BF16) */
+    LBM_NN_MMA_SYNC = 16    /* forward: use the mma.sync kernels even where the tcgen05 kernel applies
+                               (same arithmetic, other summation order) */
 };
 
 /* y = act(conv_KS(x, w) + bias), act = ReLU with LBM_NN_RELU; flags as above (any other
@@ -45,6 +49,11 @@ enum {
 lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int32_t C2, const void* w_bf16,
                                const float* bias, float* y1, int32_t Co1, float* y2, int32_t Cout, int32_t B,
                                int32_t H, int32_t W, int32_t KS, int32_t flags, void* stream);
+
+/* Synchronises `stream`; LBM_ERR_TIMEOUT if a bounded wait inside a tcgen05 convolution ran
+ * out since the last call (the output of that convolution is invalid; the flag is cleared),
+ * LBM_ERR_CUDA if a launch or the stream failed, else LBM_OK. */
+lbm_status lbm_nn_check(void* stream);
 
 /* Workspace bytes lbm_nn_conv_backward_weight needs for these sizes (Cin = C1 + C2). */
 int64_t lbm_nn_wgrad_workspace_bytes(int32_t Cin, int32_t Cout, int32_t B, int32_t H, int32_t W, int32_t KS);

@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include "lbm_nn.h"
+#include "nn_conv_tc.h"
 
 namespace {
 
@@ -922,13 +923,20 @@ lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int
 {
     if (!x1 || !w_bf16 || !y1 || C1 <= 0 || C1 % 32 || C2 < 0 || C2 % 32 || (C2 > 0 && !x2) || Cout <= 0 ||
         Cout % 8 || Co1 <= 0 || Co1 > Cout || (Co1 < Cout && !y2) || B <= 0 || !pow2(H) || !pow2(W) ||
-        (KS != 1 && KS != 3) || (flags & ~15) || ((flags & LBM_NN_X1_HALF) && (H < 2 || W < 2)))
+        (KS != 1 && KS != 3) || (flags & ~31) || ((flags & LBM_NN_X1_HALF) && (H < 2 || W < 2)))
         return LBM_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (KS == 3 && !(flags & LBM_NN_MMA_SYNC)) {
+        // tcgen05 kernel where its tiling applies (H >= 16, W >= 8, Cout a multiple of 32)
+        const ConvTcArgs t{x1, x2, C1, C2, static_cast<const uint16_t*>(w_bf16), bias, y1, y2, Co1, Cout, B, H, W,
+                           (flags & LBM_NN_RELU) ? 1 : 0, (flags & LBM_NN_ACCUMULATE) ? 1 : 0,
+                           (flags & LBM_NN_X1_HALF) ? 1 : 0, (flags & LBM_NN_ACT_BF16) ? 1 : 0};
+        if (conv3_tc_launch(t, s, 0)) return launch_status();
+    }
     ConvArgs a{x1, x2, C1, C2, static_cast<const __nv_bfloat16*>(w_bf16), bias, y1, y2, Co1, Cout, B, H, W,
                (flags & LBM_NN_RELU) ? 1 : 0, (flags & LBM_NN_ACCUMULATE) ? 1 : 0, (flags & LBM_NN_X1_HALF) ? 1 : 0,
                (flags & LBM_NN_ACT_BF16) ? 1 : 0};
     const long long P = (long long)B * H * W;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (KS == 3 && H >= 8 && W >= TW && Cout % 32 == 0) {
         // halo-tiled kernel: BN = 64 when it divides Cout, else 32; 16-row tiles when H allows
         const bool lo = !a.act_bf16;
@@ -971,6 +979,11 @@ lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int
         else conv_fwd_kernel<16, 1><<<grid, 256, 0, s>>>(a);
     }
     return launch_status();
+}
+
+lbm_status lbm_nn_check(void* stream)
+{
+    return conv3_tc_take_timeout(static_cast<cudaStream_t>(stream)) ? LBM_ERR_TIMEOUT : launch_status();
 }
 
 int64_t lbm_nn_wgrad_workspace_bytes(int32_t Cin, int32_t Cout, int32_t B, int32_t H, int32_t W, int32_t KS)

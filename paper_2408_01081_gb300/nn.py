@@ -9,7 +9,7 @@ import ctypes
 
 from . import lbm as _lbm
 
-EXPORTS = ["lbm_nn_conv_forward", "lbm_nn_wgrad_workspace_bytes", "lbm_nn_conv_backward_weight",
+EXPORTS = ["lbm_nn_conv_forward", "lbm_nn_check", "lbm_nn_wgrad_workspace_bytes", "lbm_nn_conv_backward_weight",
            "lbm_nn_bias_grad_workspace_bytes", "lbm_nn_bias_grad",
            "lbm_nn_weight_flip", "lbm_nn_relu_backward", "lbm_nn_pool", "lbm_nn_pool_backward", "lbm_nn_upsample",
            "lbm_nn_upsample_backward", "lbm_nn_mse", "lbm_nn_adam", "lbm_nn_to_bf16", "lbm_nn_pack_input",
@@ -25,6 +25,7 @@ def _lib():
         vp, i32, i64, f32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
         sig = {
             "lbm_nn_conv_forward": [vp, i32, vp, i32, vp, vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, vp],
+            "lbm_nn_check": [vp],
             "lbm_nn_wgrad_workspace_bytes": [i32, i32, i32, i32, i32, i32],
             "lbm_nn_conv_backward_weight": [vp, i32, vp, i32, vp, i32, i32, i32, i32, i32, vp, i32, vp, i64, vp],
             "lbm_nn_bias_grad_workspace_bytes": [i64, i32],
@@ -65,15 +66,21 @@ def _ok(name, st):
         raise _lbm.LbmError(st, f"{name} failed")
 
 
-RELU, ACCUMULATE, X1_HALF, ACT_BF16 = 1, 2, 4, 8     # flags of include/lbm_nn.h
+RELU, ACCUMULATE, X1_HALF, ACT_BF16, MMA_SYNC = 1, 2, 4, 8, 16     # flags of include/lbm_nn.h
 
 
 def conv_forward(x1, C1, x2, C2, w_bf16, bias, y1, Co1, y2, Cout, B, H, W, KS, relu=False, beta=False,
-                 x1_half=False, act_bf16=False):
+                 x1_half=False, act_bf16=False, mma_sync=False):
     flags = (RELU if relu else 0) | (ACCUMULATE if beta else 0) | (X1_HALF if x1_half else 0) | \
-        (ACT_BF16 if act_bf16 else 0)
+        (ACT_BF16 if act_bf16 else 0) | (MMA_SYNC if mma_sync else 0)
     _ok("lbm_nn_conv_forward", _lib().lbm_nn_conv_forward(_p(x1), C1, _p(x2), C2, _p(w_bf16), _p(bias), _p(y1), Co1,
                                                           _p(y2), Cout, B, H, W, KS, flags, _s()))
+
+
+def check():
+    """Synchronise the current stream; raises LbmError(LBM_ERR_TIMEOUT) if a bounded wait in a
+    tcgen05 convolution ran out since the last check."""
+    _ok("lbm_nn_check", _lib().lbm_nn_check(_s()))
 
 
 def wgrad_workspace_bytes(Cin, Cout, B, H, W, KS) -> int:

@@ -75,6 +75,47 @@ def test_conv3_halo_tile_forward(lbm, H, W, C1, C2, Cout, Co1):
     assert np.max(np.abs(got - ref)) < 1e-4 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("B,H,W,C1,C2,Cout,Co1,act_bf16,x1_half", [
+    (8, 128, 128, 32, 0, 32, 32, False, False),     # 32 channels per CTA, two 128-pixel tiles
+    (8, 128, 128, 32, 0, 32, 32, True, False),      # the same with single-BF16 activations
+    (8, 128, 128, 64, 0, 64, 64, False, False),     # 64 channels, two tiles
+    (8, 128, 128, 32, 32, 128, 128, True, False),   # 128 channels, two tiles, two inputs
+    (4, 64, 64, 64, 64, 128, 64, False, False),     # one tile per CTA, two inputs, two outputs
+    (2, 16, 8, 32, 0, 64, 64, False, False),        # one 16x8 tile per image: the halo wraps on every side
+    (2, 32, 32, 256, 0, 256, 256, False, False),    # two CTAs along the output channels, 16 chunks
+    (4, 64, 64, 64, 32, 96, 32, False, True),       # 96 channels (32 per CTA), x1 upsampled, accumulate
+])
+def test_conv3_tcgen05(lbm, B, H, W, C1, C2, Cout, Co1, act_bf16, x1_half):
+    """The tcgen05 3x3 kernel (accumulator in tensor memory): against the reference on the
+    first and last image, and against the mma.sync kernel (same products, other summation
+    order) on every pixel; no bounded wait ran out."""
+    from paper_2408_01081_gb300 import nn as K
+    h1, w1 = (H // 2, W // 2) if x1_half else (H, W)
+    x1 = RNG.standard_normal((B, h1, w1, C1)).astype(np.float32)
+    x2 = RNG.standard_normal((B, H, W, C2)).astype(np.float32) if C2 else None
+    w = _bf16(RNG.standard_normal((Cout, 3, 3, C1 + C2)) * 0.1)
+    b = RNG.standard_normal(Cout).astype(np.float32)
+    prev = RNG.standard_normal((B, H, W, Cout)).astype(np.float32)
+    outs = []
+    for mma_sync in (False, True):
+        y1 = _t(prev[..., :Co1].copy())
+        y2 = _t(prev[..., Co1:].copy()) if Co1 < Cout else None
+        K.conv_forward(_t(x1), C1, _t(x2) if C2 else None, C2, _wb(w), _t(b), y1, Co1, y2, Cout, B, H, W, 3,
+                       relu=True, beta=x1_half, x1_half=x1_half, act_bf16=act_bf16, mma_sync=mma_sync)
+        K.check()
+        outs.append(y1.cpu().numpy() if y2 is None else np.concatenate([y1.cpu().numpy(), y2.cpu().numpy()], 3))
+    got, legacy = outs
+    assert rel_l2(got, legacy) < 2e-6, rel_l2(got, legacy)
+    idx = [0, B - 1]
+    xu = np.repeat(np.repeat(x1[idx], 2, axis=1), 2, axis=2) if x1_half else x1[idx]
+    x = xu if C2 == 0 else np.concatenate([xu, x2[idx]], axis=3)
+    if act_bf16:
+        x = _bf16(x)
+    ref = np.maximum(R.conv(x.astype(np.float64), w, b), 0.0) + (prev[idx] if x1_half else 0.0)
+    assert rel_l2(got[idx], ref) < 2e-5, rel_l2(got[idx], ref)
+    assert np.max(np.abs(got[idx] - ref)) < 1e-4 * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("P,C", [(1, 5), (100, 32), (70000, 64), (5000, 384), (1 << 21, 32)])
 def test_bias_grad_sizes(lbm, P, C):
     """Channel counts below, at and above one block's 256 threads; one to many blocks."""
