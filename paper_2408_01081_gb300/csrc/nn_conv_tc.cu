@@ -142,34 +142,51 @@ __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) { return *rein
 
 template <int BN, int MT, bool LO>
 struct TcShape {
-    static constexpr int TH = 16, TW = 8 * MT;           // output block (MT tiles of 16 x 8)
+    static constexpr int TH = 16, TW = 8 * MT;               // output block (MT tiles of 16 x 8)
     static constexpr int HWD = TW + 2, HP = (TH + 2) * HWD;  // halo block width, pixels
-    static constexpr int PLANE = HP * 16;                // 8 channels of every halo pixel
-    static constexpr int A_HALF = 2 * PLANE;             // one BF16 half of a 16-channel chunk
+    static constexpr int NQ = (HP * 4 + 255) / 256;          // 16-byte loads per thread per chunk
+    static constexpr int PLANE = HP * 16;                    // 8 channels of every halo pixel
+    static constexpr int A_HALF = 2 * PLANE;                 // one BF16 half of a 16-channel chunk
     static constexpr int A_BYTES = (LO ? 2 : 1) * A_HALF;
-    static constexpr int B_PLANE = BN * 16;              // 8 input channels of BN weight rows
+    static constexpr int B_PLANE = BN * 16;                  // 8 input channels of BN weight rows
     static constexpr int B_TAP = 2 * B_PLANE;
-    static constexpr int STAGE = A_BYTES + 9 * B_TAP;
-    static constexpr int COLS = MT * BN <= 32 ? 32 : MT * BN <= 64 ? 64 : MT * BN <= 128 ? 128 : 256;
+    static constexpr int B_BYTES = 9 * B_TAP;                // weights of one 16-channel chunk
+    static constexpr int ACC = MT * BN;                      // accumulator columns of one block
+    static constexpr int COLS = 2 * ACC <= 32 ? 32 : 2 * ACC <= 64 ? 64 : 2 * ACC <= 128 ? 128
+                                : 2 * ACC <= 256 ? 256 : 512;   // two accumulators
     static constexpr uint32_t IDESC = idesc_bf16_f32(128, BN);
-    static_assert(BN % 16 == 0 && BN >= 32 && BN <= 128 && MT * BN <= 256, "tile");
+    static_assert(BN % 16 == 0 && BN >= 32 && BN <= 128 && MT >= 1 && MT <= 2, "tile");
 };
 
+// Persistent CTAs: CTA b takes the output blocks b, b + gridDim.x, ... (all with the
+// output channels of blockIdx.y), and walks their 16-channel chunks as one sequence
+// g = 0 .. G-1, so the pipeline runs on across blocks.  Per chunk g: the input chunk
+// loaded into registers one step earlier is converted and stored (buffer g % stages);
+// the loads of chunk g + 1 are issued; the weights of chunk g + 1 are copied (unless
+// all chunks' weights are resident); one thread issues the MMAs of chunk g into
+// accumulator (block & 1).  The epilogue of block t - 1 runs right after the first
+// MMAs of block t are issued, so it overlaps them.
+// CTAs per SM the register budget is sized for (shared and tensor memory allow as many)
+constexpr int tc_min_blocks(int BN, int MT) { return BN == 32 ? 3 : (BN == 128 && MT == 2) ? 1 : 2; }
+
 template <int BN, int MT, bool LO>
-__global__ void __launch_bounds__(256, 1) conv3_tc_kernel(ConvTcArgs a, int stages)
+__global__ void __launch_bounds__(256, tc_min_blocks(BN, MT)) conv3_tc_kernel(ConvTcArgs a, int stages, int resident)
 {
     using S = TcShape<BN, MT, LO>;
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mbar[kMaxStages];
+    __shared__ __align__(8) uint64_t mbar[kMaxStages];   // buffer s: MMAs of its latest chunk done
+    __shared__ __align__(8) uint64_t accbar[2];          // accumulator b: MMAs of its latest block done
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = a.W / S::TW, tiles_y = a.H / S::TH;
-    const int tile = blockIdx.x;
-    const int n = tile / (tiles_x * tiles_y);
-    const int ty0 = ((tile / tiles_x) % tiles_y) * S::TH, tx0 = (tile % tiles_x) * S::TW;
+    const int ntiles = a.B * tiles_x * tiles_y;
     const int co0 = blockIdx.y * BN;
     const int Cin = a.C1 + a.C2;
     const int nchunk = Cin / 16;
+    const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int G = my_tiles * nchunk;
+    uint8_t* const ring = smem;                            // stages x A_BYTES
+    uint8_t* const wts = smem + stages * S::A_BYTES;       // resident: nchunk x B_BYTES, else stages x B_BYTES
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -180,6 +197,8 @@ __global__ void __launch_bounds__(256, 1) conv3_tc_kernel(ConvTcArgs a, int stag
     }
     if (tid == 0) {
         for (int i = 0; i < stages; ++i) mbar_init(smem_addr(&mbar[i]), 1);
+        mbar_init(smem_addr(&accbar[0]), 1);
+        mbar_init(smem_addr(&accbar[1]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
@@ -187,89 +206,86 @@ __global__ void __launch_bounds__(256, 1) conv3_tc_kernel(ConvTcArgs a, int stag
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    int bad = 0, issued = -1;     // a wait ran out; last chunk whose MMAs were issued
-    for (int c = 0; c < nchunk; ++c) {
-        const int s = c % stages;
-        uint8_t* st = smem + s * S::STAGE;
-        // the buffer was last read by the MMAs of chunk c - stages
-        if (c >= stages && !mbar_wait(smem_addr(&mbar[s]), (uint32_t)((c / stages - 1) & 1))) bad = 1;
-        if (!bad) {
-            const int ci0 = c * 16;
-            // weights of the nine taps: row co, plane p = input channels ci0 + 8p .. + 7
-            const uint32_t bs = smem_addr(st + S::A_BYTES);
-            for (int q = tid; q < 9 * BN * 2; q += 256) {
-                const int plane = q & 1, r = q >> 1;         // r = co * 9 + tap
-                const int co = r / 9, tap = r - co * 9;
-                cp_async16(bs + tap * S::B_TAP + plane * S::B_PLANE + co * 16,
-                           a.w + ((long long)(co0 + co) * 9 + tap) * Cin + ci0 + plane * 8);
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            // halo block: pixel hp = hy * HWD + hx at image (ty0 + hy - 1, tx0 + hx - 1), periodic
-            const bool from1 = ci0 < a.C1;
-            const float* base = from1 ? a.x1 : a.x2;
-            const int cstride = from1 ? a.C1 : a.C2;
-            const int coff = from1 ? ci0 : ci0 - a.C1;
-            const int half = (from1 && a.x1_half) ? 1 : 0;     // nearest upsampling of a half-size x1
-            const int hs = a.H >> half, ws = a.W >> half;
-#pragma unroll 4
-            for (int q = tid; q < S::HP * 4; q += 256) {
+    auto tile_of = [&](int t, int& n, int& ty0, int& tx0) {
+        const int tile = (int)blockIdx.x + t * (int)gridDim.x;
+        n = tile / (tiles_x * tiles_y);
+        ty0 = ((tile / tiles_x) % tiles_y) * S::TH;
+        tx0 = (tile % tiles_x) * S::TW;
+    };
+    // chunk g of the halo block into registers: pixel hp = hy * HWD + hx at image
+    // (ty0 + hy - 1, tx0 + hx - 1), periodic; four channels per load
+    auto load_a = [&](int g, float4 (&v)[S::NQ]) {
+        const int t = g / nchunk, ci0 = (g - t * nchunk) * 16;
+        int n, ty0, tx0;
+        tile_of(t, n, ty0, tx0);
+        const bool from1 = ci0 < a.C1;
+        const float* base = from1 ? a.x1 : a.x2;
+        const int cstride = from1 ? a.C1 : a.C2;
+        const int coff = from1 ? ci0 : ci0 - a.C1;
+        const int half = (from1 && a.x1_half) ? 1 : 0;     // nearest upsampling of a half-size x1
+        const int hs = a.H >> half, ws = a.W >> half;
+#pragma unroll
+        for (int i = 0; i < S::NQ; ++i) {
+            const int q = tid + 256 * i;
+            if (q < S::HP * 4) {
                 const int hp = q >> 2, c4 = q & 3;
                 const int hy = hp / S::HWD, hx = hp - hy * S::HWD;
                 const int sy = (ty0 + hy - 1) & (a.H - 1), sx = (tx0 + hx - 1) & (a.W - 1);
                 const long long spix = ((long long)n * hs + (sy >> half)) * ws + (sx >> half);
-                const float4 v = __ldg(reinterpret_cast<const float4*>(base + spix * cstride + coff + c4 * 4));
+                v[i] = __ldg(reinterpret_cast<const float4*>(base + spix * cstride + coff + c4 * 4));
+            }
+        }
+    };
+    // registers -> BF16 hi (and lo) planes of one buffer
+    auto store_a = [&](const float4 (&v)[S::NQ], uint8_t* st) {
+#pragma unroll
+        for (int i = 0; i < S::NQ; ++i) {
+            const int q = tid + 256 * i;
+            if (q < S::HP * 4) {
+                const int hp = q >> 2, c4 = q & 3;
                 const int off = (c4 >> 1) * S::PLANE + hp * 16 + (c4 & 1) * 8;
-                const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+                const __nv_bfloat162 h01 = __floats2bfloat162_rn(v[i].x, v[i].y);
+                const __nv_bfloat162 h23 = __floats2bfloat162_rn(v[i].z, v[i].w);
                 *reinterpret_cast<uint2*>(st + off) = make_uint2(bf16x2_bits(h01), bf16x2_bits(h23));
                 if constexpr (LO) {
                     const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-                    const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
-                    const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
-                    *reinterpret_cast<uint2*>(st + S::A_HALF + off) = make_uint2(bf16x2_bits(l01), bf16x2_bits(l23));
+                    const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[i].x - f01.x, v[i].y - f01.y);
+                    const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[i].z - f23.x, v[i].w - f23.y);
+                    *reinterpret_cast<uint2*>(st + S::A_HALF + off) =
+                        make_uint2(bf16x2_bits(l01), bf16x2_bits(l23));
                 }
             }
         }
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes -> tensor core
-        bad = __syncthreads_or(bad);
-        if (bad) break;
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t ab = smem_addr(st), bb = smem_addr(st + S::A_BYTES);
-#pragma unroll 1
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = tap / 3, dx = tap - dy * 3;
-                const uint64_t bd = smem_desc(bb + tap * S::B_TAP, S::B_PLANE, 128);
-#pragma unroll
-                for (int j = 0; j < MT; ++j) {
-                    const uint32_t aoff = (uint32_t)((dy * S::HWD + 8 * j + dx) * 16);
-                    const uint32_t d = tmem + (uint32_t)(j * BN);
-                    mma_bf16_ss(d, smem_desc(ab + aoff, S::PLANE, S::HWD * 16), bd, S::IDESC, (c | tap) != 0);
-                    if constexpr (LO)
-                        mma_bf16_ss(d, smem_desc(ab + S::A_HALF + aoff, S::PLANE, S::HWD * 16), bd, S::IDESC, 1u);
-                }
-            }
-            mma_commit(smem_addr(&mbar[s]));
+    };
+    // weights of chunk c: row co, plane p = input channels 16 c + 8 p .. + 7, all nine taps
+    auto load_b = [&](int c, uint8_t* dst) {
+        const uint32_t bs = smem_addr(dst);
+        const int ci0 = c * 16;
+        for (int q = tid; q < 9 * BN * 2; q += 256) {
+            const int plane = q & 1, r = q >> 1;         // r = co * 9 + tap
+            const int co = r / 9, tap = r - co * 9;
+            cp_async16(bs + tap * S::B_TAP + plane * S::B_PLANE + co * 16,
+                       a.w + ((long long)(co0 + co) * 9 + tap) * Cin + ci0 + plane * 8);
         }
-        issued = c;
-    }
-    // the last commit covers every MMA issued before it
-    int last_ok = 0;
-    if (issued >= 0) last_ok = mbar_wait(smem_addr(&mbar[issued % stages]), (uint32_t)((issued / stages) & 1));
-    bad = __syncthreads_or(bad || !last_ok);
-    tc_fence_after();
-    if (!bad) {
+    };
+    // accumulator of block t -> bias, ReLU, FP32 stores; false if the wait ran out
+    auto epilogue = [&](int t) -> bool {
+        if (!mbar_wait(smem_addr(&accbar[t & 1]), (uint32_t)((t >> 1) & 1))) return false;
+        tc_fence_after();
+        int n, ty0, tx0;
+        tile_of(t, n, ty0, tx0);
         const int q = warp & 3, hw = warp >> 2;
-        const int j = MT == 2 ? hw : 0;                     // M tile of this warp
+        const int j = MT == 2 ? hw : 0;                     // 128-pixel tile of this warp
         constexpr int NCW = MT == 2 ? BN : BN / 2;          // accumulator columns per warp
         const int cb = MT == 2 ? 0 : hw * NCW;
         const int m = q * 32 + lane;                        // pixel of the tile = TMEM lane
         const int oy = ty0 + (m >> 3), ox = tx0 + 8 * j + (m & 7);
         const long long p = ((long long)n * a.H + oy) * a.W + ox;
+        const uint32_t col0 = (uint32_t)((t & 1) * S::ACC + j * BN + cb);
 #pragma unroll 1
         for (int cc = 0; cc < NCW; cc += 16) {
             float v[16];
-            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(j * BN + cb + cc), v);
+            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + col0 + (uint32_t)cc, v);
             const int co = co0 + cb + cc;                   // 16 channels, all in y1 or all in y2
             float* dst = co < a.Co1 ? a.y1 + p * a.Co1 + co : a.y2 + p * (a.Cout - a.Co1) + (co - a.Co1);
 #pragma unroll
@@ -290,8 +306,68 @@ __global__ void __launch_bounds__(256, 1) conv3_tc_kernel(ConvTcArgs a, int stag
                 *d4 = r;
             }
         }
-    } else if (tid == 0) {
-        atomicExch(&g_tc_timeout, 1);
+        tc_fence_before();
+        return true;
+    };
+
+    if (G > 0) {
+        if (resident)
+            for (int c = 0; c < nchunk; ++c) load_b(c, wts + c * S::B_BYTES);
+        else
+            load_b(0, wts);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    float4 v[S::NQ];
+    if (G > 0) load_a(0, v);
+    int bad = 0, issued = -1;     // a wait ran out; last chunk whose MMAs were issued
+    for (int g = 0; g < G; ++g) {
+        const int t = g / nchunk, c = g - t * nchunk, s = g % stages;
+        uint8_t* st = ring + s * S::A_BYTES;
+        store_a(v, st);
+        if (g + 1 < G) {
+            load_a(g + 1, v);
+            // buffer (g + 1) % stages was last read by the MMAs of chunk g + 1 - stages
+            const int g1 = g + 1, s1 = g1 % stages;
+            if (g1 >= stages && !mbar_wait(smem_addr(&mbar[s1]), (uint32_t)((g1 / stages - 1) & 1))) bad = 1;
+            if (!resident && !bad) load_b(g1 % nchunk, wts + s1 * S::B_BYTES);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");            // the weights of chunk g have landed
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes -> tensor core
+        bad = __syncthreads_or(bad);
+        if (bad) break;
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t ab = smem_addr(st);
+            const uint32_t bb = smem_addr(wts + (resident ? c : s) * S::B_BYTES);
+            const uint32_t acc = tmem + (uint32_t)((t & 1) * S::ACC);
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap - dy * 3;
+                const uint64_t bd = smem_desc(bb + tap * S::B_TAP, S::B_PLANE, 128);
+#pragma unroll
+                for (int j = 0; j < MT; ++j) {
+                    const uint32_t aoff = (uint32_t)((dy * S::HWD + 8 * j + dx) * 16);
+                    const uint32_t d = acc + (uint32_t)(j * BN);
+                    mma_bf16_ss(d, smem_desc(ab + aoff, S::PLANE, S::HWD * 16), bd, S::IDESC, (c | tap) != 0);
+                    if constexpr (LO)
+                        mma_bf16_ss(d, smem_desc(ab + S::A_HALF + aoff, S::PLANE, S::HWD * 16), bd, S::IDESC, 1u);
+                }
+            }
+            mma_commit(smem_addr(&mbar[s]));
+            if (c == nchunk - 1) mma_commit(smem_addr(&accbar[t & 1]));
+        }
+        issued = g;
+        if (c == 0 && t > 0 && !epilogue(t - 1)) bad = 1;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    bad = __syncthreads_or(bad);
+    if (!bad && my_tiles > 0 && !epilogue(my_tiles - 1)) bad = 1;
+    bad = __syncthreads_or(bad);
+    if (bad) {
+        // stop: wait (bounded) for the MMAs in flight before the tensor memory is freed
+        if (issued >= 0) mbar_wait(smem_addr(&mbar[issued % stages]), (uint32_t)((issued / stages) & 1));
+        if (tid == 0) atomicExch(&g_tc_timeout, 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -303,34 +379,70 @@ __global__ void __launch_bounds__(256, 1) conv3_tc_kernel(ConvTcArgs a, int stag
 }
 
 constexpr int kMaxDevices = 64;
-// per device and variant: dynamic shared memory opted in (stages), CTAs per SM
-int g_ready[kMaxDevices][12][kMaxStages + 1];
+constexpr int kResidentLimit = 112 * 1024;      // resident weights while two CTAs still fit on an SM
+
+struct VariantInfo {
+    int ready;          // attributes set and read
+    int regs_per_cta;   // registers allocated to one CTA (per-warp granularity of 256)
+    int static_smem;
+};
+VariantInfo g_var[kMaxDevices][12];
+int g_sms[kMaxDevices], g_smem_sm[kMaxDevices], g_smem_reserved[kMaxDevices];
+
+// CTAs of 256 threads that fit on one SM with `smem` bytes of dynamic shared memory:
+// the limits of threads, registers and shared memory (with the shared-memory carveout
+// at its maximum, which the variant requests)
+int ctas_per_sm(const VariantInfo& v, int dev, long long smem)
+{
+    int k = 2048 / 256;
+    const int by_regs = 65536 / v.regs_per_cta;
+    if (by_regs < k) k = by_regs;
+    const long long by_smem = g_smem_sm[dev] / (smem + v.static_smem + g_smem_reserved[dev]);
+    if (by_smem < k) k = (int)by_smem;
+    return k;
+}
 
 template <int BN, int MT, bool LO>
 bool launch_variant(const ConvTcArgs& a, cudaStream_t s, int stages, int slot)
 {
     using S = TcShape<BN, MT, LO>;
-    if (stages <= 0) stages = 3;
-    while (stages > 2 && stages * S::STAGE > kSmemLimit) --stages;
-    if (stages > kMaxStages || stages * S::STAGE > kSmemLimit) return false;
-    const int smem = stages * S::STAGE;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
-    int& per_sm = g_ready[dev][slot][stages];
-    if (per_sm == 0) {
-        if (cudaFuncSetAttribute(conv3_tc_kernel<BN, MT, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-            cudaSuccess)
+    VariantInfo& v = g_var[dev][slot];
+    if (!v.ready) {
+        cudaFuncAttributes fa;
+        if (cudaFuncSetAttribute(conv3_tc_kernel<BN, MT, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemLimit) != cudaSuccess ||
+            cudaFuncSetAttribute(conv3_tc_kernel<BN, MT, LO>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, conv3_tc_kernel<BN, MT, LO>) != cudaSuccess ||
+            cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&g_smem_sm[dev], cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&g_smem_reserved[dev], cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+                cudaSuccess)
             return false;
-        int k = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, conv3_tc_kernel<BN, MT, LO>, 256, smem) != cudaSuccess)
-            return false;
-        per_sm = k > 0 ? k : -1;
+        v.regs_per_cta = 8 * ((fa.numRegs * 32 + 255) / 256 * 256);
+        v.static_smem = (int)fa.sharedSizeBytes;
+        v.ready = 1;
     }
+    const int nchunk = (a.C1 + a.C2) / 16;
+    if (stages <= 0) stages = 2;
+    if (stages > kMaxStages) return false;
+    const long long res_smem = (long long)stages * S::A_BYTES + (long long)nchunk * S::B_BYTES;
+    const int resident = res_smem <= kResidentLimit ? 1 : 0;
+    const long long smem = resident ? res_smem : (long long)stages * (S::A_BYTES + S::B_BYTES);
+    if (smem > kSmemLimit) return false;
+    const int per_sm = ctas_per_sm(v, dev, smem);
     // the CTAs resident on one SM must fit in its tensor memory together, so that no
     // allocation ever waits for another CTA
     if (per_sm < 1 || per_sm * S::COLS > kTmemColumns) return false;
-    const dim3 grid((unsigned)((long long)a.B * (a.H / S::TH) * (a.W / S::TW)), (unsigned)(a.Cout / BN));
-    conv3_tc_kernel<BN, MT, LO><<<grid, 256, smem, s>>>(a, stages);
+    const long long ntiles = (long long)a.B * (a.H / S::TH) * (a.W / S::TW);
+    const int cob = a.Cout / BN;
+    long long gx = ((long long)per_sm * g_sms[dev] + cob - 1) / cob;
+    if (gx > ntiles) gx = ntiles;
+    if (gx < 1) gx = 1;
+    conv3_tc_kernel<BN, MT, LO><<<dim3((unsigned)gx, (unsigned)cob), 256, (size_t)smem, s>>>(a, stages, resident);
     return true;
 }
 
@@ -350,13 +462,18 @@ bool conv3_tc_launch(const ConvTcArgs& a, cudaStream_t s, int stages)
 {
     const auto aligned = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
     if (a.H < 16 || a.W < 8 || a.C1 % 32 || a.C2 % 32 || a.Co1 % 16 || a.Cout % 32 || a.Co1 > a.Cout ||
-        !aligned(a.x1) || !aligned(a.x2) || !aligned(a.w) || !aligned(a.bias) || !aligned(a.y1) || !aligned(a.y2))
+        a.B <= 0 || (long long)a.B * a.H * a.W > (1LL << 31) - 1 || !aligned(a.x1) || !aligned(a.x2) ||
+        !aligned(a.w) || !aligned(a.bias) || !aligned(a.y1) || !aligned(a.y2))
         return false;
     if (stages <= 0) stages = LBM_CONV_TC_STAGES;
     const int bn = a.Cout % 128 == 0 ? 128 : a.Cout % 64 == 0 ? 64 : 32;
+#ifdef LBM_CONV_TC_MT
+    const int mt = (LBM_CONV_TC_MT == 2 && a.W >= 16) ? 2 : 1;
+#else
     // two tiles per CTA when that still gives two CTAs per SM on 152 SMs
     const long long ctas2 = a.W >= 16 ? (long long)a.B * (a.H / 16) * (a.W / 16) * (a.Cout / bn) : 0;
     const int mt = ctas2 >= 2 * 152 ? 2 : 1;
+#endif
     if (bn == 128) return launch_bn<128>(a, s, stages, mt);
     if (bn == 64) return launch_bn<64>(a, s, stages, mt);
     return launch_bn<32>(a, s, stages, mt);

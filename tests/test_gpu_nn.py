@@ -84,11 +84,13 @@ def test_conv3_halo_tile_forward(lbm, H, W, C1, C2, Cout, Co1):
     (2, 16, 8, 32, 0, 64, 64, False, False),        # one 16x8 tile per image: the halo wraps on every side
     (2, 32, 32, 256, 0, 256, 256, False, False),    # two CTAs along the output channels, 16 chunks
     (4, 64, 64, 64, 32, 96, 32, False, True),       # 96 channels (32 per CTA), x1 upsampled, accumulate
+    (16, 256, 256, 32, 0, 32, 32, False, False),    # about nine blocks per persistent CTA, resident weights
+    (16, 128, 128, 64, 64, 64, 64, False, False),   # several blocks per CTA, weights streamed per chunk
 ])
 def test_conv3_tcgen05(lbm, B, H, W, C1, C2, Cout, Co1, act_bf16, x1_half):
-    """The tcgen05 3x3 kernel (accumulator in tensor memory): against the reference on the
-    first and last image, and against the mma.sync kernel (same products, other summation
-    order) on every pixel; no bounded wait ran out."""
+    """The tcgen05 3x3 kernel (persistent CTAs, two accumulators in tensor memory): against
+    the reference on the first and last image, and against the mma.sync kernel (same
+    products, other summation order) on every pixel; no bounded wait ran out."""
     from paper_2408_01081_gb300 import nn as K
     h1, w1 = (H // 2, W // 2) if x1_half else (H, W)
     x1 = RNG.standard_normal((B, h1, w1, C1)).astype(np.float32)
