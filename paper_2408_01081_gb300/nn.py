@@ -69,8 +69,20 @@ def _ok(name, st):
 RELU, ACCUMULATE, X1_HALF, ACT_BF16, MMA_SYNC = 1, 2, 4, 8, 16     # flags of include/lbm_nn.h
 
 
+_mma_sync_default = False
+
+
+def use_mma_sync(on: bool) -> None:
+    """Route 3x3 forward convolutions through the mma.sync kernels instead of the tcgen05
+    kernel (same arithmetic, other summation order; for comparisons)."""
+    global _mma_sync_default
+    _mma_sync_default = bool(on)
+
+
 def conv_forward(x1, C1, x2, C2, w_bf16, bias, y1, Co1, y2, Cout, B, H, W, KS, relu=False, beta=False,
-                 x1_half=False, act_bf16=False, mma_sync=False):
+                 x1_half=False, act_bf16=False, mma_sync=None):
+    if mma_sync is None:
+        mma_sync = _mma_sync_default
     flags = (RELU if relu else 0) | (ACCUMULATE if beta else 0) | (X1_HALF if x1_half else 0) | \
         (ACT_BF16 if act_bf16 else 0) | (MMA_SYNC if mma_sync else 0)
     _ok("lbm_nn_conv_forward", _lib().lbm_nn_conv_forward(_p(x1), C1, _p(x2), C2, _p(w_bf16), _p(bias), _p(y1), Co1,

@@ -571,6 +571,78 @@ def kernel_workload(what, batch=16, H=256, W=256, repeats=3, act_bf16=False):
     torch.cuda.synchronize()
 
 
+def layer_timing(batch=16, H=256, W=256, reps=20, chans=(32, 64, 128, 256)):
+    """Microseconds per launch of every 3x3 convolution of the U-Net (random inputs and
+    weights, ReLU, the decoder's first convolution reading its upsampled input at half
+    size), tcgen05 kernel vs mma.sync kernels, hi/lo and single-BF16 activations; then
+    inference (ms per lattice, `timing`) and one training step (batch 8) with each."""
+    import torch
+    c = list(chans)
+    shapes = []
+    for l in range(4):
+        shapes += [(f"enc{l}a", H >> l, c[l - 1] if l else CIN_PAD, 0, c[l], False),
+                   (f"enc{l}b", H >> l, c[l], 0, c[l], False)]
+    for l in (2, 1, 0):
+        shapes += [(f"dec{l}a", H >> l, c[l + 1], c[l], c[l], True), (f"dec{l}b", H >> l, c[l], 0, c[l], False)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    layers = []
+    for name, h, C1, C2, Co, half in shapes:
+        w_ = h * W // H
+        h1, w1 = (h // 2, w_ // 2) if half else (h, w_)
+        x1 = torch.randn(batch, h1, w1, C1, device="cuda", generator=gen)
+        x2 = torch.randn(batch, h, w_, C2, device="cuda", generator=gen) if C2 else None
+        wt = (torch.randn(Co, 3, 3, C1 + C2, device="cuda", generator=gen) * 0.05).to(torch.bfloat16)
+        bias = torch.randn(Co, device="cuda", generator=gen)
+        y = torch.empty(batch, h, w_, Co, device="cuda")
+        flop = 2.0 * batch * h * w_ * 9 * (C1 + C2) * Co
+        r = {"layer": name, "H": h, "W": w_, "Cin": C1 + C2, "Cout": Co}
+        for act in (False, True):
+            for ms in (False, True):
+                def f():
+                    K.conv_forward(x1, C1, x2, C2, wt, bias, y, Co, None, Co, batch, h, w_, 3, relu=True,
+                                   x1_half=half, act_bf16=act, mma_sync=ms)
+                for _ in range(3):
+                    f()
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(reps):
+                    f()
+                e1.record()
+                torch.cuda.synchronize()
+                us = e0.elapsed_time(e1) / reps * 1e3
+                key = ("bf16_act_" if act else "") + ("mma_sync" if ms else "tcgen05")
+                r[key + "_us"] = round(us, 1)
+                r[key + "_tflops"] = round(flop / us / 1e6, 1)
+        K.check()
+        layers.append(r)
+    out = {"batch": batch, "layers": layers,
+           "sum_us": {k: round(sum(r[k] for r in layers), 1) for k in layers[0] if k.endswith("_us")}}
+    net = UNet(chans, seed=0)
+    sur = Surrogate(net, np.ones(NF), 32)
+    for ms in (False, True):
+        K.use_mma_sync(ms)
+        try:
+            t = timing(sur, n=batch, H=H, W=W)
+            net._alloc(8, H, W)
+            net.A["x0"].normal_(generator=gen)
+            net.A["tgt"].normal_(generator=gen)
+            for _ in range(2):
+                net.train_step(8, H, W, 1e-4)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(5):
+                net.train_step(8, H, W, 1e-4)
+            e1.record()
+            torch.cuda.synchronize()
+            t["train_step_ms_batch8"] = e0.elapsed_time(e1) / 5
+            K.check()
+        finally:
+            K.use_mma_sync(False)
+        out["mma_sync" if ms else "tcgen05"] = t
+    return out
+
+
 if __name__ == "__main__":
     import argparse
     ap = argparse.ArgumentParser(description="train and evaluate the surrogate on solver trajectories")
@@ -584,8 +656,13 @@ if __name__ == "__main__":
     ap.add_argument("--budget", type=float, default=None, help="training time budget in seconds")
     ap.add_argument("--kernels", choices=["infer", "train"], default=None,
                     help="only run a fixed launch sequence of the layer kernels (for profiling)")
+    ap.add_argument("--layer-timing", action="store_true",
+                    help="time every 3x3 convolution, inference and a training step (tcgen05 vs mma.sync)")
     a = ap.parse_args()
-    if a.kernels:
+    if a.layer_timing:
+        import json
+        print(json.dumps(layer_timing(batch=a.batch, H=a.size, W=a.size), indent=1))
+    elif a.kernels:
         kernel_workload(a.kernels, batch=a.batch, H=a.size, W=a.size)
         print("done")
     else:
