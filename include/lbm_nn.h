@@ -50,6 +50,10 @@ lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int
                                const float* bias, float* y1, int32_t Co1, float* y2, int32_t Cout, int32_t B,
                                int32_t H, int32_t W, int32_t KS, int32_t flags, void* stream);
 
+/* out[0] = forward convolutions launched on the tcgen05 kernel, out[1] = on the mma.sync
+ * kernels, since the library was loaded (host counters; out must hold two values). */
+lbm_status lbm_nn_conv_counts(int64_t* out);
+
 /* Synchronises `stream`; LBM_ERR_TIMEOUT if a bounded wait inside a tcgen05 convolution ran
  * out since the last call (the output of that convolution is invalid; the flag is cleared),
  * LBM_ERR_CUDA if a launch or the stream failed, else LBM_OK. */

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "lbm_nn.h"
 #include "nn_conv_tc.h"
 
@@ -908,6 +910,9 @@ long long wgrad_pixels_per_split(int Cin, int Cout, long long P, int KS)
     return (pps + 63) / 64 * 64;
 }
 
+// forward convolutions launched since the library was loaded: [0] tcgen05, [1] mma.sync
+std::atomic<long long> g_conv_launches[2];
+
 lbm_status launch_status()
 {
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
@@ -931,8 +936,12 @@ lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int
         const ConvTcArgs t{x1, x2, C1, C2, static_cast<const uint16_t*>(w_bf16), bias, y1, y2, Co1, Cout, B, H, W,
                            (flags & LBM_NN_RELU) ? 1 : 0, (flags & LBM_NN_ACCUMULATE) ? 1 : 0,
                            (flags & LBM_NN_X1_HALF) ? 1 : 0, (flags & LBM_NN_ACT_BF16) ? 1 : 0};
-        if (conv3_tc_launch(t, s, 0)) return launch_status();
+        if (conv3_tc_launch(t, s, 0)) {
+            g_conv_launches[0].fetch_add(1, std::memory_order_relaxed);
+            return launch_status();
+        }
     }
+    g_conv_launches[1].fetch_add(1, std::memory_order_relaxed);
     ConvArgs a{x1, x2, C1, C2, static_cast<const __nv_bfloat16*>(w_bf16), bias, y1, y2, Co1, Cout, B, H, W,
                (flags & LBM_NN_RELU) ? 1 : 0, (flags & LBM_NN_ACCUMULATE) ? 1 : 0, (flags & LBM_NN_X1_HALF) ? 1 : 0,
                (flags & LBM_NN_ACT_BF16) ? 1 : 0};
@@ -979,6 +988,14 @@ lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int
         else conv_fwd_kernel<16, 1><<<grid, 256, 0, s>>>(a);
     }
     return launch_status();
+}
+
+lbm_status lbm_nn_conv_counts(int64_t* out)
+{
+    if (!out) return LBM_ERR_ARG;
+    out[0] = g_conv_launches[0].load(std::memory_order_relaxed);
+    out[1] = g_conv_launches[1].load(std::memory_order_relaxed);
+    return LBM_OK;
 }
 
 lbm_status lbm_nn_check(void* stream)

@@ -9,7 +9,7 @@ import ctypes
 
 from . import lbm as _lbm
 
-EXPORTS = ["lbm_nn_conv_forward", "lbm_nn_check", "lbm_nn_wgrad_workspace_bytes", "lbm_nn_conv_backward_weight",
+EXPORTS = ["lbm_nn_conv_forward", "lbm_nn_check", "lbm_nn_conv_counts", "lbm_nn_wgrad_workspace_bytes", "lbm_nn_conv_backward_weight",
            "lbm_nn_bias_grad_workspace_bytes", "lbm_nn_bias_grad",
            "lbm_nn_weight_flip", "lbm_nn_relu_backward", "lbm_nn_pool", "lbm_nn_pool_backward", "lbm_nn_upsample",
            "lbm_nn_upsample_backward", "lbm_nn_mse", "lbm_nn_adam", "lbm_nn_to_bf16", "lbm_nn_pack_input",
@@ -26,6 +26,7 @@ def _lib():
         sig = {
             "lbm_nn_conv_forward": [vp, i32, vp, i32, vp, vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, vp],
             "lbm_nn_check": [vp],
+            "lbm_nn_conv_counts": [vp],
             "lbm_nn_wgrad_workspace_bytes": [i32, i32, i32, i32, i32, i32],
             "lbm_nn_conv_backward_weight": [vp, i32, vp, i32, vp, i32, i32, i32, i32, i32, vp, i32, vp, i64, vp],
             "lbm_nn_bias_grad_workspace_bytes": [i64, i32],
@@ -93,6 +94,13 @@ def check():
     """Synchronise the current stream; raises LbmError(LBM_ERR_TIMEOUT) if a bounded wait in a
     tcgen05 convolution ran out since the last check."""
     _ok("lbm_nn_check", _lib().lbm_nn_check(_s()))
+
+
+def conv_counts():
+    """(tcgen05 launches, mma.sync launches) of forward convolutions since the library was loaded."""
+    out = (ctypes.c_int64 * 2)()
+    _ok("lbm_nn_conv_counts", _lib().lbm_nn_conv_counts(ctypes.cast(out, ctypes.c_void_p)))
+    return int(out[0]), int(out[1])
 
 
 def wgrad_workspace_bytes(Cin, Cout, B, H, W, KS) -> int:

@@ -86,6 +86,9 @@ def test_conv3_halo_tile_forward(lbm, H, W, C1, C2, Cout, Co1):
     (4, 64, 64, 64, 32, 96, 32, False, True),       # 96 channels (32 per CTA), x1 upsampled, accumulate
     (16, 256, 256, 32, 0, 32, 32, False, False),    # about nine blocks per persistent CTA, resident weights
     (16, 128, 128, 64, 64, 64, 64, False, False),   # several blocks per CTA, weights streamed per chunk
+    (1, 16, 8, 32, 0, 32, 32, True, False),         # the smallest image the kernel takes: one block
+    (1, 16, 16, 32, 0, 32, 16, False, True),        # x1 upsampled from 8x8, two outputs of 16 channels
+    (2, 32, 32, 256, 256, 128, 128, False, False),  # 512 input channels: 32 chunks, weights streamed
 ])
 def test_conv3_tcgen05(lbm, B, H, W, C1, C2, Cout, Co1, act_bf16, x1_half):
     """The tcgen05 3x3 kernel (persistent CTAs, two accumulators in tensor memory): against
@@ -100,11 +103,15 @@ def test_conv3_tcgen05(lbm, B, H, W, C1, C2, Cout, Co1, act_bf16, x1_half):
     prev = RNG.standard_normal((B, H, W, Cout)).astype(np.float32)
     outs = []
     for mma_sync in (False, True):
+        before = K.conv_counts()
         y1 = _t(prev[..., :Co1].copy())
         y2 = _t(prev[..., Co1:].copy()) if Co1 < Cout else None
         K.conv_forward(_t(x1), C1, _t(x2) if C2 else None, C2, _wb(w), _t(b), y1, Co1, y2, Cout, B, H, W, 3,
                        relu=True, beta=x1_half, x1_half=x1_half, act_bf16=act_bf16, mma_sync=mma_sync)
         K.check()
+        after = K.conv_counts()
+        # the launch went to the kernel asked for, not to a fallback
+        assert (after[0] - before[0], after[1] - before[1]) == ((0, 1) if mma_sync else (1, 0)), (before, after)
         outs.append(y1.cpu().numpy() if y2 is None else np.concatenate([y1.cpu().numpy(), y2.cpu().numpy()], 3))
     got, legacy = outs
     assert rel_l2(got, legacy) < 2e-6, rel_l2(got, legacy)
@@ -116,6 +123,28 @@ def test_conv3_tcgen05(lbm, B, H, W, C1, C2, Cout, Co1, act_bf16, x1_half):
     ref = np.maximum(R.conv(x.astype(np.float64), w, b), 0.0) + (prev[idx] if x1_half else 0.0)
     assert rel_l2(got[idx], ref) < 2e-5, rel_l2(got[idx], ref)
     assert np.max(np.abs(got[idx] - ref)) < 1e-4 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("H,W,Cout,Co1,KS,tc", [(16, 8, 32, 32, 3, True), (8, 16, 32, 32, 3, False),
+                                                  (16, 16, 48, 48, 3, False), (16, 16, 32, 8, 3, False),
+                                                  (16, 16, 32, 32, 1, False), (16, 4, 32, 32, 3, False)])
+def test_conv_kernel_selection(lbm, H, W, Cout, Co1, KS, tc):
+    """3x3 convolutions with H >= 16, W >= 8, Cout a multiple of 32 and Co1 a multiple of 16 run
+    on the tcgen05 kernel, everything else on the mma.sync kernels; both give the reference."""
+    from paper_2408_01081_gb300 import nn as K
+    B, C1 = 2, 32
+    x1 = RNG.standard_normal((B, H, W, C1)).astype(np.float32)
+    w = _bf16(RNG.standard_normal((Cout, KS, KS, C1)) * 0.1)
+    y1 = _t(np.zeros((B, H, W, Co1), np.float32))
+    y2 = _t(np.zeros((B, H, W, Cout - Co1), np.float32)) if Co1 < Cout else None
+    before = K.conv_counts()
+    K.conv_forward(_t(x1), C1, None, 0, _wb(w), None, y1, Co1, y2, Cout, B, H, W, KS)
+    K.check()
+    after = K.conv_counts()
+    assert (after[0] - before[0], after[1] - before[1]) == ((1, 0) if tc else (0, 1))
+    got = y1.cpu().numpy() if y2 is None else np.concatenate([y1.cpu().numpy(), y2.cpu().numpy()], axis=3)
+    ref = R.conv(x1.astype(np.float64), w)
+    assert rel_l2(got, ref) < 2e-5, rel_l2(got, ref)
 
 
 @pytest.mark.parametrize("P,C", [(1, 5), (100, 32), (70000, 64), (5000, 384), (1 << 21, 32)])
