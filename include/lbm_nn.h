@@ -40,8 +40,10 @@ enum {
     LBM_NN_X1_HALF = 4,     /* x1 is stored at (H/2, W/2) and read nearest-upsampled to (H, W) */
     LBM_NN_ACT_BF16 = 8,    /* forward: activations as one BF16 value instead of the hi/lo pair
                                (half the tensor-core work; activations rounded to BF16) */
-    LBM_NN_MMA_SYNC = 16    /* forward: use the mma.sync kernels even where the tcgen05 kernel applies
+    LBM_NN_MMA_SYNC = 16,   /* forward: use the mma.sync kernels even where the tcgen05 kernel applies
                                (same arithmetic, other summation order) */
+    LBM_NN_WGRAD_PER_TAP = 32 /* weight gradient: the per-tap kernel even where the block-tiled 3x3
+                                 kernel applies (same products, other summation order) */
 };
 
 /* y = act(conv_KS(x, w) + bias), act = ReLU with LBM_NN_RELU; flags as above (any other
@@ -50,8 +52,9 @@ lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int
                                const float* bias, float* y1, int32_t Co1, float* y2, int32_t Cout, int32_t B,
                                int32_t H, int32_t W, int32_t KS, int32_t flags, void* stream);
 
-/* out[0] = forward convolutions launched on the tcgen05 kernel, out[1] = on the mma.sync
- * kernels, since the library was loaded (host counters; out must hold two values). */
+/* Launch counters since the library was loaded (host side; out must hold four values):
+ * forward convolutions on the tcgen05 kernel (out[0]) and on the mma.sync kernels (out[1]);
+ * weight gradients on the block-tiled 3x3 kernel (out[2]) and on the per-tap kernel (out[3]). */
 lbm_status lbm_nn_conv_counts(int64_t* out);
 
 /* Synchronises `stream`; LBM_ERR_TIMEOUT if a bounded wait inside a tcgen05 convolution ran
@@ -63,8 +66,10 @@ lbm_status lbm_nn_check(void* stream);
 int64_t lbm_nn_wgrad_workspace_bytes(int32_t Cin, int32_t Cout, int32_t B, int32_t H, int32_t W, int32_t KS);
 
 /* dw[co][ky][kx][ci] (+)= sum over pixels of dy[p][co] * x[p + (ky, kx) - KS/2][ci]; FP32 output,
- * reduced over pixel splits in a fixed order (deterministic).  flags: LBM_NN_ACCUMULATE,
- * LBM_NN_X1_HALF (others return LBM_ERR_ARG). */
+ * reduced over pixel splits in a fixed order (deterministic).  3x3 with H, W >= 16 and Cout a
+ * multiple of 32 runs on 16x16-pixel blocks with all nine taps per CTA; other sizes (and
+ * LBM_NN_WGRAD_PER_TAP) one tap per CTA.  flags: LBM_NN_ACCUMULATE, LBM_NN_X1_HALF,
+ * LBM_NN_WGRAD_PER_TAP (others return LBM_ERR_ARG). */
 lbm_status lbm_nn_conv_backward_weight(const float* dy, int32_t Cout, const float* x1, int32_t C1, const float* x2,
                                        int32_t C2, int32_t B, int32_t H, int32_t W, int32_t KS, float* dw,
                                        int32_t flags, void* workspace, int64_t workspace_bytes, void* stream);

@@ -536,6 +536,134 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(WgradArgs a)
         }
 }
 
+// ---------------------------------------------------------------------------
+// 3x3 weight gradient on 16 x 16 pixel blocks (H, W >= 16; Cin, Cout multiples of 32).
+// A CTA takes 32 output x 32 input channels and all nine taps.  Per block it stages dY
+// (256 pixels) and X with its one-pixel halo (18 x 18 pixels) once, as BF16 hi / lo in
+// [pixel][channel] rows, and warp w accumulates tap w: its B fragments are read
+// (ldmatrix.trans, one row address per lane) from the halo block at the tap's offset,
+// so nothing is staged per tap.  Products as in conv_wgrad_kernel (dY_hi X_hi +
+// dY_hi X_lo + dY_lo X_hi); split over ranges of blocks (gridDim.z),
+// partial[split][co][tap][ci] reduced in fixed order by sum_splits_kernel.
+// ---------------------------------------------------------------------------
+struct Wgrad3Args {
+    const float* dy;          // [B][H][W][Cout]
+    const float* x1;          // [B][H][W][C1] (or [B][H/2][W/2][C1] with x1_half)
+    const float* x2;          // [B][H][W][C2] or null
+    int C1, C2, Cout;
+    int B, H, W;
+    int blocks_per_split;
+    float* partial;           // [splits][Cout][9][Cin]
+    int x1_half;
+};
+
+constexpr int G3ROW = 40;                 // smem row: 32 channels + 8 pad (80 bytes, conflict-free ldmatrix)
+constexpr int G3Y = 256, G3X = 18 * 18;   // pixels of the dY block and of the X halo block
+constexpr int G3THREADS = 9 * 32;         // one warp per tap
+constexpr int conv_wgrad3_smem_bytes() { return 2 * (G3Y + G3X) * G3ROW * (int)sizeof(__nv_bfloat16); }
+
+__global__ void __launch_bounds__(G3THREADS, 2) conv_wgrad3_tile_kernel(Wgrad3Args a)
+{
+    extern __shared__ __align__(16) __nv_bfloat16 sm3[];
+    __nv_bfloat16* Yh = sm3;                      // [256][G3ROW]
+    __nv_bfloat16* Yl = Yh + G3Y * G3ROW;
+    __nv_bfloat16* Xh = Yl + G3Y * G3ROW;         // [324][G3ROW]
+    __nv_bfloat16* Xl = Xh + G3X * G3ROW;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;   // warp = tap
+    const int g = lane >> 2, t4 = lane & 3, mi = lane >> 3, r8 = lane & 7;
+    const int dy = warp / 3, dx = warp - 3 * (warp / 3);              // halo offsets 0..2
+    const int Cin = a.C1 + a.C2;
+    const int co0 = blockIdx.x * 32, ci0 = blockIdx.y * 32;
+    const int bx = a.W / 16, by = a.H / 16;
+    const int nblocks = a.B * by * bx;
+    const int b0 = blockIdx.z * a.blocks_per_split;
+    const int b1 = min(nblocks, b0 + a.blocks_per_split);
+    // input channels ci0 .. ci0 + 31 lie in x1 or in x2 (C1 is a multiple of 32)
+    const bool from1 = ci0 < a.C1;
+    const float* xs = from1 ? a.x1 : a.x2;
+    const int xstride = from1 ? a.C1 : a.C2;
+    const int xoff = from1 ? ci0 : ci0 - a.C1;
+    const int half = (from1 && a.x1_half) ? 1 : 0;      // nearest upsampling of a half-size x1
+    const int hs = a.H >> half, ws = a.W >> half;
+
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+    for (int b = b0; b < b1; ++b) {
+        const int n = b / (by * bx), ty0 = ((b / bx) % by) * 16, tx0 = (b % bx) * 16;
+#pragma unroll 4
+        for (int q = tid; q < G3Y * 8; q += G3THREADS) {            // dY: 256 pixels x 8 float4
+            const int pk = q >> 3, c4 = (q & 7) * 4;
+            const long long p = ((long long)n * a.H + ty0 + (pk >> 4)) * a.W + tx0 + (pk & 15);
+            uint2 h, l;
+            split_bf16x4(__ldg(reinterpret_cast<const float4*>(a.dy + p * a.Cout + co0 + c4)), h, l);
+            *reinterpret_cast<uint2*>(Yh + pk * G3ROW + c4) = h;
+            *reinterpret_cast<uint2*>(Yl + pk * G3ROW + c4) = l;
+        }
+#pragma unroll 4
+        for (int q = tid; q < G3X * 8; q += G3THREADS) {            // X: 18 x 18 halo pixels, periodic
+            const int hp = q >> 3, c4 = (q & 7) * 4;
+            const int hy = hp / 18, hx = hp - hy * 18;
+            const int sy = (ty0 + hy - 1) & (a.H - 1), sx = (tx0 + hx - 1) & (a.W - 1);
+            const long long sp = ((long long)n * hs + (sy >> half)) * ws + (sx >> half);
+            uint2 h, l;
+            split_bf16x4(__ldg(reinterpret_cast<const float4*>(xs + sp * xstride + xoff + c4)), h, l);
+            *reinterpret_cast<uint2*>(Xh + hp * G3ROW + c4) = h;
+            *reinterpret_cast<uint2*>(Xl + hp * G3ROW + c4) = l;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int r = 0; r < 16; ++r) {            // K step: row r of the block (16 pixels)
+            // A = dY^T (co x pixel): matrices (m, k), (m+8, k), (m, k+8), (m+8, k+8)
+            uint32_t fah[2][4], fal[2][4];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int m0 = i * 16 + (mi & 1) * 8;
+                const int k0 = r * 16 + (mi >> 1) * 8 + r8;
+                ldsm_x4_trans(fah[i], Yh + k0 * G3ROW + m0);
+                ldsm_x4_trans(fal[i], Yl + k0 * G3ROW + m0);
+            }
+            // B = X (pixel x ci): pixel (r, c) of the block is halo pixel (r + dy, c + dx)
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+                uint32_t fbh[4], fbl[4];
+                const int n0 = jj * 16 + (mi >> 1) * 8;
+                const int hp = (r + dy) * 18 + (mi & 1) * 8 + r8 + dx;
+                ldsm_x4_trans(fbh, Xh + hp * G3ROW + n0);
+                ldsm_x4_trans(fbl, Xl + hp * G3ROW + n0);
+#pragma unroll
+                for (int j2 = 0; j2 < 2; ++j2) {
+                    const uint32_t bh[2] = {fbh[2 * j2], fbh[2 * j2 + 1]}, bl[2] = {fbl[2 * j2], fbl[2 * j2 + 1]};
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        mma_bf16(acc[i][jj * 2 + j2], fah[i], bh);
+                        mma_bf16(acc[i][jj * 2 + j2], fah[i], bl);
+                        mma_bf16(acc[i][jj * 2 + j2], fal[i], bh);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    float* out = a.partial + (long long)blockIdx.z * a.Cout * 9 * Cin;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int co = co0 + i * 16 + g + 8 * h;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int e = 0; e < 2; ++e)
+                    out[((long long)co * 9 + warp) * Cin + ci0 + j * 8 + 2 * t4 + e] = acc[i][j][2 * h + e];
+        }
+}
+
 // sum the split partials in order into dW (FP32)
 __global__ void sum_splits_kernel(const float* __restrict__ partial, int splits, long long n, float* __restrict__ out,
                                   int beta)
@@ -896,6 +1024,7 @@ int ilog2(long long v)
 // (setting it twice from racing threads is harmless)
 constexpr int kMaxDevices = 64;
 bool g_conv3_attr[kMaxDevices][8] = {};
+bool g_wgrad3_attr[kMaxDevices] = {};
 
 // pixels per split of the weight gradient: enough splits for about four blocks per
 // SM (a block walks its pixels serially), at least 1024 pixels (16 chunks) each
@@ -910,8 +1039,23 @@ long long wgrad_pixels_per_split(int Cin, int Cout, long long P, int KS)
     return (pps + 63) / 64 * 64;
 }
 
-// forward convolutions launched since the library was loaded: [0] tcgen05, [1] mma.sync
-std::atomic<long long> g_conv_launches[2];
+// convolutions launched since the library was loaded: forward [0] tcgen05, [1] mma.sync;
+// weight gradient [2] block-tiled, [3] per tap
+std::atomic<long long> g_conv_launches[4];
+
+// the block-tiled 3x3 weight gradient applies (C1, C2 are multiples of 32 already)
+bool wgrad3_applies(int Cout, int H, int W, int KS) { return KS == 3 && H >= 16 && W >= 16 && Cout % 32 == 0; }
+
+// 16 x 16 pixel blocks per split of the block-tiled kernel: about four CTAs per SM
+long long wgrad3_blocks_per_split(int Cin, int Cout, int B, int H, int W)
+{
+    const long long nblocks = (long long)B * (H / 16) * (W / 16);
+    const long long tiles = (long long)(Cout / 32) * (Cin / 32);
+    long long splits = (4 * 152 + tiles - 1) / tiles;
+    if (splits > nblocks) splits = nblocks;
+    if (splits < 1) splits = 1;
+    return (nblocks + splits - 1) / splits;
+}
 
 lbm_status launch_status()
 {
@@ -993,8 +1137,7 @@ lbm_status lbm_nn_conv_forward(const float* x1, int32_t C1, const float* x2, int
 lbm_status lbm_nn_conv_counts(int64_t* out)
 {
     if (!out) return LBM_ERR_ARG;
-    out[0] = g_conv_launches[0].load(std::memory_order_relaxed);
-    out[1] = g_conv_launches[1].load(std::memory_order_relaxed);
+    for (int i = 0; i < 4; ++i) out[i] = g_conv_launches[i].load(std::memory_order_relaxed);
     return LBM_OK;
 }
 
@@ -1007,7 +1150,13 @@ int64_t lbm_nn_wgrad_workspace_bytes(int32_t Cin, int32_t Cout, int32_t B, int32
 {
     const long long P = (long long)B * H * W;
     const long long pps = wgrad_pixels_per_split(Cin, Cout, P, KS);
-    const long long splits = (P + pps - 1) / pps;
+    long long splits = (P + pps - 1) / pps;
+    if (wgrad3_applies(Cout, H, W, KS)) {       // either kernel may run: room for the larger split count
+        const long long nblocks = (long long)B * (H / 16) * (W / 16);
+        const long long bps = wgrad3_blocks_per_split(Cin, Cout, B, H, W);
+        const long long s3 = (nblocks + bps - 1) / bps;
+        if (s3 > splits) splits = s3;
+    }
     return splits * (long long)Cout * KS * KS * Cin * (long long)sizeof(float);
 }
 
@@ -1017,11 +1166,34 @@ lbm_status lbm_nn_conv_backward_weight(const float* dy, int32_t Cout, const floa
 {
     if (!dy || !x1 || !dw || !workspace || C1 <= 0 || C1 % 32 || C2 < 0 || C2 % 32 || (C2 > 0 && !x2) ||
         Cout <= 0 || Cout % 8 || B <= 0 || !pow2(H) || !pow2(W) || (KS != 1 && KS != 3) ||
-        (flags & ~(LBM_NN_ACCUMULATE | LBM_NN_X1_HALF)) || ((flags & LBM_NN_X1_HALF) && (H < 2 || W < 2)))
+        (flags & ~(LBM_NN_ACCUMULATE | LBM_NN_X1_HALF | LBM_NN_WGRAD_PER_TAP)) ||
+        ((flags & LBM_NN_X1_HALF) && (H < 2 || W < 2)))
         return LBM_ERR_ARG;
     const int beta = (flags & LBM_NN_ACCUMULATE) ? 1 : 0;
     const int Cin = C1 + C2;
     if (workspace_bytes < lbm_nn_wgrad_workspace_bytes(Cin, Cout, B, H, W, KS)) return LBM_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (wgrad3_applies(Cout, H, W, KS) && !(flags & LBM_NN_WGRAD_PER_TAP)) {
+        const long long nblocks = (long long)B * (H / 16) * (W / 16);
+        const int bps = (int)wgrad3_blocks_per_split(Cin, Cout, B, H, W);
+        const int splits = (int)((nblocks + bps - 1) / bps);
+        Wgrad3Args g3{dy, x1, x2, C1, C2, Cout, B, H, W, bps, static_cast<float*>(workspace),
+                      (flags & LBM_NN_X1_HALF) ? 1 : 0};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev >= 0 && dev < kMaxDevices && !g_wgrad3_attr[dev]) {
+            cudaFuncSetAttribute(conv_wgrad3_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 conv_wgrad3_smem_bytes());
+            g_wgrad3_attr[dev] = true;
+        }
+        conv_wgrad3_tile_kernel<<<dim3((unsigned)(Cout / 32), (unsigned)(Cin / 32), (unsigned)splits), G3THREADS,
+                                  conv_wgrad3_smem_bytes(), st>>>(g3);
+        const long long n = (long long)Cout * 9 * Cin;
+        sum_splits_kernel<<<grid_for(n), 256, 0, st>>>(static_cast<const float*>(workspace), splits, n, dw, beta);
+        g_conv_launches[2].fetch_add(1, std::memory_order_relaxed);
+        return launch_status();
+    }
+    g_conv_launches[3].fetch_add(1, std::memory_order_relaxed);
     const long long P = (long long)B * H * W;
     const int pps = (int)wgrad_pixels_per_split(Cin, Cout, P, KS);
     const int splits = (int)((P + pps - 1) / pps);

@@ -67,7 +67,7 @@ def _ok(name, st):
         raise _lbm.LbmError(st, f"{name} failed")
 
 
-RELU, ACCUMULATE, X1_HALF, ACT_BF16, MMA_SYNC = 1, 2, 4, 8, 16     # flags of include/lbm_nn.h
+RELU, ACCUMULATE, X1_HALF, ACT_BF16, MMA_SYNC, WGRAD_PER_TAP = 1, 2, 4, 8, 16, 32     # flags of include/lbm_nn.h
 
 
 _mma_sync_default = False
@@ -97,18 +97,20 @@ def check():
 
 
 def conv_counts():
-    """(tcgen05 launches, mma.sync launches) of forward convolutions since the library was loaded."""
-    out = (ctypes.c_int64 * 2)()
+    """Launches since the library was loaded: (forward tcgen05, forward mma.sync, weight gradient
+    block-tiled, weight gradient per tap)."""
+    out = (ctypes.c_int64 * 4)()
     _ok("lbm_nn_conv_counts", _lib().lbm_nn_conv_counts(ctypes.cast(out, ctypes.c_void_p)))
-    return int(out[0]), int(out[1])
+    return tuple(int(v) for v in out)
 
 
 def wgrad_workspace_bytes(Cin, Cout, B, H, W, KS) -> int:
     return int(_lib().lbm_nn_wgrad_workspace_bytes(Cin, Cout, B, H, W, KS))
 
 
-def conv_backward_weight(dy, Cout, x1, C1, x2, C2, B, H, W, KS, dw, workspace, beta=False, x1_half=False):
-    flags = (ACCUMULATE if beta else 0) | (X1_HALF if x1_half else 0)
+def conv_backward_weight(dy, Cout, x1, C1, x2, C2, B, H, W, KS, dw, workspace, beta=False, x1_half=False,
+                         per_tap=False):
+    flags = (ACCUMULATE if beta else 0) | (X1_HALF if x1_half else 0) | (WGRAD_PER_TAP if per_tap else 0)
     _ok("lbm_nn_conv_backward_weight",
         _lib().lbm_nn_conv_backward_weight(_p(dy), Cout, _p(x1), C1, _p(x2), C2, B, H, W, KS, _p(dw), flags,
                                            _p(workspace), workspace.numel() * workspace.element_size(), _s()))

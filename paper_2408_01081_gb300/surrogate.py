@@ -574,8 +574,9 @@ def kernel_workload(what, batch=16, H=256, W=256, repeats=3, act_bf16=False):
 def layer_timing(batch=16, H=256, W=256, reps=20, chans=(32, 64, 128, 256)):
     """Microseconds per launch of every 3x3 convolution of the U-Net (random inputs and
     weights, ReLU, the decoder's first convolution reading its upsampled input at half
-    size), tcgen05 kernel vs mma.sync kernels, hi/lo and single-BF16 activations; then
-    inference (ms per lattice, `timing`) and one training step (batch 8) with each."""
+    size), tcgen05 kernel vs mma.sync kernels, hi/lo and single-BF16 activations, and of
+    its weight gradient (block-tiled vs per-tap kernel); then inference (ms per lattice,
+    `timing`) and one training step (batch 8) with each forward kernel family."""
     import torch
     c = list(chans)
     shapes = []
@@ -614,6 +615,23 @@ def layer_timing(batch=16, H=256, W=256, reps=20, chans=(32, 64, 128, 256)):
                 key = ("bf16_act_" if act else "") + ("mma_sync" if ms else "tcgen05")
                 r[key + "_us"] = round(us, 1)
                 r[key + "_tflops"] = round(flop / us / 1e6, 1)
+        # weight gradient of the same layer (dY = y), block-tiled vs per-tap kernel
+        ws_w = torch.empty(K.wgrad_workspace_bytes(C1 + C2, Co, batch, h, w_, 3) // 4 + 1, device="cuda")
+        dw = torch.empty(Co, 3, 3, C1 + C2, device="cuda")
+        for per_tap in (False, True):
+            def fw():
+                K.conv_backward_weight(y, Co, x1, C1, x2, C2, batch, h, w_, 3, dw, ws_w, x1_half=half,
+                                       per_tap=per_tap)
+            for _ in range(2):
+                fw()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(max(1, reps // 4)):
+                fw()
+            e1.record()
+            torch.cuda.synchronize()
+            r["wgrad_" + ("per_tap" if per_tap else "tiled") + "_us"] = round(
+                e0.elapsed_time(e1) / max(1, reps // 4) * 1e3, 1)
         K.check()
         layers.append(r)
     out = {"batch": batch, "layers": layers,

@@ -190,6 +190,45 @@ def test_conv_gradients(lbm, KS, C1, C2, Cout):
         assert rel_l2(got, rdx) < 2e-5, rel_l2(got, rdx)
 
 
+@pytest.mark.parametrize("B,H,W,C1,C2,Cout,x1_half,beta", [
+    (2, 32, 16, 32, 0, 32, False, False),       # one 32x32 channel tile, 4 blocks
+    (8, 64, 64, 32, 0, 32, False, True),        # 128 blocks over many splits, accumulate
+    (4, 32, 32, 64, 32, 32, True, False),       # x1 half size + x2 (decoder), Cin 96
+    (2, 32, 32, 64, 0, 128, False, False),      # 4 x 2 channel tiles
+    (1, 16, 16, 256, 256, 64, False, False),    # 512 input channels, one block per image
+])
+def test_conv_wgrad_block_tiled(lbm, B, H, W, C1, C2, Cout, x1_half, beta):
+    """The block-tiled 3x3 weight gradient (all nine taps per CTA, halo block staged once)
+    against the FP64 reference and against the per-tap kernel; the launch went to it."""
+    import torch
+    from paper_2408_01081_gb300 import nn as K
+    h1, w1 = (H // 2, W // 2) if x1_half else (H, W)
+    x1 = RNG.standard_normal((B, h1, w1, C1)).astype(np.float32)
+    x2 = RNG.standard_normal((B, H, W, C2)).astype(np.float32) if C2 else None
+    xu = np.repeat(np.repeat(x1, 2, axis=1), 2, axis=2) if x1_half else x1
+    x = xu if C2 == 0 else np.concatenate([xu, x2], axis=3)
+    w = _bf16(RNG.standard_normal((Cout, 3, 3, C1 + C2)) * 0.1)
+    dy = RNG.standard_normal((B, H, W, Cout)).astype(np.float32)
+    _, rdw, _ = R.conv_backward(dy.astype(np.float64), x.astype(np.float64), w)
+    prev = RNG.standard_normal((Cout, 3, 3, C1 + C2)).astype(np.float32)
+    ws = torch.empty(K.wgrad_workspace_bytes(C1 + C2, Cout, B, H, W, 3) // 4 + 1, dtype=torch.float32,
+                     device="cuda")
+    outs = []
+    for per_tap in (False, True):
+        dw = _t(prev.copy())
+        before = K.conv_counts()
+        K.conv_backward_weight(_t(dy), Cout, _t(x1), C1, _t(x2) if C2 else None, C2, B, H, W, 3, dw, ws,
+                               beta=beta, x1_half=x1_half, per_tap=per_tap)
+        K.check()
+        after = K.conv_counts()
+        assert (after[2] - before[2], after[3] - before[3]) == ((0, 1) if per_tap else (1, 0)), (before, after)
+        outs.append(dw.cpu().numpy() - (prev if beta else 0.0))
+    got, per_tap_result = outs
+    assert rel_l2(got, rdw) < 2e-5, rel_l2(got, rdw)
+    # same products, FP32 sums over the pixels in another order
+    assert rel_l2(got, per_tap_result) < 1e-5, rel_l2(got, per_tap_result)
+
+
 def test_pool_upsample_mse_adam_pack(lbm):
     import torch
     from paper_2408_01081_gb300 import nn as K
