@@ -4,8 +4,11 @@
 // and every convolution pads circularly (the lattices are periodic).  Weights
 // are BF16, [Cout][KS][KS][Cin], with FP32 master copies for the optimiser.
 //
-// Convolutions are implicit GEMMs on the tensor cores with mma.sync m16n8k16
-// (BF16 inputs, FP32 accumulation).  An FP32 activation a is split into
+// 3x3 forward convolutions go to the tcgen05 kernel of nn_conv_tc.cu where its tiling
+// applies; the kernels here are implicit GEMMs with mma.sync m16n8k16 (BF16 inputs,
+// FP32 accumulation) for the forward sizes that tiling does not take (the data
+// gradient is a forward convolution too) and for the weight gradients.  An FP32
+// activation a is split into
 // a_hi = bf16(a) and a_lo = bf16(a - a_hi); products use both halves, so the
 // only rounding of the forward pass is the BF16 weights themselves:
 //   forward / data gradient: W x (a_hi + a_lo)           (2 MMAs per tile)
