@@ -100,14 +100,19 @@ lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t row
  * scheme this does not change).  The FP64 step needs 35 additions and 12 fused
  * multiply-adds per node and GB300 issues FP64 operations at 2 per clock per SM,
  * so the step is bound by the FP64 pipe.  At level > 0 a set of the additions is
- * computed exactly (IEEE 754 binary64, round to nearest even) on the integer
- * pipes, in parallel with the FP64 pipe; results are bit-identical to level 0.
- * Lanes whose operands leave the exact integer path (subnormal, infinite or NaN
- * results) recompute on the FP64 pipe.  Levels 1..7 select different sets of
- * additions (level 1: the 10 pair sums and the 5 sums U, the fastest measured
- * and the default); level 0 runs every operation on the FP64 pipe.  Applies to
- * steps without body load and with omega = 2; other steps use the FP64 pipe
- * only.  A level outside [0, 7] returns LBM_ERR_ARG. */
+ * computed on the integer pipes, in parallel with the FP64 pipe.  Levels 1..7
+ * compute them exactly (IEEE 754 binary64, round to nearest even): results are
+ * bit-identical to level 0 (level 1: the 10 pair sums and the 5 sums U, the
+ * fastest of them).  Levels 8..11 round them faithfully, within (1/2 + 2^-9) ulp
+ * of the exact sum, with fewer integer instructions: the 15 sums of level 1, plus
+ * 1, 2 or 5 of the f*_(-1,0) subtractions; results stay within FP64 accuracy of
+ * level 0 but are not bit-identical, and the rounding is biased (half up, no sticky
+ * bit): over 10^5 steps the discrete energy drifts by about 3e-12 instead of 4e-16.
+ * Level 9 (16 additions) runs about 3 % faster than level 1, which stays the
+ * default.  Lanes whose operands leave the integer path (subnormal, infinite or
+ * NaN results) recompute on the FP64 pipe.  Level 0 runs every operation on
+ * the FP64 pipe.  Applies to steps without body load and with omega = 2; other
+ * steps use the FP64 pipe only.  A level outside [0, 11] returns LBM_ERR_ARG. */
 lbm_status lbm_set_fp64_split(lbm_ctx* ctx, int32_t level);
 
 /* Relaxation rate of the BGK collision (Eq. collision); the paper's scheme is

@@ -396,7 +396,7 @@ lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t row
 lbm_status lbm_set_fp64_split(lbm_ctx* ctx, int32_t level)
 {
     LBM_CHECK_CTX(ctx);
-    if (level < 0 || level > 7) return fail(ctx, LBM_ERR_ARG, "split level must be in [0, 7]");
+    if (level < 0 || level >= lbmh::STEP_SPLIT_LEVELS) return fail(ctx, LBM_ERR_ARG, "split level must be in [0, 11]");
     ctx->split = level;
     return LBM_OK;
 }

@@ -12,8 +12,9 @@
 
 namespace lbmh {
 
-// step variant bits; bits 4-6 hold the FP64 split level (0 = every addition on the FP64 pipe)
-enum { STEP_DIRICHLET = 1, STEP_FORCING = 2, STEP_TRACK = 4, STEP_OMEGA = 8, STEP_SPLIT_SHIFT = 4 };
+// step variant bits; bits 4-7 hold the FP64 split level (0 = every addition on the FP64 pipe)
+enum { STEP_DIRICHLET = 1, STEP_FORCING = 2, STEP_TRACK = 4, STEP_OMEGA = 8, STEP_SPLIT_SHIFT = 4,
+       STEP_SPLIT_LEVELS = 12 };
 
 // additions moved to the integer pipes at split level 1..7, as bit masks over the
 // node's 35 additions (bit layout of lbmk::collide_split): 0-4 f*_(-1,0), 5-9
@@ -29,13 +30,18 @@ constexpr unsigned long long split_mask(int level)
          : level == 5 ? 0x000F07C1Full    // 14: f*_(-1,0), y-pair sums, U 0-3
          : level == 6 ? 0x001FFFC1Full    // 20: f*_(-1,0), pair sums, U
          : level == 7 ? 0x007F07C1Full    // 17: f*_(-1,0), y-pair sums, U, U/2 + t of (1,0) 0-1
+         // levels 8-11: faithfully rounded integer-pipe additions (emu_add_faithful_bits)
+         : level == 8 ? (lbmk::kSplitDefaultMask | lbmk::kSplitFaithful)   // 15: pair sums, U
+         : level == 9 ? lbmk::kSplitFastMask                               // 16: + f*_(-1,0) 0
+         : level == 10 ? (0x001FFFC03ull | lbmk::kSplitFaithful)           // 17: + f*_(-1,0) 0-1
+         : level == 11 ? (0x001FFFC1Full | lbmk::kSplitFaithful)           // 20: + f*_(-1,0)
                       : 0ull;
 }
 
 constexpr int split_adds(int level)
 {
     int n = 0;
-    for (unsigned long long m = split_mask(level); m; m >>= 1) n += (int)(m & 1);
+    for (unsigned long long m = split_mask(level) & ~lbmk::kSplitFaithful; m; m >>= 1) n += (int)(m & 1);
     return n;
 }
 

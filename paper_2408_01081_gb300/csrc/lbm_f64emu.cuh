@@ -14,6 +14,10 @@
 // the caller recomputes with the hardware instruction, so whenever `ok` stays
 // set the result is bit-identical to the hardware sum.
 //
+// emu_add_faithful_bits() is a cheaper variant rounded faithfully (within 1/2 + 2^-9 units
+// in the last place), for callers that need FP64 accuracy but not the hardware's bits;
+// its rounding is biased (half up on a truncated sum), which long runs accumulate.
+//
 // emu_half_add(u, t) returns round(u/2 + t), the value of fma(0.5, u, t): u/2 is
 // exact for normal u with exponent field >= 2 (its exponent field minus one) and
 // for zero; other u clear `ok`.
@@ -74,6 +78,41 @@ EMU_HD u64 emu_add_bits(u64 ua, u64 ub, bool& ok)
     return zero ? (ua & ub & SIGN) : (r | (h & SIGN));
 }
 
+// The same sum rounded faithfully instead of correctly: the aligned smaller significand
+// keeps its ten guard bits and is truncated below them (no sticky bit), and the
+// normalised sum is rounded half up.  The smaller operand loses bits only when the
+// exponents differ by more than ten, and then the sum cancels at most two leading
+// bits, so the truncation moves the result by less than 2^-9 units in the last place:
+// |result - exact sum| <= (1/2 + 2^-9) ulp.  Not bit-identical to the hardware sum (it
+// differs in the last bit near ties); about 17 % fewer integer instructions than
+// emu_add_bits.  The error is biased: the truncation lowers the magnitude of sums and
+// raises that of differences, and ties round up.  `ok` is cleared for infinite or NaN inputs and for subnormal or
+// overflowing results, as there.
+EMU_HD u64 emu_add_faithful_bits(u64 ua, u64 ub, bool& ok)
+{
+    const u64 SIGN = 0x8000000000000000ull, FRAC = 0x000FFFFFFFFFFFFFull, HID = 0x0010000000000000ull;
+    const u64 xa = ua & ~SIGN, xb = ub & ~SIGN;
+    const bool sw = xb > xa;                        // order by magnitude: |h| >= |l|
+    const u64 h = sw ? ub : ua, l = sw ? ua : ub;
+    const u64 xh = h & ~SIGN, xl = l & ~SIGN;
+    const int eh = (int)(xh >> 52), el = (int)(xl >> 52);
+    const u64 mh = ((xh & FRAC) | (eh ? HID : 0ull)) << 10;
+    const u64 ml = ((xl & FRAC) | (el ? HID : 0ull)) << 10;
+    const int e = eh > 1 ? eh : 1;
+    int d = e - (el > 1 ? el : 1);
+    d = d > 63 ? 63 : d;
+    const u64 al = ml >> d;                         // truncated below the guard bits
+    const bool sub = ((h ^ l) & SIGN) != 0;
+    u64 s = sub ? mh - al : mh + al;
+    const int lz = clz64(s | 1ull);
+    s <<= lz;
+    const int er = e + 1 - lz;                      // exponent field of the result
+    const u64 m = (s >> 11) + ((s >> 10) & 1ull);   // 53-bit significand, rounded half up
+    const u64 r = ((u64)(er - 1) << 52) + m;        // a carry out of m bumps the exponent
+    ok = ok && eh < 2047 && (s == 0 || (er >= 1 && (r >> 52) < 2047ull));
+    return s == 0 ? 0ull : (r | (h & SIGN));
+}
+
 EMU_HD u64 emu_half_bits(u64 u, bool& ok)
 {
     const u64 SIGN = 0x8000000000000000ull;
@@ -114,6 +153,22 @@ __device__ __forceinline__ double emu_sub(double a, double b, bool& ok)
 __device__ __forceinline__ double emu_half_add(double u, double t, bool& ok)
 {
     return double_of(emu_add_bits(emu_half_bits(bits_of(u), ok), bits_of(t), ok));
+}
+
+// faithfully rounded counterparts (emu_add_faithful_bits)
+__device__ __forceinline__ double emu_add_f(double a, double b, bool& ok)
+{
+    return double_of(emu_add_faithful_bits(bits_of(a), bits_of(b), ok));
+}
+
+__device__ __forceinline__ double emu_sub_f(double a, double b, bool& ok)
+{
+    return double_of(emu_add_faithful_bits(bits_of(a), bits_of(b) ^ 0x8000000000000000ull, ok));
+}
+
+__device__ __forceinline__ double emu_half_add_f(double u, double t, bool& ok)
+{
+    return double_of(emu_add_faithful_bits(emu_half_bits(bits_of(u), ok), bits_of(t), ok));
 }
 #endif
 

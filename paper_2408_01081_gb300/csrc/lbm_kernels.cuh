@@ -16,7 +16,7 @@
 //     f*_{0,-1} = (U - f_{0,1} - f_{0,-1}) - f*_{0,1}.
 // That is 47 FP64 operations per node without forcing (35 additions, 12 fused
 // multiply-adds), the FP64 ALU bound on GB300; the SPLIT variants compute part of
-// the additions exactly on the integer pipes (collide_split).
+// the additions on the integer pipes (collide_split), exactly or faithfully rounded.
 #pragma once
 
 #include "lbm_f64emu.cuh"
@@ -169,25 +169,35 @@ __device__ __forceinline__ void collide(const M (&f)[4][5], const M (&U)[5], con
 
 // the default split: the 10 pair sums and the 5 sums U on the integer pipes
 constexpr unsigned long long kSplitDefaultMask = 0x001FFFC00ull;
+// mask bit 63: the integer-pipe additions are rounded faithfully (emu_add_faithful_bits)
+// instead of correctly
+constexpr unsigned long long kSplitFaithful = 1ull << 63;
+// the fastest faithful split measured (opt-in, level 9): the 15 sums and the (-1,0)
+// subtraction of component 0; its rounding is biased (half up, no sticky bit), which a
+// long run shows as energy drift
+constexpr unsigned long long kSplitFastMask = 0x001FFFC01ull | kSplitFaithful;
 
-template <bool EMU>
+template <bool EMU, bool FAITHFUL>
 __device__ __forceinline__ double split_add(double x, double y, bool& ok)
 {
-    if constexpr (EMU) return lbmemu::emu_add(x, y, ok);
+    if constexpr (EMU && FAITHFUL) return lbmemu::emu_add_f(x, y, ok);
+    else if constexpr (EMU) return lbmemu::emu_add(x, y, ok);
     else return x + y;
 }
 
-template <bool EMU>
+template <bool EMU, bool FAITHFUL>
 __device__ __forceinline__ double split_sub(double x, double y, bool& ok)
 {
-    if constexpr (EMU) return lbmemu::emu_sub(x, y, ok);
+    if constexpr (EMU && FAITHFUL) return lbmemu::emu_sub_f(x, y, ok);
+    else if constexpr (EMU) return lbmemu::emu_sub(x, y, ok);
     else return x - y;
 }
 
-template <bool EMU>
+template <bool EMU, bool FAITHFUL>
 __device__ __forceinline__ double split_half_add(double u, double t, bool& ok)
 {
-    if constexpr (EMU) return lbmemu::emu_half_add(u, t, ok);
+    if constexpr (EMU && FAITHFUL) return lbmemu::emu_half_add_f(u, t, ok);
+    else if constexpr (EMU) return lbmemu::emu_half_add(u, t, ok);
     else return fma(0.5, u, t);
 }
 
@@ -196,19 +206,21 @@ template <unsigned long long M, int k>
 __device__ __forceinline__ void split_sums(const double (&f)[4][5], double (&rx)[5], double (&ry)[5],
                                            double (&U)[5], bool& ok)
 {
-    rx[k] = split_add<((M >> (10 + k)) & 1) != 0>(f[1][k], f[3][k], ok);
-    ry[k] = split_add<((M >> (15 + k)) & 1) != 0>(f[0][k], f[2][k], ok);
-    U[k] = split_add<((M >> (20 + k)) & 1) != 0>(rx[k], ry[k], ok);
+    constexpr bool FA = (M & kSplitFaithful) != 0;
+    rx[k] = split_add<((M >> (10 + k)) & 1) != 0, FA>(f[1][k], f[3][k], ok);
+    ry[k] = split_add<((M >> (15 + k)) & 1) != 0, FA>(f[0][k], f[2][k], ok);
+    U[k] = split_add<((M >> (20 + k)) & 1) != 0, FA>(rx[k], ry[k], ok);
 }
 
 template <unsigned long long M, int k>
 __device__ __forceinline__ void split_outputs(const double (&U)[5], const double (&rx)[5], const double (&ry)[5],
                                               const double (&t)[2][5], double (&o)[4][5], bool& ok)
 {
-    o[0][k] = split_half_add<((M >> (25 + k)) & 1) != 0>(U[k], t[0][k], ok);
-    o[1][k] = split_half_add<((M >> (30 + k)) & 1) != 0>(U[k], t[1][k], ok);
-    o[2][k] = split_sub<((M >> k) & 1) != 0>(rx[k], o[0][k], ok);
-    o[3][k] = split_sub<((M >> (5 + k)) & 1) != 0>(ry[k], o[1][k], ok);
+    constexpr bool FA = (M & kSplitFaithful) != 0;
+    o[0][k] = split_half_add<((M >> (25 + k)) & 1) != 0, FA>(U[k], t[0][k], ok);
+    o[1][k] = split_half_add<((M >> (30 + k)) & 1) != 0, FA>(U[k], t[1][k], ok);
+    o[2][k] = split_sub<((M >> k) & 1) != 0, FA>(rx[k], o[0][k], ok);
+    o[3][k] = split_sub<((M >> (5 + k)) & 1) != 0, FA>(ry[k], o[1][k], ok);
 }
 
 // The same FP64 node update (pair sums, U, collision; no body load) with the
@@ -216,9 +228,10 @@ __device__ __forceinline__ void split_outputs(const double (&U)[5], const double
 // (lbm_f64emu.cuh) and the rest, with the 12 fused multiply-adds, on the FP64
 // pipe.  Bits: f*_(-1,0) (0-4), f*_(0,-1) (5-9), y-pair sums (10-14), x-pair sums
 // (15-19), U (20-24), U/2 + t for (1,0) (25-29) and (0,1) (30-34), component k at
-// offset k.  Every result is bit-identical to collide<double>; a lane whose
-// operands leave the exact integer path (a subnormal, infinite or NaN result)
-// recomputes on the FP64 pipe.
+// offset k; bit 63 (kSplitFaithful) rounds the integer-pipe additions faithfully.
+// Without it every result is bit-identical to collide<double>; with it each such
+// addition is within (1/2 + 2^-9) ulp of the exact sum.  A lane whose operands leave
+// the integer path (a subnormal, infinite or NaN result) recomputes on the FP64 pipe.
 template <unsigned long long M>
 __device__ __forceinline__ void collide_split(const double (&f)[4][5], double a, double b, double (&U)[5],
                                               double (&o)[4][5])

@@ -55,6 +55,10 @@ cudaError_t step_split(const lbmk::StepArgs& a, int level, dim3 g, dim3 b, cudaS
         case 5: return step_v<D, false, T, false, lbmh::split_mask(5)>(a, g, b, s);
         case 6: return step_v<D, false, T, false, lbmh::split_mask(6)>(a, g, b, s);
         case 7: return step_v<D, false, T, false, lbmh::split_mask(7)>(a, g, b, s);
+        case 8: return step_v<D, false, T, false, lbmh::split_mask(8)>(a, g, b, s);
+        case 9: return step_v<D, false, T, false, lbmh::split_mask(9)>(a, g, b, s);
+        case 10: return step_v<D, false, T, false, lbmh::split_mask(10)>(a, g, b, s);
+        case 11: return step_v<D, false, T, false, lbmh::split_mask(11)>(a, g, b, s);
         default: return cudaErrorInvalidValue;
         }
     }
@@ -77,7 +81,7 @@ cudaError_t step_o(const lbmk::StepArgs& a, int variant, dim3 g, dim3 b, cudaStr
 
 cudaError_t step(const lbmk::StepArgs& a, int variant, dim3 g, dim3 b, cudaStream_t s)
 {
-    const int level = (variant >> lbmh::STEP_SPLIT_SHIFT) & 7;
+    const int level = (variant >> lbmh::STEP_SPLIT_SHIFT) & 15;
     if (level && !(variant & (lbmh::STEP_FORCING | lbmh::STEP_OMEGA))) {
         const bool d = variant & lbmh::STEP_DIRICHLET, t = variant & lbmh::STEP_TRACK;
         return d ? (t ? step_split<true, true>(a, level, g, b, s) : step_split<true, false>(a, level, g, b, s))

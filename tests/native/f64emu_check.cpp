@@ -61,6 +61,33 @@ static void check_half(u64 u, u64 t)
     }
 }
 
+// faithful variant: within (1/2 + 2^-9) ulp of the exact sum a + b = s + err (TwoSum), and on
+// the integer path whenever the exact variant is
+static long ffails = 0, ftotal = 0;
+
+static void check_faithful(u64 a, u64 b)
+{
+    bool ok_exact = true, ok = true;
+    lbmemu::emu_add_bits(a, b, ok_exact);
+    const u64 r = lbmemu::emu_add_faithful_bits(a, b, ok);
+    ++ftotal;
+    if (ok_exact && !ok) {
+        if (ffails++ < 10) std::printf("FAITHFUL FALLBACK %016llx + %016llx\n", a, b);
+        return;
+    }
+    if (!ok) return;
+    const double x = dbl(a), y = dbl(b), s = x + y;
+    const double bb = s - x, err = (x - (s - bb)) + (y - bb);       // a + b = s + err exactly
+    const double res = dbl(r);
+    const double ulp = s != 0.0 ? std::ldexp(1.0, std::ilogb(s) - 52) : std::ldexp(1.0, -1074);
+    const double dev = std::fabs((res - s) - err);                  // res - s is exact (Sterbenz)
+    if (!(dev <= (0.5 + 1.0 / 512) * ulp) || (s == 0.0 && res != 0.0)) {
+        if (ffails++ < 10)
+            std::printf("FAITHFUL OFF %016llx + %016llx: emu %016llx hw %016llx (%.3g ulp)\n", a, b, r, bits(s),
+                        dev / ulp);
+    }
+}
+
 static u64 with_exp(u64 x, int e) { return (x & 0x800FFFFFFFFFFFFFull) | ((u64)e << 52); }
 
 int main(int argc, char** argv)
@@ -111,5 +138,19 @@ int main(int argc, char** argv)
         check_half(next(), next());
     }
     std::printf("half add: %ld cases, %ld on the fast path, %ld failures\n", total, fast, fails);
-    return fails ? 1 : 0;
+    // 7. the faithful variant on the same families (ranges that keep a + b normal)
+    for (long i = 0; i < n; ++i) {
+        const int e = 100 + (int)(next() % 1800);
+        const int d = (int)(next() % 71);
+        check_faithful(with_exp(next(), e), with_exp(next(), e - d));
+        const u64 a = with_exp(next(), 100 + (int)(next() % 1800));
+        check_faithful(a, (a ^ 0x8000000000000000ull) + (next() % 4096) - 2048);
+        check_faithful(a, a ^ 0x8000000000000000ull);
+        check_faithful(with_exp(next() & 0x800FFFFFFFFFFC00ull, e), with_exp(next(), e - (int)(next() % 12)));
+        check_faithful(next(), next());
+    }
+    for (int i = 0; i < ns; ++i)
+        for (int j = 0; j < ns; ++j) check_faithful(sp[i], sp[j]);
+    std::printf("faithful add: %ld cases, %ld failures\n", ftotal, ffails);
+    return (fails || ffails) ? 1 : 0;
 }

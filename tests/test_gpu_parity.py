@@ -332,11 +332,59 @@ def test_fp64_split_handles_zeros_subnormals_and_wide_ranges(lbm):
 
 def test_fp64_split_rejects_unsupported_counts(lbm):
     lat = lbm.Lattice(8, 8, 0.1, 0.1 / 3.2, 1.0, 0.6, storage="f64")
-    for bad in (-1, 8, 100):
+    for bad in (-1, 12, 100):
         with pytest.raises(lbm.LbmError):
             lat.set_fp64_split(bad)
-    lat.set_fp64_split(7)
+    lat.set_fp64_split(11)
     lat.close()
+
+
+@pytest.mark.parametrize("nx,ny,dirichlet", [(67, 45, False), (1031, 7, False), (150, 70, True)])
+def test_fp64_faithful_split_levels_stay_at_fp64_accuracy(lbm, nx, ny, dirichlet):
+    """Levels 8-11 round their integer-pipe additions faithfully (within 1/2 + 2^-9 ulp):
+    after 40 steps every population stays within a few ulp-scale relative L2 of the
+    all-FP64-pipe result, far inside the oracle tolerance."""
+    rng = np.random.default_rng(3 * nx + ny)
+    f = rng.standard_normal((4, 5, ny, nx)) * (1e-2 if dirichlet else 1.0)
+    us = rng.standard_normal((2, ny, nx))
+    wall = rng.standard_normal((40, 2, 2 * (nx + ny))) * 1e-2 if dirichlet else None
+    outs = _split_runs(lbm, nx, ny, f, us, 40, [0, 8, 9, 10, 11], dirichlet=dirichlet, wall=wall, track=True)
+    for level in (8, 9, 10, 11):
+        for part in (0, 1):
+            got, ref = outs[level][part], outs[0][part]
+            rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert rel < 1e-14, (level, part, rel)
+        # the faithful path ran: it differs from the hardware sums in the last bit somewhere
+        assert not np.array_equal(outs[level][0].view(np.int64), outs[0][0].view(np.int64)), level
+
+
+def test_fp64_faithful_split_handles_zeros_subnormals_and_wide_ranges(lbm):
+    """The faithful path hands subnormal, infinite or NaN results back to the FP64 pipe and
+    handles exact zeros and operands 1e300 apart: finite where level 0 is finite, within FP64
+    accuracy of level 0 over the whole field and over the band of tiny values."""
+    nx, ny = 96, 40
+    rng = np.random.default_rng(6)
+    f = rng.standard_normal((4, 5, ny, nx))
+    pick = rng.integers(0, 6, size=f.shape)
+    f[pick == 0] = 0.0
+    f[pick == 1] = -0.0
+    f[pick == 2] *= 1e-310
+    f[pick == 3] *= 1e-300
+    f[pick == 4] *= 1e300
+    f[:, :, :, :8] = 0.0
+    outs = _split_runs(lbm, nx, ny, f, None, 5, [0, 8, 9, 10, 11])
+    def rel(a, b):                      # relative L2, scaled first (values near 1e300 would overflow)
+        sc = np.max(np.abs(b))
+        return np.linalg.norm((a - b) / sc) / np.linalg.norm(b / sc)
+
+    ref = outs[0][0]
+    tiny = (np.abs(ref) < 1e-250) & (ref != 0.0)
+    for level in (8, 9, 10, 11):
+        got = outs[level][0]
+        assert np.array_equal(np.isfinite(got), np.isfinite(ref)), level
+        assert rel(got, ref) <= 1e-14, (level, rel(got, ref))
+        if tiny.any():
+            assert rel(got[tiny], ref[tiny]) <= 1e-12, (level, rel(got[tiny], ref[tiny]))
 
 
 @pytest.mark.parametrize("dirichlet", [False, True])
