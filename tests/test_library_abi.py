@@ -56,3 +56,44 @@ def test_create_rejects_sizes_beyond_the_limits(lib):
     with pytest.raises(lib.LbmError) as e:
         lib.lbm_create(8, 8, 0.1, 0.01, 1.0, -0.1)           # negative shear speed
     assert e.value.status == lib.LBM_ERR_ARG
+
+
+def test_nn_host_side_validation_and_counters(lib):
+    """Surrogate-layer calls reject invalid arguments before any CUDA call, and the launch
+    counters are host values (four of them, none negative)."""
+    import ctypes
+    from paper_2408_01081_gb300 import nn as K
+    counts = K.conv_counts()
+    assert len(counts) == 4 and all(c >= 0 for c in counts)
+    so = K._lib()
+    assert so.lbm_nn_conv_counts(None) == lib.LBM_ERR_ARG
+    fake = ctypes.c_void_p(16)            # never dereferenced: validation fails first
+    # forward: unknown flag bit, channel counts off the 32 grid, a missing second output
+    assert so.lbm_nn_conv_forward(fake, 32, None, 0, fake, None, fake, 32, None, 32, 1, 16, 16, 3, 64,
+                                  None) == lib.LBM_ERR_ARG
+    assert so.lbm_nn_conv_forward(fake, 48, None, 0, fake, None, fake, 32, None, 32, 1, 16, 16, 3, 0,
+                                  None) == lib.LBM_ERR_ARG
+    assert so.lbm_nn_conv_forward(fake, 32, None, 0, fake, None, fake, 16, None, 32, 1, 16, 16, 3, 0,
+                                  None) == lib.LBM_ERR_ARG
+    assert so.lbm_nn_conv_forward(None, 32, None, 0, fake, None, fake, 32, None, 32, 1, 16, 16, 3, 0,
+                                  None) == lib.LBM_ERR_ARG
+    # weight gradient: forward-only flags, too small a workspace
+    ws = K.wgrad_workspace_bytes(32, 32, 1, 16, 16, 3)
+    assert ws > 0
+    assert so.lbm_nn_conv_backward_weight(fake, 32, fake, 32, None, 0, 1, 16, 16, 3, fake, K.ACT_BF16, fake, ws,
+                                          None) == lib.LBM_ERR_ARG
+    assert so.lbm_nn_conv_backward_weight(fake, 32, fake, 32, None, 0, 1, 16, 16, 3, fake, 0, fake, ws - 4,
+                                          None) == lib.LBM_ERR_ARG
+
+
+def test_wgrad_workspace_holds_whole_partials(lib):
+    """The weight-gradient workspace is a whole number of [Cout][KS*KS][Cin] FP32 partial
+    sums, grows with the pixel count up to a cap on the splits, and covers at least one
+    split for every size."""
+    from paper_2408_01081_gb300 import nn as K
+    for Cin, Cout, B, H, W, KS in [(32, 32, 16, 256, 256, 3), (96, 32, 16, 256, 256, 3), (384, 128, 16, 64, 64, 3),
+                                   (32, 48, 2, 32, 16, 3), (32, 32, 2, 8, 16, 3), (64, 32, 4, 64, 64, 1)]:
+        unit = Cout * KS * KS * Cin * 4
+        ws = K.wgrad_workspace_bytes(Cin, Cout, B, H, W, KS)
+        assert ws % unit == 0 and ws >= unit, (Cin, Cout, B, H, W, KS)
+        assert ws // unit <= 4 * 152 + B * H * W // 1024 + 1
