@@ -291,27 +291,36 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_tc_kernel(ConvTcArgs a, TcC
 
     if (warp < kProducerWarps) {
         // ---- activations: FP32 chunk g + rawd copied while chunk g is converted ----
+        // pixel indices of this thread's halo elements in the block being copied, the same for
+        // every channel chunk of the block: full resolution, and halved for an x1 stored at half size
+        int cached_t = -1;
+        uint32_t pix_full[S::NQ], pix_half[S::NQ];
         auto issue_raw = [&](int g) {
             const int t = g / nchunk, ci0 = (g - t * nchunk) * 16;
-            int n, ty0, tx0;
-            tile_of(t, n, ty0, tx0);
+            if (t != cached_t) {
+                int n, ty0, tx0;
+                tile_of(t, n, ty0, tx0);
+#pragma unroll
+                for (int i = 0; i < S::NQ; ++i) {
+                    const int hp = (tid + kProducers * i) >> 2;
+                    const int hy = hp / S::HWD, hx = hp - hy * S::HWD;
+                    const int sy = (ty0 + hy - 1) & (a.H - 1), sx = (tx0 + hx - 1) & (a.W - 1);
+                    pix_full[i] = ((uint32_t)n * (uint32_t)a.H + (uint32_t)sy) * (uint32_t)a.W + (uint32_t)sx;
+                    pix_half[i] = ((uint32_t)n * (uint32_t)(a.H >> 1) + (uint32_t)(sy >> 1)) * (uint32_t)(a.W >> 1) +
+                                  (uint32_t)(sx >> 1);
+                }
+                cached_t = t;
+            }
             const bool from1 = ci0 < a.C1;
-            const float* base = from1 ? a.x1 : a.x2;
-            const int cstride = from1 ? a.C1 : a.C2;
-            const int coff = from1 ? ci0 : ci0 - a.C1;
-            const int half = (from1 && a.x1_half) ? 1 : 0;     // nearest upsampling of a half-size x1
-            const int hs = a.H >> half, ws = a.W >> half;
+            const float* base = from1 ? a.x1 + ci0 : a.x2 + (ci0 - a.C1);
+            const size_t cstride = (size_t)(from1 ? a.C1 : a.C2);
+            const bool half = from1 && a.x1_half;          // nearest upsampling of a half-size x1
             const uint32_t dst = smem_addr(raw + (g % rawd) * S::RAW_BYTES);
 #pragma unroll
             for (int i = 0; i < S::NQ; ++i) {
                 const int q = tid + kProducers * i;
-                if (q < S::HP * 4) {
-                    const int hp = q >> 2, c4 = q & 3;
-                    const int hy = hp / S::HWD, hx = hp - hy * S::HWD;
-                    const int sy = (ty0 + hy - 1) & (a.H - 1), sx = (tx0 + hx - 1) & (a.W - 1);
-                    const long long spix = ((long long)n * hs + (sy >> half)) * ws + (sx >> half);
-                    cp_async16(dst + q * 16, base + spix * cstride + coff + c4 * 4);
-                }
+                if (q < S::HP * 4)
+                    cp_async16(dst + q * 16, base + (size_t)(half ? pix_half[i] : pix_full[i]) * cstride + (q & 3) * 4);
             }
         };
         for (int d = 0; d < rawd; ++d) {
