@@ -570,6 +570,10 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
     A.nwall = ctx->nwall;
     A.omega = ctx->omega;
     A.neq_scale = ctx->neq_scale;
+    A.af = (float)ctx->a;
+    A.bf = (float)ctx->b;
+    A.scale_f = (float)ctx->neq_scale;
+    A.inv_scale_f = (float)(1.0 / ctx->neq_scale);
     const int variant = (ctx->p.bc == LBM_DIRICHLET ? lbmh::STEP_DIRICHLET : 0) |
                         (ctx->R > 0 ? lbmh::STEP_FORCING : 0) | (ctx->w ? lbmh::STEP_TRACK : 0) |
                         (ctx->omega != 2.0 ? lbmh::STEP_OMEGA : 0) |

@@ -118,6 +118,10 @@ struct StepArgs {
     int nwall;
     double omega;          // relaxation rate when the kernel is built for omega != 2
     double neq_scale;      // moment-space storage: scale of the stored deviations
+    // FP32 copies for the FP32-arithmetic formats, converted once on the host (a conversion
+    // from FP64 runs on the FP64 pipe, two per clock per SM)
+    float af, bf;          // a, b
+    float scale_f, inv_scale_f;   // neq_scale and its reciprocal (exact: a power of two)
 };
 
 // ---------------------------------------------------------------------------
@@ -361,7 +365,14 @@ step_kernel(StepArgs A)
         }
     }
 
-    const M a = M(A.a), b = M(A.b);
+    M a, b;
+    if constexpr (sizeof(M) == 4) {
+        a = A.af;
+        b = A.bf;
+    } else {
+        a = A.a;
+        b = A.b;
+    }
     M out[4][5][V];
     double wv[2][V];
     double bxs[V], bys[V];

@@ -150,7 +150,7 @@ __device__ __forceinline__ void ms_moments(const float (&o)[4][5], float a, floa
 // fused pull-collide step on the moment-space state (same structure as step_kernel)
 // ---------------------------------------------------------------------------
 template <int K, int V, bool DIRICHLET, bool FORCING, bool TRACK, bool OMEGA>
-__global__ void __launch_bounds__(256) ms_step_kernel(StepArgs A)
+__global__ void __launch_bounds__(256, 2) ms_step_kernel(StepArgs A)
 {
     constexpr int H = Ms<K>::H;
     using E16 = typename Fmt<H>::E;
@@ -162,9 +162,9 @@ __global__ void __launch_bounds__(256) ms_step_kernel(StepArgs A)
     const int nx = A.nx, ny = A.ny;
     const long long plane = A.plane;
     const int lane = threadIdx.x & 31;
-    const float fa = (float)A.a, fb = (float)A.b;
-    // the scale is a power of two: its FP32 reciprocal is exact (no FP64 division in the kernel)
-    const float sc = (float)A.neq_scale, inv_s = 1.0f / sc;
+    const float fa = A.af, fb = A.bf;
+    // the scale is a power of two, its FP32 reciprocal exact; both converted on the host
+    const float sc = A.scale_f, inv_s = A.inv_scale_f;
     const bool bot = DIRICHLET && (y == 0);
     const bool top = DIRICHLET && (y == ny - 1);
     const int ym = (y == 0) ? ny - 1 : y - 1;
