@@ -591,6 +591,8 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
         T.plane = ctx->plane;
         T.a = ctx->a;
         T.b = ctx->b;
+        T.af = (float)ctx->a;
+        T.bf = (float)ctx->b;
         T.rows = ctx->tb_rows;
         const int nstrip = (ctx->p.nx + lbmk::TB_OUT - 1) / lbmk::TB_OUT;
         const dim3 tblock(128), tgrid((nstrip + 3) / 4, (ctx->p.ny + T.rows - 1) / T.rows);

@@ -25,6 +25,7 @@ struct TbArgs {
     int nx, ny, pitch;
     long long plane;
     double a, b;
+    float af, bf;         // a, b in FP32, converted on the host
     int rows;             // rows per block (gridDim.y blocks of rows)
 };
 
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(128, LBM_TB_MIN_BLOCKS) tb2_kernel(TbArgs A)
     const bool out_lane = (lane >= 1) && (lane <= TB_OUT) && inside;
     const int y0 = blockIdx.y * A.rows;
     const int y1 = min(ny, y0 + A.rows);
-    const float fa = (float)A.a, fb = (float)A.b;
+    const float fa = A.af, fb = A.bf;
     const float Dk[5] = {-1.f, -1.f, 1.f, 1.f, 1.f};
 
     float keep_py[5];          // S1(r-2), direction (0,1)
