@@ -1,35 +1,35 @@
 // 3x3 circular convolution of the surrogate as an implicit GEMM on the fifth-
 // generation tensor cores: tcgen05.mma (kind::f16, BF16 operands from shared
-// memory, FP32 accumulator in tensor memory), one thread issuing for the CTA.
+// memory, FP32 accumulator in tensor memory), issued by one elected lane of a warp.
 //
 // Tiling.  A CTA computes MT tiles of 128 output pixels (each 16 rows x 8 columns;
 // the MT tiles side by side) for BN output channels: the accumulator
 // D[pixel][co] of tile j sits in tensor-memory lanes 0..127 (lane = pixel) and
-// columns j BN .. j BN + BN - 1.  The input block with its one-pixel halo
-// ((16 + 2) x (8 MT + 2) pixels) is staged per 16-channel chunk as two planes of
-// 8 channels, one 16-byte row per pixel: the K-major operand layout without
-// swizzle, whose 8-row core matrices are then 8 consecutive pixels of one image
-// row.  A stencil tap (dy, dx) is a descriptor into that same block, started dy
-// halo rows and dx pixels further on, with the stride between 8-row groups (SBO)
-// = one halo row and between the two K halves (LBO) = one plane; no im2col copy
-// is made.  The weights of the chunk's nine taps are copied (cp.async) into the
-// same layout with output channels as rows.
+// columns j BN .. j BN + BN - 1 (two such accumulators, alternating between output
+// blocks).  The input block with its one-pixel halo ((16 + 2) x (8 MT + 2) pixels)
+// is staged per 16-channel chunk as two planes of 8 channels, one 16-byte row per
+// pixel: the K-major operand layout without swizzle, whose 8-row core matrices are
+// then 8 consecutive pixels of one image row.  A stencil tap (dy, dx) is a
+// descriptor into that same block, started dy halo rows and dx pixels further on,
+// with the stride between 8-row groups (SBO) = one halo row and between the two K
+// halves (LBO) = one plane; no im2col copy is made.  The weights of a chunk's nine
+// taps are copied (cp.async) into the same layout with output channels as rows;
+// they stay resident for the whole kernel when all chunks fit in shared memory.
 //
 // Precision is that of the mma.sync kernels: activations split into BF16 hi + lo
 // (two MMAs per tap; one with act_bf16), BF16 weights, FP32 accumulation.
 //
-// Pipeline.  `stages` buffers.  All 256 threads stage chunk c (FP32 loads, BF16
-// split, shared stores; weights by cp.async) while the tensor core works on the
-// previous chunks; after a proxy fence and a barrier one thread issues the
-// chunk's 9 MT (hi/lo) MMAs and commits them to the buffer's mbarrier, which the
-// threads wait on before they refill that buffer.  Epilogue: warp w reads lanes
-// 32 (w % 4) .. of the accumulator (tcgen05.ld), adds the bias, applies ReLU and
-// stores FP32 (or adds into the destination).
+// Pipeline (conv3_tc_kernel below): persistent CTAs, one per SM, with warp roles.
+// Producer warps copy the FP32 chunks a few steps ahead with cp.async and convert
+// them into the BF16 operand buffers; one warp issues the MMAs; four warps read the
+// accumulators (tcgen05.ld), add the bias, apply ReLU and store FP32 (or add into
+// the destination); one warp streams the weights when they are not resident.  The
+// roles hand buffers and accumulators to each other through mbarriers.
 //
 // Every wait is bounded (about two seconds of SM clock).  A wait that runs out
-// sets a device flag (read by conv3_tc_take_timeout); the CTA then stops issuing,
-// waits (bounded) for the MMAs it has in flight, frees its tensor memory and
-// returns.
+// sets a device flag (read by conv3_tc_take_timeout) and makes every role leave its
+// loop; the MMA warp waits (bounded) for the MMAs it has in flight, and the CTA
+// frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -173,7 +173,7 @@ struct TcShape {
 // warp roles
 constexpr int kProducerWarps = 8;       // warps 0-7: activations (cp.async FP32 -> BF16 hi / lo)
 constexpr int kEpilogueWarp0 = 8;       // warps 8-11: accumulator -> global (TMEM lanes 32 (w % 4) ..)
-constexpr int kMmaWarp = 12;            // warp 12: tensor-memory allocation; lane 0 issues the MMAs
+constexpr int kMmaWarp = 12;            // warp 12: tensor-memory allocation; the MMA loop (elected lane issues)
 constexpr int kWeightWarp = 13;         // warp 13: weights per chunk when they are not resident
 constexpr int kThreads = 14 * 32;
 constexpr int kProducers = kProducerWarps * 32;
@@ -215,10 +215,11 @@ __device__ __forceinline__ void cp_async_wait_upto(int n)   // at most n of this
 
 // Persistent, warp-specialised.  CTA b takes the output blocks b, b + gridDim.x, ...
 // (output channels of blockIdx.y) and walks their 16-channel chunks as one sequence
-// g = 0 .. G-1.  Barriers: full[s] (operands of the chunk in buffer s staged: every
-// producer thread, and the weight warp when weights stream), empty[s] (the MMAs that
+// g = 0 .. G-1.  Barriers: full[s] (operands of the chunk in buffer s staged: one
+// arrival per producer warp, and one from the weight warp when weights stream), empty[s] (the MMAs that
 // read buffer s completed: tcgen05.commit), acc_full[b] (the MMAs of the block in
-// accumulator b completed), acc_empty[b] (the epilogue has read accumulator b).
+// accumulator b completed), acc_empty[b] (the epilogue warps have read accumulator b:
+// one arrival per warp).
 // Shared memory: [BF16 operand buffers][FP32 chunk ring][weights].
 template <int BN, int MT, bool LO>
 __global__ void __launch_bounds__(kThreads, 1) conv3_tc_kernel(ConvTcArgs a, TcConf cf)
