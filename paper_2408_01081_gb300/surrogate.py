@@ -456,6 +456,14 @@ class FallbackDriver:
             bsz = min(16, n - i0)
             self.sur.predict(U[i0], stride, nu_norm[i0:], bsz, H, W, pred[i0], stride)
         self.jumps += 1
+        try:
+            K.check()                   # a convolution whose bounded wait ran out left invalid output
+        except L.LbmError as e:
+            if e.status != L.LBM_ERR_TIMEOUT:
+                raise
+            ref = relift_and_step(U, nu, self.sur.k, self.storage)
+            self.fallbacks += n
+            return ref, None
         errs = None
         if self.check_every and self.jumps % self.check_every == 0:
             ref = relift_and_step(U, nu, self.sur.k, self.storage)

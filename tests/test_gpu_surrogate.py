@@ -51,3 +51,28 @@ def test_jump_costs_less_than_the_fp64_solver_at_the_workload_size(lbm):
     tm = S.timing(sur, n=16, H=256, W=256, reps=5)
     assert tm["gain_bf16_act_vs_f64"] > 1.2, tm
     assert tm["gain_vs_f64"] > 1.0, tm
+
+
+def test_fallback_driver_takes_the_solver_after_a_convolution_timeout(lbm, monkeypatch):
+    """A convolution whose bounded wait ran out reports LBM_ERR_TIMEOUT through lbm_nn_check
+    (its output is invalid): the driver then returns the solver's jump for every lattice.
+    The timeout is injected on the host (a fake check), no GPU wait is made to run out."""
+    import torch
+    from paper_2408_01081_gb300 import lbm as L
+    from paper_2408_01081_gb300 import nn as K
+    from paper_2408_01081_gb300 import surrogate as S
+    H = W = 32
+    net = S.UNet((32, 32, 32, 32), seed=1)
+    sur = S.Surrogate(net, np.ones(S.NF), 8)
+    chunk = S.generate_chunk(8, 123, H=H, W=W, k=8, J=1, ell_range=(4.0, 8.0))
+    U = chunk.U[0, :8].contiguous()
+
+    def timed_out():
+        raise L.LbmError(L.LBM_ERR_TIMEOUT, "lbm_nn_check failed")
+
+    monkeypatch.setattr(K, "check", timed_out)
+    drv = S.FallbackDriver(sur, tol=10.0, check_every=1)
+    out, errs = drv.jump(U, chunk.nu[:8])
+    assert errs is None and drv.fallbacks == 8
+    ref = S.relift_and_step(U, chunk.nu[:8], 8)
+    torch.testing.assert_close(out, ref, rtol=0, atol=0)
