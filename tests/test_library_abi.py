@@ -97,3 +97,26 @@ def test_wgrad_workspace_holds_whole_partials(lib):
         ws = K.wgrad_workspace_bytes(Cin, Cout, B, H, W, KS)
         assert ws % unit == 0 and ws >= unit, (Cin, Cout, B, H, W, KS)
         assert ws // unit <= 4 * 152 + B * H * W // 1024 + 1
+
+
+def test_binding_constants_match_the_headers(lib):
+    """Every enumerator of include/*.h that the Python bindings mirror has the same value there
+    (status codes, boundary and storage kinds, convolution flags)."""
+    from paper_2408_01081_gb300 import nn as K
+    values = {}
+    for fn in ("lbm.h", "lbm_nn.h"):
+        src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", fn)).read(), flags=re.S)
+        for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+            for name, val in re.findall(r"(LBM_\w+)\s*=\s*(\d+)", body):
+                values[name] = int(val)
+    assert len(values) >= 20, values
+    checked = 0
+    for name, v in values.items():
+        if hasattr(lib, name):
+            assert getattr(lib, name) == v, name
+            checked += 1
+        short = name[len("LBM_NN_"):] if name.startswith("LBM_NN_") else None
+        if short and hasattr(K, short):
+            assert getattr(K, short) == v, name
+            checked += 1
+    assert checked >= len(values) - 1, (checked, sorted(values))
