@@ -119,4 +119,4 @@ def test_binding_constants_match_the_headers(lib):
         if short and hasattr(K, short):
             assert getattr(K, short) == v, name
             checked += 1
-    assert checked >= len(values) - 1, (checked, sorted(values))
+    assert checked == len(values), (checked, sorted(values))
