@@ -485,6 +485,8 @@ struct VariantInfo {
     int regs_per_cta;   // registers allocated to one CTA (per-warp granularity of 256)
     int static_smem;
 };
+// filled on the first launch of a variant on a device; first launches racing from several host
+// threads write the same values
 VariantInfo g_var[kMaxDevices][12];
 int g_sms[kMaxDevices], g_smem_sm[kMaxDevices], g_smem_reserved[kMaxDevices];
 
