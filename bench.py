@@ -43,8 +43,6 @@ FP64_OPS_PER_NODE = 47                                                # DADD/DFM
 SPLIT_LEVEL = 1               # lbm_set_fp64_split default: the 15 sums of a node on the integer pipe
 SPLIT_INTEGER_ADDS = 15
 FUSED = {"f32"}      # formats the library advances two steps per pass by default (lbm_set_step_fusion)
-# DRAM bytes per node of one step launch from an ncu capture (profiles/step_kernel_*.md), valid only
-# for the kernel sources with this digest; any change to them reports traffic as null until re-captured
 # DRAM bytes per node and launch (dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of
 # 4096x2048, scaled by the node count); valid only while the kernel sources hash to "sha256".
 # "f32_fused" is one launch of the two-step kernel.

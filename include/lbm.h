@@ -180,7 +180,7 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, double* ustar, int32_t o
 lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, const double* ustar, int64_t m,
                                int32_t on_device);
 
-/* LBM_UNSTABLE if any stored population is NaN or infinite, else LBM_OK (waits). */
+/* LBM_ERR_UNSTABLE if any stored population is NaN or infinite, else LBM_OK (waits). */
 lbm_status lbm_check_finite(lbm_ctx* ctx);
 
 /* Current step counter m (t = m dt). */
@@ -284,6 +284,11 @@ const char* lbm_batch_last_error(const lbm_batch* b);
  *   out    : one double; device memory when out_on_device = 1 (written in stream
  *            order, no wait), else host memory (the call waits for the stream)
  *   stream : cudaStream_t to run on (NULL = legacy stream)
+ * The call works on the current device: f, and out when out_on_device = 1, must be
+ * device memory of that device (or managed memory), else LBM_ERR_ARG.  The size of
+ * the buffer behind f cannot be checked here: it must hold 20 * nx * ny doubles.
+ * With out_on_device = 0 the call waits for the stream; on a stream that is being
+ * captured that wait is not allowed, and such a call returns LBM_ERR_ARG.
  * Scratch: a static 128 KB array (16384 + 32 doubles) in the library's device
  * image, held by every GPU that loads the library until the process exits.  The
  * first call on each device looks up its device address (cudaGetSymbolAddress)

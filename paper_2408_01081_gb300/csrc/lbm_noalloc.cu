@@ -164,6 +164,31 @@ extern "C" lbm_status lbm_energy_noalloc(const double* f, int32_t nx, int32_t ny
         lbmh::set_thread_error("lbm_energy_noalloc: no usable current device");
         return LBM_ERR_CUDA;
     }
+    // the scratch address and the launch belong to the current device: f (and a device
+    // result) must be device memory of that device (or managed memory)
+    for (int i = 0; i < (out_on_device ? 2 : 1); ++i) {
+        cudaPointerAttributes at{};
+        const cudaError_t e = cudaPointerGetAttributes(&at, i == 0 ? static_cast<const void*>(f)
+                                                                   : static_cast<const void*>(out));
+        const bool here = (at.type == cudaMemoryTypeDevice && at.device == dev) || at.type == cudaMemoryTypeManaged;
+        if (e != cudaSuccess || !here) {
+            cudaGetLastError();   // a failed query leaves no sticky error behind
+            lbmh::set_thread_error(i == 0 ? "lbm_energy_noalloc: f is not device memory of the current device"
+                                          : "lbm_energy_noalloc: out is not device memory of the current device");
+            return LBM_ERR_ARG;
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!out_on_device) {
+        // a host result needs a wait for the stream, which a capturing stream does not allow
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            lbmh::set_thread_error("lbm_energy_noalloc: out_on_device = 0 waits for the stream, which is not "
+                                   "allowed while the stream is being captured");
+            return LBM_ERR_ARG;
+        }
+    }
     double* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
@@ -179,7 +204,6 @@ extern "C" lbm_status lbm_energy_noalloc(const double* f, int32_t nx, int32_t ny
         }
         scratch = g_scratch_addr[dev];
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     int blocks = ny < 152 * 8 ? ny : 152 * 8;
     noalloc_rows_kernel<<<blocks, 256, 0, s>>>(f, nx, ny, K, scratch);
     double* dst = out_on_device ? out : scratch + kNoAllocMaxRows;

@@ -291,21 +291,34 @@ def lbm_energy_noalloc(f, nx, ny, dx, dt, cK, cmu, out=None, stream=None) -> flo
     """||f||_P^2 of device populations f [4, 5, ny, nx] without any device allocation.
 
     ``out``: optional 1-element float64 CUDA tensor to receive the result on the
-    device (no wait); otherwise the value is returned through host memory."""
+    device (no wait); otherwise the value is returned through host memory.
+
+    The C call takes nx and ny apart from the pointer and cannot see how large the
+    buffer is, so the shape of ``f`` is checked here against (4, 5, ny, nx) before
+    anything reaches the library: a short buffer would otherwise be read past its end.
+    The call runs with the device that holds ``f`` current."""
+    nx, ny = int(nx), int(ny)
+    shape = tuple(getattr(f, "shape", ()))
+    if shape != (4, 5, ny, nx):
+        raise ValueError(f"f must have shape (4, 5, ny, nx) = (4, 5, {ny}, {nx}), got {shape}")
+    if out is not None and (getattr(out, "numel", lambda: 0)() < 1):
+        raise ValueError("out must hold at least one element")
     if not _is_torch_cuda(f):
         raise TypeError("f must be a CUDA tensor (device memory)")
     p, _, _keep = _arr(f, "f")
-    if out is not None:
-        po, on, _k2 = _arr(out, "out")
-        if on != 1:
-            raise TypeError("out must be a CUDA tensor")
-        _check(None, load().lbm_energy_noalloc(p, int(nx), int(ny), float(dx), float(dt), float(cK), float(cmu),
-                                               po, 1, ctypes.c_void_p(stream or 0)))
-        return None
-    v = ctypes.c_double()
-    _check(None, load().lbm_energy_noalloc(p, int(nx), int(ny), float(dx), float(dt), float(cK), float(cmu),
-                                           ctypes.cast(ctypes.byref(v), ctypes.c_void_p), 0,
-                                           ctypes.c_void_p(stream or 0)))
+    import torch
+    with torch.cuda.device(f.device):
+        if out is not None:
+            po, on, _k2 = _arr(out, "out")
+            if on != 1 or out.device != f.device:
+                raise TypeError("out must be a CUDA tensor on the device of f")
+            _check(None, load().lbm_energy_noalloc(p, nx, ny, float(dx), float(dt), float(cK), float(cmu),
+                                                   po, 1, ctypes.c_void_p(stream or 0)))
+            return None
+        v = ctypes.c_double()
+        _check(None, load().lbm_energy_noalloc(p, nx, ny, float(dx), float(dt), float(cK), float(cmu),
+                                               ctypes.cast(ctypes.byref(v), ctypes.c_void_p), 0,
+                                               ctypes.c_void_p(stream or 0)))
     return float(v.value)
 
 

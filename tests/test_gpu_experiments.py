@@ -14,7 +14,11 @@ def test_dirichlet_convergence_fp64(lbm, nu):
     res = X.dirichlet_convergence((32, 64, 128, 256), nus=(nu,), log=None)[str(nu)]
     for o in res["order_u_L2"] + res["order_u_Linf"]:
         assert 1.75 < o < 2.4, res
-    assert res["order_sigma_L2"][-1] > 1.6, res
+    # an O(dx) error in a boundary layer a few cells wide bounds the L2 order of sigma at 1.5
+    # asymptotically (the interior converges at second order); Sec. 6.1's second order is the
+    # pre-asymptotic range
+    for o in res["order_sigma_L2"]:
+        assert o > 1.45, res
 
 
 def test_dirichlet_separable_wall_tables_match_dense(lbm):

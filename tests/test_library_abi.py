@@ -120,3 +120,19 @@ def test_binding_constants_match_the_headers(lib):
             assert getattr(K, short) == v, name
             checked += 1
     assert checked == len(values), (checked, sorted(values))
+
+
+def test_noalloc_binding_checks_the_shape_before_any_call(lib):
+    """lbm_energy_noalloc takes nx, ny apart from the buffer; the binding refuses a
+    buffer whose shape is not (4, 5, ny, nx) before the C call (so before any launch)."""
+    import torch
+    short = torch.zeros((4, 5, 3, 8), dtype=torch.float64)          # ny = 3 rows, 96 asked for
+    with pytest.raises(ValueError):
+        lib.lbm_energy_noalloc(short, 8, 96, 0.1, 0.01, 1.0, 0.5)
+    with pytest.raises(ValueError):
+        lib.lbm_energy_noalloc(torch.zeros(20 * 8 * 96, dtype=torch.float64), 8, 96, 0.1, 0.01, 1.0, 0.5)
+    good = torch.zeros((4, 5, 96, 8), dtype=torch.float64)
+    with pytest.raises(ValueError):
+        lib.lbm_energy_noalloc(good, 8, 96, 0.1, 0.01, 1.0, 0.5, out=torch.zeros(0, dtype=torch.float64))
+    with pytest.raises(TypeError):                                  # right shape, but host memory
+        lib.lbm_energy_noalloc(good, 8, 96, 0.1, 0.01, 1.0, 0.5)
