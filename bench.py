@@ -51,6 +51,13 @@ TRAFFIC_CAPTURE = {"sha256": "22ff8278f564022134e687af31699f9b283682cba10a995608
                                       "ms_f16": 94.48}}
 KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_01081_gb300/csrc/lbm_kind.cu",
                   "paper_2408_01081_gb300/csrc/lbm_tb.cuh", "paper_2408_01081_gb300/csrc/lbm_ms.cuh"]
+# Pipe instruction counts of the default FP64 step kernel per node (thread instructions:
+# 32 x smsp__inst_executed_pipe_{alu,fp64,fma}.sum / nodes from one ncu capture of 4096x2048),
+# valid only while the kernel sources hash to "sha256".  Each SM issues 64 ALU-pipe and 2
+# FP64-pipe thread instructions per clock, so one node needs at least
+# max(alu / 64, fp64 / 2) SM clocks: the arithmetic roof of this kernel.
+PIPE_CAPTURE = {"sha256": None, "alu_per_node": None, "fp64_per_node": None, "fma_per_node": None}
+ALU_LANES_PER_SM, FP64_LANES_PER_SM, N_SM = 64, 2, 152
 
 
 def kernel_digest():
@@ -59,6 +66,13 @@ def kernel_digest():
     for rel in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, rel), "rb").read())
     return h.hexdigest()
+
+
+def pipe_counts():
+    """(alu, fp64, fma) thread instructions per node of the FP64 step kernel, or None."""
+    if PIPE_CAPTURE["sha256"] is None or PIPE_CAPTURE["sha256"] != kernel_digest():
+        return None
+    return PIPE_CAPTURE["alu_per_node"], PIPE_CAPTURE["fp64_per_node"], PIPE_CAPTURE["fma_per_node"]
 
 
 def traffic_per_launch(fmt, nodes):
@@ -388,6 +402,20 @@ def run_ours(args):
         results[s]["speedup_vs_f64"] = results[s]["mlups"] / results["f64"]["mlups"]
     del finals
 
+    # untimed: every storage format against the FP64 run over the workload's 5000 steps, errors
+    # of every moment field at each checkpoint (the precision configuration of the workload set)
+    precision = None
+    if args.precision_steps > 0 and len(args.formats) > 1:
+        from paper_2408_01081_gb300 import experiments as X
+        del U0, Ux, Uy
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        precision = X.precision_errors(n=nx, steps=args.precision_steps, every=args.precision_every,
+                                       formats=tuple(s for s in args.formats if s != "f64"), ell=ELL, std=STD,
+                                       cK2=CK2, cmu2=CMU2, cfl=CFL, wl=wl if nx == ny else None)
+        precision["wall_s"] = round(time.perf_counter() - t0, 1)
+        torch.cuda.empty_cache()
+
     batch = None
     if not args.no_batch:
         batch = run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws)
@@ -437,11 +465,33 @@ def run_ours(args):
     fp64_peak = 152 * 2 * sm_mhz * 1e6 / 1e9
     fp64_ach = FP64_OPS_PER_NODE * nodes_per_s / 1e9
     fp64_pipe_ops = FP64_OPS_PER_NODE - SPLIT_INTEGER_ADDS
-    roofline = {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(hbm_ach / hbm_peak, 4),
-                "traffic": args.traffic if args.traffic is not None else traffic_per_launch("f64", n_nodes),
+    hbm_part = {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(hbm_ach / hbm_peak, 4), "bytes_per_node": BYTES_PER_NODE["f64"],
+                "peak_source": peak_src}
+    pc = pipe_counts()
+    if pc is not None:
+        # arithmetic roof: SM clocks per node = max(ALU-pipe / 64, FP64-pipe / 2) thread instructions
+        alu_pn, fp64_pn, fma_pn = pc
+        alu_bound = alu_pn / ALU_LANES_PER_SM >= fp64_pn / FP64_LANES_PER_SM
+        inst_pn, lanes = (alu_pn, ALU_LANES_PER_SM) if alu_bound else (fp64_pn, FP64_LANES_PER_SM)
+        clk_pn = inst_pn / lanes
+        node_peak = N_SM * sm_mhz * 1e6 / clk_pn
+        roofline = {"bound": "alu", "achieved": round(inst_pn * nodes_per_s / 1e9, 1),
+                    "peak": round(N_SM * lanes * sm_mhz * 1e6 / 1e9, 1),
+                    "unit": "G ALU-pipe inst/s" if alu_bound else "G FP64-pipe inst/s",
+                    "frac": round(nodes_per_s / node_peak, 4),
+                    "model": {"alu_inst_per_node": alu_pn, "fp64_inst_per_node": fp64_pn, "fma_inst_per_node": fma_pn,
+                              "sm_clocks_per_node": round(clk_pn, 3),
+                              "node_rate_peak_G_per_s": round(node_peak / 1e9, 3),
+                              "node_rate_achieved_G_per_s": round(nodes_per_s / 1e9, 3),
+                              "hbm_node_rate_peak_G_per_s": round(hbm_peak * 1e9 / BYTES_PER_NODE["f64"] / 1e9, 3),
+                              "source": "ncu pipe instruction counts of this kernel x 152 SMs x median SM clock "
+                                        "sampled in the timed region"},
+                    "hbm": hbm_part}
+    else:
+        roofline = dict(hbm_part)
+    roofline.update({"traffic": args.traffic if args.traffic is not None else traffic_per_launch("f64", n_nodes),
                 "kernel": f"lbmk::step_kernel<F64,1,periodic,split level {SPLIT_LEVEL}>",
-                "bytes_per_node": BYTES_PER_NODE["f64"], "peak_source": peak_src,
                 "compute": {"limiter": "FP64 pipe and integer ALU pipe together (exact binary64 additions "
                                        "moved to the integer pipe); below the HBM roof",
                             "fp64_pipe_ops_per_node": fp64_pipe_ops,
@@ -451,7 +501,7 @@ def run_ours(args):
                             "fp64_pipe_frac": round(fp64_pipe_ops * nodes_per_s / 1e9 / fp64_peak, 4),
                             "fp64_pipe_peak_source": "152 SMs x 2 FP64 ops/clk x median SM clock sampled in the "
                                                      "timed region",
-                            "fp64_pipe_only": results.get("f64_pipe_only")}}
+                            "fp64_pipe_only": results.get("f64_pipe_only")}})
     mixed = {}
     for s in args.formats:
         if s == "f64":
@@ -466,8 +516,15 @@ def run_ours(args):
                     "hbm": {"achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                             "frac": round(ach / hbm_peak, 4), "bytes_per_node_step": bpn,
                             "traffic": traffic_per_launch(s if r["steps_per_pass"] == 1 else s + "_fused", n_nodes)},
-                    "rel_l2_vs_f64": {k: float(f"{v:.3e}") for k, v in r["rel_l2_vs_f64"].items()},
-                    "error_at_step": args.warmup + args.steps}
+                    "rel_l2_vs_f64_after_timed_run": {k: float(f"{v:.3e}") for k, v in r["rel_l2_vs_f64"].items()},
+                    "timed_run_error_at_step": args.warmup + args.steps}
+        if precision is not None and s in precision["formats"]:
+            by_step = precision["formats"][s]["rel_l2_vs_f64"]
+            mixed[s]["rel_l2_vs_f64"] = {str(cp): {k: float(f"{v:.3e}") for k, v in e.items()}
+                                         for cp, e in by_step.items()}
+            mixed[s]["max_rel_l2_vs_f64"] = {str(cp): float(f"{max(e.values()):.3e}") for cp, e in by_step.items()}
+            last = max(by_step)
+            mixed[s]["meets_1e-5_at_step"] = {str(last): bool(max(by_step[last].values()) <= 1e-5)}
     cpu = None
     if ws == 1 and not args.no_cpu:
         cx = cy = 1024
@@ -483,7 +540,12 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": f"inputs larger than L2: state {2 * 20 * n_nodes * 8 / 1e9:.1f} GB double-buffered"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-            "clocks": clocks, "mixed_precision": mixed, "batch": batch, "surrogate": surrogate}
+            "clocks": clocks, "mixed_precision": mixed, "batch": batch, "surrogate": surrogate,
+            "precision_run": None if precision is None else
+            {"workload": _workload_desc(nx, ny), "steps": precision["steps"], "checkpoints": precision["checkpoints"],
+             "reference": "FP64 GPU run of the same workload (tied to the oracle at <= 1e-12 by the parity tests)",
+             "mlups_untimed": {k: round(v["mlups"], 1) for k, v in precision["formats"].items()},
+             "wall_s": precision["wall_s"]}}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -506,6 +568,9 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-budget", type=float, default=60.0, help="surrogate training seconds")
     ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--precision-steps", type=int, default=5000,
+                    help="untimed run of every format against FP64 (0: skip)")
+    ap.add_argument("--precision-every", type=int, default=1000)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the step kernel from an ncu capture (null if unknown)")
     args = ap.parse_args()
