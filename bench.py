@@ -50,7 +50,8 @@ TRAFFIC_CAPTURE = {"sha256": "22ff8278f564022134e687af31699f9b283682cba10a995608
                    "bytes_per_node": {"f64": 317.16, "f32": 153.31, "f32_fused": 157.58, "bf16": 73.58, "f16": 73.55,
                                       "ms_f16": 94.48}}
 KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_01081_gb300/csrc/lbm_kind.cu",
-                  "paper_2408_01081_gb300/csrc/lbm_tb.cuh", "paper_2408_01081_gb300/csrc/lbm_ms.cuh"]
+                  "paper_2408_01081_gb300/csrc/lbm_tb.cuh", "paper_2408_01081_gb300/csrc/lbm_ms.cuh",
+                  "paper_2408_01081_gb300/csrc/lbm_tbt.cuh", "paper_2408_01081_gb300/csrc/lbm_tma.cuh"]
 # Pipe instruction counts of the default FP64 step kernel per node (thread instructions:
 # 32 x smsp__inst_executed_pipe_{alu,fp64,fma}.sum / nodes from one ncu capture of 4096x2048),
 # valid only while the kernel sources hash to "sha256".  Each SM issues 64 ALU-pipe and 2
@@ -340,6 +341,9 @@ def run_ours(args):
                           track_displacement=False, stream=stream.cuda_stream)
         if args.no_fusion:
             lat.set_step_fusion(1)
+        elif storage in args.fuse_formats:
+            lat.set_step_fusion(2, args.rows_per_block)
+        lat.set_staging(args.staging)
         lat.init(U0, Ux, Uy)
         lat.step(args.warmup)
         barrier()
@@ -362,7 +366,7 @@ def run_ours(args):
         del out
         lat.close()
         mlups_rank = n_nodes * args.steps / (ms * 1e-3) / 1e6
-        fused = storage in FUSED and not args.no_fusion
+        fused = (storage in FUSED or storage in args.fuse_formats) and not args.no_fusion
         results[storage] = {"ms_per_step": ms / args.steps, "mlups": mlups_rank * ws,
                             "steps_per_pass": 2 if fused else 1,
                             "launches": (args.steps // 2 + args.steps % 2) if fused else args.steps}
@@ -402,28 +406,6 @@ def run_ours(args):
         results[s]["speedup_vs_f64"] = results[s]["mlups"] / results["f64"]["mlups"]
     del finals
 
-    # untimed: every storage format against the FP64 run over the workload's 5000 steps, errors
-    # of every moment field at each checkpoint (the precision configuration of the workload set)
-    precision = None
-    if args.precision_steps > 0 and len(args.formats) > 1:
-        from paper_2408_01081_gb300 import experiments as X
-        del U0, Ux, Uy
-        torch.cuda.empty_cache()
-        t0 = time.perf_counter()
-        precision = X.precision_errors(n=nx, steps=args.precision_steps, every=args.precision_every,
-                                       formats=tuple(s for s in args.formats if s != "f64"), ell=ELL, std=STD,
-                                       cK2=CK2, cmu2=CMU2, cfl=CFL, wl=wl if nx == ny else None)
-        precision["wall_s"] = round(time.perf_counter() - t0, 1)
-        torch.cuda.empty_cache()
-
-    batch = None
-    if not args.no_batch:
-        batch = run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws)
-
-    surrogate = None
-    if not args.no_surrogate and rank == 0:
-        surrogate = run_surrogate(args)
-
     # end to end through the C ABI with host buffers: H2D of the initial data from pinned
     # memory, init, K steps, D2H of the ten output fields, all inside the timed region
     e2e = None
@@ -448,6 +430,28 @@ def run_ours(args):
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
                "wall_s": round(wall, 3)}
         del hU0, hUx, hUy, hout
+
+    # untimed: every storage format against the FP64 run over the workload's 5000 steps, errors
+    # of every moment field at each checkpoint (the precision configuration of the workload set)
+    precision = None
+    if args.precision_steps > 0 and len(args.formats) > 1:
+        from paper_2408_01081_gb300 import experiments as X
+        del U0, Ux, Uy
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        precision = X.precision_errors(n=nx, steps=args.precision_steps, every=args.precision_every,
+                                       formats=tuple(s for s in args.formats if s != "f64"), ell=ELL, std=STD,
+                                       cK2=CK2, cmu2=CMU2, cfl=CFL, wl=wl if nx == ny else None)
+        precision["wall_s"] = round(time.perf_counter() - t0, 1)
+        torch.cuda.empty_cache()
+
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws)
+
+    surrogate = None
+    if not args.no_surrogate and rank == 0:
+        surrogate = run_surrogate(args)
 
     if rank != 0:
         if dist is not None:
@@ -564,6 +568,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-fusion", action="store_true", help="one kernel per step for every format")
+    ap.add_argument("--fuse-formats", default="", help="formats advanced two steps per pass besides the default")
+    ap.add_argument("--staging", type=int, default=1, help="two-step kernel: 1 rows staged by tensor copies, 0 registers")
+    ap.add_argument("--rows-per-block", type=int, default=64)
     ap.add_argument("--batch-count", type=int, default=512, help="lattices in the batch leg")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-budget", type=float, default=60.0, help="surrogate training seconds")
@@ -575,6 +582,7 @@ def main():
                     help="DRAM bytes per launch of the step kernel from an ncu capture (null if unknown)")
     args = ap.parse_args()
     args.formats = [s for s in args.formats.split(",") if s]
+    args.fuse_formats = [s for s in args.fuse_formats.split(",") if s]
     if "f64" not in args.formats:
         args.formats.insert(0, "f64")
     if args.warmup < 3 and args.impl == "ours":

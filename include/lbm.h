@@ -88,13 +88,27 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const d
  * formats, where the fused kernel is not yet faster) lbm_step advances pairs of
  * steps with one kernel that keeps the intermediate state on chip (halving the
  * memory traffic per step) whenever the lattice stores FP32 / BF16 / FP16
- * populations, omega = 2, there is no body load and no displacement tracking,
- * and the boundary is periodic or homogeneous Dirichlet; otherwise, and for an
- * odd last step, one kernel per step runs.  FP32 results are bit-identical to
- * single steps; 16-bit results skip one rounding per pair and are more accurate.
+ * populations (or moment-space deviations, with staged rows: lbm_set_staging),
+ * omega = 2, there is no body load and no displacement tracking, and the
+ * boundary is periodic or homogeneous Dirichlet; otherwise, and for an odd last
+ * step, one kernel per step runs.  FP32 results are bit-identical to single
+ * steps; 16-bit and moment-space results skip one rounding per pair and are more
+ * accurate.
  * rows_per_block (default 64) sets the rows each thread block streams through.
  * steps_per_pass = 1 always uses one kernel per step. */
 lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t rows_per_block);
+
+/* How the two-step kernel of lbm_set_step_fusion reads its input (no counterpart in
+ * the paper; results are identical either way).  1 (the default): each block's
+ * input rows are copied into a ring of shared-memory stages by tensor copies
+ * (TMA) issued by one producer warp, as far ahead as the ring allows.  0: each
+ * thread prefetches the next row into registers.  A bounded wait of the staged
+ * kernel that runs out (about 2 s) makes the next lbm_synchronize return
+ * LBM_ERR_TIMEOUT.  Mode 2 is a test hook: staged, but the producer withholds one
+ * input row of every block, so that the compute warps' waits run out and the
+ * bounded-wait path is exercised (the state is then undefined).  Other modes
+ * return LBM_ERR_ARG. */
+lbm_status lbm_set_staging(lbm_ctx* ctx, int32_t mode);
 
 /* FP64 arithmetic split (LBM_F64 storage only; no counterpart in the paper, whose
  * scheme this does not change).  The FP64 step needs 35 additions and 12 fused
@@ -186,7 +200,8 @@ lbm_status lbm_check_finite(lbm_ctx* ctx);
 /* Current step counter m (t = m dt). */
 lbm_status lbm_time_step(const lbm_ctx* ctx, int64_t* m);
 
-/* Wait until all work enqueued by this context has finished. */
+/* Wait until all work enqueued by this context has finished; LBM_ERR_TIMEOUT if a
+ * bounded device-side wait of the staged two-step kernel ran out since the last call. */
 lbm_status lbm_synchronize(lbm_ctx* ctx);
 
 /* Release all device memory of the context; NULL is accepted. */
@@ -201,6 +216,51 @@ const char* lbm_last_error(const lbm_ctx* ctx);
 lbm_status lbm_state_bytes(const lbm_ctx* ctx, int64_t* nbytes);
 lbm_status lbm_save_state(lbm_ctx* ctx, void* dst, int32_t on_device);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t m, int32_t on_device);
+
+/* ------------------------------------------------------------------------
+ * Row slabs: one lattice split across devices or processes (no counterpart in
+ * the paper; the step itself is unchanged).  In the pull form of Eq. streaming
+ * the only values that cross a horizontal cut are the populations moving along
+ * y: a node of row y pulls f*_(0,1) from row y-1 and f*_(0,-1) from row y+1.
+ * A slab therefore keeps one halo row on each side that has a neighbour slab,
+ * and before every step receives 5 values per column from each neighbour:
+ *   lbm_halo_pack    writes f*_(0,-1) of its first row (for the slab below) and
+ *                    f*_(0,1) of its last row (for the slab above),
+ *   (the caller moves the messages: NCCL send/recv, a peer copy, ...)
+ *   lbm_halo_unpack  stores the neighbours' messages into the halo rows,
+ *   lbm_step(ctx, 1) advances the slab's own rows.
+ * A periodic lattice wraps: the slab holding row 0 has the slab holding row
+ * ny - 1 below it (a single periodic slab is its own neighbour on both sides).
+ * A Dirichlet lattice has no neighbour below row 0 or above row ny - 1.  The
+ * own rows of all slabs together follow exactly the trajectory of the whole
+ * lattice (same arithmetic per node).
+ * Restrictions: population formats (LBM_F64 / F32 / BF16 / F16), no body load,
+ * homogeneous Dirichlet data, one kernel per step (lbm_set_step_fusion is
+ * ignored).  Every other call works on the slab's own rows: field arrays of
+ * lbm_init, lbm_moments, lbm_error_sums, lbm_get/set_populations are
+ * [.][rows][nx], and lbm_energy sums the own rows (add the slabs' values for the
+ * whole lattice).
+ * ------------------------------------------------------------------------ */
+
+/* Rows [y_begin, y_begin + rows) of the lattice described by p (p->ny = the
+ * whole lattice's rows), 1 <= rows, 0 <= y_begin, y_begin + rows <= p->ny.  As
+ * lbm_create otherwise (the halo rows add at most 2 rows of device memory). */
+lbm_status lbm_create_slab(const lbm_params* p, int32_t y_begin, int32_t rows, lbm_ctx** out);
+
+/* Bytes of one halo message: 5 * nx elements of the storage type, [5][nx]
+ * (components of U, x fastest); 0 for a context that is not a slab. */
+lbm_status lbm_halo_bytes(const lbm_ctx* ctx, int64_t* nbytes);
+
+/* Write the messages for the neighbours into device buffers of lbm_halo_bytes
+ * each: to_lower for the slab below, to_upper for the slab above.  A pointer must
+ * be given exactly when that neighbour exists (LBM_ERR_ARG otherwise).  Stream
+ * ordered on the context's stream; no wait. */
+lbm_status lbm_halo_pack(lbm_ctx* ctx, void* to_lower, void* to_upper);
+
+/* Store the neighbours' messages (device buffers: from_lower = the to_upper
+ * message of the slab below, from_upper = the to_lower message of the slab
+ * above) into the halo rows; same pointer rule and ordering as lbm_halo_pack. */
+lbm_status lbm_halo_unpack(lbm_ctx* ctx, const void* from_lower, const void* from_upper);
 
 /* ------------------------------------------------------------------------
  * Batches: many independent lattices of uneven size and material advanced

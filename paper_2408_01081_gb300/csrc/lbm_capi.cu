@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -48,6 +49,37 @@ __global__ void wall_tables_kernel(int R, const double* __restrict__ Xn, const d
 }
 
 
+// one row of five planes (first plane p0, consecutive) <-> a dense [5][nx] message
+template <typename T>
+__global__ void halo_copy_kernel(T* __restrict__ state, long long plane, int pitch, int row, int p0,
+                                 T* __restrict__ msg, int nx, bool to_msg)
+{
+    const int n = 5 * nx;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int k = i / nx, x = i - k * nx;
+        T* s = state + (long long)(p0 + k) * plane + (long long)row * pitch + x;
+        if (to_msg) msg[i] = *s;
+        else *s = msg[i];
+    }
+}
+
+cudaError_t halo_copy(int es, void* state, long long plane, int pitch, int row, int p0, void* msg, int nx,
+                      bool to_msg, cudaStream_t s)
+{
+    const int blocks = (5 * nx + 255) / 256 < 152 * 4 ? (5 * nx + 255) / 256 : 152 * 4;
+    if (es == 8)
+        halo_copy_kernel<unsigned long long><<<blocks, 256, 0, s>>>(static_cast<unsigned long long*>(state), plane,
+                                                                    pitch, row, p0,
+                                                                    static_cast<unsigned long long*>(msg), nx, to_msg);
+    else if (es == 4)
+        halo_copy_kernel<unsigned int><<<blocks, 256, 0, s>>>(static_cast<unsigned int*>(state), plane, pitch, row, p0,
+                                                              static_cast<unsigned int*>(msg), nx, to_msg);
+    else
+        halo_copy_kernel<unsigned short><<<blocks, 256, 0, s>>>(static_cast<unsigned short*>(state), plane, pitch, row,
+                                                                p0, static_cast<unsigned short*>(msg), nx, to_msg);
+    return cudaGetLastError();
+}
+
 thread_local std::string g_create_error;
 
 const KindOps* ops_for(int storage)
@@ -65,6 +97,43 @@ const KindOps* ops_for(int storage)
 
 constexpr int kRedBlocks = 152 * 4;   // blocks of the FP64 reductions (one partial each)
 constexpr int kMaxR = 16;
+constexpr int kTimeoutSlot = kRedBlocks * 30 + 56;   // scratch double index of the staged kernel's timeout flag
+
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry point (no link to libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// 3D map of a lattice buffer: x = column (extent nx), y = row (extent ny), z = plane
+// (extent nplanes); box {box_w, 1, nplanes}, out-of-range elements read as zero
+bool encode_rows_map(CUtensorMap* m, void* base, int esize, int nx, int ny, int pitch, long long plane,
+                     int nplanes, int box_w)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nplanes};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * esize, (cuuint64_t)plane * esize};
+    const cuuint32_t box[3] = {(cuuint32_t)box_w, 1u, (cuuint32_t)nplanes};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return fn(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // 5x5 inverse by Gauss-Jordan elimination with partial pivoting (FP64)
 bool invert5(const double (&a_in)[25], double (&inv)[25])
@@ -127,6 +196,14 @@ struct lbm_ctx {
     int fuse = 1;                // steps per pass over memory when the fused kernel applies
     int tb_rows = 64;            // rows per block of the fused kernel
     int split = 1;               // FP64: split level (which additions run on the integer pipes)
+    int staging = 1;             // fused kernel: 1 = rows staged by tensor copies, 0 = register prefetch
+    int nyi = 0;                 // rows of the lattice's own (a slab: without its halo rows)
+    int yo = 0;                  // storage row of own row 0 (1 when a halo row sits below)
+    bool slab = false;           // a row slab of a larger lattice (lbm_create_slab)
+    int halo_lo = 0, halo_hi = 0;  // halo rows below / above the slab's own rows (0 or 1)
+    bool maps_ok = false;        // row maps of both buffers encoded (all formats but FP64)
+    CUtensorMap map[2][2];       // row maps of buf[0], buf[1] for the staged fused kernel
+                                 // ([buffer][part]; moment space: FP32 part, 16-bit part)
 };
 
 namespace {
@@ -164,7 +241,8 @@ lbmk::NodeArgs node_args(const lbm_ctx* ctx, long long m_time)
     A.Sout = ctx->buf[ctx->cur];
     A.w = ctx->w;
     A.nx = ctx->p.nx;
-    A.ny = ctx->p.ny;
+    A.ny = ctx->nyi;
+    A.yo = ctx->yo;
     A.pitch = ctx->pitch;
     A.plane = ctx->plane;
     A.a = ctx->a;
@@ -190,7 +268,7 @@ lbmk::NodeArgs node_args(const lbm_ctx* ctx, long long m_time)
 
 void node_grid(const lbm_ctx* ctx, dim3& grid, dim3& block)
 {
-    const long long n = (long long)ctx->p.nx * ctx->p.ny;
+    const long long n = (long long)ctx->p.nx * ctx->nyi;
     long long nb = (n + 255) / 256;
     if (nb > 152 * 16) nb = 152 * 16;
     grid = dim3((unsigned)nb);
@@ -300,6 +378,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
         return LBM_ERR_OOM;
     }
     ctx->p = *p;
+    ctx->nyi = p->ny;
     ctx->s = static_cast<cudaStream_t>(p->stream);
     ctx->ops = ops_for(p->storage);
     ctx->pitch = (p->nx + 63) / 64 * 64;
@@ -335,13 +414,109 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->buf[0], 0, state_bytes, ctx->s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->buf[1], 0, state_bytes, ctx->s);
     if (e == cudaSuccess && ctx->w) e = cudaMemsetAsync(ctx->w, 0, (size_t)2 * ctx->plane * sizeof(double), ctx->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->scratch, 0, (size_t)(kRedBlocks * 30 + 64) * sizeof(double), ctx->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s);
+    if (e == cudaSuccess && (p->storage == LBM_F32 || p->storage == LBM_BF16 || p->storage == LBM_F16)) {
+        const int es = ctx->ops->elem_bytes;
+        const int win = es == 4 ? lbmk::TbtGeom<4>::WIN : lbmk::TbtGeom<2>::WIN;
+        ctx->maps_ok = true;
+        for (int i = 0; i < 2; ++i)
+            ctx->maps_ok = ctx->maps_ok && encode_rows_map(&ctx->map[i][0], ctx->buf[i], es, p->nx, p->ny, ctx->pitch,
+                                                           ctx->plane, 20, win);
+    }
+    if (e == cudaSuccess && (p->storage == LBM_MS_BF16 || p->storage == LBM_MS_F16)) {
+        const int win = lbmk::TbtMsGeom::WIN;
+        ctx->maps_ok = true;
+        for (int i = 0; i < 2; ++i) {
+            char* b = static_cast<char*>(ctx->buf[i]);
+            ctx->maps_ok = ctx->maps_ok &&
+                           encode_rows_map(&ctx->map[i][0], b, 4, p->nx, p->ny, ctx->pitch, ctx->plane, 5, win) &&
+                           encode_rows_map(&ctx->map[i][1], b + 20 * ctx->plane, 2, p->nx, p->ny, ctx->pitch,
+                                           ctx->plane, 15, win);
+        }
+    }
     if (e != cudaSuccess) {
         g_create_error = std::string("device allocation failed: ") + cudaGetErrorString(e);
         lbm_destroy(ctx);
         return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
     }
     *out = ctx;
+    return LBM_OK;
+}
+
+lbm_status lbm_create_slab(const lbm_params* p, int32_t y_begin, int32_t rows, lbm_ctx** out)
+{
+    g_create_error.clear();
+    if (!out || !p) {
+        g_create_error = "params and out are required";
+        return LBM_ERR_ARG;
+    }
+    *out = nullptr;
+    if (p->ny < 2 || y_begin < 0 || rows < 1 || (long long)y_begin + rows > p->ny) {
+        g_create_error = "slab rows [y_begin, y_begin + rows) must lie in [0, ny), ny >= 2";
+        return LBM_ERR_ARG;
+    }
+    if (p->storage == LBM_MS_BF16 || p->storage == LBM_MS_F16) {
+        g_create_error = "slabs take the population formats (the moment-space scale is chosen per context)";
+        return LBM_ERR_ARG;
+    }
+    const bool dir = p->bc == LBM_DIRICHLET;
+    const int lo = (dir && y_begin == 0) ? 0 : 1;               // no neighbour below the bottom wall
+    const int hi = (dir && y_begin + rows == p->ny) ? 0 : 1;    // nor above the top wall
+    lbm_params q = *p;
+    q.ny = rows + lo + hi;
+    lbm_status st = lbm_create(&q, out);
+    if (st != LBM_OK) return st;
+    lbm_ctx* ctx = *out;
+    ctx->slab = true;
+    ctx->nyi = rows;
+    ctx->yo = lo;
+    ctx->halo_lo = lo;
+    ctx->halo_hi = hi;
+    ctx->fuse = 1;
+    return LBM_OK;
+}
+
+lbm_status lbm_halo_bytes(const lbm_ctx* ctx, int64_t* nbytes)
+{
+    if (!ctx || !nbytes) return LBM_ERR_ARG;
+    *nbytes = ctx->slab ? (int64_t)5 * ctx->p.nx * ctx->ops->elem_bytes : 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_halo_pack(lbm_ctx* ctx, void* to_lower, void* to_upper)
+{
+    LBM_CHECK_CTX(ctx);
+    if (!ctx->slab) return fail(ctx, LBM_ERR_ARG, "not a slab");
+    if ((to_lower != nullptr) != (ctx->halo_lo == 1) || (to_upper != nullptr) != (ctx->halo_hi == 1))
+        return fail(ctx, LBM_ERR_ARG, "a message buffer is needed exactly for each neighbour of the slab");
+    lbm_status st = check_ready(ctx);
+    if (st != LBM_OK) return st;
+    const int es = ctx->ops->elem_bytes;
+    // pull scheme: the lower neighbour's top row pulls f*_(0,-1) of our first row, the upper
+    // neighbour's bottom row pulls f*_(0,1) of our last row
+    if (to_lower)
+        LBM_CUDA(ctx, halo_copy(es, ctx->buf[ctx->cur], ctx->plane, ctx->pitch, ctx->yo, 3 * 5, to_lower, ctx->p.nx,
+                                true, ctx->s));
+    if (to_upper)
+        LBM_CUDA(ctx, halo_copy(es, ctx->buf[ctx->cur], ctx->plane, ctx->pitch, ctx->yo + ctx->nyi - 1, 1 * 5,
+                                to_upper, ctx->p.nx, true, ctx->s));
+    return LBM_OK;
+}
+
+lbm_status lbm_halo_unpack(lbm_ctx* ctx, const void* from_lower, const void* from_upper)
+{
+    LBM_CHECK_CTX(ctx);
+    if (!ctx->slab) return fail(ctx, LBM_ERR_ARG, "not a slab");
+    if ((from_lower != nullptr) != (ctx->halo_lo == 1) || (from_upper != nullptr) != (ctx->halo_hi == 1))
+        return fail(ctx, LBM_ERR_ARG, "a message buffer is needed exactly for each neighbour of the slab");
+    const int es = ctx->ops->elem_bytes;
+    if (from_lower)
+        LBM_CUDA(ctx, halo_copy(es, ctx->buf[ctx->cur], ctx->plane, ctx->pitch, 0, 1 * 5, const_cast<void*>(from_lower),
+                                ctx->p.nx, false, ctx->s));
+    if (from_upper)
+        LBM_CUDA(ctx, halo_copy(es, ctx->buf[ctx->cur], ctx->plane, ctx->pitch, ctx->yo + ctx->nyi, 3 * 5,
+                                const_cast<void*>(from_upper), ctx->p.nx, false, ctx->s));
     return LBM_OK;
 }
 
@@ -379,7 +554,24 @@ lbm_status lbm_time_step(const lbm_ctx* ctx, int64_t* m)
 lbm_status lbm_synchronize(lbm_ctx* ctx)
 {
     LBM_CHECK_CTX(ctx);
+    int* flag = reinterpret_cast<int*>(ctx->scratch + kTimeoutSlot);
+    int h = 0;
+    LBM_CUDA(ctx, cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
     LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+    if (h) {
+        LBM_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->s));
+        LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+        return fail(ctx, LBM_ERR_TIMEOUT, "a bounded wait of the staged two-step kernel ran out; the state is "
+                                          "undefined until re-initialised");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_staging(lbm_ctx* ctx, int32_t mode)
+{
+    LBM_CHECK_CTX(ctx);
+    if (mode < 0 || mode > 2) return fail(ctx, LBM_ERR_ARG, "staging mode must be 0, 1 or 2");
+    ctx->staging = mode;
     return LBM_OK;
 }
 
@@ -415,6 +607,7 @@ lbm_status lbm_set_forcing(lbm_ctx* ctx, int32_t R, const double* X, const doubl
 {
     LBM_CHECK_CTX(ctx);
     if (R < 0 || R > kMaxR) return fail(ctx, LBM_ERR_ARG, "R must be in [0, 16]");
+    if (ctx->slab && R > 0) return fail(ctx, LBM_ERR_ARG, "a slab has no body load");
     LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
     cudaFree(ctx->fX);
     cudaFree(ctx->fY);
@@ -455,6 +648,7 @@ lbm_status lbm_set_dirichlet(lbm_ctx* ctx, const double* g, int64_t nt, int32_t 
 {
     LBM_CHECK_CTX(ctx);
     if (ctx->p.bc != LBM_DIRICHLET) return fail(ctx, LBM_ERR_ARG, "lattice is periodic");
+    if (ctx->slab && g) return fail(ctx, LBM_ERR_ARG, "a slab takes homogeneous Dirichlet data only");
     LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
     cudaFree(ctx->g);
     ctx->g = nullptr;
@@ -475,6 +669,7 @@ lbm_status lbm_set_dirichlet_separable(lbm_ctx* ctx, int32_t R, const double* Xn
 {
     LBM_CHECK_CTX(ctx);
     if (ctx->p.bc != LBM_DIRICHLET) return fail(ctx, LBM_ERR_ARG, "lattice is periodic");
+    if (ctx->slab) return fail(ctx, LBM_ERR_ARG, "a slab takes homogeneous Dirichlet data only");
     if (R < 1 || R > kMaxR || !Xn || !Xw || !Yn || !Yw || !T || nt < 1)
         return fail(ctx, LBM_ERR_ARG, "R must be in [1, 16], tables non-NULL and nt >= 1");
     const int nx = ctx->p.nx, ny = ctx->p.ny;
@@ -509,7 +704,7 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const d
 {
     LBM_CHECK_CTX(ctx);
     if (!U0 || !dU0dx || !dU0dy) return fail(ctx, LBM_ERR_ARG, "U0, dU0dx and dU0dy are required");
-    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    const size_t n = (size_t)ctx->p.nx * ctx->nyi;
     const double *dU0, *dUx, *dUy, *dB0, *du0;
     double *o1, *o2, *o3, *o4, *o5;
     lbm_status st;
@@ -578,10 +773,13 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
                         (ctx->R > 0 ? lbmh::STEP_FORCING : 0) | (ctx->w ? lbmh::STEP_TRACK : 0) |
                         (ctx->omega != 2.0 ? lbmh::STEP_OMEGA : 0) |
                         (split ? ctx->split << lbmh::STEP_SPLIT_SHIFT : 0);
-    // two steps per pass: population formats in FP32 / BF16 / FP16, omega = 2, no body load,
-    // no displacement tracking, periodic or homogeneous Dirichlet
-    const bool fusable = ctx->fuse == 2 &&
-                         (ctx->p.storage == LBM_F32 || ctx->p.storage == LBM_BF16 || ctx->p.storage == LBM_F16) &&
+    // two steps per pass: population formats in FP32 / BF16 / FP16 (and the moment-space formats
+    // with staged rows), omega = 2, no body load, no displacement tracking, periodic or
+    // homogeneous Dirichlet
+    const bool ms = ctx->p.storage == LBM_MS_BF16 || ctx->p.storage == LBM_MS_F16;
+    const bool fusable = ctx->fuse == 2 && !ctx->slab &&
+                         (ctx->p.storage == LBM_F32 || ctx->p.storage == LBM_BF16 || ctx->p.storage == LBM_F16 ||
+                          (ms && ctx->staging >= 1)) &&
                          ctx->omega == 2.0 && ctx->R == 0 && !ctx->w && !(ctx->p.bc == LBM_DIRICHLET && ctx->g);
     if (fusable) {
         lbmk::TbArgs T;
@@ -596,6 +794,32 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
         T.rows = ctx->tb_rows;
         const int nstrip = (ctx->p.nx + lbmk::TB_OUT - 1) / lbmk::TB_OUT;
         const dim3 tblock(128), tgrid((nstrip + 3) / 4, (ctx->p.ny + T.rows - 1) / T.rows);
+        if (ctx->staging >= 1) {
+            if (!ctx->maps_ok) return fail(ctx, LBM_ERR_CUDA, "tensor maps of the state buffers could not be encoded");
+            lbmk::TbtArgs Q;
+            Q.nx = ctx->p.nx;
+            Q.ny = ctx->p.ny;
+            Q.pitch = ctx->pitch;
+            Q.plane = ctx->plane;
+            Q.af = (float)ctx->a;
+            Q.bf = (float)ctx->b;
+            Q.rows = ctx->tb_rows;
+            Q.timeout = reinterpret_cast<int*>(ctx->scratch + kTimeoutSlot);
+            Q.withhold = ctx->staging == 2 ? 2 : -1;
+            Q.scale = (float)ctx->neq_scale;
+            Q.inv_s = (float)(1.0 / ctx->neq_scale);
+            const dim3 qgrid((ctx->p.nx + lbmk::TBT_OUT - 1) / lbmk::TBT_OUT, (ctx->p.ny + Q.rows - 1) / Q.rows);
+            while (n >= 2) {
+                Q.src = ctx->buf[ctx->cur];
+                Q.dst = ctx->buf[ctx->cur ^ 1];
+                cudaError_t e = ops->tbt_step(ctx->map[ctx->cur], Q, ctx->p.bc == LBM_DIRICHLET, qgrid, ctx->s);
+                if (e == cudaErrorNotSupported) return fail(ctx, LBM_ERR_ARG, "no staged two-step kernel for this format");
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "staged two-step kernel");
+                ctx->cur ^= 1;
+                ctx->m += 2;
+                n -= 2;
+            }
+        }
         while (n >= 2) {
             T.src = ctx->buf[ctx->cur];
             T.dst = ctx->buf[ctx->cur ^ 1];
@@ -627,7 +851,7 @@ lbm_status lbm_moments(lbm_ctx* ctx, double* out, int32_t on_device)
     if (!out) return fail(ctx, LBM_ERR_ARG, "out is NULL");
     lbm_status st = check_ready(ctx);
     if (st != LBM_OK) return st;
-    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    const size_t n = (size_t)ctx->p.nx * ctx->nyi;
     double* dst = out;
     if (!on_device) LBM_CUDA(ctx, cudaMallocAsync((void**)&dst, 10 * n * sizeof(double), ctx->s));
     dim3 grid, block;
@@ -662,7 +886,7 @@ lbm_status lbm_error_sums(lbm_ctx* ctx, const double* exact, int32_t on_device, 
     if (!exact || !out) return fail(ctx, LBM_ERR_ARG, "exact and out are required");
     lbm_status st = check_ready(ctx);
     if (st != LBM_OK) return st;
-    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    const size_t n = (size_t)ctx->p.nx * ctx->nyi;
     const double* dex;
     double* owned;
     if ((st = stage_in(ctx, exact, 10 * n, on_device, &dex, &owned)) != LBM_OK) return st;
@@ -683,7 +907,7 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, double* ustar, int32_t o
     if (!f) return fail(ctx, LBM_ERR_ARG, "f is NULL");
     lbm_status st = check_ready(ctx);
     if (st != LBM_OK) return st;
-    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    const size_t n = (size_t)ctx->p.nx * ctx->nyi;
     double *df = f, *du = ustar;
     if (!on_device) {
         LBM_CUDA(ctx, cudaMallocAsync((void**)&df, 22 * n * sizeof(double), ctx->s));
@@ -708,7 +932,7 @@ lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, const double* usta
     LBM_CHECK_CTX(ctx);
     if (!f || m < 0) return fail(ctx, LBM_ERR_ARG, "f is NULL or m < 0");
     if (ctx->R > 0 && m >= ctx->fnt) return fail(ctx, LBM_ERR_STATE, "body-load table has no row for step m");
-    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    const size_t n = (size_t)ctx->p.nx * ctx->nyi;
     const double *df, *du;
     double *o1, *o2;
     lbm_status st;

@@ -9,6 +9,7 @@
 #include "lbm_kernels.cuh"
 #include "lbm_ms.cuh"
 #include "lbm_tb.cuh"
+#include "lbm_tbt.cuh"
 
 namespace lbmh {
 
@@ -66,6 +67,10 @@ struct KindOps {
     cudaError_t (*batch_occupancy)(int* blocks_per_sm);
     // two fused steps (FP32 / BF16 / FP16 populations only; others return cudaErrorNotSupported)
     cudaError_t (*tb2_step)(const lbmk::TbArgs&, bool dirichlet, dim3 grid, dim3 block, cudaStream_t s);
+    // two fused steps with the input rows staged by tensor copies (FP32 / BF16 / FP16 populations
+    // and the moment-space formats); maps: the row maps of the source buffer, one for the
+    // population formats (box {TbtGeom::WIN, 1, 20}), two for moment space (FP32 part, 16-bit part)
+    cudaError_t (*tbt_step)(const CUtensorMap* maps, const lbmk::TbtArgs&, bool dirichlet, dim3 grid, cudaStream_t s);
     int vec_split;                 // nodes per thread of the FP64 split-level step kernels
     int batch_vec;                 // nodes per thread of the batch kernel
 };

@@ -525,7 +525,8 @@ struct NodeArgs {
     const void* S;         // f* planes at the current time (storage type)
     void* Sout;            // f* planes to write (init / set_populations)
     double* w;             // u*(t+dt) [2][ny][pitch] or nullptr
-    int nx, ny, pitch;
+    int nx, ny, pitch;     // ny: the rows these kernels visit (a slab's own rows, not its halo rows)
+    int yo = 0;            // storage row of visited row 0 (1 for a slab with a halo row below, else 0)
     long long plane;
     double a, b;           // cK/c, cmu/c
     double cK, cmu;        // wave speeds (stress output)
@@ -563,7 +564,7 @@ __device__ __forceinline__ void load_node(const NodeArgs& A, int x, int y, doubl
     } else {
     using E = typename Fmt<K>::E;
     const E* p = static_cast<const E*>(A.S);
-    const long long off = (long long)y * A.pitch + x;
+    const long long off = (long long)(y + A.yo) * A.pitch + x;
 #pragma unroll
     for (int d = 0; d < 4; ++d)
 #pragma unroll
@@ -580,7 +581,7 @@ __device__ __forceinline__ void store_node(const NodeArgs& A, int x, int y, cons
     using E = typename Fmt<K>::E;
     using M = typename Fmt<K>::M;
     E* p = static_cast<E*>(A.Sout);
-    const long long off = (long long)y * A.pitch + x;
+    const long long off = (long long)(y + A.yo) * A.pitch + x;
 #pragma unroll
     for (int d = 0; d < 4; ++d)
 #pragma unroll
@@ -723,7 +724,7 @@ __global__ void init_kernel(NodeArgs A, const double* __restrict__ U0, const dou
         store_node<K>(A, x, y, S);
         if (A.w) {
             // u*(dt) = u*(0) + dt v(0) with u*(0) = u0 - dt/2 v(0)  (Eq. trapezoidal)
-            const long long off = (long long)y * A.pitch + x;
+            const long long off = (long long)(y + A.yo) * A.pitch + x;
             const double u0x = u0 ? u0[id] : 0.0, u0y = u0 ? u0[n + id] : 0.0;
             A.w[off] = u0x + 0.5 * A.dt * U[0];
             A.w[A.plane + off] = u0y + 0.5 * A.dt * U[1];
@@ -752,7 +753,7 @@ __device__ __forceinline__ void node_outputs(const NodeArgs& A, int x, int y, do
     for (int k = 0; k < 5; ++k) o[k] = U[k];
     if (A.w) {
         // u(t) = u*(t) + dt/2 v(t) and the stored helper is u*(t) + dt v(t)
-        const long long off = (long long)y * A.pitch + x;
+        const long long off = (long long)(y + A.yo) * A.pitch + x;
         o[5] = A.w[off] - 0.5 * A.dt * U[0];
         o[6] = A.w[A.plane + off] - 0.5 * A.dt * U[1];
     } else {
@@ -792,7 +793,7 @@ __global__ void get_populations_kernel(NodeArgs A, double* __restrict__ fout, do
 #pragma unroll
             for (int k = 0; k < 5; ++k) fout[(d * 5 + k) * n + id] = f[d][k];
         if (ustar) {
-            const long long off = (long long)y * A.pitch + x;
+            const long long off = (long long)(y + A.yo) * A.pitch + x;
             ustar[id] = A.w ? A.w[off] - A.dt * U[0] : 0.0;
             ustar[n + id] = A.w ? A.w[A.plane + off] - A.dt * U[1] : 0.0;
         }
@@ -817,7 +818,7 @@ __global__ void set_populations_kernel(NodeArgs A, const double* __restrict__ fi
         collide_node(f, bx, by, A.dt, A.omega, A.a, A.b, S, U);
         store_node<K>(A, x, y, S);
         if (A.w) {
-            const long long off = (long long)y * A.pitch + x;
+            const long long off = (long long)(y + A.yo) * A.pitch + x;
             A.w[off] = (ustar ? ustar[id] : 0.0) + A.dt * U[0];
             A.w[A.plane + off] = (ustar ? ustar[n + id] : 0.0) + A.dt * U[1];
         }

@@ -192,6 +192,34 @@ cudaError_t tb2_step(const lbmk::TbArgs& a, bool dirichlet, dim3 g, dim3 b, cuda
     return tb2_t<K>(a, dirichlet, g, b, s);
 }
 
+template <int KK>
+cudaError_t tbt_t(const CUtensorMap* maps, const lbmk::TbtArgs& a, bool dirichlet, dim3 g, cudaStream_t s)
+{
+    if constexpr (KK == lbmk::K_F32 || KK == lbmk::K_BF16 || KK == lbmk::K_F16) {
+        using G = lbmk::TbtGeom<(int)sizeof(typename lbmk::Fmt<KK>::E)>;
+        void (*kern)(CUtensorMap, lbmk::TbtArgs) = dirichlet ? lbmk::tbt_kernel<KK, true> : lbmk::tbt_kernel<KK, false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        kern<<<g, lbmk::TBT_THREADS, G::SMEM, s>>>(maps[0], a);
+        return cudaGetLastError();
+    } else if constexpr (KK == lbmk::K_MSBF16 || KK == lbmk::K_MSF16) {
+        using G = lbmk::TbtMsGeom;
+        void (*kern)(CUtensorMap, CUtensorMap, lbmk::TbtArgs) =
+            dirichlet ? lbmk::tbt_ms_kernel<KK, true> : lbmk::tbt_ms_kernel<KK, false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        kern<<<g, lbmk::TBT_THREADS, G::SMEM, s>>>(maps[0], maps[1], a);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
+cudaError_t tbt_step(const CUtensorMap* maps, const lbmk::TbtArgs& a, bool dirichlet, dim3 g, cudaStream_t s)
+{
+    return tbt_t<K>(maps, a, dirichlet, g, s);
+}
+
 cudaError_t batch_occupancy(int* n)
 {
     return batch_occupancy_t<K>(n);
@@ -206,7 +234,7 @@ namespace lbmh {
 
 const KindOps LBM_OPS_NAME(LBM_KIND) = {
     K, V, ELEM, NODE_BYTES,
-    step, init, moments, get_pop, set_pop, energy, error, finite, batch_step, batch_occupancy, tb2_step,
+    step, init, moments, get_pop, set_pop, energy, error, finite, batch_step, batch_occupancy, tb2_step, tbt_step,
     LBM_VEC_SPLIT, VB,
 };
 

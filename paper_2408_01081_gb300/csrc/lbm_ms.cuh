@@ -344,7 +344,7 @@ __device__ void ms_load_node(const NodeArgs& A, int x, int y, double (&S)[4][5])
     constexpr int H = Ms<K>::H;
     const float* m0p = static_cast<const float*>(A.S);
     const unsigned short* dv = reinterpret_cast<const unsigned short*>(m0p + 5 * A.plane);
-    const long long off = (long long)y * A.pitch + x;
+    const long long off = (long long)(y + A.yo) * A.pitch + x;
     const float inv_s = 1.0f / (float)A.neq_scale;     // exact: the scale is a power of two
     float m0[5], gx[5], gy[5], dd[5];
 #pragma unroll
@@ -382,7 +382,7 @@ __device__ void ms_store_node(const NodeArgs& A, int x, int y, const double (&S)
     }
     float* m0p = static_cast<float*>(A.Sout);
     typename Fmt<H>::E* dv = reinterpret_cast<typename Fmt<H>::E*>(m0p + 5 * A.plane);
-    const long long off = (long long)y * A.pitch + x;
+    const long long off = (long long)(y + A.yo) * A.pitch + x;
     const float sc = (float)A.neq_scale;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {

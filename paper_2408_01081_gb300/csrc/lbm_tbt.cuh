@@ -1,0 +1,520 @@
+// Two time steps per pass with the input rows staged in shared memory by tensor
+// copies (TMA), for the population formats stored in FP32 / BF16 / FP16 (FP32
+// arithmetic), periodic or homogeneous-Dirichlet lattices without body load,
+// omega = 2.  Same arithmetic as tb2_kernel (lbm_tb.cuh), so FP32 results are
+// bit-identical to two single steps.
+//
+// Block = 4 compute warps + 1 producer warp over a tile of 120 output columns and
+// `rows` output rows.  The producer's elected lane streams the input rows
+// y0-2 .. y1+1 of all 20 planes, columns [X0 - HL, X0 + 120 + HL), into a ring of
+// shared-memory stages, one tensor copy per row (lbm_tma.cuh), as far ahead as the
+// ring allows; the compute warps never wait on registers for global loads.  Compute
+// warp w owns the S1 columns X0 - 1 + 30 w + lane: S1 = f*(t+dt) of row r from the
+// staged rows r-1, r, r+1 (pull + collision), then S2 = f*(t+2dt) of row r-1 from S1
+// of rows r-2, r-1, r kept in registers (x-neighbours by warp shuffles), written by
+// lanes 1..30.  A staged row is released (empty barrier) as soon as S1 of the row
+// above it is done.
+//
+// Periodic lattices: a lane whose S1 column or its x-neighbours wrap around the
+// lattice (only at x = 0 and x = nx - 1) reads those values from global memory;
+// every other read comes from shared memory.  Dirichlet lattices need no wrap:
+// the edge reflections use the node's own staged values, and rows outside the
+// lattice are not loaded (their stages complete without data).
+#pragma once
+
+#include "lbm_kernels.cuh"
+#include "lbm_ms.cuh"
+#include "lbm_tb.cuh"
+#include "lbm_tma.cuh"
+
+namespace lbmk {
+
+struct TbtArgs {
+    const void* src;       // f*(t) planes (wrapped edge columns are read here)
+    void* dst;             // f*(t+2dt) planes
+    int nx, ny, pitch;
+    long long plane;
+    float af, bf;          // cK/c, cmu/c in FP32
+    int rows;              // output rows per block
+    int* timeout;          // device flag: set when a bounded wait ran out
+    int withhold;          // test hook: staged input row the producer never copies (-1: none)
+    float scale, inv_s;    // moment-space storage: scale of the stored deviations and its reciprocal
+};
+
+constexpr int TBT_WARPS = 4;                  // compute warps per block
+constexpr int TBT_OUT = TBT_WARPS * TB_OUT;   // output columns per block (120)
+constexpr int TBT_THREADS = 32 * (TBT_WARPS + 1);
+
+template <int ES>
+struct TbtGeom {
+    static constexpr int HL = 16 / ES;                                 // staged columns left of the tile
+    static constexpr int WIN = HL + TBT_OUT + HL;                      // staged columns per row
+    static constexpr int ROW_BYTES = 20 * WIN * ES;                    // one row of the 20 planes
+    static constexpr int STAGE_BYTES = (ROW_BYTES + 127) / 128 * 128;  // stage starts 128-byte aligned
+    static constexpr int NST = (ES == 4) ? 5 : 6;                      // stages in the ring
+    static constexpr int SMEM = NST * STAGE_BYTES + 128;               // dynamic shared memory per block
+                                                                       // (+128: the ring starts 128-B aligned)
+    static_assert((WIN * ES) % 16 == 0, "staged row width must be a multiple of 16 bytes");
+    static_assert(WIN <= 256, "tensor-copy box width");
+};
+
+template <int K, bool DIRICHLET>
+__global__ void __launch_bounds__(TBT_THREADS, 3) tbt_kernel(const __grid_constant__ CUtensorMap map, TbtArgs A)
+{
+    using E = typename Fmt<K>::E;
+    using G = TbtGeom<(int)sizeof(E)>;
+    constexpr int NST = G::NST, WIN = G::WIN, HL = G::HL;
+    extern __shared__ __align__(128) unsigned char tbt_smem_raw[];
+    __shared__ __align__(8) unsigned long long full_bar[NST], empty_bar[NST];
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nx = A.nx, ny = A.ny;
+    const int X0 = blockIdx.x * TBT_OUT;
+    const int y0 = blockIdx.y * A.rows;
+    const int y1 = min(ny, y0 + A.rows);
+    const int nin = (y1 - y0) + 4;                   // staged input rows y0-2 .. y1+1
+    const uint32_t raw = lbmt::smem_u32(tbt_smem_raw);
+    const uint32_t sbase = (raw + 127u) & ~127u;                    // 128-byte aligned ring
+    unsigned char* tbt_smem = tbt_smem_raw + (sbase - raw);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            lbmt::mbar_init(lbmt::smem_u32(&full_bar[s]), 1);
+            lbmt::mbar_init(lbmt::smem_u32(&empty_bar[s]), TBT_WARPS);
+        }
+        abort_flag = 0;
+        lbmt::fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == TBT_WARPS) {
+        // ---- producer: one tensor copy per input row, as far ahead as the ring allows ----
+        if (lane == 0) {
+            lbmt::prefetch_map(&map);
+            int j = 0;
+            for (; j < nin; ++j) {
+                const int s = j % NST;
+                const uint32_t fb = lbmt::smem_u32(&full_bar[s]);
+                if (j == A.withhold) continue;               // test hook: this row never arrives
+                if (j >= NST && !lbmt::mbar_wait(lbmt::smem_u32(&empty_bar[s]), ((j / NST) - 1) & 1, &abort_flag))
+                    break;
+                int y = y0 - 2 + j;
+                if (DIRICHLET && (y < 0 || y >= ny)) {
+                    lbmt::mbar_arrive(fb);                   // row outside the lattice: never read
+                    continue;
+                }
+                if (!DIRICHLET) y = (y < 0) ? y + ny : (y >= ny ? y - ny : y);
+                lbmt::mbar_arrive_expect_tx(fb, G::ROW_BYTES);
+                lbmt::tma_load_3d(sbase + s * G::STAGE_BYTES, &map, X0 - HL, y, 0, fb);
+            }
+            // every copy issued has landed before the block leaves
+            for (int q = (j > NST ? j - NST : 0); q < j; ++q)
+                if (q != A.withhold) lbmt::mbar_drain(lbmt::smem_u32(&full_bar[q % NST]), (q / NST) & 1);
+            if (abort_flag) atomicExch(A.timeout, 1);
+        }
+        return;
+    }
+
+    // ---- compute warps ----
+    const E* __restrict__ src = static_cast<const E*>(A.src);
+    E* __restrict__ dst = static_cast<E*>(A.dst);
+    const long long plane = A.plane;
+    const int xs = X0 - 1 + TB_OUT * warp + lane;        // this lane's S1 column (may be -1 or >= nx)
+    const int xc = DIRICHLET ? (xs < 0 ? 0 : (xs >= nx ? nx - 1 : xs)) : ((xs % nx) + nx) % nx;
+    const bool out_lane = (lane >= 1) && (lane <= TB_OUT) && (xs >= 0) && (xs < nx);
+    const bool staged = DIRICHLET || (xs >= 1 && xs + 1 <= nx - 1);   // all three columns in the tile
+    const int xl = (xc == 0) ? nx - 1 : xc - 1, xr = (xc == nx - 1) ? 0 : xc + 1;
+    const int idx = xs - X0 + HL;                        // shared-memory column of xs
+    const float fa = A.af, fb = A.bf;
+    const float Dk[5] = {-1.f, -1.f, 1.f, 1.f, 1.f};
+
+    float keep_py[5], prev[4][5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        keep_py[k] = 0.f;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) prev[d][k] = 0.f;
+    }
+    bool ok = lbmt::mbar_wait(lbmt::smem_u32(&full_bar[0]), 0, &abort_flag) &&
+              lbmt::mbar_wait(lbmt::smem_u32(&full_bar[1 % NST]), (1 / NST) & 1, &abort_flag);
+    for (int i = 0; i + 2 < nin; ++i) {
+        const int r = y0 - 1 + i;                        // S1 row, from staged rows i, i+1, i+2
+        {
+            const int j = i + 2;
+            ok = ok && lbmt::mbar_wait(lbmt::smem_u32(&full_bar[j % NST]), (j / NST) & 1, &abort_flag);
+        }
+        if (!__all_sync(0xffffffffu, ok)) break;
+        const E* rm = reinterpret_cast<const E*>(tbt_smem + (i % NST) * G::STAGE_BYTES);
+        const E* rc = reinterpret_cast<const E*>(tbt_smem + ((i + 1) % NST) * G::STAGE_BYTES);
+        const E* rp = reinterpret_cast<const E*>(tbt_smem + ((i + 2) % NST) * G::STAGE_BYTES);
+        // ---- S1(r) at column xc ----
+        float cur[4][5];
+        const bool row_ok = DIRICHLET ? (r >= 0 && r < ny) : true;
+        {
+            float f[4][5];
+            if (staged) {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    f[0][k] = Fmt<K>::ld(rc[(0 * 5 + k) * WIN + idx - 1]);
+                    f[2][k] = Fmt<K>::ld(rc[(2 * 5 + k) * WIN + idx + 1]);
+                    f[1][k] = Fmt<K>::ld(rm[(1 * 5 + k) * WIN + idx]);
+                    f[3][k] = Fmt<K>::ld(rp[(3 * 5 + k) * WIN + idx]);
+                }
+            } else {
+                // periodic wrap around x = 0 / x = nx - 1: read the wrapped columns directly
+                const int ry = (r < 0) ? r + ny : (r >= ny ? r - ny : r);
+                const int rmy = (ry == 0) ? ny - 1 : ry - 1, rpy = (ry == ny - 1) ? 0 : ry + 1;
+                const long long o = (long long)ry * A.pitch;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    f[0][k] = sload<K>(src + (0 * 5 + k) * plane + o + xl);
+                    f[2][k] = sload<K>(src + (2 * 5 + k) * plane + o + xr);
+                    f[1][k] = sload<K>(src + (1 * 5 + k) * plane + (long long)rmy * A.pitch + xc);
+                    f[3][k] = sload<K>(src + (3 * 5 + k) * plane + (long long)rpy * A.pitch + xc);
+                }
+            }
+            if (DIRICHLET) {
+                const bool bot = r == 0, top = r == ny - 1;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    if (xc == 0) f[0][k] = Dk[k] * Fmt<K>::ld(rc[(2 * 5 + k) * WIN + idx]);
+                    if (xc == nx - 1) f[2][k] = Dk[k] * Fmt<K>::ld(rc[(0 * 5 + k) * WIN + idx]);
+                    if (bot) f[1][k] = Dk[k] * Fmt<K>::ld(rc[(3 * 5 + k) * WIN + idx]);
+                    if (top) f[3][k] = Dk[k] * Fmt<K>::ld(rc[(1 * 5 + k) * WIN + idx]);
+                }
+            }
+            float U[5], rx[5], ry2[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                rx[k] = f[1][k] + f[3][k];
+                ry2[k] = f[0][k] + f[2][k];
+                U[k] = rx[k] + ry2[k];
+            }
+            collide<float>(f, U, rx, ry2, fa, fb, cur);
+            if (!row_ok)
+#pragma unroll
+                for (int d = 0; d < 4; ++d)
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) cur[d][k] = 0.f;
+        }
+        // staged row i (row r-1) is not read again
+        __syncwarp();
+        if (lane == 0) lbmt::mbar_arrive(lbmt::smem_u32(&empty_bar[i % NST]));
+        // ---- S2(r-1) from S1(r-2), S1(r-1), S1(r) ----
+        const int q = r - 1;
+        if (q >= y0) {
+            const bool bot = DIRICHLET && q == 0, top = DIRICHLET && q == ny - 1;
+            float f[4][5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                f[0][k] = __shfl_up_sync(0xffffffffu, prev[0][k], 1);
+                f[2][k] = __shfl_down_sync(0xffffffffu, prev[2][k], 1);
+                f[1][k] = bot ? Dk[k] * prev[3][k] : keep_py[k];
+                f[3][k] = top ? Dk[k] * prev[1][k] : cur[3][k];
+                if (DIRICHLET && xs == 0) f[0][k] = Dk[k] * prev[2][k];
+                if (DIRICHLET && xs == nx - 1) f[2][k] = Dk[k] * prev[0][k];
+            }
+            float U[5], rx[5], ry2[5], o[4][5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                rx[k] = f[1][k] + f[3][k];
+                ry2[k] = f[0][k] + f[2][k];
+                U[k] = rx[k] + ry2[k];
+            }
+            collide<float>(f, U, rx, ry2, fa, fb, o);
+            if (out_lane) {
+                const long long off = (long long)q * A.pitch + xs;
+#pragma unroll
+                for (int d = 0; d < 4; ++d)
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) dst[(d * 5 + k) * plane + off] = Fmt<K>::st(o[d][k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            keep_py[k] = prev[1][k];
+#pragma unroll
+            for (int d = 0; d < 4; ++d) prev[d][k] = cur[d][k];
+        }
+    }
+    if (lane == 0 && abort_flag) atomicExch(A.timeout, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Moment-space storage (lbm_ms.cuh): the same two-step pass over a state of 5 FP32
+// planes m0 followed by 15 16-bit planes (dx[5], dy[5], dd[5]) of deviations scaled
+// by s.  Each staged row holds columns [X0 - 8, X0 + 128) of both parts (two tensor
+// copies, one barrier); populations are rebuilt from the moments on the fly.  The
+// intermediate step S1 stays in FP32 registers (not rounded to 16 bits); S2 is
+// stored as moments.
+// ---------------------------------------------------------------------------
+struct TbtMsGeom {
+    static constexpr int HL = 8;                                       // 16 bytes of 16-bit values
+    static constexpr int WIN = HL + TBT_OUT + HL;                      // 136 staged columns
+    static constexpr int M0_BYTES = 5 * WIN * 4;                       // FP32 part of a row
+    static constexpr int DEV_OFF = (M0_BYTES + 127) / 128 * 128;       // 16-bit part starts 128-B aligned
+    static constexpr int DEV_BYTES = 15 * WIN * 2;
+    static constexpr int ROW_BYTES = M0_BYTES + DEV_BYTES;             // bytes the two copies bring
+    static constexpr int STAGE_BYTES = (DEV_OFF + DEV_BYTES + 127) / 128 * 128;
+    static constexpr int NST = 6;
+    static constexpr int SMEM = NST * STAGE_BYTES + 128;
+    static_assert((WIN * 4) % 16 == 0 && (WIN * 2) % 16 == 0, "staged row width must be a multiple of 16 bytes");
+};
+
+// the four moment sets of one node from a staged row (column c of the window)
+// or from global memory (column c of row y), deviations unscaled
+struct MsNode {
+    float m0[5], dx[5], dy[5], dd[5];
+};
+
+template <int H>
+__device__ __forceinline__ void ms_node_smem(const unsigned char* stage, int c, float inv_s, MsNode& n)
+{
+    const float* m0 = reinterpret_cast<const float*>(stage);
+    const unsigned short* dv = reinterpret_cast<const unsigned short*>(stage + TbtMsGeom::DEV_OFF);
+    constexpr int W = TbtMsGeom::WIN;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        n.m0[k] = m0[k * W + c];
+        n.dx[k] = Fmt<H>::ld(dv[k * W + c]) * inv_s;
+        n.dy[k] = Fmt<H>::ld(dv[(5 + k) * W + c]) * inv_s;
+        n.dd[k] = Fmt<H>::ld(dv[(10 + k) * W + c]) * inv_s;
+    }
+}
+
+template <int H>
+__device__ __forceinline__ void ms_node_global(const void* S, long long plane, long long off, float inv_s, MsNode& n)
+{
+    const float* m0 = static_cast<const float*>(S);
+    const unsigned short* dv = reinterpret_cast<const unsigned short*>(m0 + 5 * plane);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        n.m0[k] = __ldg(m0 + k * plane + off);
+        n.dx[k] = Fmt<H>::ld(__ldg(dv + k * plane + off)) * inv_s;
+        n.dy[k] = Fmt<H>::ld(__ldg(dv + (5 + k) * plane + off)) * inv_s;
+        n.dd[k] = Fmt<H>::ld(__ldg(dv + (10 + k) * plane + off)) * inv_s;
+    }
+}
+
+__device__ __forceinline__ void ms_node_dir(const MsNode& n, int d, float a, float b, float (&f)[5])
+{
+    ms_dir(d, n.m0, (d == 0 || d == 2) ? n.dx : n.dy, n.dd, a, b, f);
+}
+
+template <int K, bool DIRICHLET>
+__global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_constant__ CUtensorMap map32,
+                                                                const __grid_constant__ CUtensorMap map16, TbtArgs A)
+{
+    const float scale = A.scale, inv_s = A.inv_s;
+    constexpr int H = Ms<K>::H;
+    using G = TbtMsGeom;
+    constexpr int NST = G::NST, HL = G::HL;
+    extern __shared__ __align__(128) unsigned char tbt_smem_raw[];
+    __shared__ __align__(8) unsigned long long full_bar[NST], empty_bar[NST];
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nx = A.nx, ny = A.ny;
+    const int X0 = blockIdx.x * TBT_OUT;
+    const int y0 = blockIdx.y * A.rows;
+    const int y1 = min(ny, y0 + A.rows);
+    const int nin = (y1 - y0) + 4;
+    const uint32_t raw = lbmt::smem_u32(tbt_smem_raw);
+    const uint32_t sbase = (raw + 127u) & ~127u;
+    unsigned char* tbt_smem = tbt_smem_raw + (sbase - raw);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            lbmt::mbar_init(lbmt::smem_u32(&full_bar[s]), 1);
+            lbmt::mbar_init(lbmt::smem_u32(&empty_bar[s]), TBT_WARPS);
+        }
+        abort_flag = 0;
+        lbmt::fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == TBT_WARPS) {
+        if (lane == 0) {
+            lbmt::prefetch_map(&map32);
+            lbmt::prefetch_map(&map16);
+            int j = 0;
+            for (; j < nin; ++j) {
+                const int s = j % NST;
+                const uint32_t fb = lbmt::smem_u32(&full_bar[s]);
+                if (j == A.withhold) continue;
+                if (j >= NST && !lbmt::mbar_wait(lbmt::smem_u32(&empty_bar[s]), ((j / NST) - 1) & 1, &abort_flag))
+                    break;
+                int y = y0 - 2 + j;
+                if (DIRICHLET && (y < 0 || y >= ny)) {
+                    lbmt::mbar_arrive(fb);
+                    continue;
+                }
+                if (!DIRICHLET) y = (y < 0) ? y + ny : (y >= ny ? y - ny : y);
+                const uint32_t st = sbase + s * G::STAGE_BYTES;
+                lbmt::mbar_arrive_expect_tx(fb, G::ROW_BYTES);
+                lbmt::tma_load_3d(st, &map32, X0 - HL, y, 0, fb);
+                lbmt::tma_load_3d(st + G::DEV_OFF, &map16, X0 - HL, y, 0, fb);
+            }
+            for (int q = (j > NST ? j - NST : 0); q < j; ++q)
+                if (q != A.withhold) lbmt::mbar_drain(lbmt::smem_u32(&full_bar[q % NST]), (q / NST) & 1);
+            if (abort_flag) atomicExch(A.timeout, 1);
+        }
+        return;
+    }
+
+    const long long plane = A.plane;
+    const int xs = X0 - 1 + TB_OUT * warp + lane;
+    const int xc = DIRICHLET ? (xs < 0 ? 0 : (xs >= nx ? nx - 1 : xs)) : ((xs % nx) + nx) % nx;
+    const bool out_lane = (lane >= 1) && (lane <= TB_OUT) && (xs >= 0) && (xs < nx);
+    const bool own_staged = DIRICHLET || (xs >= 0 && xs < nx);         // own column inside the lattice
+    const int xl = (xc == 0) ? nx - 1 : xc - 1, xr = (xc == nx - 1) ? 0 : xc + 1;
+    const bool left_staged = DIRICHLET || (xs - 1 >= 0 && xs - 1 < nx);
+    const bool right_staged = DIRICHLET || (xs + 1 >= 0 && xs + 1 < nx);
+    const int idx = xs - X0 + HL;
+    const float fa = A.af, fb = A.bf;
+    const float Dk[5] = {-1.f, -1.f, 1.f, 1.f, 1.f};
+
+    float keep_py[5], prev[4][5], d1_prev[5];        // S1 rows r-2 (direction (0,1)), r-1; f*_(0,1)(t) of row r-1
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        keep_py[k] = 0.f;
+        d1_prev[k] = 0.f;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) prev[d][k] = 0.f;
+    }
+    auto row_of = [&](int r) { return (r < 0) ? r + ny : (r >= ny ? r - ny : r); };
+    bool ok = lbmt::mbar_wait(lbmt::smem_u32(&full_bar[0]), 0, &abort_flag) &&
+              lbmt::mbar_wait(lbmt::smem_u32(&full_bar[1 % NST]), (1 / NST) & 1, &abort_flag);
+    if (__all_sync(0xffffffffu, ok)) {
+        // f*_(0,1)(t) of the own column in staged row 0 (row y0-2): the pull source of row y0-1
+        MsNode n;
+        if (own_staged) ms_node_smem<H>(tbt_smem + 0 * G::STAGE_BYTES, idx, inv_s, n);
+        else ms_node_global<H>(A.src, plane, (long long)row_of(y0 - 2) * A.pitch + xc, inv_s, n);
+        ms_node_dir(n, 1, fa, fb, d1_prev);
+    }
+    for (int i = 0; i + 2 < nin; ++i) {
+        const int r = y0 - 1 + i;
+        {
+            const int j = i + 2;
+            ok = ok && lbmt::mbar_wait(lbmt::smem_u32(&full_bar[j % NST]), (j / NST) & 1, &abort_flag);
+        }
+        if (!__all_sync(0xffffffffu, ok)) break;
+        const unsigned char* sc = tbt_smem + ((i + 1) % NST) * G::STAGE_BYTES;   // row r
+        const unsigned char* sp = tbt_smem + ((i + 2) % NST) * G::STAGE_BYTES;   // row r+1
+        float cur[4][5];
+        const bool row_ok = DIRICHLET ? (r >= 0 && r < ny) : true;
+        {
+            // own node of row r (all four directions) and (0,-1) of row r+1
+            MsNode n;
+            if (own_staged) ms_node_smem<H>(sc, idx, inv_s, n);
+            else ms_node_global<H>(A.src, plane, (long long)row_of(r) * A.pitch + xc, inv_s, n);
+            float o0[5], o1[5], o2[5], o3[5], p3[5];
+            ms_node_dir(n, 0, fa, fb, o0);
+            ms_node_dir(n, 1, fa, fb, o1);
+            ms_node_dir(n, 2, fa, fb, o2);
+            ms_node_dir(n, 3, fa, fb, o3);
+            {
+                MsNode np;
+                if (own_staged) ms_node_smem<H>(sp, idx, inv_s, np);
+                else ms_node_global<H>(A.src, plane, (long long)row_of(r + 1) * A.pitch + xc, inv_s, np);
+                ms_node_dir(np, 3, fa, fb, p3);
+            }
+            float hl[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, hr[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            if (lane == 0) {
+                MsNode h;
+                if (left_staged) ms_node_smem<H>(sc, idx - 1, inv_s, h);
+                else ms_node_global<H>(A.src, plane, (long long)row_of(r) * A.pitch + xl, inv_s, h);
+                ms_node_dir(h, 0, fa, fb, hl);
+            }
+            if (lane == 31) {
+                MsNode h;
+                if (right_staged) ms_node_smem<H>(sc, idx + 1, inv_s, h);
+                else ms_node_global<H>(A.src, plane, (long long)row_of(r) * A.pitch + xr, inv_s, h);
+                ms_node_dir(h, 2, fa, fb, hr);
+            }
+            float f[4][5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const float l = __shfl_up_sync(0xffffffffu, o0[k], 1);
+                const float rr = __shfl_down_sync(0xffffffffu, o2[k], 1);
+                f[0][k] = (lane == 0) ? hl[k] : l;
+                f[2][k] = (lane == 31) ? hr[k] : rr;
+                f[1][k] = d1_prev[k];
+                f[3][k] = p3[k];
+            }
+            if (DIRICHLET) {
+                const bool bot = r == 0, top = r == ny - 1;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    if (xc == 0) f[0][k] = Dk[k] * o2[k];
+                    if (xc == nx - 1) f[2][k] = Dk[k] * o0[k];
+                    if (bot) f[1][k] = Dk[k] * o3[k];
+                    if (top) f[3][k] = Dk[k] * o1[k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) d1_prev[k] = o1[k];
+            float U[5], rx[5], ry2[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                rx[k] = f[1][k] + f[3][k];
+                ry2[k] = f[0][k] + f[2][k];
+                U[k] = rx[k] + ry2[k];
+            }
+            collide<float>(f, U, rx, ry2, fa, fb, cur);
+            if (!row_ok)
+#pragma unroll
+                for (int d = 0; d < 4; ++d)
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) cur[d][k] = 0.f;
+        }
+        __syncwarp();
+        if (lane == 0) lbmt::mbar_arrive(lbmt::smem_u32(&empty_bar[i % NST]));
+        const int q = r - 1;
+        if (q >= y0) {
+            const bool bot = DIRICHLET && q == 0, top = DIRICHLET && q == ny - 1;
+            float f[4][5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                f[0][k] = __shfl_up_sync(0xffffffffu, prev[0][k], 1);
+                f[2][k] = __shfl_down_sync(0xffffffffu, prev[2][k], 1);
+                f[1][k] = bot ? Dk[k] * prev[3][k] : keep_py[k];
+                f[3][k] = top ? Dk[k] * prev[1][k] : cur[3][k];
+                if (DIRICHLET && xs == 0) f[0][k] = Dk[k] * prev[2][k];
+                if (DIRICHLET && xs == nx - 1) f[2][k] = Dk[k] * prev[0][k];
+            }
+            float U[5], rx[5], ry2[5], o[4][5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                rx[k] = f[1][k] + f[3][k];
+                ry2[k] = f[0][k] + f[2][k];
+                U[k] = rx[k] + ry2[k];
+            }
+            collide<float>(f, U, rx, ry2, fa, fb, o);
+            if (out_lane) {
+                float m0[5], dx[5], dy[5], dd[5];
+                ms_moments(o, fa, fb, m0, dx, dy, dd);
+                float* m0p = static_cast<float*>(A.dst);
+                typename Fmt<H>::E* dv = reinterpret_cast<typename Fmt<H>::E*>(m0p + 5 * plane);
+                const long long off = (long long)q * A.pitch + xs;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    m0p[k * plane + off] = m0[k];
+                    dv[k * plane + off] = Fmt<H>::st(dx[k] * scale);
+                    dv[(5 + k) * plane + off] = Fmt<H>::st(dy[k] * scale);
+                    dv[(10 + k) * plane + off] = Fmt<H>::st(dd[k] * scale);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            keep_py[k] = prev[1][k];
+#pragma unroll
+            for (int d = 0; d < 4; ++d) prev[d][k] = cur[d][k];
+        }
+    }
+    if (lane == 0 && abort_flag) atomicExch(A.timeout, 1);
+}
+
+}  // namespace lbmk

@@ -25,10 +25,11 @@ STATUS_NAMES = ["LBM_OK", "LBM_ERR_ARG", "LBM_ERR_CFL", "LBM_ERR_OOM", "LBM_ERR_
                 "LBM_ERR_TIMEOUT", "LBM_ERR_STATE"]
 
 # every symbol declared in include/lbm.h
-EXPORTS = ["lbm_create", "lbm_init", "lbm_set_relaxation", "lbm_set_step_fusion", "lbm_set_fp64_split", "lbm_set_forcing", "lbm_set_dirichlet", "lbm_set_dirichlet_separable", "lbm_step", "lbm_moments",
+EXPORTS = ["lbm_create", "lbm_init", "lbm_set_relaxation", "lbm_set_step_fusion", "lbm_set_staging", "lbm_set_fp64_split", "lbm_set_forcing", "lbm_set_dirichlet", "lbm_set_dirichlet_separable", "lbm_step", "lbm_moments",
            "lbm_energy", "lbm_error_sums", "lbm_get_populations", "lbm_set_populations", "lbm_check_finite",
            "lbm_time_step", "lbm_synchronize", "lbm_destroy", "lbm_last_error", "lbm_state_bytes",
-           "lbm_save_state", "lbm_load_state", "lbm_energy_noalloc", "lbm_batch_create", "lbm_batch_init",
+           "lbm_save_state", "lbm_load_state", "lbm_energy_noalloc", "lbm_create_slab", "lbm_halo_bytes",
+           "lbm_halo_pack", "lbm_halo_unpack", "lbm_batch_create", "lbm_batch_init",
            "lbm_batch_tune", "lbm_batch_set_mode", "lbm_batch_step", "lbm_batch_synchronize", "lbm_batch_moments",
            "lbm_batch_energy", "lbm_batch_info", "lbm_batch_set_barrier", "lbm_batch_destroy",
            "lbm_batch_last_error"]
@@ -77,6 +78,7 @@ def load(path: Optional[str] = None):
         "lbm_set_forcing": ([vp, i32, dp, dp, dp, i64, i32], i32),
         "lbm_set_relaxation": ([vp, ctypes.c_double], i32),
         "lbm_set_step_fusion": ([vp, i32, i32], i32),
+        "lbm_set_staging": ([vp, i32], i32),
         "lbm_set_fp64_split": ([vp, i32], i32),
         "lbm_set_dirichlet": ([vp, dp, i64, i32], i32),
         "lbm_set_dirichlet_separable": ([vp, i32, dp, dp, dp, dp, dp, i64, i32], i32),
@@ -96,6 +98,10 @@ def load(path: Optional[str] = None):
         "lbm_load_state": ([vp, vp, i64, i32], i32),
         "lbm_energy_noalloc": ([dp, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, dp, i32, vp], i32),
+        "lbm_create_slab": ([ctypes.POINTER(LbmParams), i32, i32, ctypes.POINTER(vp)], i32),
+        "lbm_halo_bytes": ([vp, ctypes.POINTER(i64)], i32),
+        "lbm_halo_pack": ([vp, vp, vp], i32),
+        "lbm_halo_unpack": ([vp, vp, vp], i32),
         "lbm_batch_create": ([i32, ctypes.POINTER(LatticeDesc), i32, vp, ctypes.POINTER(vp)], i32),
         "lbm_batch_init": ([vp, i32, dp, dp, dp, i32], i32),
         "lbm_batch_tune": ([vp, ctypes.c_char_p], i32),
@@ -162,6 +168,39 @@ def lbm_create(nx, ny, dx, dt, cK, cmu, bc=LBM_PERIODIC, storage=LBM_F64, track_
     return ctx
 
 
+def lbm_create_slab(nx, ny, dx, dt, cK, cmu, y_begin, rows, bc=LBM_PERIODIC, storage=LBM_F64,
+                    track_displacement=False, stream=None):
+    """Context for rows [y_begin, y_begin + rows) of an nx x ny lattice (see include/lbm.h)."""
+    p = LbmParams(int(nx), int(ny), int(bc), int(storage), float(dx), float(dt), float(cK), float(cmu),
+                  int(bool(track_displacement)), 0, ctypes.c_void_p(stream or 0))
+    ctx = ctypes.c_void_p()
+    _check(None, load().lbm_create_slab(ctypes.byref(p), int(y_begin), int(rows), ctypes.byref(ctx)))
+    return ctx
+
+
+def lbm_halo_bytes(ctx) -> int:
+    n = ctypes.c_int64()
+    _check(ctx, load().lbm_halo_bytes(ctx, ctypes.byref(n)))
+    return int(n.value)
+
+
+def _dev_ptr(t, name):
+    if t is None:
+        return None
+    if not _is_torch_cuda(t) or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def lbm_halo_pack(ctx, to_lower, to_upper):
+    """Device tensors of lbm_halo_bytes bytes (or None where the slab has no neighbour)."""
+    _check(ctx, load().lbm_halo_pack(ctx, _dev_ptr(to_lower, "to_lower"), _dev_ptr(to_upper, "to_upper")))
+
+
+def lbm_halo_unpack(ctx, from_lower, from_upper):
+    _check(ctx, load().lbm_halo_unpack(ctx, _dev_ptr(from_lower, "from_lower"), _dev_ptr(from_upper, "from_upper")))
+
+
 def lbm_init(ctx, U0, dU0dx, dU0dy, B0=None, u0=None):
     a = [_arr(U0, "U0"), _arr(dU0dx, "dU0dx"), _arr(dU0dy, "dU0dy"), _arr(B0, "B0"), _arr(u0, "u0")]
     on = _where(*[t[1] for t in a])
@@ -170,6 +209,10 @@ def lbm_init(ctx, U0, dU0dx, dU0dy, B0=None, u0=None):
 
 def lbm_set_step_fusion(ctx, steps_per_pass=2, rows_per_block=64):
     _check(ctx, load().lbm_set_step_fusion(ctx, int(steps_per_pass), int(rows_per_block)))
+
+
+def lbm_set_staging(ctx, mode=1):
+    _check(ctx, load().lbm_set_staging(ctx, int(mode)))
 
 
 def lbm_set_fp64_split(ctx, level):
@@ -428,6 +471,9 @@ class Lattice:
 
     def set_step_fusion(self, steps_per_pass=2, rows_per_block=64):
         lbm_set_step_fusion(self.ctx, steps_per_pass, rows_per_block)
+
+    def set_staging(self, mode=1):
+        lbm_set_staging(self.ctx, mode)
 
     def set_fp64_split(self, level):
         lbm_set_fp64_split(self.ctx, level)

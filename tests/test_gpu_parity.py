@@ -236,20 +236,48 @@ def test_moment_space_storage_dirichlet_with_forcing(lbm, storage, tol):
 
 
 @pytest.mark.parametrize("dirichlet", [False, True])
-@pytest.mark.parametrize("nx,ny", [(5, 3), (67, 45), (1031, 7), (130, 70), (31, 200)])
+@pytest.mark.parametrize("nx,ny", [(5, 3), (2, 2), (67, 45), (1031, 7), (130, 70), (31, 200), (241, 37),
+                                   (360, 19), (121, 66)])
 def test_two_step_fusion_fp32_is_bit_identical(lbm, dirichlet, nx, ny):
-    """The fused two-step kernel equals two single steps exactly in FP32 (even and odd step counts)."""
+    """Both fused two-step kernels (rows staged by tensor copies, and register prefetch) equal
+    two single steps exactly in FP32 (even and odd step counts; tiles of 120 columns with a
+    ragged last tile, the lattice's wrap columns, blocks of 16 rows with a ragged last block)."""
     rng = np.random.default_rng(nx + 1000 * ny)
     f = rng.standard_normal((4, 5, ny, nx)) * 1e-3
     outs = []
-    for fuse in (1, 2):
+    for fuse, staging in ((1, 1), (2, 0), (2, 1)):
         lat = lbm.Lattice(nx, ny, 0.1, 0.1 / 3.2, 1.0, 0.6, dirichlet=dirichlet, storage="f32",
                           track_displacement=False)
         lat.set_step_fusion(fuse, 16)
+        lat.set_staging(staging)
         lat.set_populations(f)
         lat.step(9)
+        lat.synchronize()
         g, _ = lat.populations()
         outs.append(g)
+        lat.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("dirichlet", [False, True])
+@pytest.mark.parametrize("nx,ny", [(5, 3), (130, 70), (361, 41)])
+def test_two_step_fusion_16bit_staged_equals_register_prefetch(lbm, storage, dirichlet, nx, ny):
+    """16-bit populations: the staged and the register-prefetch two-step kernels do the same
+    arithmetic (the intermediate step kept in FP32), so their states are identical."""
+    rng = np.random.default_rng(7 * nx + ny)
+    f = rng.standard_normal((4, 5, ny, nx)) * 1e-3
+    outs = []
+    for staging in (0, 1):
+        lat = lbm.Lattice(nx, ny, 0.1, 0.1 / 3.2, 1.0, 0.6, dirichlet=dirichlet, storage=storage,
+                          track_displacement=False)
+        lat.set_step_fusion(2, 16)
+        lat.set_staging(staging)
+        lat.set_populations(f)
+        lat.step(8)
+        lat.synchronize()
+        outs.append(lat.populations()[0])
         lat.close()
     np.testing.assert_array_equal(outs[0], outs[1])
 
@@ -268,6 +296,37 @@ def test_two_step_fusion_16bit_against_oracle(lbm, storage, tol):
         lat.set_step_fusion(fuse, 64)
         lat.init(wl.U0, wl.dU0dx, wl.dU0dy)
         lat.step(200)
+        errs[fuse] = max(field_errors(lat.moments(), ref, fields=range(5)))
+        lat.close()
+    assert errs[2] < tol and errs[2] <= 1.2 * errs[1], errs
+
+
+@pytest.mark.parametrize("storage,tol", [("ms_bf16", 1e-2), ("ms_f16", 1e-3)])
+@pytest.mark.parametrize("dirichlet", [False, True])
+def test_two_step_fusion_moment_space_against_oracle(lbm, storage, tol, dirichlet):
+    """Moment-space storage advanced two steps per pass by the staged kernel: the moment
+    fields against the FP64 oracle (periodic GRF on 250 x 64, three tiles of 120 columns
+    with a ragged last one; Dirichlet: the homogeneous box of Sec. 6.2 on 96 x 96), no worse
+    than one kernel per step."""
+    if dirichlet:
+        wl = W.energy_box(96, 1.1, 0.4, 1.0 / 240.0, 0)
+    else:
+        wl = W.grf_periodic(250, 64, 1.5, 0.5, ell=8.0, std=1e-3, seeds=(5, 6), steps=0)
+    steps = 120
+    o = Oracle(Params(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet))
+    o.init(wl.U0, wl.dU0dx, wl.dU0dy)
+    for _ in range(steps):
+        o.step(track_displacement=False)
+    ref = o.moments()
+    errs = {}
+    for fuse in (1, 2):
+        lat = lbm.Lattice(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet=dirichlet, storage=storage,
+                          track_displacement=False)
+        lat.set_step_fusion(fuse, 16)
+        lat.init(wl.U0, wl.dU0dx, wl.dU0dy)
+        lat.step(steps - 1)                 # an odd count: the last step runs alone
+        lat.step(1)
+        lat.synchronize()
         errs[fuse] = max(field_errors(lat.moments(), ref, fields=range(5)))
         lat.close()
     assert errs[2] < tol and errs[2] <= 1.2 * errs[1], errs
@@ -421,3 +480,32 @@ def test_largest_row_count(lbm, storage, tol):
     g, _ = lat.populations()
     lat.close()
     np.testing.assert_allclose(g, o.f, rtol=0, atol=tol * np.max(np.abs(o.f)))
+
+
+def test_staged_two_step_kernel_reports_a_wait_that_runs_out(lbm):
+    """Test hook: the producer withholds one staged row, so every compute warp's bounded
+    wait runs out (about 2 s); lbm_synchronize reports LBM_ERR_TIMEOUT once, the context
+    stays usable, and a re-initialised lattice steps correctly afterwards."""
+    nx, ny = 100, 12                        # one block of 120 columns x 64 rows
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal((4, 5, ny, nx)) * 1e-3
+    lat = lbm.Lattice(nx, ny, 0.1, 0.1 / 3.2, 1.0, 0.6, storage="f32", track_displacement=False)
+    lat.set_populations(f)
+    lat.set_staging(2)
+    lat.step(2)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.synchronize()
+    assert e.value.status == lbm.LBM_ERR_TIMEOUT
+    lat.synchronize()                       # the flag was cleared
+    lat.set_staging(1)
+    lat.set_populations(f)
+    lat.step(4)
+    lat.synchronize()
+    got = lat.populations()[0]
+    ref = lbm.Lattice(nx, ny, 0.1, 0.1 / 3.2, 1.0, 0.6, storage="f32", track_displacement=False)
+    ref.set_step_fusion(1, 64)
+    ref.set_populations(f)
+    ref.step(4)
+    np.testing.assert_array_equal(got, ref.populations()[0])
+    ref.close()
+    lat.close()
