@@ -274,6 +274,10 @@ def run_surrogate(args):
     errs, pers = S.evaluate(sur, held, batch=16)
     errs_fast, _ = S.evaluate(sur, held, batch=16, act_bf16=True)
     tm = S.timing(sur, n=16, H=256, W=256)
+    drv = S.driver_timing(sur, held, check_every=(1, 4, 16), tol=1e-3, storage="f32", n=16)
+    for v in drv.values():
+        v["net_gain_vs_f32"] = round(tm["lbm_f32_ms_per_lattice"] / v["ms_per_lattice_jump"], 3)
+        v["net_gain_vs_f64"] = round(tm["lbm_f64_ms_per_lattice"] / v["ms_per_lattice_jump"], 3)
     del held
     torch.cuda.empty_cache()
     med = float(np.median(errs))
@@ -287,6 +291,9 @@ def run_surrogate(args):
             "lbm_f64_ms_per_lattice": round(tm["lbm_f64_ms_per_lattice"], 4),
             "lbm_f32_ms_per_lattice": round(tm["lbm_f32_ms_per_lattice"], 4),
             "gain_vs_f64": round(tm["gain_vs_f64"], 3), "gain_vs_f32": round(tm["gain_vs_f32"], 3),
+            "driver": {"what": "whole fallback-driver jumps per lattice (batch 16): inference + FP32 solver check "
+                               "every N jumps + fallback copies, keyed by N; net gain = solver ms / driver ms",
+                       "by_check_interval": drv},
             "bf16_activations": {"heldout_rel_l2_median": float(np.median(errs_fast)),
                                  "surrogate_ms_per_lattice": round(tm["surrogate_bf16_act_ms_per_lattice"], 4),
                                  "gain_vs_f64": round(tm["gain_bf16_act_vs_f64"], 3),
@@ -370,6 +377,34 @@ def run_ours(args):
         results[storage] = {"ms_per_step": ms / args.steps, "mlups": mlups_rank * ws,
                             "steps_per_pass": 2 if fused else 1,
                             "launches": (args.steps // 2 + args.steps % 2) if fused else args.steps}
+
+    # N > 1: one lattice of nx x (N ny) rows split into row slabs, one per rank, with the halo
+    # exchange of the streaming step (5 values per column and cut each way) over NCCL every
+    # step; every rank's slab starts from the same periodic tile, so the global initial field
+    # is the tile repeated N times along y (smooth and periodic, weak scaling)
+    slabs = None
+    if ws > 1 and args.multi == "slabs":
+        from paper_2408_01081_gb300 import slab as SL
+        sl = SL.DistributedSlab(dist, nx, ny * ws, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet=False, storage="f64",
+                                track_displacement=False)
+        sl.init(U0, Ux, Uy)
+        sl.step(args.warmup)
+        barrier()
+        clk = Clocks(local)
+        clk.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sl.step(args.steps)
+        e1.record(stream)
+        barrier()
+        clocks = clk.stop()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        sl.close()
+        slabs = {"ms_per_step": ms / args.steps, "mlups": n_nodes * ws * args.steps / (ms * 1e-3) / 1e6,
+                 "global_lattice": f"{nx}x{ny * ws}", "rows_per_rank": ny,
+                 "halo_bytes_per_step_per_cut_each_way": 5 * nx * 8,
+                 "launches_per_step": 3, "exchange": "NCCL send/recv (torch.distributed.batch_isend_irecv)"}
 
     # the FP64 step with every operation on the FP64 pipe (split level 0), for reference
     if "f64" in args.formats:
@@ -536,14 +571,20 @@ def run_ours(args):
         cpu = {"value": round(mlups_cpu, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
                "sample": f"FP64 C oracle, {cx}x{cy} periodic lattice of the same workload, "
                          f"{args.cpu_steps} steps ({wall:.1f} s)"}
-    line = {"metric": METRIC, "value": round(r64["mlups"], 1), "unit": "MLUPS", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r64["ms_per_step"], 4),
+    head = slabs if slabs is not None else r64
+    line = {"metric": METRIC, "value": round(head["mlups"], 1), "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(head["ms_per_step"], 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": _workload_desc(nx, ny), "nodes": n_nodes, "storage": "f64",
-                       "parallelism": "replicas" if ws > 1 else "single",
+            "config": {"workload": _workload_desc(nx, ny) + (
+                           f"; {ws} row slabs of one {nx}x{ny * ws} lattice (the tile repeated along y)"
+                           if slabs is not None else ""),
+                       "nodes": n_nodes * (ws if slabs is not None else 1), "storage": "f64",
+                       "parallelism": ("row slabs, NCCL halo exchange" if slabs is not None else
+                                       "replicas" if ws > 1 else "single"),
                        "l2": f"inputs larger than L2: state {2 * 20 * n_nodes * 8 / 1e9:.1f} GB double-buffered"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 3 * args.steps if slabs is not None else args.steps, "slabs": slabs,
             "clocks": clocks, "mixed_precision": mixed, "batch": batch, "surrogate": surrogate,
             "precision_run": None if precision is None else
             {"workload": _workload_desc(nx, ny), "steps": precision["steps"], "checkpoints": precision["checkpoints"],
@@ -564,13 +605,15 @@ def main():
     ap.add_argument("--nx", type=int, default=NX)
     ap.add_argument("--ny", type=int, default=NY)
     ap.add_argument("--formats", default="f64,f32,bf16,f16,ms_bf16,ms_f16")
+    ap.add_argument("--multi", default="slabs", choices=["slabs", "replicas"],
+                    help="N > 1: FP64 line as row slabs of one lattice (halo exchange) or independent replicas")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-fusion", action="store_true", help="one kernel per step for every format")
     ap.add_argument("--fuse-formats", default="", help="formats advanced two steps per pass besides the default")
     ap.add_argument("--staging", type=int, default=1, help="two-step kernel: 1 rows staged by tensor copies, 0 registers")
-    ap.add_argument("--rows-per-block", type=int, default=64)
+    ap.add_argument("--rows-per-block", type=int, default=32)
     ap.add_argument("--batch-count", type=int, default=512, help="lattices in the batch leg")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-budget", type=float, default=60.0, help="surrogate training seconds")

@@ -94,7 +94,7 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const d
  * step, one kernel per step runs.  FP32 results are bit-identical to single
  * steps; 16-bit and moment-space results skip one rounding per pair and are more
  * accurate.
- * rows_per_block (default 64) sets the rows each thread block streams through.
+ * rows_per_block (default 32) sets the rows each thread block streams through.
  * steps_per_pass = 1 always uses one kernel per step. */
 lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t rows_per_block);
 

@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -194,9 +195,11 @@ struct lbm_ctx {
     double omega = 2.0;
     double neq_scale = 1.0;      // moment-space storage: scale of the stored deviations
     int fuse = 1;                // steps per pass over memory when the fused kernel applies
-    int tb_rows = 64;            // rows per block of the fused kernel
+    int tb_rows = 32;            // rows per block of the fused kernel
     int split = 1;               // FP64: split level (which additions run on the integer pipes)
     int staging = 1;             // fused kernel: 1 = rows staged by tensor copies, 0 = register prefetch
+    int l2_ahead = lbmk::TBT_L2_AHEAD;   // staged kernel: rows prefetched into L2 ahead of the ring
+                                         // (environment LBM_TBT_L2_AHEAD, 0..64, read at lbm_create)
     int nyi = 0;                 // rows of the lattice's own (a slab: without its halo rows)
     int yo = 0;                  // storage row of own row 0 (1 when a halo row sits below)
     bool slab = false;           // a row slab of a larger lattice (lbm_create_slab)
@@ -379,6 +382,10 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
     }
     ctx->p = *p;
     ctx->nyi = p->ny;
+    if (const char* v = std::getenv("LBM_TBT_L2_AHEAD")) {
+        const int a = std::atoi(v);
+        if (a >= 0 && a <= 64) ctx->l2_ahead = a;
+    }
     ctx->s = static_cast<cudaStream_t>(p->stream);
     ctx->ops = ops_for(p->storage);
     ctx->pitch = (p->nx + 63) / 64 * 64;
@@ -806,6 +813,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
             Q.rows = ctx->tb_rows;
             Q.timeout = reinterpret_cast<int*>(ctx->scratch + kTimeoutSlot);
             Q.withhold = ctx->staging == 2 ? 2 : -1;
+            Q.l2_ahead = ctx->l2_ahead;
             Q.scale = (float)ctx->neq_scale;
             Q.inv_s = (float)(1.0 / ctx->neq_scale);
             const dim3 qgrid((ctx->p.nx + lbmk::TBT_OUT - 1) / lbmk::TBT_OUT, (ctx->p.ny + Q.rows - 1) / Q.rows);

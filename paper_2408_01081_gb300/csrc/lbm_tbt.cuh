@@ -39,9 +39,11 @@ struct TbtArgs {
     int* timeout;          // device flag: set when a bounded wait ran out
     int withhold;          // test hook: staged input row the producer never copies (-1: none)
     float scale, inv_s;    // moment-space storage: scale of the stored deviations and its reciprocal
+    int l2_ahead;          // rows prefetched into L2 ahead of the row the ring loads (0: none)
 };
 
 constexpr int TBT_WARPS = 4;                  // compute warps per block
+constexpr int TBT_L2_AHEAD = 8;               // default rows the producer prefetches into L2 beyond the ring
 constexpr int TBT_OUT = TBT_WARPS * TB_OUT;   // output columns per block (120)
 constexpr int TBT_THREADS = 32 * (TBT_WARPS + 1);
 
@@ -92,6 +94,11 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_kernel(const __grid_consta
         // ---- producer: one tensor copy per input row, as far ahead as the ring allows ----
         if (lane == 0) {
             lbmt::prefetch_map(&map);
+            for (int jp = NST; jp < NST + A.l2_ahead && jp < nin; ++jp) {
+                const int yp = y0 - 2 + jp;
+                if (!DIRICHLET || (yp >= 0 && yp < ny))
+                    lbmt::tma_prefetch_3d(&map, X0 - HL, (yp < 0) ? yp + ny : (yp >= ny ? yp - ny : yp), 0);
+            }
             int j = 0;
             for (; j < nin; ++j) {
                 const int s = j % NST;
@@ -99,6 +106,13 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_kernel(const __grid_consta
                 if (j == A.withhold) continue;               // test hook: this row never arrives
                 if (j >= NST && !lbmt::mbar_wait(lbmt::smem_u32(&empty_bar[s]), ((j / NST) - 1) & 1, &abort_flag))
                     break;
+                {
+                    // the row the ring will reach l2_ahead copies later: into L2 now
+                    const int jp = j + A.l2_ahead;
+                    const int yp = y0 - 2 + jp;
+                    if (j >= NST && A.l2_ahead > 0 && jp < nin && (!DIRICHLET || (yp >= 0 && yp < ny)))
+                        lbmt::tma_prefetch_3d(&map, X0 - HL, (yp < 0) ? yp + ny : (yp >= ny ? yp - ny : yp), 0);
+                }
                 int y = y0 - 2 + j;
                 if (DIRICHLET && (y < 0 || y >= ny)) {
                     lbmt::mbar_arrive(fb);                   // row outside the lattice: never read
@@ -338,6 +352,15 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
         if (lane == 0) {
             lbmt::prefetch_map(&map32);
             lbmt::prefetch_map(&map16);
+            auto l2_row = [&](int jp) {
+                const int yp = y0 - 2 + jp;
+                if (jp < nin && (!DIRICHLET || (yp >= 0 && yp < ny))) {
+                    const int yw = (yp < 0) ? yp + ny : (yp >= ny ? yp - ny : yp);
+                    lbmt::tma_prefetch_3d(&map32, X0 - HL, yw, 0);
+                    lbmt::tma_prefetch_3d(&map16, X0 - HL, yw, 0);
+                }
+            };
+            for (int jp = NST; jp < NST + A.l2_ahead; ++jp) l2_row(jp);
             int j = 0;
             for (; j < nin; ++j) {
                 const int s = j % NST;
@@ -345,6 +368,7 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
                 if (j == A.withhold) continue;
                 if (j >= NST && !lbmt::mbar_wait(lbmt::smem_u32(&empty_bar[s]), ((j / NST) - 1) & 1, &abort_flag))
                     break;
+                if (j >= NST && A.l2_ahead > 0) l2_row(j + A.l2_ahead);
                 int y = y0 - 2 + j;
                 if (DIRICHLET && (y < 0 || y >= ny)) {
                     lbmt::mbar_arrive(fb);

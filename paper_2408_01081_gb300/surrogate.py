@@ -410,9 +410,11 @@ def _descs_for(nu, H, W, cfl=0.9):
     return out
 
 
-def relift_and_step(U, nu, k, storage="f64"):
+def relift_and_step(U, nu, k, storage="f64", batch=None):
     """The solver as reference: re-initialise populations from U (Eq. ic_second with periodic
-    central-difference derivatives) and run k steps.  U: [n, 10, H, W] FP64 device tensor."""
+    central-difference derivatives) and run k steps.  U: [n, 10, H, W] FP64 device tensor.
+    ``batch``: a lattice batch made for these lattices (lbm_batch_create), reused across
+    calls; without it one is created and destroyed here."""
     import torch
     n, _, H, W = U.shape
     descs = _descs_for(nu, H, W)
@@ -421,7 +423,8 @@ def relift_and_step(U, nu, k, storage="f64"):
     dUx = torch.zeros_like(U)
     dUy = torch.zeros_like(U)
     K.gradient(U, stride, NF, n, H, W, dx, dUx, dUy)
-    b = L.lbm_batch_create(descs, storage=L.STORAGE[storage], stream=torch.cuda.current_stream().cuda_stream)
+    b = batch if batch is not None else L.lbm_batch_create(descs, storage=L.STORAGE[storage],
+                                                           stream=torch.cuda.current_stream().cuda_stream)
     out = torch.empty_like(U)
     try:
         for i in range(n):
@@ -431,7 +434,8 @@ def relift_and_step(U, nu, k, storage="f64"):
             L.lbm_batch_moments(b, i, out[i])
         L.lbm_batch_synchronize(b)
     finally:
-        L.lbm_batch_destroy(b)
+        if batch is None:
+            L.lbm_batch_destroy(b)
     return out
 
 
@@ -445,6 +449,23 @@ class FallbackDriver:
         self.jumps = 0
         self.fallbacks = 0
         self.checked = 0
+        self._batch, self._key = None, None
+
+    def close(self):
+        if self._batch is not None:
+            L.lbm_batch_destroy(self._batch)
+            self._batch, self._key = None, None
+
+    def _solver(self, nu, H, W):
+        """The solver batch for these lattices, made once and reused by later checks."""
+        import torch
+        key = (tuple(float(v) for v in nu), H, W)
+        if key != self._key:
+            self.close()
+            self._batch = L.lbm_batch_create(_descs_for(nu, H, W), storage=L.STORAGE[self.storage],
+                                             stream=torch.cuda.current_stream().cuda_stream)
+            self._key = key
+        return self._batch
 
     def jump(self, U, nu):
         import torch
@@ -461,12 +482,12 @@ class FallbackDriver:
         except L.LbmError as e:
             if e.status != L.LBM_ERR_TIMEOUT:
                 raise
-            ref = relift_and_step(U, nu, self.sur.k, self.storage)
+            ref = relift_and_step(U, nu, self.sur.k, self.storage, self._solver(nu, H, W))
             self.fallbacks += n
             return ref, None
         errs = None
         if self.check_every and self.jumps % self.check_every == 0:
-            ref = relift_and_step(U, nu, self.sur.k, self.storage)
+            ref = relift_and_step(U, nu, self.sur.k, self.storage, self._solver(nu, H, W))
             errs = relative_error(self.sur, pred, ref, stride, n, H, W)
             self.checked += n
             for i, e in enumerate(errs):
@@ -474,6 +495,39 @@ class FallbackDriver:
                     pred[i].copy_(ref[i])
                     self.fallbacks += 1
         return pred, errs
+
+
+def driver_timing(sur, chunk, check_every=(1, 4, 16), tol=1e-3, storage="f32", n=16):
+    """Wall-clock of whole fallback-driver jumps on held-out lattices, per lattice and jump,
+    everything included: inference, the solver's check every `check_every` jumps and the
+    fallback copies.  Each jump starts from the solver's snapshot of the chunk.  Returns, per
+    check interval, ms per lattice and jump, the fraction of checked lattices that fell back,
+    and the median checked error."""
+    import time
+    import torch
+    H, W = chunk.U.shape[-2:]
+    n = min(n, chunk.n)
+    nu = chunk.nu[:n]
+    out = {}
+    for ce in check_every:
+        drv = FallbackDriver(sur, tol=tol, check_every=ce, storage=storage)
+        drv.jump(chunk.U[0, :n].contiguous(), nu)           # warm-up: builds the solver batch
+        drv.jumps = drv.fallbacks = drv.checked = 0
+        errs = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j in range(chunk.J):
+            for _ in range(ce):
+                _, e = drv.jump(chunk.U[j, :n], nu)
+                if e is not None:
+                    errs.extend(e)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[str(ce)] = {"ms_per_lattice_jump": 1e3 * dt / (drv.jumps * n), "jumps": drv.jumps,
+                        "checked_lattices": drv.checked, "fallback_fraction": drv.fallbacks / max(1, drv.checked),
+                        "median_checked_error": float(np.median(errs)) if errs else None}
+        drv.close()
+    return out
 
 
 def timing(sur, n=16, H=256, W=256, reps=5):
