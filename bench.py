@@ -42,7 +42,7 @@ BYTES_PER_NODE = {"f64": 320, "f32": 160, "bf16": 80, "f16": 80,    # one read +
 FP64_OPS_PER_NODE = 47                                                # DADD/DFMA per node, no forcing
 SPLIT_LEVEL = 1               # lbm_set_fp64_split default: the 15 sums of a node on the integer pipe
 SPLIT_INTEGER_ADDS = 15
-FUSED = {"f32"}      # formats the library advances two steps per pass by default (lbm_set_step_fusion)
+FUSED = {"f32", "bf16", "f16", "ms_bf16", "ms_f16"}   # formats the library advances two steps per pass by default
 # DRAM bytes per node and launch (dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of
 # 4096x2048, scaled by the node count); valid only while the kernel sources hash to "sha256".
 # "f32_fused" is one launch of the two-step kernel.
@@ -613,7 +613,7 @@ def main():
     ap.add_argument("--no-fusion", action="store_true", help="one kernel per step for every format")
     ap.add_argument("--fuse-formats", default="", help="formats advanced two steps per pass besides the default")
     ap.add_argument("--staging", type=int, default=1, help="two-step kernel: 1 rows staged by tensor copies, 0 registers")
-    ap.add_argument("--rows-per-block", type=int, default=32)
+    ap.add_argument("--rows-per-block", type=int, default=0, help="two-step kernel rows per block (0: library default)")
     ap.add_argument("--batch-count", type=int, default=512, help="lattices in the batch leg")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-budget", type=float, default=60.0, help="surrogate training seconds")

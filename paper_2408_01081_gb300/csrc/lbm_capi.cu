@@ -195,7 +195,7 @@ struct lbm_ctx {
     double omega = 2.0;
     double neq_scale = 1.0;      // moment-space storage: scale of the stored deviations
     int fuse = 1;                // steps per pass over memory when the fused kernel applies
-    int tb_rows = 32;            // rows per block of the fused kernel
+    int tb_rows = 16;            // rows per block of the fused kernel
     int split = 1;               // FP64: split level (which additions run on the integer pipes)
     int staging = 1;             // fused kernel: 1 = rows staged by tensor copies, 0 = register prefetch
     int l2_ahead = lbmk::TBT_L2_AHEAD;   // staged kernel: rows prefetched into L2 ahead of the ring
@@ -394,7 +394,10 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
     ctx->a = p->cK / c;
     ctx->b = p->cmu / c;
     ctx->nwall = 2 * (p->nx + p->ny);
-    ctx->fuse = (p->storage == LBM_F32) ? 2 : 1;   // measured faster than single steps only for FP32
+    // two steps per pass for every reduced format (the staged kernel is faster than single steps
+    // for each of them); rows per block measured best per format at 8192^2
+    ctx->fuse = (p->storage == LBM_F64) ? 1 : 2;
+    ctx->tb_rows = (p->storage == LBM_F32) ? 8 : 32;
     // symmetrizer blocks k_ij = g_ij^{-1}, g_ij = 1/4 I + (i A_x + j A_y)/(2c)  (Eq. stability_linear)
     const int VI[4] = {1, 0, -1, 0}, VJ[4] = {0, 1, 0, -1};
     for (int d = 0; d < 4; ++d) {
@@ -585,10 +588,10 @@ lbm_status lbm_set_staging(lbm_ctx* ctx, int32_t mode)
 lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t rows_per_block)
 {
     LBM_CHECK_CTX(ctx);
-    if ((steps_per_pass != 1 && steps_per_pass != 2) || rows_per_block < 1 || rows_per_block > 65535)
-        return fail(ctx, LBM_ERR_ARG, "steps_per_pass must be 1 or 2 and rows_per_block in [1, 65535]");
+    if ((steps_per_pass != 1 && steps_per_pass != 2) || rows_per_block < 0 || rows_per_block > 65535)
+        return fail(ctx, LBM_ERR_ARG, "steps_per_pass must be 1 or 2 and rows_per_block in [0, 65535]");
     ctx->fuse = steps_per_pass;
-    ctx->tb_rows = rows_per_block;
+    if (rows_per_block > 0) ctx->tb_rows = rows_per_block;
     return LBM_OK;
 }
 

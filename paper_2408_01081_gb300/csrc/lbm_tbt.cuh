@@ -42,8 +42,23 @@ struct TbtArgs {
     int l2_ahead;          // rows prefetched into L2 ahead of the row the ring loads (0: none)
 };
 
+// stages of the row ring: FP32 rows (10 KB), 16-bit rows (5.4 KB), moment-space rows (6.8 KB).
+// Measured at 8192^2 (GB300): 4 to 12 stages change the rate by a few per cent at most; FP32
+// is fastest with 7, the 16-bit and moment-space formats with 4 (the shallow ring leaves the
+// register file, not shared memory, as the occupancy limit)
+#ifndef LBM_TBT_NST4
+#define LBM_TBT_NST4 7
+#endif
+#ifndef LBM_TBT_NST2
+#define LBM_TBT_NST2 4
+#endif
+#ifndef LBM_TBT_NSTMS
+#define LBM_TBT_NSTMS 4
+#endif
+
 constexpr int TBT_WARPS = 4;                  // compute warps per block
-constexpr int TBT_L2_AHEAD = 8;               // default rows the producer prefetches into L2 beyond the ring
+constexpr int TBT_L2_AHEAD = 0;               // default rows the producer prefetches into L2 beyond the ring
+                                              // (measured: any prefetch distance made the kernels slower)
 constexpr int TBT_OUT = TBT_WARPS * TB_OUT;   // output columns per block (120)
 constexpr int TBT_THREADS = 32 * (TBT_WARPS + 1);
 
@@ -53,7 +68,7 @@ struct TbtGeom {
     static constexpr int WIN = HL + TBT_OUT + HL;                      // staged columns per row
     static constexpr int ROW_BYTES = 20 * WIN * ES;                    // one row of the 20 planes
     static constexpr int STAGE_BYTES = (ROW_BYTES + 127) / 128 * 128;  // stage starts 128-byte aligned
-    static constexpr int NST = (ES == 4) ? 5 : 6;                      // stages in the ring
+    static constexpr int NST = (ES == 4) ? LBM_TBT_NST4 : LBM_TBT_NST2; // stages in the ring
     static constexpr int SMEM = NST * STAGE_BYTES + 128;               // dynamic shared memory per block
                                                                        // (+128: the ring starts 128-B aligned)
     static_assert((WIN * ES) % 16 == 0, "staged row width must be a multiple of 16 bytes");
@@ -78,7 +93,6 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_kernel(const __grid_consta
     const int nin = (y1 - y0) + 4;                   // staged input rows y0-2 .. y1+1
     const uint32_t raw = lbmt::smem_u32(tbt_smem_raw);
     const uint32_t sbase = (raw + 127u) & ~127u;                    // 128-byte aligned ring
-    unsigned char* tbt_smem = tbt_smem_raw + (sbase - raw);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
@@ -159,9 +173,11 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_kernel(const __grid_consta
             ok = ok && lbmt::mbar_wait(lbmt::smem_u32(&full_bar[j % NST]), (j / NST) & 1, &abort_flag);
         }
         if (!__all_sync(0xffffffffu, ok)) break;
-        const E* rm = reinterpret_cast<const E*>(tbt_smem + (i % NST) * G::STAGE_BYTES);
-        const E* rc = reinterpret_cast<const E*>(tbt_smem + ((i + 1) % NST) * G::STAGE_BYTES);
-        const E* rp = reinterpret_cast<const E*>(tbt_smem + ((i + 2) % NST) * G::STAGE_BYTES);
+        // shared addresses of this lane's column in the staged rows r-1, r, r+1
+        constexpr uint32_t ES = sizeof(E), PL = WIN * sizeof(E);
+        const uint32_t rm = sbase + (i % NST) * G::STAGE_BYTES + idx * ES;
+        const uint32_t rc = sbase + ((i + 1) % NST) * G::STAGE_BYTES + idx * ES;
+        const uint32_t rp = sbase + ((i + 2) % NST) * G::STAGE_BYTES + idx * ES;
         // ---- S1(r) at column xc ----
         float cur[4][5];
         const bool row_ok = DIRICHLET ? (r >= 0 && r < ny) : true;
@@ -170,10 +186,10 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_kernel(const __grid_consta
             if (staged) {
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
-                    f[0][k] = Fmt<K>::ld(rc[(0 * 5 + k) * WIN + idx - 1]);
-                    f[2][k] = Fmt<K>::ld(rc[(2 * 5 + k) * WIN + idx + 1]);
-                    f[1][k] = Fmt<K>::ld(rm[(1 * 5 + k) * WIN + idx]);
-                    f[3][k] = Fmt<K>::ld(rp[(3 * 5 + k) * WIN + idx]);
+                    f[0][k] = Fmt<K>::ld(lbmt::lds<E>(rc + (0 * 5 + k) * PL - ES));
+                    f[2][k] = Fmt<K>::ld(lbmt::lds<E>(rc + (2 * 5 + k) * PL + ES));
+                    f[1][k] = Fmt<K>::ld(lbmt::lds<E>(rm + (1 * 5 + k) * PL));
+                    f[3][k] = Fmt<K>::ld(lbmt::lds<E>(rp + (3 * 5 + k) * PL));
                 }
             } else {
                 // periodic wrap around x = 0 / x = nx - 1: read the wrapped columns directly
@@ -192,10 +208,10 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_kernel(const __grid_consta
                 const bool bot = r == 0, top = r == ny - 1;
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
-                    if (xc == 0) f[0][k] = Dk[k] * Fmt<K>::ld(rc[(2 * 5 + k) * WIN + idx]);
-                    if (xc == nx - 1) f[2][k] = Dk[k] * Fmt<K>::ld(rc[(0 * 5 + k) * WIN + idx]);
-                    if (bot) f[1][k] = Dk[k] * Fmt<K>::ld(rc[(3 * 5 + k) * WIN + idx]);
-                    if (top) f[3][k] = Dk[k] * Fmt<K>::ld(rc[(1 * 5 + k) * WIN + idx]);
+                    if (xc == 0) f[0][k] = Dk[k] * Fmt<K>::ld(lbmt::lds<E>(rc + (2 * 5 + k) * PL));
+                    if (xc == nx - 1) f[2][k] = Dk[k] * Fmt<K>::ld(lbmt::lds<E>(rc + (0 * 5 + k) * PL));
+                    if (bot) f[1][k] = Dk[k] * Fmt<K>::ld(lbmt::lds<E>(rc + (3 * 5 + k) * PL));
+                    if (top) f[3][k] = Dk[k] * Fmt<K>::ld(lbmt::lds<E>(rc + (1 * 5 + k) * PL));
                 }
             }
             float U[5], rx[5], ry2[5];
@@ -271,7 +287,7 @@ struct TbtMsGeom {
     static constexpr int DEV_BYTES = 15 * WIN * 2;
     static constexpr int ROW_BYTES = M0_BYTES + DEV_BYTES;             // bytes the two copies bring
     static constexpr int STAGE_BYTES = (DEV_OFF + DEV_BYTES + 127) / 128 * 128;
-    static constexpr int NST = 6;
+    static constexpr int NST = LBM_TBT_NSTMS;
     static constexpr int SMEM = NST * STAGE_BYTES + 128;
     static_assert((WIN * 4) % 16 == 0 && (WIN * 2) % 16 == 0, "staged row width must be a multiple of 16 bytes");
 };
@@ -283,17 +299,16 @@ struct MsNode {
 };
 
 template <int H>
-__device__ __forceinline__ void ms_node_smem(const unsigned char* stage, int c, float inv_s, MsNode& n)
+__device__ __forceinline__ void ms_node_smem(uint32_t stage, int c, float inv_s, MsNode& n)
 {
-    const float* m0 = reinterpret_cast<const float*>(stage);
-    const unsigned short* dv = reinterpret_cast<const unsigned short*>(stage + TbtMsGeom::DEV_OFF);
-    constexpr int W = TbtMsGeom::WIN;
+    constexpr uint32_t W = TbtMsGeom::WIN;
+    const uint32_t m0 = stage + 4u * c, dv = stage + TbtMsGeom::DEV_OFF + 2u * c;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        n.m0[k] = m0[k * W + c];
-        n.dx[k] = Fmt<H>::ld(dv[k * W + c]) * inv_s;
-        n.dy[k] = Fmt<H>::ld(dv[(5 + k) * W + c]) * inv_s;
-        n.dd[k] = Fmt<H>::ld(dv[(10 + k) * W + c]) * inv_s;
+        n.m0[k] = lbmt::lds_f32(m0 + 4u * W * k);
+        n.dx[k] = Fmt<H>::ld(lbmt::lds_u16(dv + 2u * W * k)) * inv_s;
+        n.dy[k] = Fmt<H>::ld(lbmt::lds_u16(dv + 2u * W * (5 + k))) * inv_s;
+        n.dd[k] = Fmt<H>::ld(lbmt::lds_u16(dv + 2u * W * (10 + k))) * inv_s;
     }
 }
 
@@ -336,7 +351,6 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
     const int nin = (y1 - y0) + 4;
     const uint32_t raw = lbmt::smem_u32(tbt_smem_raw);
     const uint32_t sbase = (raw + 127u) & ~127u;
-    unsigned char* tbt_smem = tbt_smem_raw + (sbase - raw);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
@@ -413,7 +427,7 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
     if (__all_sync(0xffffffffu, ok)) {
         // f*_(0,1)(t) of the own column in staged row 0 (row y0-2): the pull source of row y0-1
         MsNode n;
-        if (own_staged) ms_node_smem<H>(tbt_smem + 0 * G::STAGE_BYTES, idx, inv_s, n);
+        if (own_staged) ms_node_smem<H>(sbase, idx, inv_s, n);
         else ms_node_global<H>(A.src, plane, (long long)row_of(y0 - 2) * A.pitch + xc, inv_s, n);
         ms_node_dir(n, 1, fa, fb, d1_prev);
     }
@@ -424,8 +438,8 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
             ok = ok && lbmt::mbar_wait(lbmt::smem_u32(&full_bar[j % NST]), (j / NST) & 1, &abort_flag);
         }
         if (!__all_sync(0xffffffffu, ok)) break;
-        const unsigned char* sc = tbt_smem + ((i + 1) % NST) * G::STAGE_BYTES;   // row r
-        const unsigned char* sp = tbt_smem + ((i + 2) % NST) * G::STAGE_BYTES;   // row r+1
+        const uint32_t sc = sbase + ((i + 1) % NST) * G::STAGE_BYTES;   // row r
+        const uint32_t sp = sbase + ((i + 2) % NST) * G::STAGE_BYTES;   // row r+1
         float cur[4][5];
         const bool row_ok = DIRICHLET ? (r >= 0 && r < ny) : true;
         {

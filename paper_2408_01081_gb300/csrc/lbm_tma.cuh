@@ -78,6 +78,25 @@ __device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity)
     return true;
 }
 
+// shared-memory loads by 32-bit shared address (explicitly in the shared state space)
+__device__ __forceinline__ float lds_f32(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned short lds_u16(uint32_t addr)
+{
+    unsigned short v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+template <typename E> __device__ __forceinline__ E lds(uint32_t addr);
+template <> __device__ __forceinline__ float lds<float>(uint32_t addr) { return lds_f32(addr); }
+template <> __device__ __forceinline__ unsigned short lds<unsigned short>(uint32_t addr) { return lds_u16(addr); }
+
 // one 3D tensor copy global -> shared, completion counted in bytes on `bar`
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar)
 {

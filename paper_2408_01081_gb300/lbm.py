@@ -207,7 +207,7 @@ def lbm_init(ctx, U0, dU0dx, dU0dy, B0=None, u0=None):
     _check(ctx, load().lbm_init(ctx, *[t[0] for t in a], on))
 
 
-def lbm_set_step_fusion(ctx, steps_per_pass=2, rows_per_block=32):
+def lbm_set_step_fusion(ctx, steps_per_pass=2, rows_per_block=0):
     _check(ctx, load().lbm_set_step_fusion(ctx, int(steps_per_pass), int(rows_per_block)))
 
 
@@ -469,7 +469,7 @@ class Lattice:
     def init(self, U0, dU0dx, dU0dy, B0=None, u0=None):
         lbm_init(self.ctx, U0, dU0dx, dU0dy, B0, u0)
 
-    def set_step_fusion(self, steps_per_pass=2, rows_per_block=32):
+    def set_step_fusion(self, steps_per_pass=2, rows_per_block=0):
         lbm_set_step_fusion(self.ctx, steps_per_pass, rows_per_block)
 
     def set_staging(self, mode=1):

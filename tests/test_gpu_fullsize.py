@@ -1,7 +1,8 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
 times (periodic, no body load, no displacement tracking):
 
-* periodic 8192^2 GRF, FP64 and FP32: sampled nodes (edges, corners, interior)
+* periodic 8192^2 GRF, every storage format (the reduced ones two steps per pass,
+  the library default): sampled nodes (edges, corners, interior)
   after 3 steps against the oracle run on a periodic patch around each sample
   (the domain of dependence of 3 steps is 3 nodes, the patch is 16 wide);
   properties that hold at any size: sum of U and ||f||_P conserved;
@@ -29,7 +30,8 @@ def grf8192():
     return W.grf_periodic(8192, 8192, 1.5, 0.5, cfl=0.9, ell=64.0, std=1e-3, seeds=(1, 2), steps=3)
 
 
-@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5), ("bf16", 5e-2), ("f16", 5e-3),
+                                         ("ms_bf16", 1e-2), ("ms_f16", 1e-3)])
 def test_periodic_8192_sampled_against_oracle_patches(lbm, grf8192, storage, tol):
     import torch
     wl = grf8192
@@ -67,10 +69,13 @@ def test_periodic_8192_sampled_against_oracle_patches(lbm, grf8192, storage, tol
         ref[0:5, s] = U[:, P // 2, P // 2]
     for q in range(5):
         assert rel_l2(got[q], ref[q]) < tol, (storage, q, rel_l2(got[q], ref[q]))
-    # properties at full size: sum of U and the weighted norm are invariants (periodic, b = 0)
-    atol = 1e-12 if storage == "f64" else 1e-6
-    assert np.all(np.abs(s1 - s0) <= atol * (np.abs(s0) + np.sqrt(n * n) * 1e-3))
-    assert abs(e1 - e0) <= (1e-13 if storage == "f64" else 1e-5) * e0
+    # properties at full size: sum of U and the weighted norm are invariants (periodic, b = 0), up
+    # to the storage format's rounding (populations in 16 bits carry U in 16 bits; the moment
+    # space keeps U itself in FP32)
+    atol = {"f64": 1e-12, "f32": 1e-6, "ms_bf16": 1e-6, "ms_f16": 1e-6, "f16": 1e-3, "bf16": 1e-2}[storage]
+    assert np.all(np.abs(s1 - s0) <= atol * (np.abs(s0) + np.sqrt(n * n) * 1e-3)), (storage, s1 - s0)
+    etol = {"f64": 1e-13, "f32": 1e-5, "ms_bf16": 1e-3, "ms_f16": 1e-4, "f16": 1e-3, "bf16": 1e-2}[storage]
+    assert abs(e1 - e0) <= etol * e0, (storage, (e1 - e0) / e0)
 
 
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 2e-5)])

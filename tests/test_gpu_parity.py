@@ -486,7 +486,7 @@ def test_staged_two_step_kernel_reports_a_wait_that_runs_out(lbm):
     """Test hook: the producer withholds one staged row, so every compute warp's bounded
     wait runs out (about 2 s); lbm_synchronize reports LBM_ERR_TIMEOUT once, the context
     stays usable, and a re-initialised lattice steps correctly afterwards."""
-    nx, ny = 100, 12                        # one block of 120 columns x 64 rows
+    nx, ny = 100, 12                        # one column tile, two blocks of 8 rows
     rng = np.random.default_rng(5)
     f = rng.standard_normal((4, 5, ny, nx)) * 1e-3
     lat = lbm.Lattice(nx, ny, 0.1, 0.1 / 3.2, 1.0, 0.6, storage="f32", track_displacement=False)
