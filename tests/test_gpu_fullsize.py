@@ -30,8 +30,8 @@ def grf8192():
     return W.grf_periodic(8192, 8192, 1.5, 0.5, cfl=0.9, ell=64.0, std=1e-3, seeds=(1, 2), steps=3)
 
 
-@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5), ("bf16", 5e-2), ("f16", 5e-3),
-                                         ("ms_bf16", 1e-2), ("ms_f16", 1e-3)])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5), ("bf16", 1e-2), ("f16", 1.5e-3),
+                                         ("ms_bf16", 5e-3), ("ms_f16", 1e-3)])
 def test_periodic_8192_sampled_against_oracle_patches(lbm, grf8192, storage, tol):
     import torch
     wl = grf8192
@@ -67,8 +67,17 @@ def test_periodic_8192_sampled_against_oracle_patches(lbm, grf8192, storage, tol
             o.step(track_displacement=False)
         U = o.moments()
         ref[0:5, s] = U[:, P // 2, P // 2]
-    for q in range(5):
-        assert rel_l2(got[q], ref[q]) < tol, (storage, q, rel_l2(got[q], ref[q]))
+    if storage in ("f64", "f32"):
+        for q in range(5):
+            assert rel_l2(got[q], ref[q]) < tol, (storage, q, rel_l2(got[q], ref[q]))
+    else:
+        # 16-bit storage quantises every population to about 2^-9 (BF16) or 2^-12 (FP16) of its
+        # size; after 3 steps the stress fields are still about 1 % of the velocities, so their
+        # errors are measured against the velocity scale, the size the quantum is relative to
+        vscale = np.linalg.norm(ref[0:2]) / math.sqrt(2)
+        for q in range(5):
+            err = np.linalg.norm(got[q] - ref[q]) / max(np.linalg.norm(ref[q]), vscale)
+            assert err < tol, (storage, q, err)
     # properties at full size: sum of U and the weighted norm are invariants (periodic, b = 0), up
     # to the storage format's rounding (populations in 16 bits carry U in 16 bits; the moment
     # space keeps U itself in FP32)
