@@ -43,12 +43,16 @@ FP64_OPS_PER_NODE = 47                                                # DADD/DFM
 SPLIT_LEVEL = 1               # lbm_set_fp64_split default: the 15 sums of a node on the integer pipe
 SPLIT_INTEGER_ADDS = 15
 FUSED = {"f32", "bf16", "f16", "ms_bf16", "ms_f16"}   # formats the library advances two steps per pass by default
-# DRAM bytes per node and launch (dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of
-# 4096x2048, scaled by the node count); valid only while the kernel sources hash to "sha256".
-# "f32_fused" is one launch of the two-step kernel.
-TRAFFIC_CAPTURE = {"sha256": "22ff8278f564022134e687af31699f9b283682cba10a995608ed9212f4a7dfa0",
-                   "bytes_per_node": {"f64": 317.16, "f32": 153.31, "f32_fused": 157.58, "bf16": 73.58, "f16": 73.55,
-                                      "ms_f16": 94.48}}
+# DRAM bytes per node and launch of each step kernel (dram__bytes_read.sum + dram__bytes_write.sum
+# from one ncu capture of this benchmark's own 8192^2 workload, averaged over its launches; no
+# scaling), valid only while the kernel sources hash to "sha256".  "<fmt>_fused" is one launch of
+# the two-step kernel (two steps), "f64_pipe" the FP64 step with every operation on the FP64 pipe.
+TRAFFIC_CAPTURE = {"sha256": "a36b2a53d9ea97ec738afd2a84cce9f03c5744d0ce56d38d83ec993ce1540427",
+                   "nodes": 8192 * 8192,
+                   "bytes_per_node": {"f64": 321.56, "f64_pipe": 319.24, "f32": 159.34, "f32_fused": 160.63,
+                                      "bf16": 79.29, "bf16_fused": 84.64, "f16": 79.30, "f16_fused": 84.64,
+                                      "ms_bf16": 99.33, "ms_bf16_fused": 105.19, "ms_f16": 99.32,
+                                      "ms_f16_fused": 105.21}}
 KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_01081_gb300/csrc/lbm_kind.cu",
                   "paper_2408_01081_gb300/csrc/lbm_tb.cuh", "paper_2408_01081_gb300/csrc/lbm_ms.cuh",
                   "paper_2408_01081_gb300/csrc/lbm_tbt.cuh", "paper_2408_01081_gb300/csrc/lbm_tma.cuh"]
@@ -57,7 +61,8 @@ KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_010
 # valid only while the kernel sources hash to "sha256".  Each SM issues 64 ALU-pipe and 2
 # FP64-pipe thread instructions per clock, so one node needs at least
 # max(alu / 64, fp64 / 2) SM clocks: the arithmetic roof of this kernel.
-PIPE_CAPTURE = {"sha256": None, "alu_per_node": None, "fp64_per_node": None, "fma_per_node": None}
+PIPE_CAPTURE = {"sha256": "a36b2a53d9ea97ec738afd2a84cce9f03c5744d0ce56d38d83ec993ce1540427",
+                "alu_per_node": 1127.0, "fp64_per_node": 32.0, "fma_per_node": 260.0}
 ALU_LANES_PER_SM, FP64_LANES_PER_SM, N_SM = 64, 2, 152
 
 
@@ -77,7 +82,10 @@ def pipe_counts():
 
 
 def traffic_per_launch(fmt, nodes):
-    if TRAFFIC_CAPTURE["sha256"] != kernel_digest():
+    """Measured DRAM bytes of one launch, or None when the sources changed since the capture or
+    the lattice is not the captured one (traffic has a fixed L2-resident part, so it is not
+    scaled to other sizes)."""
+    if TRAFFIC_CAPTURE["sha256"] != kernel_digest() or nodes != TRAFFIC_CAPTURE["nodes"]:
         return None
     bpn = TRAFFIC_CAPTURE["bytes_per_node"].get(fmt)
     return None if bpn is None else round(bpn * nodes)

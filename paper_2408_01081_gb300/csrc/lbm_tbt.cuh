@@ -91,9 +91,6 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_kernel(const __grid_consta
     const int y0 = blockIdx.y * A.rows;
     const int y1 = min(ny, y0 + A.rows);
     const int nin = (y1 - y0) + 4;                   // staged input rows y0-2 .. y1+1
-    // odd row blocks sweep downwards: both neighbours of a block boundary then read the rows
-    // around it at about the same time (both first or both last), so the second read hits L2
-    const bool dn = (blockIdx.y & 1) != 0;
     const uint32_t raw = lbmt::smem_u32(tbt_smem_raw);
     const uint32_t sbase = (raw + 127u) & ~127u;                    // 128-byte aligned ring
 
@@ -112,7 +109,7 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_kernel(const __grid_consta
         if (lane == 0) {
             lbmt::prefetch_map(&map);
             for (int jp = NST; jp < NST + A.l2_ahead && jp < nin; ++jp) {
-                const int yp = dn ? y1 + 1 - jp : y0 - 2 + jp;
+                const int yp = y0 - 2 + jp;
                 if (!DIRICHLET || (yp >= 0 && yp < ny))
                     lbmt::tma_prefetch_3d(&map, X0 - HL, (yp < 0) ? yp + ny : (yp >= ny ? yp - ny : yp), 0);
             }
@@ -126,11 +123,11 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_kernel(const __grid_consta
                 {
                     // the row the ring will reach l2_ahead copies later: into L2 now
                     const int jp = j + A.l2_ahead;
-                    const int yp = dn ? y1 + 1 - jp : y0 - 2 + jp;
+                    const int yp = y0 - 2 + jp;
                     if (j >= NST && A.l2_ahead > 0 && jp < nin && (!DIRICHLET || (yp >= 0 && yp < ny)))
                         lbmt::tma_prefetch_3d(&map, X0 - HL, (yp < 0) ? yp + ny : (yp >= ny ? yp - ny : yp), 0);
                 }
-                int y = dn ? y1 + 1 - j : y0 - 2 + j;
+                int y = y0 - 2 + j;
                 if (DIRICHLET && (y < 0 || y >= ny)) {
                     lbmt::mbar_arrive(fb);                   // row outside the lattice: never read
                     continue;
@@ -160,20 +157,17 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_kernel(const __grid_consta
     const float fa = A.af, fb = A.bf;
     const float Dk[5] = {-1.f, -1.f, 1.f, 1.f, 1.f};
 
-    // S1 rows kept in registers: prev = the row before the current one in sweep order (all
-    // directions), keep = the y-moving direction of the row before that which the next S2 pulls
-    // ((0,1) sweeping up, (0,-1) sweeping down)
-    float keep[5], prev[4][5];
+    float keep_py[5], prev[4][5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        keep[k] = 0.f;
+        keep_py[k] = 0.f;
 #pragma unroll
         for (int d = 0; d < 4; ++d) prev[d][k] = 0.f;
     }
     bool ok = lbmt::mbar_wait(lbmt::smem_u32(&full_bar[0]), 0, &abort_flag) &&
               lbmt::mbar_wait(lbmt::smem_u32(&full_bar[1 % NST]), (1 / NST) & 1, &abort_flag);
     for (int i = 0; i + 2 < nin; ++i) {
-        const int r = dn ? y1 - i : y0 - 1 + i;          // S1 row, from staged rows i, i+1, i+2
+        const int r = y0 - 1 + i;                        // S1 row, from staged rows i, i+1, i+2
         {
             const int j = i + 2;
             ok = ok && lbmt::mbar_wait(lbmt::smem_u32(&full_bar[j % NST]), (j / NST) & 1, &abort_flag);
@@ -181,9 +175,9 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_kernel(const __grid_consta
         if (!__all_sync(0xffffffffu, ok)) break;
         // shared addresses of this lane's column in the staged rows r-1, r, r+1
         constexpr uint32_t ES = sizeof(E), PL = WIN * sizeof(E);
-        const uint32_t rm = sbase + ((dn ? i + 2 : i) % NST) * G::STAGE_BYTES + idx * ES;   // row r-1
-        const uint32_t rc = sbase + ((i + 1) % NST) * G::STAGE_BYTES + idx * ES;            // row r
-        const uint32_t rp = sbase + ((dn ? i : i + 2) % NST) * G::STAGE_BYTES + idx * ES;   // row r+1
+        const uint32_t rm = sbase + (i % NST) * G::STAGE_BYTES + idx * ES;
+        const uint32_t rc = sbase + ((i + 1) % NST) * G::STAGE_BYTES + idx * ES;
+        const uint32_t rp = sbase + ((i + 2) % NST) * G::STAGE_BYTES + idx * ES;
         // ---- S1(r) at column xc ----
         float cur[4][5];
         const bool row_ok = DIRICHLET ? (r >= 0 && r < ny) : true;
@@ -234,20 +228,20 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_kernel(const __grid_consta
 #pragma unroll
                     for (int k = 0; k < 5; ++k) cur[d][k] = 0.f;
         }
-        // staged row i (row r-1 sweeping up, r+1 sweeping down) is not read again
+        // staged row i (row r-1) is not read again
         __syncwarp();
         if (lane == 0) lbmt::mbar_arrive(lbmt::smem_u32(&empty_bar[i % NST]));
-        // ---- S2(q) of the previous S1 row q from S1(q-1), S1(q), S1(q+1) ----
-        const int q = dn ? r + 1 : r - 1;
-        if (dn ? q < y1 : q >= y0) {
+        // ---- S2(r-1) from S1(r-2), S1(r-1), S1(r) ----
+        const int q = r - 1;
+        if (q >= y0) {
             const bool bot = DIRICHLET && q == 0, top = DIRICHLET && q == ny - 1;
             float f[4][5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 f[0][k] = __shfl_up_sync(0xffffffffu, prev[0][k], 1);
                 f[2][k] = __shfl_down_sync(0xffffffffu, prev[2][k], 1);
-                f[1][k] = bot ? Dk[k] * prev[3][k] : (dn ? cur[1][k] : keep[k]);
-                f[3][k] = top ? Dk[k] * prev[1][k] : (dn ? keep[k] : cur[3][k]);
+                f[1][k] = bot ? Dk[k] * prev[3][k] : keep_py[k];
+                f[3][k] = top ? Dk[k] * prev[1][k] : cur[3][k];
                 if (DIRICHLET && xs == 0) f[0][k] = Dk[k] * prev[2][k];
                 if (DIRICHLET && xs == nx - 1) f[2][k] = Dk[k] * prev[0][k];
             }
@@ -269,7 +263,7 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_kernel(const __grid_consta
         }
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            keep[k] = dn ? prev[3][k] : prev[1][k];
+            keep_py[k] = prev[1][k];
 #pragma unroll
             for (int d = 0; d < 4; ++d) prev[d][k] = cur[d][k];
         }
@@ -355,7 +349,6 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
     const int y0 = blockIdx.y * A.rows;
     const int y1 = min(ny, y0 + A.rows);
     const int nin = (y1 - y0) + 4;
-    const bool dn = (blockIdx.y & 1) != 0;           // odd row blocks sweep downwards
     const uint32_t raw = lbmt::smem_u32(tbt_smem_raw);
     const uint32_t sbase = (raw + 127u) & ~127u;
 
@@ -374,7 +367,7 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
             lbmt::prefetch_map(&map32);
             lbmt::prefetch_map(&map16);
             auto l2_row = [&](int jp) {
-                const int yp = dn ? y1 + 1 - jp : y0 - 2 + jp;
+                const int yp = y0 - 2 + jp;
                 if (jp < nin && (!DIRICHLET || (yp >= 0 && yp < ny))) {
                     const int yw = (yp < 0) ? yp + ny : (yp >= ny ? yp - ny : yp);
                     lbmt::tma_prefetch_3d(&map32, X0 - HL, yw, 0);
@@ -390,7 +383,7 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
                 if (j >= NST && !lbmt::mbar_wait(lbmt::smem_u32(&empty_bar[s]), ((j / NST) - 1) & 1, &abort_flag))
                     break;
                 if (j >= NST && A.l2_ahead > 0) l2_row(j + A.l2_ahead);
-                int y = dn ? y1 + 1 - j : y0 - 2 + j;
+                int y = y0 - 2 + j;
                 if (DIRICHLET && (y < 0 || y >= ny)) {
                     lbmt::mbar_arrive(fb);
                     continue;
@@ -420,15 +413,11 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
     const float fa = A.af, fb = A.bf;
     const float Dk[5] = {-1.f, -1.f, 1.f, 1.f, 1.f};
 
-    // S1 rows in registers as in tbt_kernel (prev, keep), and the y-moving population f*(t) of
-    // the own column in the previous staged row: (0,1) sweeping up, (0,-1) sweeping down (the
-    // pull source on that side of the next S1 row)
-    const int kd = dn ? 3 : 1, ad = dn ? 1 : 3;       // kept direction, direction pulled from the row ahead
-    float keep[5], prev[4][5], kept[5];
+    float keep_py[5], prev[4][5], d1_prev[5];        // S1 rows r-2 (direction (0,1)), r-1; f*_(0,1)(t) of row r-1
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        keep[k] = 0.f;
-        kept[k] = 0.f;
+        keep_py[k] = 0.f;
+        d1_prev[k] = 0.f;
 #pragma unroll
         for (int d = 0; d < 4; ++d) prev[d][k] = 0.f;
     }
@@ -436,21 +425,21 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
     bool ok = lbmt::mbar_wait(lbmt::smem_u32(&full_bar[0]), 0, &abort_flag) &&
               lbmt::mbar_wait(lbmt::smem_u32(&full_bar[1 % NST]), (1 / NST) & 1, &abort_flag);
     if (__all_sync(0xffffffffu, ok)) {
-        // staged row 0 (row y0-2 up, y1+1 down) feeds the first S1 row from its side
+        // f*_(0,1)(t) of the own column in staged row 0 (row y0-2): the pull source of row y0-1
         MsNode n;
         if (own_staged) ms_node_smem<H>(sbase, idx, inv_s, n);
-        else ms_node_global<H>(A.src, plane, (long long)row_of(dn ? y1 + 1 : y0 - 2) * A.pitch + xc, inv_s, n);
-        ms_node_dir(n, kd, fa, fb, kept);
+        else ms_node_global<H>(A.src, plane, (long long)row_of(y0 - 2) * A.pitch + xc, inv_s, n);
+        ms_node_dir(n, 1, fa, fb, d1_prev);
     }
     for (int i = 0; i + 2 < nin; ++i) {
-        const int r = dn ? y1 - i : y0 - 1 + i;
+        const int r = y0 - 1 + i;
         {
             const int j = i + 2;
             ok = ok && lbmt::mbar_wait(lbmt::smem_u32(&full_bar[j % NST]), (j / NST) & 1, &abort_flag);
         }
         if (!__all_sync(0xffffffffu, ok)) break;
         const uint32_t sc = sbase + ((i + 1) % NST) * G::STAGE_BYTES;   // row r
-        const uint32_t sp = sbase + ((i + 2) % NST) * G::STAGE_BYTES;   // the row ahead (r+1 up, r-1 down)
+        const uint32_t sp = sbase + ((i + 2) % NST) * G::STAGE_BYTES;   // row r+1
         float cur[4][5];
         const bool row_ok = DIRICHLET ? (r >= 0 && r < ny) : true;
         {
@@ -458,17 +447,16 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
             MsNode n;
             if (own_staged) ms_node_smem<H>(sc, idx, inv_s, n);
             else ms_node_global<H>(A.src, plane, (long long)row_of(r) * A.pitch + xc, inv_s, n);
-            float o0[5], o1[5], o2[5], o3[5], pa[5];
+            float o0[5], o1[5], o2[5], o3[5], p3[5];
             ms_node_dir(n, 0, fa, fb, o0);
             ms_node_dir(n, 1, fa, fb, o1);
             ms_node_dir(n, 2, fa, fb, o2);
             ms_node_dir(n, 3, fa, fb, o3);
             {
-                // the row ahead in sweep order (r+1 up, r-1 down)
                 MsNode np;
                 if (own_staged) ms_node_smem<H>(sp, idx, inv_s, np);
-                else ms_node_global<H>(A.src, plane, (long long)row_of(dn ? r - 1 : r + 1) * A.pitch + xc, inv_s, np);
-                ms_node_dir(np, ad, fa, fb, pa);
+                else ms_node_global<H>(A.src, plane, (long long)row_of(r + 1) * A.pitch + xc, inv_s, np);
+                ms_node_dir(np, 3, fa, fb, p3);
             }
             float hl[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, hr[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
             if (lane == 0) {
@@ -490,8 +478,8 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
                 const float rr = __shfl_down_sync(0xffffffffu, o2[k], 1);
                 f[0][k] = (lane == 0) ? hl[k] : l;
                 f[2][k] = (lane == 31) ? hr[k] : rr;
-                f[1][k] = dn ? pa[k] : kept[k];
-                f[3][k] = dn ? kept[k] : pa[k];
+                f[1][k] = d1_prev[k];
+                f[3][k] = p3[k];
             }
             if (DIRICHLET) {
                 const bool bot = r == 0, top = r == ny - 1;
@@ -504,7 +492,7 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 5; ++k) kept[k] = dn ? o3[k] : o1[k];
+            for (int k = 0; k < 5; ++k) d1_prev[k] = o1[k];
             float U[5], rx[5], ry2[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
@@ -521,16 +509,16 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
         }
         __syncwarp();
         if (lane == 0) lbmt::mbar_arrive(lbmt::smem_u32(&empty_bar[i % NST]));
-        const int q = dn ? r + 1 : r - 1;
-        if (dn ? q < y1 : q >= y0) {
+        const int q = r - 1;
+        if (q >= y0) {
             const bool bot = DIRICHLET && q == 0, top = DIRICHLET && q == ny - 1;
             float f[4][5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 f[0][k] = __shfl_up_sync(0xffffffffu, prev[0][k], 1);
                 f[2][k] = __shfl_down_sync(0xffffffffu, prev[2][k], 1);
-                f[1][k] = bot ? Dk[k] * prev[3][k] : (dn ? cur[1][k] : keep[k]);
-                f[3][k] = top ? Dk[k] * prev[1][k] : (dn ? keep[k] : cur[3][k]);
+                f[1][k] = bot ? Dk[k] * prev[3][k] : keep_py[k];
+                f[3][k] = top ? Dk[k] * prev[1][k] : cur[3][k];
                 if (DIRICHLET && xs == 0) f[0][k] = Dk[k] * prev[2][k];
                 if (DIRICHLET && xs == nx - 1) f[2][k] = Dk[k] * prev[0][k];
             }
@@ -559,7 +547,7 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
         }
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            keep[k] = dn ? prev[3][k] : prev[1][k];
+            keep_py[k] = prev[1][k];
 #pragma unroll
             for (int d = 0; d < 4; ++d) prev[d][k] = cur[d][k];
         }

@@ -27,8 +27,11 @@ def test_reference_arm_prints_one_json_line():
 def test_traffic_figure_only_for_the_captured_sources():
     sys.path.insert(0, ROOT)
     import bench
-    t = bench.traffic_per_launch("f64", 1000)
+    n = bench.TRAFFIC_CAPTURE["nodes"]
+    t = bench.traffic_per_launch("f64", n)
     if bench.TRAFFIC_CAPTURE["sha256"] == bench.kernel_digest():
-        assert t == round(bench.TRAFFIC_CAPTURE["bytes_per_node"]["f64"] * 1000)
+        assert t == round(bench.TRAFFIC_CAPTURE["bytes_per_node"]["f64"] * n)
+        assert bench.pipe_counts() == (1127.0, 32.0, 260.0)
     else:
-        assert t is None
+        assert t is None and bench.pipe_counts() is None
+    assert bench.traffic_per_launch("f64", 1000) is None      # captured size only, never scaled
