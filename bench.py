@@ -38,11 +38,11 @@ CK2, CMU2, CFL = 1.5, 0.5, 0.9
 ELL, STD = 64.0, 1e-3
 METRIC = "MLUPS and % of HBM roofline; mixed-precision vs FP64 at stated L2 error"
 BYTES_PER_NODE = {"f64": 320, "f32": 160, "bf16": 80, "f16": 80,    # one read + one write of 20 values
-                  "ms_bf16": 100, "ms_f16": 100}                   # 5 FP32 + 15 16-bit moments, read + write
+                  "ms_bf16": 100, "ms_f16": 100, "ms_bfp": 100}    # 5 FP32 + 15 16-bit moments, read + write
 FP64_OPS_PER_NODE = 47                                                # DADD/DFMA per node, no forcing
 SPLIT_LEVEL = 1               # lbm_set_fp64_split default: the 15 sums of a node on the integer pipe
 SPLIT_INTEGER_ADDS = 15
-FUSED = {"f32", "bf16", "f16", "ms_bf16", "ms_f16"}   # formats the library advances two steps per pass by default
+FUSED = {"f32", "bf16", "f16", "ms_bf16", "ms_f16", "ms_bfp"}   # two steps per pass by default
 # DRAM bytes per node and launch of each step kernel (dram__bytes_read.sum + dram__bytes_write.sum
 # from one ncu capture of this benchmark's own 8192^2 workload, averaged over its launches; no
 # scaling), valid only while the kernel sources hash to "sha256".  "<fmt>_fused" is one launch of
@@ -612,7 +612,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nx", type=int, default=NX)
     ap.add_argument("--ny", type=int, default=NY)
-    ap.add_argument("--formats", default="f64,f32,bf16,f16,ms_bf16,ms_f16")
+    ap.add_argument("--formats", default="f64,f32,bf16,f16,ms_bf16,ms_f16,ms_bfp")
     ap.add_argument("--multi", default="slabs", choices=["slabs", "replicas"],
                     help="N > 1: FP64 line as row slabs of one lattice (halo exchange) or independent replicas")
     ap.add_argument("--no-e2e", action="store_true")

@@ -53,10 +53,18 @@ typedef enum { LBM_PERIODIC = 0, LBM_DIRICHLET = 1 } lbm_bc;
  * LBM_MS_F16 store per node the zeroth moment U (FP32) and the 15 deviations of
  * the other moments from their local-equilibrium values (Eq. cond_eq) in BF16 /
  * FP16, scaled by a power of two chosen at lbm_init / lbm_set_populations
- * (50 bytes per node instead of 80 for 16-bit populations).  In every reduced
- * format the initialisation, the Dirichlet reconstruction and all reductions
- * stay in FP64.  Batches accept formats 0..3. */
-typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_BF16 = 2, LBM_F16 = 3, LBM_MS_BF16 = 4, LBM_MS_F16 = 5 } lbm_storage;
+ * (50 bytes per node instead of 80 for 16-bit populations).  LBM_MS_BFP stores
+ * the same 15 deviations in 16-bit words as block floating point: the three
+ * deviations of one component of one node share a 3-bit exponent (one bit in
+ * each word) and keep 15-bit mantissas, about 8 times finer than FP16 for the
+ * largest of the three.  Its range holds deviations at least 8 times the largest
+ * one at initialisation; a block beyond it is clamped and lbm_check_finite then
+ * returns LBM_ERR_UNSTABLE.  In every reduced format the initialisation, the
+ * Dirichlet reconstruction and all reductions stay in FP64.  Batches accept
+ * formats 0..3. */
+typedef enum {
+    LBM_F64 = 0, LBM_F32 = 1, LBM_BF16 = 2, LBM_F16 = 3, LBM_MS_BF16 = 4, LBM_MS_F16 = 5, LBM_MS_BFP = 6
+} lbm_storage;
 
 typedef struct {
     int32_t nx, ny;              /* nodes per row / number of rows, each >= 2            */
@@ -195,7 +203,8 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, double* ustar, int32_t o
 lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, const double* ustar, int64_t m,
                                int32_t on_device);
 
-/* LBM_ERR_UNSTABLE if any stored population is NaN or infinite, else LBM_OK (waits). */
+/* LBM_ERR_UNSTABLE if any stored population is NaN or infinite, or (LBM_MS_BFP) if a
+ * block of deviations was clamped since the last call; else LBM_OK (waits). */
 lbm_status lbm_check_finite(lbm_ctx* ctx);
 
 /* Current step counter m (t = m dt). */

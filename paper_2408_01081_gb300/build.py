@@ -1,6 +1,6 @@
 """Build the CUDA library ``liblbm.so`` in-tree for sm_103a (GB300).
 
-One translation unit per storage format (FP64, FP32, BF16, FP16 and the two
+One translation unit per storage format (FP64, FP32, BF16, FP16 and the three
 moment-space formats) plus the host API, compiled in parallel with nvcc and linked into a shared library with the C
 ABI of ``include/lbm.h``.
 """
@@ -48,7 +48,7 @@ def build(force: bool = False, verbose: bool = False, out: str = None, defines=(
     nvcc = _nvcc()
     dflags = [f"-D{d}" for d in defines]
     units = [(os.path.join(CSRC, "lbm_kind.cu"), os.path.join(build_dir, f"lbm_kind{k}.o"),
-              [f"-DLBM_KIND={k}"] + dflags) for k in range(6)]
+              [f"-DLBM_KIND={k}"] + dflags) for k in range(7)]
     extra = [f for f in sorted(os.listdir(CSRC)) if f.endswith(".cu") and f != "lbm_kind.cu"]
     units += [(os.path.join(CSRC, f), os.path.join(build_dir, f[:-3] + ".o"), dflags) for f in extra]
     procs = []

@@ -92,6 +92,7 @@ const KindOps* ops_for(int storage)
     case LBM_F16: return &lbmh::kind_ops_3;
     case LBM_MS_BF16: return &lbmh::kind_ops_4;
     case LBM_MS_F16: return &lbmh::kind_ops_5;
+    case LBM_MS_BFP: return &lbmh::kind_ops_6;
     default: return nullptr;
     }
 }
@@ -99,6 +100,7 @@ const KindOps* ops_for(int storage)
 constexpr int kRedBlocks = 152 * 4;   // blocks of the FP64 reductions (one partial each)
 constexpr int kMaxR = 16;
 constexpr int kTimeoutSlot = kRedBlocks * 30 + 56;   // scratch double index of the staged kernel's timeout flag
+constexpr int kSatSlot = kRedBlocks * 30 + 58;       // scratch double index of the block-floating-point saturation flag
 
 // cuTensorMapEncodeTiled, reached through the runtime's driver entry point (no link to libcuda)
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -266,6 +268,7 @@ lbmk::NodeArgs node_args(const lbm_ctx* ctx, long long m_time)
     A.omega = ctx->omega;
     A.neq_scale = ctx->neq_scale;
     A.measure = nullptr;
+    A.sat = reinterpret_cast<int*>(ctx->scratch + kSatSlot);
     return A;
 }
 
@@ -434,7 +437,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
             ctx->maps_ok = ctx->maps_ok && encode_rows_map(&ctx->map[i][0], ctx->buf[i], es, p->nx, p->ny, ctx->pitch,
                                                            ctx->plane, 20, win);
     }
-    if (e == cudaSuccess && (p->storage == LBM_MS_BF16 || p->storage == LBM_MS_F16)) {
+    if (e == cudaSuccess && (p->storage == LBM_MS_BF16 || p->storage == LBM_MS_F16 || p->storage == LBM_MS_BFP)) {
         const int win = lbmk::TbtMsGeom::WIN;
         ctx->maps_ok = true;
         for (int i = 0; i < 2; ++i) {
@@ -466,7 +469,7 @@ lbm_status lbm_create_slab(const lbm_params* p, int32_t y_begin, int32_t rows, l
         g_create_error = "slab rows [y_begin, y_begin + rows) must lie in [0, ny), ny >= 2";
         return LBM_ERR_ARG;
     }
-    if (p->storage == LBM_MS_BF16 || p->storage == LBM_MS_F16) {
+    if (p->storage == LBM_MS_BF16 || p->storage == LBM_MS_F16 || p->storage == LBM_MS_BFP) {
         g_create_error = "slabs take the population formats (the moment-space scale is chosen per context)";
         return LBM_ERR_ARG;
     }
@@ -779,6 +782,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
     A.bf = (float)ctx->b;
     A.scale_f = (float)ctx->neq_scale;
     A.inv_scale_f = (float)(1.0 / ctx->neq_scale);
+    A.sat = reinterpret_cast<int*>(ctx->scratch + kSatSlot);
     const int variant = (ctx->p.bc == LBM_DIRICHLET ? lbmh::STEP_DIRICHLET : 0) |
                         (ctx->R > 0 ? lbmh::STEP_FORCING : 0) | (ctx->w ? lbmh::STEP_TRACK : 0) |
                         (ctx->omega != 2.0 ? lbmh::STEP_OMEGA : 0) |
@@ -786,7 +790,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
     // two steps per pass: population formats in FP32 / BF16 / FP16 (and the moment-space formats
     // with staged rows), omega = 2, no body load, no displacement tracking, periodic or
     // homogeneous Dirichlet
-    const bool ms = ctx->p.storage == LBM_MS_BF16 || ctx->p.storage == LBM_MS_F16;
+    const bool ms = ctx->p.storage == LBM_MS_BF16 || ctx->p.storage == LBM_MS_F16 || ctx->p.storage == LBM_MS_BFP;
     const bool fusable = ctx->fuse == 2 && !ctx->slab &&
                          (ctx->p.storage == LBM_F32 || ctx->p.storage == LBM_BF16 || ctx->p.storage == LBM_F16 ||
                           (ms && ctx->staging >= 1)) &&
@@ -819,6 +823,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
             Q.l2_ahead = ctx->l2_ahead;
             Q.scale = (float)ctx->neq_scale;
             Q.inv_s = (float)(1.0 / ctx->neq_scale);
+            Q.sat = reinterpret_cast<int*>(ctx->scratch + kSatSlot);
             const dim3 qgrid((ctx->p.nx + lbmk::TBT_OUT - 1) / lbmk::TBT_OUT, (ctx->p.ny + Q.rows - 1) / Q.rows);
             while (n >= 2) {
                 Q.src = ctx->buf[ctx->cur];
@@ -975,10 +980,19 @@ lbm_status lbm_check_finite(lbm_ctx* ctx)
     int* flag = reinterpret_cast<int*>(ctx->scratch + kRedBlocks * 30 + 40);
     LBM_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->s));
     LBM_CUDA(ctx, ctx->ops->finite(node_args(ctx, ctx->m), flag, dim3(152 * 8), dim3(256), ctx->s));
-    int h = 0;
+    int h = 0, sat = 0;
+    int* satp = reinterpret_cast<int*>(ctx->scratch + kSatSlot);
     LBM_CUDA(ctx, cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    LBM_CUDA(ctx, cudaMemcpyAsync(&sat, satp, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
     LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
-    return h ? fail(ctx, LBM_ERR_UNSTABLE, "non-finite population found") : LBM_OK;
+    if (h) return fail(ctx, LBM_ERR_UNSTABLE, "non-finite population found");
+    if (sat) {
+        LBM_CUDA(ctx, cudaMemsetAsync(satp, 0, sizeof(int), ctx->s));
+        LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+        return fail(ctx, LBM_ERR_UNSTABLE, "a stored block of deviations exceeded the block-floating-point range "
+                                           "(at least 8x the largest deviation at initialisation) and was clamped");
+    }
+    return LBM_OK;
 }
 
 lbm_status lbm_state_bytes(const lbm_ctx* ctx, int64_t* nbytes)

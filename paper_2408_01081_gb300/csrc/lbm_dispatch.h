@@ -81,6 +81,7 @@ extern const KindOps kind_ops_2;  // BF16
 extern const KindOps kind_ops_3;  // FP16
 extern const KindOps kind_ops_4;  // moment space, BF16 deviations
 extern const KindOps kind_ops_5;  // moment space, FP16 deviations
+extern const KindOps kind_ops_6;  // moment space, block-floating-point deviations
 
 // reduction tails (format independent), defined in lbm_capi.cu
 cudaError_t finish_sum1(const double* partial, int nblk, double* out, cudaStream_t s);

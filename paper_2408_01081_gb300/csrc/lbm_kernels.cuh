@@ -122,6 +122,7 @@ struct StepArgs {
     // from FP64 runs on the FP64 pipe, two per clock per SM)
     float af, bf;          // a, b
     float scale_f, inv_scale_f;   // neq_scale and its reciprocal (exact: a power of two)
+    int* sat = nullptr;    // moment space, block floating point: set when a block saturated
 };
 
 // ---------------------------------------------------------------------------
@@ -539,6 +540,7 @@ struct NodeArgs {
     double omega;          // relaxation rate (2 for the paper's scheme; never 1)
     double neq_scale;      // moment-space storage: scale of the stored deviations
     float* measure;        // moment-space storage: if set, store_node records max |deviation| instead
+    int* sat = nullptr;    // moment space, block floating point: set when a stored block saturated
 };
 
 // moment-space storage (lbm_ms.cuh)

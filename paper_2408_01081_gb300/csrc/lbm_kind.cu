@@ -1,5 +1,6 @@
 // Instantiates every kernel for one storage format; compiled once per format
-// with -DLBM_KIND=<0|1|2|3> (FP64, FP32, BF16, FP16).
+// with -DLBM_KIND=<0..6> (FP64, FP32, BF16, FP16, and moment space with BF16, FP16
+// or block-floating-point deviations).
 #include "lbm_dispatch.h"
 
 #ifndef LBM_KIND
@@ -202,7 +203,7 @@ cudaError_t tbt_t(const CUtensorMap* maps, const lbmk::TbtArgs& a, bool dirichle
         if (e != cudaSuccess) return e;
         kern<<<g, lbmk::TBT_THREADS, G::SMEM, s>>>(maps[0], a);
         return cudaGetLastError();
-    } else if constexpr (KK == lbmk::K_MSBF16 || KK == lbmk::K_MSF16) {
+    } else if constexpr (KK == lbmk::K_MSBF16 || KK == lbmk::K_MSF16 || KK == lbmk::K_MSBFP) {
         using G = lbmk::TbtMsGeom;
         void (*kern)(CUtensorMap, CUtensorMap, lbmk::TbtArgs) =
             dirichlet ? lbmk::tbt_ms_kernel<KK, true> : lbmk::tbt_ms_kernel<KK, false>;

@@ -12,17 +12,70 @@
 //     f*_{0,+-1} = 1/4 (m0 +- 2 (Phi_y/c + dy) - dd)
 // Layout of one buffer: 5 FP32 planes of m0, then 15 16-bit planes (dx[5], dy[5],
 // dd[5]), each [ny][pitch]: 50 bytes per node.
+//
+// Three codecs for the 16-bit words (MsCodec): BF16 and FP16 store each scaled
+// deviation on its own; block floating point (lbm_mscodec.cuh) stores the three
+// deviations of one component with a shared exponent, so the three words of a
+// component are always decoded together.
 #pragma once
 
 #include "lbm_kernels.cuh"
+#include "lbm_mscodec.cuh"
 
 namespace lbmk {
 
-enum { K_MSBF16 = 4, K_MSF16 = 5 };
+enum { K_MSBF16 = 4, K_MSF16 = 5, K_MSBFP = 6, K_RAW16 = 15 };
 
-template <int K> struct Ms;                       // 16-bit format of the deviations
-template <> struct Ms<K_MSBF16> { static constexpr int H = K_BF16; };
-template <> struct Ms<K_MSF16> { static constexpr int H = K_F16; };
+// raw 16-bit words (no conversion): the moment-space kernels load and store the words
+// through this format and convert them with MsCodec
+template <> struct Fmt<K_RAW16> {
+    using E = unsigned short;
+    using M = unsigned short;
+    static __device__ __forceinline__ M ld(E e) { return e; }
+    static __device__ __forceinline__ E st(M m) { return m; }
+};
+
+// one component's three scaled deviations <-> its three words
+template <int H>
+struct MsFloatCodec {
+    static constexpr bool kJoint = false;         // each word decodes on its own
+    static constexpr int kH = H;
+    static __device__ __forceinline__ void decode(unsigned short wx, unsigned short wy, unsigned short wz, float inv_s,
+                                                  float& x, float& y, float& z)
+    {
+        x = Fmt<H>::ld(wx) * inv_s;
+        y = Fmt<H>::ld(wy) * inv_s;
+        z = Fmt<H>::ld(wz) * inv_s;
+    }
+    // X, Y, Z already multiplied by the scale
+    static __device__ __forceinline__ void encode(float X, float Y, float Z, unsigned short& wx, unsigned short& wy,
+                                                  unsigned short& wz, bool&)
+    {
+        wx = Fmt<H>::st(X);
+        wy = Fmt<H>::st(Y);
+        wz = Fmt<H>::st(Z);
+    }
+};
+
+struct MsBfpCodec {
+    static constexpr bool kJoint = true;          // the three words of a component decode together
+    static constexpr int kH = K_F16;              // (unused: element type only)
+    static __device__ __forceinline__ void decode(unsigned short wx, unsigned short wy, unsigned short wz, float inv_s,
+                                                  float& x, float& y, float& z)
+    {
+        lbmc::bfp_decode(wx, wy, wz, inv_s, x, y, z);
+    }
+    static __device__ __forceinline__ void encode(float X, float Y, float Z, unsigned short& wx, unsigned short& wy,
+                                                  unsigned short& wz, bool& sat)
+    {
+        lbmc::bfp_encode(X, Y, Z, wx, wy, wz, sat);
+    }
+};
+
+template <int K> struct Ms;                       // codec of the deviations
+template <> struct Ms<K_MSBF16> { using C = MsFloatCodec<K_BF16>; };
+template <> struct Ms<K_MSF16> { using C = MsFloatCodec<K_F16>; };
+template <> struct Ms<K_MSBFP> { using C = MsBfpCodec; };
 
 template <int K>
 __device__ __forceinline__ const float* ms_m0(const void* S) { return static_cast<const float*>(S); }
@@ -62,16 +115,40 @@ template <int K, int V, bool C>
 __device__ __forceinline__ void ms_load_dir(const void* S, long long plane, long long off, int d, float a, float b,
                                             float inv_s, float (&out)[5][V])
 {
-    constexpr int H = Ms<K>::H;
+    using Codec = typename Ms<K>::C;
     const float* m0p = ms_m0<K>(S);
     const unsigned short* dv = ms_dev<K>(S, plane);
-    float m0[5][V], g[5][V], dd[5][V];
     const int dxy_base = (d == 0 || d == 2) ? 0 : 5;
+    float m0[5][V], g[5][V], dd[5][V];
+    if constexpr (!Codec::kJoint) {
+        // float words decode on their own: read only the planes this direction needs
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        vload<K_F32, V, C>(m0p + k * plane + off, m0[k]);
-        vload<H, V, C>(dv + (dxy_base + k) * plane + off, g[k]);
-        vload<H, V, C>(dv + (10 + k) * plane + off, dd[k]);
+        for (int k = 0; k < 5; ++k) {
+            vload<K_F32, V, C>(m0p + k * plane + off, m0[k]);
+            vload<Codec::kH, V, C>(dv + (dxy_base + k) * plane + off, g[k]);
+            vload<Codec::kH, V, C>(dv + (10 + k) * plane + off, dd[k]);
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                g[k][e] *= inv_s;
+                dd[k][e] *= inv_s;
+            }
+        }
+    } else {
+        unsigned short wx[5][V], wy[5][V], wz[5][V];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            vload<K_F32, V, C>(m0p + k * plane + off, m0[k]);
+            vload<K_RAW16, V, C>(dv + k * plane + off, wx[k]);
+            vload<K_RAW16, V, C>(dv + (5 + k) * plane + off, wy[k]);
+            vload<K_RAW16, V, C>(dv + (10 + k) * plane + off, wz[k]);
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                float x, y, z;
+                Codec::decode(wx[k][e], wy[k][e], wz[k][e], inv_s, x, y, z);
+                g[k][e] = (d == 0 || d == 2) ? x : y;
+                dd[k][e] = z;
+            }
+        }
     }
 #pragma unroll
     for (int e = 0; e < V; ++e) {
@@ -79,8 +156,8 @@ __device__ __forceinline__ void ms_load_dir(const void* S, long long plane, long
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             mm[k] = m0[k][e];
-            gg[k] = g[k][e] * inv_s;
-            ee[k] = dd[k][e] * inv_s;
+            gg[k] = g[k][e];
+            ee[k] = dd[k][e];
         }
         ms_dir(d, mm, gg, ee, a, b, f);
 #pragma unroll
@@ -93,15 +170,38 @@ template <int K, int V, bool C>
 __device__ __forceinline__ void ms_load_x(const void* S, long long plane, long long off, float a, float b, float inv_s,
                                           float (&f0)[5][V], float (&f2)[5][V])
 {
-    constexpr int H = Ms<K>::H;
+    using Codec = typename Ms<K>::C;
     const float* m0p = ms_m0<K>(S);
     const unsigned short* dv = ms_dev<K>(S, plane);
     float m0[5][V], g[5][V], dd[5][V];
+    if constexpr (!Codec::kJoint) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        vload<K_F32, V, C>(m0p + k * plane + off, m0[k]);
-        vload<H, V, C>(dv + k * plane + off, g[k]);
-        vload<H, V, C>(dv + (10 + k) * plane + off, dd[k]);
+        for (int k = 0; k < 5; ++k) {
+            vload<K_F32, V, C>(m0p + k * plane + off, m0[k]);
+            vload<Codec::kH, V, C>(dv + k * plane + off, g[k]);
+            vload<Codec::kH, V, C>(dv + (10 + k) * plane + off, dd[k]);
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                g[k][e] *= inv_s;
+                dd[k][e] *= inv_s;
+            }
+        }
+    } else {
+        unsigned short wx[5][V], wy[5][V], wz[5][V];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            vload<K_F32, V, C>(m0p + k * plane + off, m0[k]);
+            vload<K_RAW16, V, C>(dv + k * plane + off, wx[k]);
+            vload<K_RAW16, V, C>(dv + (5 + k) * plane + off, wy[k]);
+            vload<K_RAW16, V, C>(dv + (10 + k) * plane + off, wz[k]);
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                float x, y, z;
+                Codec::decode(wx[k][e], wy[k][e], wz[k][e], inv_s, x, y, z);
+                g[k][e] = x;
+                dd[k][e] = z;
+            }
+        }
     }
 #pragma unroll
     for (int e = 0; e < V; ++e) {
@@ -109,8 +209,8 @@ __device__ __forceinline__ void ms_load_x(const void* S, long long plane, long l
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             mm[k] = m0[k][e];
-            gg[k] = g[k][e] * inv_s;
-            ee[k] = dd[k][e] * inv_s;
+            gg[k] = g[k][e];
+            ee[k] = dd[k][e];
         }
         ms_dir(0, mm, gg, ee, a, b, fa);
         ms_dir(2, mm, gg, ee, a, b, fb);
@@ -152,8 +252,7 @@ __device__ __forceinline__ void ms_moments(const float (&o)[4][5], float a, floa
 template <int K, int V, bool DIRICHLET, bool FORCING, bool TRACK, bool OMEGA>
 __global__ void __launch_bounds__(256, 2) ms_step_kernel(StepArgs A)
 {
-    constexpr int H = Ms<K>::H;
-    using E16 = typename Fmt<H>::E;
+    using Codec = typename Ms<K>::C;
     const int y = blockIdx.y;
     const int cx = blockIdx.x * blockDim.x + threadIdx.x;
     const int nchunk = (A.nx + V - 1) / V;
@@ -209,7 +308,9 @@ __global__ void __launch_bounds__(256, 2) ms_step_kernel(StepArgs A)
                 if (q == e) P2[k][q] = r0[k][0];
     }
 
-    float m0o[5][V], dxo[5][V], dyo[5][V], ddo[5][V];
+    float m0o[5][V];
+    unsigned short wxo[5][V], wyo[5][V], wzo[5][V];
+    bool sat = false;
     double wv[2][V];
 #pragma unroll
     for (int e = 0; e < V; ++e) {
@@ -305,9 +406,7 @@ __global__ void __launch_bounds__(256, 2) ms_step_kernel(StepArgs A)
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             m0o[k][e] = m0[k];
-            dxo[k][e] = dx[k] * sc;
-            dyo[k][e] = dy[k] * sc;
-            ddo[k][e] = dd[k] * sc;
+            Codec::encode(dx[k] * sc, dy[k] * sc, dd[k] * sc, wxo[k][e], wyo[k][e], wzo[k][e], sat);
         }
         if (TRACK) {
             wv[0][e] = (double)U[0];
@@ -315,14 +414,15 @@ __global__ void __launch_bounds__(256, 2) ms_step_kernel(StepArgs A)
         }
     }
     if (!active) return;
+    if (sat && A.sat) atomicOr(A.sat, 1);
     float* m0p = static_cast<float*>(A.dst);
-    E16* dv = reinterpret_cast<E16*>(m0p + 5 * plane);
+    unsigned short* dv = reinterpret_cast<unsigned short*>(m0p + 5 * plane);
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         vstore<K_F32, V>(m0p + k * plane + row, m0o[k]);
-        vstore<H, V>(dv + k * plane + row, dxo[k]);
-        vstore<H, V>(dv + (5 + k) * plane + row, dyo[k]);
-        vstore<H, V>(dv + (10 + k) * plane + row, ddo[k]);
+        vstore<K_RAW16, V>(dv + k * plane + row, wxo[k]);
+        vstore<K_RAW16, V>(dv + (5 + k) * plane + row, wyo[k]);
+        vstore<K_RAW16, V>(dv + (10 + k) * plane + row, wzo[k]);
     }
     if (TRACK) {
 #pragma unroll
@@ -341,7 +441,7 @@ __global__ void __launch_bounds__(256, 2) ms_step_kernel(StepArgs A)
 template <int K>
 __device__ void ms_load_node(const NodeArgs& A, int x, int y, double (&S)[4][5])
 {
-    constexpr int H = Ms<K>::H;
+    using Codec = typename Ms<K>::C;
     const float* m0p = static_cast<const float*>(A.S);
     const unsigned short* dv = reinterpret_cast<const unsigned short*>(m0p + 5 * A.plane);
     const long long off = (long long)(y + A.yo) * A.pitch + x;
@@ -350,9 +450,8 @@ __device__ void ms_load_node(const NodeArgs& A, int x, int y, double (&S)[4][5])
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         m0[k] = m0p[k * A.plane + off];
-        gx[k] = Fmt<H>::ld(dv[k * A.plane + off]) * inv_s;
-        gy[k] = Fmt<H>::ld(dv[(5 + k) * A.plane + off]) * inv_s;
-        dd[k] = Fmt<H>::ld(dv[(10 + k) * A.plane + off]) * inv_s;
+        Codec::decode(dv[k * A.plane + off], dv[(5 + k) * A.plane + off], dv[(10 + k) * A.plane + off], inv_s, gx[k],
+                      gy[k], dd[k]);
     }
     for (int d = 0; d < 4; ++d) {
         float f[5];
@@ -365,7 +464,7 @@ __device__ void ms_load_node(const NodeArgs& A, int x, int y, double (&S)[4][5])
 template <int K>
 __device__ void ms_store_node(const NodeArgs& A, int x, int y, const double (&S)[4][5])
 {
-    constexpr int H = Ms<K>::H;
+    using Codec = typename Ms<K>::C;
     float o[4][5];
 #pragma unroll
     for (int d = 0; d < 4; ++d)
@@ -381,16 +480,20 @@ __device__ void ms_store_node(const NodeArgs& A, int x, int y, const double (&S)
         return;
     }
     float* m0p = static_cast<float*>(A.Sout);
-    typename Fmt<H>::E* dv = reinterpret_cast<typename Fmt<H>::E*>(m0p + 5 * A.plane);
+    unsigned short* dv = reinterpret_cast<unsigned short*>(m0p + 5 * A.plane);
     const long long off = (long long)(y + A.yo) * A.pitch + x;
     const float sc = (float)A.neq_scale;
+    bool sat = false;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         m0p[k * A.plane + off] = m0[k];
-        dv[k * A.plane + off] = Fmt<H>::st(dx[k] * sc);
-        dv[(5 + k) * A.plane + off] = Fmt<H>::st(dy[k] * sc);
-        dv[(10 + k) * A.plane + off] = Fmt<H>::st(dd[k] * sc);
+        unsigned short wx, wy, wz;
+        Codec::encode(dx[k] * sc, dy[k] * sc, dd[k] * sc, wx, wy, wz, sat);
+        dv[k * A.plane + off] = wx;
+        dv[(5 + k) * A.plane + off] = wy;
+        dv[(10 + k) * A.plane + off] = wz;
     }
+    if (sat && A.sat) atomicOr(A.sat, 1);
 }
 
 }  // namespace lbmk

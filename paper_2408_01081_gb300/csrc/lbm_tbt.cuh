@@ -39,6 +39,7 @@ struct TbtArgs {
     int* timeout;          // device flag: set when a bounded wait ran out
     int withhold;          // test hook: staged input row the producer never copies (-1: none)
     float scale, inv_s;    // moment-space storage: scale of the stored deviations and its reciprocal
+    int* sat;              // moment space, block floating point: set when a stored block saturated
     int l2_ahead;          // rows prefetched into L2 ahead of the row the ring loads (0: none)
 };
 
@@ -298,31 +299,31 @@ struct MsNode {
     float m0[5], dx[5], dy[5], dd[5];
 };
 
-template <int H>
+template <int K>
 __device__ __forceinline__ void ms_node_smem(uint32_t stage, int c, float inv_s, MsNode& n)
 {
+    using Codec = typename Ms<K>::C;
     constexpr uint32_t W = TbtMsGeom::WIN;
     const uint32_t m0 = stage + 4u * c, dv = stage + TbtMsGeom::DEV_OFF + 2u * c;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         n.m0[k] = lbmt::lds_f32(m0 + 4u * W * k);
-        n.dx[k] = Fmt<H>::ld(lbmt::lds_u16(dv + 2u * W * k)) * inv_s;
-        n.dy[k] = Fmt<H>::ld(lbmt::lds_u16(dv + 2u * W * (5 + k))) * inv_s;
-        n.dd[k] = Fmt<H>::ld(lbmt::lds_u16(dv + 2u * W * (10 + k))) * inv_s;
+        Codec::decode(lbmt::lds_u16(dv + 2u * W * k), lbmt::lds_u16(dv + 2u * W * (5 + k)),
+                      lbmt::lds_u16(dv + 2u * W * (10 + k)), inv_s, n.dx[k], n.dy[k], n.dd[k]);
     }
 }
 
-template <int H>
+template <int K>
 __device__ __forceinline__ void ms_node_global(const void* S, long long plane, long long off, float inv_s, MsNode& n)
 {
+    using Codec = typename Ms<K>::C;
     const float* m0 = static_cast<const float*>(S);
     const unsigned short* dv = reinterpret_cast<const unsigned short*>(m0 + 5 * plane);
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         n.m0[k] = __ldg(m0 + k * plane + off);
-        n.dx[k] = Fmt<H>::ld(__ldg(dv + k * plane + off)) * inv_s;
-        n.dy[k] = Fmt<H>::ld(__ldg(dv + (5 + k) * plane + off)) * inv_s;
-        n.dd[k] = Fmt<H>::ld(__ldg(dv + (10 + k) * plane + off)) * inv_s;
+        Codec::decode(__ldg(dv + k * plane + off), __ldg(dv + (5 + k) * plane + off),
+                      __ldg(dv + (10 + k) * plane + off), inv_s, n.dx[k], n.dy[k], n.dd[k]);
     }
 }
 
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
                                                                 const __grid_constant__ CUtensorMap map16, TbtArgs A)
 {
     const float scale = A.scale, inv_s = A.inv_s;
-    constexpr int H = Ms<K>::H;
+    using Codec = typename Ms<K>::C;
     using G = TbtMsGeom;
     constexpr int NST = G::NST, HL = G::HL;
     extern __shared__ __align__(128) unsigned char tbt_smem_raw[];
@@ -427,8 +428,8 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
     if (__all_sync(0xffffffffu, ok)) {
         // f*_(0,1)(t) of the own column in staged row 0 (row y0-2): the pull source of row y0-1
         MsNode n;
-        if (own_staged) ms_node_smem<H>(sbase, idx, inv_s, n);
-        else ms_node_global<H>(A.src, plane, (long long)row_of(y0 - 2) * A.pitch + xc, inv_s, n);
+        if (own_staged) ms_node_smem<K>(sbase, idx, inv_s, n);
+        else ms_node_global<K>(A.src, plane, (long long)row_of(y0 - 2) * A.pitch + xc, inv_s, n);
         ms_node_dir(n, 1, fa, fb, d1_prev);
     }
     for (int i = 0; i + 2 < nin; ++i) {
@@ -445,8 +446,8 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
         {
             // own node of row r (all four directions) and (0,-1) of row r+1
             MsNode n;
-            if (own_staged) ms_node_smem<H>(sc, idx, inv_s, n);
-            else ms_node_global<H>(A.src, plane, (long long)row_of(r) * A.pitch + xc, inv_s, n);
+            if (own_staged) ms_node_smem<K>(sc, idx, inv_s, n);
+            else ms_node_global<K>(A.src, plane, (long long)row_of(r) * A.pitch + xc, inv_s, n);
             float o0[5], o1[5], o2[5], o3[5], p3[5];
             ms_node_dir(n, 0, fa, fb, o0);
             ms_node_dir(n, 1, fa, fb, o1);
@@ -454,21 +455,21 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
             ms_node_dir(n, 3, fa, fb, o3);
             {
                 MsNode np;
-                if (own_staged) ms_node_smem<H>(sp, idx, inv_s, np);
-                else ms_node_global<H>(A.src, plane, (long long)row_of(r + 1) * A.pitch + xc, inv_s, np);
+                if (own_staged) ms_node_smem<K>(sp, idx, inv_s, np);
+                else ms_node_global<K>(A.src, plane, (long long)row_of(r + 1) * A.pitch + xc, inv_s, np);
                 ms_node_dir(np, 3, fa, fb, p3);
             }
             float hl[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, hr[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
             if (lane == 0) {
                 MsNode h;
-                if (left_staged) ms_node_smem<H>(sc, idx - 1, inv_s, h);
-                else ms_node_global<H>(A.src, plane, (long long)row_of(r) * A.pitch + xl, inv_s, h);
+                if (left_staged) ms_node_smem<K>(sc, idx - 1, inv_s, h);
+                else ms_node_global<K>(A.src, plane, (long long)row_of(r) * A.pitch + xl, inv_s, h);
                 ms_node_dir(h, 0, fa, fb, hl);
             }
             if (lane == 31) {
                 MsNode h;
-                if (right_staged) ms_node_smem<H>(sc, idx + 1, inv_s, h);
-                else ms_node_global<H>(A.src, plane, (long long)row_of(r) * A.pitch + xr, inv_s, h);
+                if (right_staged) ms_node_smem<K>(sc, idx + 1, inv_s, h);
+                else ms_node_global<K>(A.src, plane, (long long)row_of(r) * A.pitch + xr, inv_s, h);
                 ms_node_dir(h, 2, fa, fb, hr);
             }
             float f[4][5];
@@ -534,15 +535,19 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
                 float m0[5], dx[5], dy[5], dd[5];
                 ms_moments(o, fa, fb, m0, dx, dy, dd);
                 float* m0p = static_cast<float*>(A.dst);
-                typename Fmt<H>::E* dv = reinterpret_cast<typename Fmt<H>::E*>(m0p + 5 * plane);
+                unsigned short* dv = reinterpret_cast<unsigned short*>(m0p + 5 * plane);
                 const long long off = (long long)q * A.pitch + xs;
+                bool sat = false;
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
                     m0p[k * plane + off] = m0[k];
-                    dv[k * plane + off] = Fmt<H>::st(dx[k] * scale);
-                    dv[(5 + k) * plane + off] = Fmt<H>::st(dy[k] * scale);
-                    dv[(10 + k) * plane + off] = Fmt<H>::st(dd[k] * scale);
+                    unsigned short wx, wy, wz;
+                    Codec::encode(dx[k] * scale, dy[k] * scale, dd[k] * scale, wx, wy, wz, sat);
+                    dv[k * plane + off] = wx;
+                    dv[(5 + k) * plane + off] = wy;
+                    dv[(10 + k) * plane + off] = wz;
                 }
+                if (sat && A.sat) atomicOr(A.sat, 1);
             }
         }
 #pragma unroll

@@ -141,7 +141,7 @@ def long_run(steps=100_000, nx=512, ny=256, cK2=1.1, cmu2=0.4, cfl=None, dt=None
             "wall_s": wall}
 
 
-def precision_errors(n=8192, steps=5000, formats=("f32", "bf16", "f16", "ms_bf16", "ms_f16"), seeds=(1, 2),
+def precision_errors(n=8192, steps=5000, formats=("f32", "bf16", "f16", "ms_bf16", "ms_f16", "ms_bfp"), seeds=(1, 2),
                      ell=64.0, std=1e-3, cK2=1.5, cmu2=0.5, cfl=0.9, every=1000, device="cuda", wl=None):
     """Relative L2 of v_x, v_y, j_s, j_d, j_xy at steps every, 2 every, ..., steps: each
     storage format against the FP64 run (kept as snapshots on the device).  ``wl``: the

@@ -18,9 +18,9 @@ from .build import LIB
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CFL, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LBM_ERR_STATE = range(8)
 LBM_PERIODIC, LBM_DIRICHLET = 0, 1
-LBM_F64, LBM_F32, LBM_BF16, LBM_F16, LBM_MS_BF16, LBM_MS_F16 = 0, 1, 2, 3, 4, 5
+LBM_F64, LBM_F32, LBM_BF16, LBM_F16, LBM_MS_BF16, LBM_MS_F16, LBM_MS_BFP = 0, 1, 2, 3, 4, 5, 6
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "bf16": LBM_BF16, "f16": LBM_F16, "ms_bf16": LBM_MS_BF16,
-           "ms_f16": LBM_MS_F16}
+           "ms_f16": LBM_MS_F16, "ms_bfp": LBM_MS_BFP}
 STATUS_NAMES = ["LBM_OK", "LBM_ERR_ARG", "LBM_ERR_CFL", "LBM_ERR_OOM", "LBM_ERR_CUDA", "LBM_ERR_UNSTABLE",
                 "LBM_ERR_TIMEOUT", "LBM_ERR_STATE"]
 

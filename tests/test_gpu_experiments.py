@@ -49,7 +49,8 @@ def test_long_run_energy_fp64(lbm):
 
 def test_precision_errors_ordering(lbm):
     """Storage formats against the FP64 run on a small lattice: FP32 within its 1e-5 bar,
-    FP16 and moment-space formats below BF16 (more mantissa bits or fewer rounded values)."""
+    FP16 and moment-space formats below BF16 (more mantissa bits or fewer rounded values),
+    block floating point below FP16 deviations (15-bit mantissas sharing an exponent)."""
     res = X.precision_errors(n=256, steps=300, ell=16.0, every=100)
     assert res["checkpoints"] == [100, 200, 300]
     r = res["formats"]
@@ -57,3 +58,4 @@ def test_precision_errors_ordering(lbm):
     assert worst["f32"] < 1e-5, worst
     assert worst["ms_f16"] < worst["f16"] < worst["bf16"], worst
     assert worst["ms_bf16"] < worst["bf16"], worst
+    assert worst["ms_bfp"] < worst["ms_f16"], worst

@@ -31,7 +31,7 @@ def grf8192():
 
 
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5), ("bf16", 1e-2), ("f16", 1.5e-3),
-                                         ("ms_bf16", 5e-3), ("ms_f16", 1e-3)])
+                                         ("ms_bf16", 5e-3), ("ms_f16", 1e-3), ("ms_bfp", 1e-3)])
 def test_periodic_8192_sampled_against_oracle_patches(lbm, grf8192, storage, tol):
     import torch
     wl = grf8192
@@ -81,9 +81,9 @@ def test_periodic_8192_sampled_against_oracle_patches(lbm, grf8192, storage, tol
     # properties at full size: sum of U and the weighted norm are invariants (periodic, b = 0), up
     # to the storage format's rounding (populations in 16 bits carry U in 16 bits; the moment
     # space keeps U itself in FP32)
-    atol = {"f64": 1e-12, "f32": 1e-6, "ms_bf16": 1e-6, "ms_f16": 1e-6, "f16": 1e-3, "bf16": 1e-2}[storage]
+    atol = {"f64": 1e-12, "f32": 1e-6, "ms_bf16": 1e-6, "ms_f16": 1e-6, "ms_bfp": 1e-6, "f16": 1e-3, "bf16": 1e-2}[storage]
     assert np.all(np.abs(s1 - s0) <= atol * (np.abs(s0) + np.sqrt(n * n) * 1e-3)), (storage, s1 - s0)
-    etol = {"f64": 1e-13, "f32": 1e-5, "ms_bf16": 1e-3, "ms_f16": 1e-4, "f16": 1e-3, "bf16": 1e-2}[storage]
+    etol = {"f64": 1e-13, "f32": 1e-5, "ms_bf16": 1e-3, "ms_f16": 1e-4, "ms_bfp": 1e-4, "f16": 1e-3, "bf16": 1e-2}[storage]
     assert abs(e1 - e0) <= etol * e0, (storage, (e1 - e0) / e0)
 
 

@@ -153,7 +153,7 @@ def test_checkpoint_resume_is_bit_exact(lbm):
 
 
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("bf16", 5e-2), ("f16", 5e-3), ("ms_bf16", 1e-2),
-                                         ("ms_f16", 1e-3)])
+                                         ("ms_f16", 1e-3), ("ms_bfp", 1e-3)])
 def test_reduced_precision_against_oracle(lbm, storage, tol):
     """Populations stored in FP32 / BF16 / FP16 with FP32 arithmetic: relative L2 of the
     moment fields against the FP64 oracle after 200 steps of the config-1 problem."""
@@ -216,7 +216,7 @@ def test_general_omega_matches_oracle(lbm, dirichlet):
     np.testing.assert_allclose(f, o.f, atol=1e-12 * np.max(np.abs(o.f)))
 
 
-@pytest.mark.parametrize("storage,tol", [("ms_bf16", 2e-2), ("ms_f16", 2e-3)])
+@pytest.mark.parametrize("storage,tol", [("ms_bf16", 2e-2), ("ms_f16", 2e-3), ("ms_bfp", 2e-3)])
 def test_moment_space_storage_dirichlet_with_forcing(lbm, storage, tol):
     """Moment-space storage (FP32 U, 16-bit non-equilibrium moments) on the Dirichlet
     manufactured solution with body load: every output field against the oracle."""
@@ -301,7 +301,7 @@ def test_two_step_fusion_16bit_against_oracle(lbm, storage, tol):
     assert errs[2] < tol and errs[2] <= 1.2 * errs[1], errs
 
 
-@pytest.mark.parametrize("storage,tol", [("ms_bf16", 1e-2), ("ms_f16", 1e-3)])
+@pytest.mark.parametrize("storage,tol", [("ms_bf16", 1e-2), ("ms_f16", 1e-3), ("ms_bfp", 1e-3)])
 @pytest.mark.parametrize("dirichlet", [False, True])
 def test_two_step_fusion_moment_space_against_oracle(lbm, storage, tol, dirichlet):
     """Moment-space storage advanced two steps per pass by the staged kernel: the moment
@@ -508,4 +508,26 @@ def test_staged_two_step_kernel_reports_a_wait_that_runs_out(lbm):
     ref.step(4)
     np.testing.assert_array_equal(got, ref.populations()[0])
     ref.close()
+    lat.close()
+
+
+def test_block_floating_point_saturation_is_reported(lbm):
+    """LBM_MS_BFP: the deviation scale is fixed at initialisation; a body load that drives the
+    deviations far beyond 8 times their initial size saturates blocks, which lbm_check_finite
+    reports once as LBM_ERR_UNSTABLE.  A run within range reports nothing."""
+    g = W.grf_periodic(64, 64, 1.5, 0.5, ell=8.0, std=1e-3, seeds=(3, 4), steps=0)
+    ok = lbm.Lattice(g.nx, g.ny, g.dx, g.dt, g.cK, g.cmu, storage="ms_bfp", track_displacement=False)
+    ok.init(g.U0, g.dU0dx, g.dU0dy)
+    ok.step(300)
+    assert ok.finite()
+    ok.close()
+    wl = W.periodic_mms(32, 1.5, 0.5, cfl=0.9, steps=60, amp=1e-2, kx=2 * math.pi, ky=2 * math.pi)
+    lat = lbm.Lattice(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, storage="ms_bfp", track_displacement=False)
+    lat.set_forcing(*wl.forcing)
+    tiny = 1e-7
+    lat.init(wl.U0 * tiny, wl.dU0dx * tiny, wl.dU0dy * tiny, wl.body_load(0) * tiny)
+    lat.step(wl.steps)
+    assert not lat.finite()
+    assert "block" in lbm.lbm_last_error(lat.ctx)
+    assert lat.finite()                     # reported once, the flag is cleared
     lat.close()
