@@ -42,7 +42,8 @@ BYTES_PER_NODE = {"f64": 320, "f32": 160, "bf16": 80, "f16": 80,    # one read +
 FP64_OPS_PER_NODE = 47                                                # DADD/DFMA per node, no forcing
 SPLIT_LEVEL = 1               # lbm_set_fp64_split default: the 15 sums of a node on the integer pipe
 SPLIT_INTEGER_ADDS = 15
-FUSED = {"f32", "bf16", "f16", "ms_bf16", "ms_f16", "ms_bfp"}   # two steps per pass by default
+# steps per launch of each format at the library's defaults (lbm_set_step_fusion)
+STEPS_PER_PASS = {"f64": 1, "f32": 2, "bf16": 2, "f16": 2, "ms_bf16": 3, "ms_f16": 3, "ms_bfp": 3}
 # DRAM bytes per node and launch of each step kernel (dram__bytes_read.sum + dram__bytes_write.sum
 # from one ncu capture of this benchmark's own 8192^2 workload, averaged over its launches; no
 # scaling), valid only while the kernel sources hash to "sha256".  "<fmt>_fused" is one launch of
@@ -381,10 +382,9 @@ def run_ours(args):
         del out
         lat.close()
         mlups_rank = n_nodes * args.steps / (ms * 1e-3) / 1e6
-        fused = (storage in FUSED or storage in args.fuse_formats) and not args.no_fusion
-        results[storage] = {"ms_per_step": ms / args.steps, "mlups": mlups_rank * ws,
-                            "steps_per_pass": 2 if fused else 1,
-                            "launches": (args.steps // 2 + args.steps % 2) if fused else args.steps}
+        spp = 1 if args.no_fusion else (2 if storage in args.fuse_formats else STEPS_PER_PASS[storage])
+        results[storage] = {"ms_per_step": ms / args.steps, "mlups": mlups_rank * ws, "steps_per_pass": spp,
+                            "launches": args.steps // spp + (1 if args.steps % spp else 0)}
 
     # N > 1: one lattice of nx x (N ny) rows split into row slabs, one per rank, with the halo
     # exchange of the streaming step (5 values per column and cut each way) over NCCL every
@@ -562,7 +562,8 @@ def run_ours(args):
                     "launches": r["launches"],
                     "hbm": {"achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                             "frac": round(ach / hbm_peak, 4), "bytes_per_node_step": bpn,
-                            "traffic": traffic_per_launch(s if r["steps_per_pass"] == 1 else s + "_fused", n_nodes)},
+                            "traffic": traffic_per_launch({1: s, 2: s + "_fused", 3: s + "_fused3"}[r["steps_per_pass"]],
+                                                          n_nodes)},
                     "rel_l2_vs_f64_after_timed_run": {k: float(f"{v:.3e}") for k, v in r["rel_l2_vs_f64"].items()},
                     "timed_run_error_at_step": args.warmup + args.steps}
         if precision is not None and s in precision["formats"]:

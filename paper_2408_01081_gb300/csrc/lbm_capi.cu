@@ -209,6 +209,7 @@ struct lbm_ctx {
     bool maps_ok = false;        // row maps of both buffers encoded (all formats but FP64)
     CUtensorMap map[2][2];       // row maps of buf[0], buf[1] for the staged fused kernel
                                  // ([buffer][part]; moment space: FP32 part, 16-bit part)
+    CUtensorMap map3[2][2];      // moment space: row maps of the three-step kernel (narrower box)
 };
 
 namespace {
@@ -397,10 +398,11 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
     ctx->a = p->cK / c;
     ctx->b = p->cmu / c;
     ctx->nwall = 2 * (p->nx + p->ny);
-    // two steps per pass for every reduced format (the staged kernel is faster than single steps
-    // for each of them); rows per block measured best per format at 8192^2
-    ctx->fuse = (p->storage == LBM_F64) ? 1 : 2;
-    ctx->tb_rows = (p->storage == LBM_F32) ? 8 : 32;
+    // several steps per pass for every reduced format (faster than single steps for each of them):
+    // two for the population formats, three for moment space (fewer 16-bit roundings and the
+    // decoding spread over three steps); rows per block measured best per format at 8192^2
+    ctx->fuse = (p->storage == LBM_F64) ? 1 : (p->storage >= LBM_MS_BF16) ? 3 : 2;
+    ctx->tb_rows = (p->storage == LBM_F32) ? 8 : (p->storage >= LBM_MS_BF16) ? 64 : 32;
     // symmetrizer blocks k_ij = g_ij^{-1}, g_ij = 1/4 I + (i A_x + j A_y)/(2c)  (Eq. stability_linear)
     const int VI[4] = {1, 0, -1, 0}, VJ[4] = {0, 1, 0, -1};
     for (int d = 0; d < 4; ++d) {
@@ -442,10 +444,14 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
         ctx->maps_ok = true;
         for (int i = 0; i < 2; ++i) {
             char* b = static_cast<char*>(ctx->buf[i]);
+            const int win3 = lbmk::Tbt3MsGeom::WIN;
             ctx->maps_ok = ctx->maps_ok &&
                            encode_rows_map(&ctx->map[i][0], b, 4, p->nx, p->ny, ctx->pitch, ctx->plane, 5, win) &&
                            encode_rows_map(&ctx->map[i][1], b + 20 * ctx->plane, 2, p->nx, p->ny, ctx->pitch,
-                                           ctx->plane, 15, win);
+                                           ctx->plane, 15, win) &&
+                           encode_rows_map(&ctx->map3[i][0], b, 4, p->nx, p->ny, ctx->pitch, ctx->plane, 5, win3) &&
+                           encode_rows_map(&ctx->map3[i][1], b + 20 * ctx->plane, 2, p->nx, p->ny, ctx->pitch,
+                                           ctx->plane, 15, win3);
         }
     }
     if (e != cudaSuccess) {
@@ -591,8 +597,10 @@ lbm_status lbm_set_staging(lbm_ctx* ctx, int32_t mode)
 lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t rows_per_block)
 {
     LBM_CHECK_CTX(ctx);
-    if ((steps_per_pass != 1 && steps_per_pass != 2) || rows_per_block < 0 || rows_per_block > 65535)
-        return fail(ctx, LBM_ERR_ARG, "steps_per_pass must be 1 or 2 and rows_per_block in [0, 65535]");
+    const bool ms = ctx->p.storage == LBM_MS_BF16 || ctx->p.storage == LBM_MS_F16 || ctx->p.storage == LBM_MS_BFP;
+    if (steps_per_pass < 1 || steps_per_pass > (ms ? 3 : 2) || rows_per_block < 0 || rows_per_block > 65535)
+        return fail(ctx, LBM_ERR_ARG, "steps_per_pass must be 1, 2 (or 3 for moment-space storage) and "
+                                      "rows_per_block in [0, 65535]");
     ctx->fuse = steps_per_pass;
     if (rows_per_block > 0) ctx->tb_rows = rows_per_block;
     return LBM_OK;
@@ -791,7 +799,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
     // with staged rows), omega = 2, no body load, no displacement tracking, periodic or
     // homogeneous Dirichlet
     const bool ms = ctx->p.storage == LBM_MS_BF16 || ctx->p.storage == LBM_MS_F16 || ctx->p.storage == LBM_MS_BFP;
-    const bool fusable = ctx->fuse == 2 && !ctx->slab &&
+    const bool fusable = ctx->fuse >= 2 && !ctx->slab &&
                          (ctx->p.storage == LBM_F32 || ctx->p.storage == LBM_BF16 || ctx->p.storage == LBM_F16 ||
                           (ms && ctx->staging >= 1)) &&
                          ctx->omega == 2.0 && ctx->R == 0 && !ctx->w && !(ctx->p.bc == LBM_DIRICHLET && ctx->g);
@@ -824,6 +832,19 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
             Q.scale = (float)ctx->neq_scale;
             Q.inv_s = (float)(1.0 / ctx->neq_scale);
             Q.sat = reinterpret_cast<int*>(ctx->scratch + kSatSlot);
+            if (ctx->fuse == 3 && ms) {
+                // three steps per pass (moment space): the remainder below runs as one pair or a single step
+                const dim3 q3grid((ctx->p.nx + lbmk::TBT3_OUT - 1) / lbmk::TBT3_OUT, (ctx->p.ny + Q.rows - 1) / Q.rows);
+                while (n >= 3) {
+                    Q.src = ctx->buf[ctx->cur];
+                    Q.dst = ctx->buf[ctx->cur ^ 1];
+                    cudaError_t e = ops->tbt3_step(ctx->map3[ctx->cur], Q, ctx->p.bc == LBM_DIRICHLET, q3grid, ctx->s);
+                    if (e != cudaSuccess) return cuda_fail(ctx, e, "staged three-step kernel");
+                    ctx->cur ^= 1;
+                    ctx->m += 3;
+                    n -= 3;
+                }
+            }
             const dim3 qgrid((ctx->p.nx + lbmk::TBT_OUT - 1) / lbmk::TBT_OUT, (ctx->p.ny + Q.rows - 1) / Q.rows);
             while (n >= 2) {
                 Q.src = ctx->buf[ctx->cur];

@@ -221,6 +221,27 @@ cudaError_t tbt_step(const CUtensorMap* maps, const lbmk::TbtArgs& a, bool diric
     return tbt_t<K>(maps, a, dirichlet, g, s);
 }
 
+template <int KK>
+cudaError_t tbt3_t(const CUtensorMap* maps, const lbmk::TbtArgs& a, bool dirichlet, dim3 g, cudaStream_t s)
+{
+    if constexpr (KK == lbmk::K_MSBF16 || KK == lbmk::K_MSF16 || KK == lbmk::K_MSBFP) {
+        using G = lbmk::Tbt3MsGeom;
+        void (*kern)(CUtensorMap, CUtensorMap, lbmk::TbtArgs) =
+            dirichlet ? lbmk::tbt3_ms_kernel<KK, true> : lbmk::tbt3_ms_kernel<KK, false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        kern<<<g, lbmk::TBT_THREADS, G::SMEM, s>>>(maps[0], maps[1], a);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
+cudaError_t tbt3_step(const CUtensorMap* maps, const lbmk::TbtArgs& a, bool dirichlet, dim3 g, cudaStream_t s)
+{
+    return tbt3_t<K>(maps, a, dirichlet, g, s);
+}
+
 cudaError_t batch_occupancy(int* n)
 {
     return batch_occupancy_t<K>(n);
@@ -236,6 +257,7 @@ namespace lbmh {
 const KindOps LBM_OPS_NAME(LBM_KIND) = {
     K, V, ELEM, NODE_BYTES,
     step, init, moments, get_pop, set_pop, energy, error, finite, batch_step, batch_occupancy, tb2_step, tbt_step,
+    tbt3_step,
     LBM_VEC_SPLIT, VB,
 };
 

@@ -560,4 +560,291 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
     if (lane == 0 && abort_flag) atomicExch(A.timeout, 1);
 }
 
+
+// ---------------------------------------------------------------------------
+// Moment-space storage, three steps per pass (tbt3_ms_kernel).  The same staging as
+// tbt_ms_kernel with one more level in registers: S1 = f*(t+dt) of row r from the
+// staged rows, S2 = f*(t+2dt) of row r-1 from S1 rows r-2..r, S3 = f*(t+3dt) of row
+// r-2 from S2 rows r-3..r-1, stored as moments.  Each level needs one more column
+// on each side than the next, so a warp's S1 columns are X0 - 2 + 28 w + lane and
+// lanes 2..29 store (112 columns per block), and the staged rows run from y0 - 3 to
+// y1 + 2.  The deviations are rounded to 16 bits once per three steps.
+// ---------------------------------------------------------------------------
+constexpr int TB3_OUT = 28;                    // output columns per warp
+constexpr int TBT3_OUT = TBT_WARPS * TB3_OUT;  // output columns per block (112)
+
+struct Tbt3MsGeom {
+    static constexpr int HL = 8;
+    static constexpr int WIN = HL + TBT3_OUT + HL;                     // 128 staged columns
+    static constexpr int M0_BYTES = 5 * WIN * 4;
+    static constexpr int DEV_OFF = (M0_BYTES + 127) / 128 * 128;
+    static constexpr int DEV_BYTES = 15 * WIN * 2;
+    static constexpr int ROW_BYTES = M0_BYTES + DEV_BYTES;
+    static constexpr int STAGE_BYTES = (DEV_OFF + DEV_BYTES + 127) / 128 * 128;
+    static constexpr int NST = LBM_TBT_NSTMS;
+    static constexpr int SMEM = NST * STAGE_BYTES + 128;
+    static_assert((WIN * 4) % 16 == 0 && (WIN * 2) % 16 == 0, "staged row width must be a multiple of 16 bytes");
+};
+
+template <int K>
+__device__ __forceinline__ void ms3_node_smem(uint32_t stage, int c, float inv_s, MsNode& n)
+{
+    using Codec = typename Ms<K>::C;
+    constexpr uint32_t W = Tbt3MsGeom::WIN;
+    const uint32_t m0 = stage + 4u * c, dv = stage + Tbt3MsGeom::DEV_OFF + 2u * c;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        n.m0[k] = lbmt::lds_f32(m0 + 4u * W * k);
+        Codec::decode(lbmt::lds_u16(dv + 2u * W * k), lbmt::lds_u16(dv + 2u * W * (5 + k)),
+                      lbmt::lds_u16(dv + 2u * W * (10 + k)), inv_s, n.dx[k], n.dy[k], n.dd[k]);
+    }
+}
+
+// one collide-and-pull level on rows kept in registers: f*(q) from the rows below (kb: the
+// (0,1) direction of row q-1), at (p: all directions of row q, x-neighbours by shuffles)
+// and above (ka: the (0,-1) direction of row q+1); walls as in tbt_kernel
+template <bool DIRICHLET>
+__device__ __forceinline__ void level_step(const float (&p)[4][5], const float (&kb)[5], const float (&ka)[5], int q,
+                                           int xs, int nx, int ny, float fa, float fb, float (&o)[4][5])
+{
+    const float Dk[5] = {-1.f, -1.f, 1.f, 1.f, 1.f};
+    const bool bot = DIRICHLET && q == 0, top = DIRICHLET && q == ny - 1;
+    float f[4][5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        f[0][k] = __shfl_up_sync(0xffffffffu, p[0][k], 1);
+        f[2][k] = __shfl_down_sync(0xffffffffu, p[2][k], 1);
+        f[1][k] = bot ? Dk[k] * p[3][k] : kb[k];
+        f[3][k] = top ? Dk[k] * p[1][k] : ka[k];
+        if (DIRICHLET && xs == 0) f[0][k] = Dk[k] * p[2][k];
+        if (DIRICHLET && xs == nx - 1) f[2][k] = Dk[k] * p[0][k];
+    }
+    float U[5], rx[5], ry2[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        rx[k] = f[1][k] + f[3][k];
+        ry2[k] = f[0][k] + f[2][k];
+        U[k] = rx[k] + ry2[k];
+    }
+    collide<float>(f, U, rx, ry2, fa, fb, o);
+}
+
+template <int K, bool DIRICHLET>
+__global__ void __launch_bounds__(TBT_THREADS, 2) tbt3_ms_kernel(const __grid_constant__ CUtensorMap map32,
+                                                                 const __grid_constant__ CUtensorMap map16, TbtArgs A)
+{
+    using Codec = typename Ms<K>::C;
+    using G = Tbt3MsGeom;
+    constexpr int NST = G::NST, HL = G::HL;
+    const float scale = A.scale, inv_s = A.inv_s;
+    extern __shared__ __align__(128) unsigned char tbt_smem_raw[];
+    __shared__ __align__(8) unsigned long long full_bar[NST], empty_bar[NST];
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nx = A.nx, ny = A.ny;
+    const int X0 = blockIdx.x * TBT3_OUT;
+    const int y0 = blockIdx.y * A.rows;
+    const int y1 = min(ny, y0 + A.rows);
+    const int nin = (y1 - y0) + 6;                   // staged input rows y0-3 .. y1+2
+    const uint32_t raw = lbmt::smem_u32(tbt_smem_raw);
+    const uint32_t sbase = (raw + 127u) & ~127u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            lbmt::mbar_init(lbmt::smem_u32(&full_bar[s]), 1);
+            lbmt::mbar_init(lbmt::smem_u32(&empty_bar[s]), TBT_WARPS);
+        }
+        abort_flag = 0;
+        lbmt::fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == TBT_WARPS) {
+        if (lane == 0) {
+            lbmt::prefetch_map(&map32);
+            lbmt::prefetch_map(&map16);
+            int j = 0;
+            for (; j < nin; ++j) {
+                const int s = j % NST;
+                const uint32_t fb = lbmt::smem_u32(&full_bar[s]);
+                if (j == A.withhold) continue;
+                if (j >= NST && !lbmt::mbar_wait(lbmt::smem_u32(&empty_bar[s]), ((j / NST) - 1) & 1, &abort_flag))
+                    break;
+                int y = y0 - 3 + j;
+                if (DIRICHLET && (y < 0 || y >= ny)) {
+                    lbmt::mbar_arrive(fb);
+                    continue;
+                }
+                if (!DIRICHLET) y = (y < 0) ? y + ny : (y >= ny ? y - ny : y);
+                const uint32_t st = sbase + s * G::STAGE_BYTES;
+                lbmt::mbar_arrive_expect_tx(fb, G::ROW_BYTES);
+                lbmt::tma_load_3d(st, &map32, X0 - HL, y, 0, fb);
+                lbmt::tma_load_3d(st + G::DEV_OFF, &map16, X0 - HL, y, 0, fb);
+            }
+            for (int q = (j > NST ? j - NST : 0); q < j; ++q)
+                if (q != A.withhold) lbmt::mbar_drain(lbmt::smem_u32(&full_bar[q % NST]), (q / NST) & 1);
+            if (abort_flag) atomicExch(A.timeout, 1);
+        }
+        return;
+    }
+
+    const long long plane = A.plane;
+    const int xs = X0 - 2 + TB3_OUT * warp + lane;   // this lane's S1 column
+    const int xc = DIRICHLET ? (xs < 0 ? 0 : (xs >= nx ? nx - 1 : xs)) : ((xs % nx) + nx) % nx;
+    const bool out_lane = (lane >= 2) && (lane < 2 + TB3_OUT) && (xs >= 0) && (xs < nx);
+    const bool own_staged = DIRICHLET || (xs >= 0 && xs < nx);
+    const int xl = (xc == 0) ? nx - 1 : xc - 1, xr = (xc == nx - 1) ? 0 : xc + 1;
+    const bool left_staged = DIRICHLET || (xs - 1 >= 0 && xs - 1 < nx);
+    const bool right_staged = DIRICHLET || (xs + 1 >= 0 && xs + 1 < nx);
+    const int idx = xs - X0 + HL;
+    const float fa = A.af, fb = A.bf;
+    const float Dk[5] = {-1.f, -1.f, 1.f, 1.f, 1.f};
+
+    // S1 rows r-1 (p1, all directions) and r-2 (k1: (0,1)); S2 rows r-2 (p2) and r-3 (k2: (0,1));
+    // f*_(0,1)(t) of the own column in the staged row below the current one (d1)
+    float p1[4][5], k1[5], p2[4][5], k2[5], d1[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        k1[k] = k2[k] = d1[k] = 0.f;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) p1[d][k] = p2[d][k] = 0.f;
+    }
+    auto row_of = [&](int r) { return (r < 0) ? r + ny : (r >= ny ? r - ny : r); };
+    bool ok = lbmt::mbar_wait(lbmt::smem_u32(&full_bar[0]), 0, &abort_flag) &&
+              lbmt::mbar_wait(lbmt::smem_u32(&full_bar[1 % NST]), (1 / NST) & 1, &abort_flag);
+    if (__all_sync(0xffffffffu, ok)) {
+        MsNode n;
+        if (own_staged) ms3_node_smem<K>(sbase, idx, inv_s, n);
+        else ms_node_global<K>(A.src, plane, (long long)row_of(y0 - 3) * A.pitch + xc, inv_s, n);
+        ms_node_dir(n, 1, fa, fb, d1);
+    }
+    for (int i = 0; i + 2 < nin; ++i) {
+        const int r = y0 - 2 + i;                    // S1 row, from staged rows i, i+1, i+2
+        {
+            const int j = i + 2;
+            ok = ok && lbmt::mbar_wait(lbmt::smem_u32(&full_bar[j % NST]), (j / NST) & 1, &abort_flag);
+        }
+        if (!__all_sync(0xffffffffu, ok)) break;
+        const uint32_t sc = sbase + ((i + 1) % NST) * G::STAGE_BYTES;   // row r
+        const uint32_t sp = sbase + ((i + 2) % NST) * G::STAGE_BYTES;   // row r+1
+        float c1[4][5];
+        {
+            MsNode n;
+            if (own_staged) ms3_node_smem<K>(sc, idx, inv_s, n);
+            else ms_node_global<K>(A.src, plane, (long long)row_of(r) * A.pitch + xc, inv_s, n);
+            float o0[5], o1[5], o2[5], o3[5], p3[5];
+            ms_node_dir(n, 0, fa, fb, o0);
+            ms_node_dir(n, 1, fa, fb, o1);
+            ms_node_dir(n, 2, fa, fb, o2);
+            ms_node_dir(n, 3, fa, fb, o3);
+            {
+                MsNode np;
+                if (own_staged) ms3_node_smem<K>(sp, idx, inv_s, np);
+                else ms_node_global<K>(A.src, plane, (long long)row_of(r + 1) * A.pitch + xc, inv_s, np);
+                ms_node_dir(np, 3, fa, fb, p3);
+            }
+            float hl[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, hr[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            if (lane == 0) {
+                MsNode h;
+                if (left_staged) ms3_node_smem<K>(sc, idx - 1, inv_s, h);
+                else ms_node_global<K>(A.src, plane, (long long)row_of(r) * A.pitch + xl, inv_s, h);
+                ms_node_dir(h, 0, fa, fb, hl);
+            }
+            if (lane == 31) {
+                MsNode h;
+                if (right_staged) ms3_node_smem<K>(sc, idx + 1, inv_s, h);
+                else ms_node_global<K>(A.src, plane, (long long)row_of(r) * A.pitch + xr, inv_s, h);
+                ms_node_dir(h, 2, fa, fb, hr);
+            }
+            float f[4][5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const float l = __shfl_up_sync(0xffffffffu, o0[k], 1);
+                const float rr = __shfl_down_sync(0xffffffffu, o2[k], 1);
+                f[0][k] = (lane == 0) ? hl[k] : l;
+                f[2][k] = (lane == 31) ? hr[k] : rr;
+                f[1][k] = d1[k];
+                f[3][k] = p3[k];
+            }
+            if (DIRICHLET) {
+                const bool bot = r == 0, top = r == ny - 1;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    if (xc == 0) f[0][k] = Dk[k] * o2[k];
+                    if (xc == nx - 1) f[2][k] = Dk[k] * o0[k];
+                    if (bot) f[1][k] = Dk[k] * o3[k];
+                    if (top) f[3][k] = Dk[k] * o1[k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) d1[k] = o1[k];
+            float U[5], rx[5], ry2[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                rx[k] = f[1][k] + f[3][k];
+                ry2[k] = f[0][k] + f[2][k];
+                U[k] = rx[k] + ry2[k];
+            }
+            collide<float>(f, U, rx, ry2, fa, fb, c1);
+            if (DIRICHLET && !(r >= 0 && r < ny))
+#pragma unroll
+                for (int d = 0; d < 4; ++d)
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) c1[d][k] = 0.f;
+        }
+        __syncwarp();
+        if (lane == 0) lbmt::mbar_arrive(lbmt::smem_u32(&empty_bar[i % NST]));
+        // ---- S2(r-1) from S1 rows r-2 (k1), r-1 (p1), r (c1) ----
+        const int q2 = r - 1;
+        float c2[4][5];
+        const bool has2 = q2 >= y0 - 1;
+        if (has2) {
+            level_step<DIRICHLET>(p1, k1, c1[3], q2, xs, nx, ny, fa, fb, c2);
+            if (DIRICHLET && !(q2 >= 0 && q2 < ny))
+#pragma unroll
+                for (int d = 0; d < 4; ++d)
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) c2[d][k] = 0.f;
+            // ---- S3(r-2) from S2 rows r-3 (k2), r-2 (p2), r-1 (c2) ----
+            const int q3 = r - 2;
+            if (q3 >= y0) {
+                float o[4][5];
+                level_step<DIRICHLET>(p2, k2, c2[3], q3, xs, nx, ny, fa, fb, o);
+                if (out_lane) {
+                    float m0[5], dx[5], dy[5], dd[5];
+                    ms_moments(o, fa, fb, m0, dx, dy, dd);
+                    float* m0p = static_cast<float*>(A.dst);
+                    unsigned short* dv = reinterpret_cast<unsigned short*>(m0p + 5 * plane);
+                    const long long off = (long long)q3 * A.pitch + xs;
+                    bool sat = false;
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        m0p[k * plane + off] = m0[k];
+                        unsigned short wx, wy, wz;
+                        Codec::encode(dx[k] * scale, dy[k] * scale, dd[k] * scale, wx, wy, wz, sat);
+                        dv[k * plane + off] = wx;
+                        dv[(5 + k) * plane + off] = wy;
+                        dv[(10 + k) * plane + off] = wz;
+                    }
+                    if (sat && A.sat) atomicOr(A.sat, 1);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                k2[k] = p2[1][k];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) p2[d][k] = c2[d][k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            k1[k] = p1[1][k];
+#pragma unroll
+            for (int d = 0; d < 4; ++d) p1[d][k] = c1[d][k];
+        }
+    }
+    if (lane == 0 && abort_flag) atomicExch(A.timeout, 1);
+}
+
 }  // namespace lbmk
