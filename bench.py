@@ -47,13 +47,15 @@ STEPS_PER_PASS = {"f64": 1, "f32": 2, "bf16": 2, "f16": 2, "ms_bf16": 3, "ms_f16
 # DRAM bytes per node and launch of each step kernel (dram__bytes_read.sum + dram__bytes_write.sum
 # from one ncu capture of this benchmark's own 8192^2 workload, averaged over its launches; no
 # scaling), valid only while the kernel sources hash to "sha256".  "<fmt>_fused" is one launch of
-# the two-step kernel (two steps), "f64_pipe" the FP64 step with every operation on the FP64 pipe.
-TRAFFIC_CAPTURE = {"sha256": "a36b2a53d9ea97ec738afd2a84cce9f03c5744d0ce56d38d83ec993ce1540427",
+# the two-step kernel (two steps), "<fmt>_fused3" of the three-step kernel, "f64_pipe" the FP64
+# step with every operation on the FP64 pipe.
+TRAFFIC_CAPTURE = {"sha256": "636853b3b8b5e11d5b731897d44f714d3ba3be4ee6225d876ead868eede7702e",
                    "nodes": 8192 * 8192,
-                   "bytes_per_node": {"f64": 321.56, "f64_pipe": 319.24, "f32": 159.34, "f32_fused": 160.63,
-                                      "bf16": 79.29, "bf16_fused": 84.64, "f16": 79.30, "f16_fused": 84.64,
-                                      "ms_bf16": 99.33, "ms_bf16_fused": 105.19, "ms_f16": 99.32,
-                                      "ms_f16_fused": 105.21}}
+                   "bytes_per_node": {"f64": 321.56, "f64_pipe": 319.25, "f32": 159.35, "f32_fused": 160.64,
+                                      "bf16": 79.29, "bf16_fused": 84.64, "f16": 79.29, "f16_fused": 84.64,
+                                      "ms_bf16_fused": 103.39, "ms_bf16_fused3": 103.96,
+                                      "ms_f16_fused": 103.41, "ms_f16_fused3": 103.94,
+                                      "ms_bfp_fused": 103.30, "ms_bfp_fused3": 103.87}}
 KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_01081_gb300/csrc/lbm_kind.cu",
                   "paper_2408_01081_gb300/csrc/lbm_tb.cuh", "paper_2408_01081_gb300/csrc/lbm_ms.cuh",
                   "paper_2408_01081_gb300/csrc/lbm_tbt.cuh", "paper_2408_01081_gb300/csrc/lbm_tma.cuh"]
@@ -62,7 +64,7 @@ KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_010
 # valid only while the kernel sources hash to "sha256".  Each SM issues 64 ALU-pipe and 2
 # FP64-pipe thread instructions per clock, so one node needs at least
 # max(alu / 64, fp64 / 2) SM clocks: the arithmetic roof of this kernel.
-PIPE_CAPTURE = {"sha256": "a36b2a53d9ea97ec738afd2a84cce9f03c5744d0ce56d38d83ec993ce1540427",
+PIPE_CAPTURE = {"sha256": "636853b3b8b5e11d5b731897d44f714d3ba3be4ee6225d876ead868eede7702e",
                 "alu_per_node": 1127.0, "fp64_per_node": 32.0, "fma_per_node": 260.0}
 ALU_LANES_PER_SM, FP64_LANES_PER_SM, N_SM = 64, 2, 152
 
