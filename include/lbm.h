@@ -17,7 +17,10 @@
  *   - `on_device` = 1: the pointer is CUDA device memory (e.g. a torch tensor's
  *     data_ptr); 0: host memory.  Host pointers are copied synchronously with
  *     respect to the context's stream; the caller keeps ownership of every buffer
- *     it passes and may free it when the call returns.
+ *     it passes and may free it when the call returns.  Pinned host memory
+ *     (cudaHostAlloc / cudaHostRegister, e.g. a pinned torch tensor) is read and
+ *     written by the kernels in place, without a device copy; pageable host memory
+ *     goes through a temporary device buffer.
  *   - The context owns all device memory it allocates (created by lbm_create,
  *     released by lbm_destroy).  Work is enqueued on the stream given at creation.
  *   - No call aborts.  Errors return a status; LBM_ERR_CUDA is sticky: every later

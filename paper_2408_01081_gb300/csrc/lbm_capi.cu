@@ -282,7 +282,26 @@ void node_grid(const lbm_ctx* ctx, dim3& grid, dim3& block)
     block = dim3(256);
 }
 
-// copy a host or device FP64 array of n values into a fresh device buffer (stream ordered)
+// The device address of pinned (page-locked) host memory, which kernels read and write in place
+// (over NVLink-C2C on GB300), or nullptr for pageable memory.
+void* pinned_view(const void* p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost) return nullptr;
+    void* d = nullptr;
+    if (cudaHostGetDevicePointer(&d, const_cast<void*>(p), 0) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return d;
+}
+
+// a device-readable view of a host or device FP64 array of n values: device memory and pinned
+// host memory as they are, pageable host memory copied into a fresh device buffer (stream ordered)
 lbm_status stage_in(lbm_ctx* ctx, const double* src, size_t n, int on_device, const double** dev, double** owned)
 {
     *owned = nullptr;
@@ -292,6 +311,10 @@ lbm_status stage_in(lbm_ctx* ctx, const double* src, size_t n, int on_device, co
     }
     if (on_device) {
         *dev = src;
+        return LBM_OK;
+    }
+    if (const void* v = pinned_view(src)) {
+        *dev = static_cast<const double*>(v);
         return LBM_OK;
     }
     double* d = nullptr;
@@ -890,13 +913,17 @@ lbm_status lbm_moments(lbm_ctx* ctx, double* out, int32_t on_device)
     if (st != LBM_OK) return st;
     const size_t n = (size_t)ctx->p.nx * ctx->nyi;
     double* dst = out;
-    if (!on_device) LBM_CUDA(ctx, cudaMallocAsync((void**)&dst, 10 * n * sizeof(double), ctx->s));
+    // pinned host memory is written in place by the kernel; pageable memory through a device buffer
+    double* view = on_device ? nullptr : static_cast<double*>(pinned_view(out));
+    const bool staged = !on_device && !view;
+    if (view) dst = view;
+    if (staged) LBM_CUDA(ctx, cudaMallocAsync((void**)&dst, 10 * n * sizeof(double), ctx->s));
     dim3 grid, block;
     node_grid(ctx, grid, block);
     cudaError_t e = ctx->ops->moments(node_args(ctx, ctx->m), dst, grid, block, ctx->s);
-    if (e == cudaSuccess && !on_device)
+    if (e == cudaSuccess && staged)
         e = cudaMemcpyAsync(out, dst, 10 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->s);
-    if (!on_device) cudaFreeAsync(dst, ctx->s);
+    if (staged) cudaFreeAsync(dst, ctx->s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "moments");
     if (!on_device) LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
     return LBM_OK;

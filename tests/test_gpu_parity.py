@@ -532,3 +532,39 @@ def test_block_floating_point_saturation_is_reported(lbm):
     assert "block" in lbm.lbm_last_error(lat.ctx)
     assert lat.finite()                     # reported once, the flag is cleared
     lat.close()
+
+
+def test_pinned_host_buffers_are_used_in_place(lbm):
+    """Host arrays in pinned memory are read and written by the kernels in place; the
+    results equal those through pageable host memory and through device memory."""
+    import torch
+    wl = _config1(steps=10)
+    outs = []
+    for kind in ("pageable", "pinned", "device"):
+        lat = gpu_lattice(lbm, wl, storage="f64")        # forcing and init as in config 1
+        if kind == "pageable":
+            lat.init(wl.U0, wl.dU0dx, wl.dU0dy, wl.body_load(0), wl.u0)
+        else:
+            conv = (lambda a: torch.from_numpy(a).pin_memory()) if kind == "pinned" else \
+                   (lambda a: torch.from_numpy(a).cuda())
+            args = [conv(a) for a in (wl.U0, wl.dU0dx, wl.dU0dy, wl.body_load(0), wl.u0)]
+            if kind == "pinned":
+                lat.init(*[a.numpy() for a in args])
+            else:
+                torch.cuda.synchronize()
+                lat.init(*args)
+        lat.step(wl.steps)
+        if kind == "pinned":
+            out = torch.empty((10, wl.ny, wl.nx), dtype=torch.float64).pin_memory()
+            lat.moments(out.numpy())
+            outs.append(out.numpy().copy())
+        elif kind == "device":
+            out = torch.empty((10, wl.ny, wl.nx), dtype=torch.float64, device="cuda")
+            lat.moments(out)
+            torch.cuda.synchronize()
+            outs.append(out.cpu().numpy())
+        else:
+            outs.append(lat.moments())
+        lat.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
