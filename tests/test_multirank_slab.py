@@ -115,6 +115,7 @@ def test_slab_creation_is_validated_before_any_device_work():
         with pytest.raises(lbm.LbmError) as e:
             lbm.lbm_create_slab(8, 8, 0.1, 0.01, 1.0, 0.5, y0, rows)
         assert e.value.status == lbm.LBM_ERR_ARG, (y0, rows)
-    with pytest.raises(lbm.LbmError) as e:
-        lbm.lbm_create_slab(8, 8, 0.1, 0.01, 1.0, 0.5, 0, 4, storage=lbm.LBM_MS_F16)
-    assert e.value.status == lbm.LBM_ERR_ARG
+    for st in (lbm.LBM_MS_BF16, lbm.LBM_MS_F16, lbm.LBM_MS_BFP):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_create_slab(8, 8, 0.1, 0.01, 1.0, 0.5, 0, 4, storage=st)
+        assert e.value.status == lbm.LBM_ERR_ARG
