@@ -557,7 +557,7 @@ def run_ours(args):
             continue
         r = results[s]
         nps = n_nodes / (r["ms_per_step"] * 1e-3)
-        bpn = BYTES_PER_NODE[s] / r["steps_per_pass"]      # algorithmic bytes per node and step
+        bpn = round(BYTES_PER_NODE[s] / r["steps_per_pass"], 3)   # algorithmic bytes per node and step
         ach = bpn * nps / 1e9
         mixed[s] = {"mlups": round(r["mlups"], 1), "ms_per_step": round(r["ms_per_step"], 4),
                     "speedup_vs_f64": round(r["speedup_vs_f64"], 3), "steps_per_pass": r["steps_per_pass"],
