@@ -209,7 +209,7 @@ struct lbm_ctx {
     bool maps_ok = false;        // row maps of both buffers encoded (all formats but FP64)
     CUtensorMap map[2][2];       // row maps of buf[0], buf[1] for the staged fused kernel
                                  // ([buffer][part]; moment space: FP32 part, 16-bit part)
-    CUtensorMap map3[2][2];      // moment space: row maps of the three-step kernel (narrower box)
+    CUtensorMap map3[2][2];      // row maps of the three-step kernels (narrower box)
 };
 
 namespace {
@@ -457,10 +457,14 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
     if (e == cudaSuccess && (p->storage == LBM_F32 || p->storage == LBM_BF16 || p->storage == LBM_F16)) {
         const int es = ctx->ops->elem_bytes;
         const int win = es == 4 ? lbmk::TbtGeom<4>::WIN : lbmk::TbtGeom<2>::WIN;
+        const int win3 = es == 4 ? lbmk::Tbt3Geom<4>::WIN : lbmk::Tbt3Geom<2>::WIN;
         ctx->maps_ok = true;
         for (int i = 0; i < 2; ++i)
-            ctx->maps_ok = ctx->maps_ok && encode_rows_map(&ctx->map[i][0], ctx->buf[i], es, p->nx, p->ny, ctx->pitch,
-                                                           ctx->plane, 20, win);
+            ctx->maps_ok = ctx->maps_ok &&
+                           encode_rows_map(&ctx->map[i][0], ctx->buf[i], es, p->nx, p->ny, ctx->pitch, ctx->plane, 20,
+                                           win) &&
+                           encode_rows_map(&ctx->map3[i][0], ctx->buf[i], es, p->nx, p->ny, ctx->pitch, ctx->plane, 20,
+                                           win3);
     }
     if (e == cudaSuccess && (p->storage == LBM_MS_BF16 || p->storage == LBM_MS_F16 || p->storage == LBM_MS_BFP)) {
         const int win = lbmk::TbtMsGeom::WIN;
@@ -620,10 +624,8 @@ lbm_status lbm_set_staging(lbm_ctx* ctx, int32_t mode)
 lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t rows_per_block)
 {
     LBM_CHECK_CTX(ctx);
-    const bool ms = ctx->p.storage == LBM_MS_BF16 || ctx->p.storage == LBM_MS_F16 || ctx->p.storage == LBM_MS_BFP;
-    if (steps_per_pass < 1 || steps_per_pass > (ms ? 3 : 2) || rows_per_block < 0 || rows_per_block > 65535)
-        return fail(ctx, LBM_ERR_ARG, "steps_per_pass must be 1, 2 (or 3 for moment-space storage) and "
-                                      "rows_per_block in [0, 65535]");
+    if (steps_per_pass < 1 || steps_per_pass > 3 || rows_per_block < 0 || rows_per_block > 65535)
+        return fail(ctx, LBM_ERR_ARG, "steps_per_pass must be 1, 2 or 3 and rows_per_block in [0, 65535]");
     ctx->fuse = steps_per_pass;
     if (rows_per_block > 0) ctx->tb_rows = rows_per_block;
     return LBM_OK;
@@ -855,8 +857,8 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
             Q.scale = (float)ctx->neq_scale;
             Q.inv_s = (float)(1.0 / ctx->neq_scale);
             Q.sat = reinterpret_cast<int*>(ctx->scratch + kSatSlot);
-            if (ctx->fuse == 3 && ms) {
-                // three steps per pass (moment space): the remainder below runs as one pair or a single step
+            if (ctx->fuse == 3) {
+                // three steps per pass: the remainder below runs as one pair or a single step
                 const dim3 q3grid((ctx->p.nx + lbmk::TBT3_OUT - 1) / lbmk::TBT3_OUT, (ctx->p.ny + Q.rows - 1) / Q.rows);
                 while (n >= 3) {
                     Q.src = ctx->buf[ctx->cur];

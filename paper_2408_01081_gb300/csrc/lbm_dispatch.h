@@ -71,7 +71,7 @@ struct KindOps {
     // and the moment-space formats); maps: the row maps of the source buffer, one for the
     // population formats (box {TbtGeom::WIN, 1, 20}), two for moment space (FP32 part, 16-bit part)
     cudaError_t (*tbt_step)(const CUtensorMap* maps, const lbmk::TbtArgs&, bool dirichlet, dim3 grid, cudaStream_t s);
-    // three fused steps, moment-space formats only (maps with box width Tbt3MsGeom::WIN)
+    // three fused steps (maps with box width Tbt3Geom::WIN, or Tbt3MsGeom::WIN for moment space)
     cudaError_t (*tbt3_step)(const CUtensorMap* maps, const lbmk::TbtArgs&, bool dirichlet, dim3 grid, cudaStream_t s);
     int vec_split;                 // nodes per thread of the FP64 split-level step kernels
     int batch_vec;                 // nodes per thread of the batch kernel

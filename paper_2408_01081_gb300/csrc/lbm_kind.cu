@@ -224,7 +224,14 @@ cudaError_t tbt_step(const CUtensorMap* maps, const lbmk::TbtArgs& a, bool diric
 template <int KK>
 cudaError_t tbt3_t(const CUtensorMap* maps, const lbmk::TbtArgs& a, bool dirichlet, dim3 g, cudaStream_t s)
 {
-    if constexpr (KK == lbmk::K_MSBF16 || KK == lbmk::K_MSF16 || KK == lbmk::K_MSBFP) {
+    if constexpr (KK == lbmk::K_F32 || KK == lbmk::K_BF16 || KK == lbmk::K_F16) {
+        using G = lbmk::Tbt3Geom<(int)sizeof(typename lbmk::Fmt<KK>::E)>;
+        void (*kern)(CUtensorMap, lbmk::TbtArgs) = dirichlet ? lbmk::tbt3_kernel<KK, true> : lbmk::tbt3_kernel<KK, false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        kern<<<g, lbmk::TBT_THREADS, G::SMEM, s>>>(maps[0], a);
+        return cudaGetLastError();
+    } else if constexpr (KK == lbmk::K_MSBF16 || KK == lbmk::K_MSF16 || KK == lbmk::K_MSBFP) {
         using G = lbmk::Tbt3MsGeom;
         void (*kern)(CUtensorMap, CUtensorMap, lbmk::TbtArgs) =
             dirichlet ? lbmk::tbt3_ms_kernel<KK, true> : lbmk::tbt3_ms_kernel<KK, false>;

@@ -847,4 +847,203 @@ __global__ void __launch_bounds__(TBT_THREADS, 2) tbt3_ms_kernel(const __grid_co
     if (lane == 0 && abort_flag) atomicExch(A.timeout, 1);
 }
 
+
+// ---------------------------------------------------------------------------
+// Population formats, three steps per pass (tbt3_kernel): tbt_kernel's staging with the
+// three register levels of tbt3_ms_kernel (S1 from the staged rows, S2, S3 stored by
+// lanes 2..29 of each warp, 112 columns per block, staged rows y0 - 3 .. y1 + 2).  Same
+// arithmetic as single steps, so FP32 results stay bit-identical to them.
+// ---------------------------------------------------------------------------
+#ifndef LBM_TBT3_NST4
+#define LBM_TBT3_NST4 7
+#endif
+#ifndef LBM_TBT3_NST2
+#define LBM_TBT3_NST2 4
+#endif
+
+template <int ES>
+struct Tbt3Geom {
+    static constexpr int HL = 16 / ES;                                 // >= 3 staged columns each side
+    static constexpr int WIN = HL + TBT3_OUT + HL;
+    static constexpr int ROW_BYTES = 20 * WIN * ES;
+    static constexpr int STAGE_BYTES = (ROW_BYTES + 127) / 128 * 128;
+    static constexpr int NST = (ES == 4) ? LBM_TBT3_NST4 : LBM_TBT3_NST2;
+    static constexpr int SMEM = NST * STAGE_BYTES + 128;
+    static_assert((WIN * ES) % 16 == 0 && HL >= 3, "staged row geometry");
+};
+
+template <int K, bool DIRICHLET>
+__global__ void __launch_bounds__(TBT_THREADS, 3) tbt3_kernel(const __grid_constant__ CUtensorMap map, TbtArgs A)
+{
+    using E = typename Fmt<K>::E;
+    using G = Tbt3Geom<(int)sizeof(E)>;
+    constexpr int NST = G::NST, WIN = G::WIN, HL = G::HL;
+    extern __shared__ __align__(128) unsigned char tbt_smem_raw[];
+    __shared__ __align__(8) unsigned long long full_bar[NST], empty_bar[NST];
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nx = A.nx, ny = A.ny;
+    const int X0 = blockIdx.x * TBT3_OUT;
+    const int y0 = blockIdx.y * A.rows;
+    const int y1 = min(ny, y0 + A.rows);
+    const int nin = (y1 - y0) + 6;                   // staged input rows y0-3 .. y1+2
+    const uint32_t raw = lbmt::smem_u32(tbt_smem_raw);
+    const uint32_t sbase = (raw + 127u) & ~127u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            lbmt::mbar_init(lbmt::smem_u32(&full_bar[s]), 1);
+            lbmt::mbar_init(lbmt::smem_u32(&empty_bar[s]), TBT_WARPS);
+        }
+        abort_flag = 0;
+        lbmt::fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == TBT_WARPS) {
+        if (lane == 0) {
+            lbmt::prefetch_map(&map);
+            int j = 0;
+            for (; j < nin; ++j) {
+                const int s = j % NST;
+                const uint32_t fb = lbmt::smem_u32(&full_bar[s]);
+                if (j == A.withhold) continue;
+                if (j >= NST && !lbmt::mbar_wait(lbmt::smem_u32(&empty_bar[s]), ((j / NST) - 1) & 1, &abort_flag))
+                    break;
+                int y = y0 - 3 + j;
+                if (DIRICHLET && (y < 0 || y >= ny)) {
+                    lbmt::mbar_arrive(fb);
+                    continue;
+                }
+                if (!DIRICHLET) y = (y < 0) ? y + ny : (y >= ny ? y - ny : y);
+                lbmt::mbar_arrive_expect_tx(fb, G::ROW_BYTES);
+                lbmt::tma_load_3d(sbase + s * G::STAGE_BYTES, &map, X0 - HL, y, 0, fb);
+            }
+            for (int q = (j > NST ? j - NST : 0); q < j; ++q)
+                if (q != A.withhold) lbmt::mbar_drain(lbmt::smem_u32(&full_bar[q % NST]), (q / NST) & 1);
+            if (abort_flag) atomicExch(A.timeout, 1);
+        }
+        return;
+    }
+
+    const E* __restrict__ src = static_cast<const E*>(A.src);
+    E* __restrict__ dst = static_cast<E*>(A.dst);
+    const long long plane = A.plane;
+    const int xs = X0 - 2 + TB3_OUT * warp + lane;   // this lane's S1 column
+    const int xc = DIRICHLET ? (xs < 0 ? 0 : (xs >= nx ? nx - 1 : xs)) : ((xs % nx) + nx) % nx;
+    const bool out_lane = (lane >= 2) && (lane < 2 + TB3_OUT) && (xs >= 0) && (xs < nx);
+    const bool staged = DIRICHLET || (xs >= 1 && xs + 1 <= nx - 1);
+    const int xl = (xc == 0) ? nx - 1 : xc - 1, xr = (xc == nx - 1) ? 0 : xc + 1;
+    const int idx = xs - X0 + HL;
+    const float fa = A.af, fb = A.bf;
+    const float Dk[5] = {-1.f, -1.f, 1.f, 1.f, 1.f};
+
+    float p1[4][5], k1[5], p2[4][5], k2[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        k1[k] = k2[k] = 0.f;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) p1[d][k] = p2[d][k] = 0.f;
+    }
+    bool ok = lbmt::mbar_wait(lbmt::smem_u32(&full_bar[0]), 0, &abort_flag) &&
+              lbmt::mbar_wait(lbmt::smem_u32(&full_bar[1 % NST]), (1 / NST) & 1, &abort_flag);
+    for (int i = 0; i + 2 < nin; ++i) {
+        const int r = y0 - 2 + i;                    // S1 row, from staged rows i, i+1, i+2
+        {
+            const int j = i + 2;
+            ok = ok && lbmt::mbar_wait(lbmt::smem_u32(&full_bar[j % NST]), (j / NST) & 1, &abort_flag);
+        }
+        if (!__all_sync(0xffffffffu, ok)) break;
+        constexpr uint32_t ES = sizeof(E), PL = WIN * sizeof(E);
+        const uint32_t rm = sbase + (i % NST) * G::STAGE_BYTES + idx * ES;
+        const uint32_t rc = sbase + ((i + 1) % NST) * G::STAGE_BYTES + idx * ES;
+        const uint32_t rp = sbase + ((i + 2) % NST) * G::STAGE_BYTES + idx * ES;
+        float c1[4][5];
+        {
+            float f[4][5];
+            if (staged) {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    f[0][k] = Fmt<K>::ld(lbmt::lds<E>(rc + (0 * 5 + k) * PL - ES));
+                    f[2][k] = Fmt<K>::ld(lbmt::lds<E>(rc + (2 * 5 + k) * PL + ES));
+                    f[1][k] = Fmt<K>::ld(lbmt::lds<E>(rm + (1 * 5 + k) * PL));
+                    f[3][k] = Fmt<K>::ld(lbmt::lds<E>(rp + (3 * 5 + k) * PL));
+                }
+            } else {
+                const int ry = (r < 0) ? r + ny : (r >= ny ? r - ny : r);
+                const int rmy = (ry == 0) ? ny - 1 : ry - 1, rpy = (ry == ny - 1) ? 0 : ry + 1;
+                const long long o = (long long)ry * A.pitch;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    f[0][k] = sload<K>(src + (0 * 5 + k) * plane + o + xl);
+                    f[2][k] = sload<K>(src + (2 * 5 + k) * plane + o + xr);
+                    f[1][k] = sload<K>(src + (1 * 5 + k) * plane + (long long)rmy * A.pitch + xc);
+                    f[3][k] = sload<K>(src + (3 * 5 + k) * plane + (long long)rpy * A.pitch + xc);
+                }
+            }
+            if (DIRICHLET) {
+                const bool bot = r == 0, top = r == ny - 1;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    if (xc == 0) f[0][k] = Dk[k] * Fmt<K>::ld(lbmt::lds<E>(rc + (2 * 5 + k) * PL));
+                    if (xc == nx - 1) f[2][k] = Dk[k] * Fmt<K>::ld(lbmt::lds<E>(rc + (0 * 5 + k) * PL));
+                    if (bot) f[1][k] = Dk[k] * Fmt<K>::ld(lbmt::lds<E>(rc + (3 * 5 + k) * PL));
+                    if (top) f[3][k] = Dk[k] * Fmt<K>::ld(lbmt::lds<E>(rc + (1 * 5 + k) * PL));
+                }
+            }
+            float U[5], rx[5], ry2[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                rx[k] = f[1][k] + f[3][k];
+                ry2[k] = f[0][k] + f[2][k];
+                U[k] = rx[k] + ry2[k];
+            }
+            collide<float>(f, U, rx, ry2, fa, fb, c1);
+            if (DIRICHLET && !(r >= 0 && r < ny))
+#pragma unroll
+                for (int d = 0; d < 4; ++d)
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) c1[d][k] = 0.f;
+        }
+        __syncwarp();
+        if (lane == 0) lbmt::mbar_arrive(lbmt::smem_u32(&empty_bar[i % NST]));
+        const int q2 = r - 1;
+        if (q2 >= y0 - 1) {
+            float c2[4][5];
+            level_step<DIRICHLET>(p1, k1, c1[3], q2, xs, nx, ny, fa, fb, c2);
+            if (DIRICHLET && !(q2 >= 0 && q2 < ny))
+#pragma unroll
+                for (int d = 0; d < 4; ++d)
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) c2[d][k] = 0.f;
+            const int q3 = r - 2;
+            if (q3 >= y0) {
+                float o[4][5];
+                level_step<DIRICHLET>(p2, k2, c2[3], q3, xs, nx, ny, fa, fb, o);
+                if (out_lane) {
+                    const long long off = (long long)q3 * A.pitch + xs;
+#pragma unroll
+                    for (int d = 0; d < 4; ++d)
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) dst[(d * 5 + k) * plane + off] = Fmt<K>::st(o[d][k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                k2[k] = p2[1][k];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) p2[d][k] = c2[d][k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            k1[k] = p1[1][k];
+#pragma unroll
+            for (int d = 0; d < 4; ++d) p1[d][k] = c1[d][k];
+        }
+    }
+    if (lane == 0 && abort_flag) atomicExch(A.timeout, 1);
+}
+
 }  // namespace lbmk
