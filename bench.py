@@ -43,7 +43,7 @@ FP64_OPS_PER_NODE = 47                                                # DADD/DFM
 SPLIT_LEVEL = 1               # lbm_set_fp64_split default: the 15 sums of a node on the integer pipe
 SPLIT_INTEGER_ADDS = 15
 # steps per launch of each format at the library's defaults (lbm_set_step_fusion)
-STEPS_PER_PASS = {"f64": 1, "f32": 2, "bf16": 2, "f16": 2, "ms_bf16": 3, "ms_f16": 3, "ms_bfp": 3}
+STEPS_PER_PASS = {"f64": 1, "f32": 3, "bf16": 3, "f16": 3, "ms_bf16": 3, "ms_f16": 3, "ms_bfp": 3}
 # DRAM bytes per node and launch of each step kernel (dram__bytes_read.sum + dram__bytes_write.sum
 # from one ncu capture of this benchmark's own 8192^2 workload, averaged over its launches; no
 # scaling), valid only while the kernel sources hash to "sha256".  "<fmt>_fused" is one launch of

@@ -95,21 +95,19 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out);
 lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const double* dU0dy,
                     const double* B0, const double* u0, int32_t on_device);
 
-/* Steps per pass over memory.  With 2 (the default for the population formats but
- * LBM_F64, whose step is bound by arithmetic, not memory) lbm_step advances pairs of
- * steps with one kernel that keeps the intermediate state on chip (halving the
- * memory traffic per step) whenever the lattice stores FP32 / BF16 / FP16
+/* Steps per pass over memory: 1, 2 or 3 (3 is the default for every format but
+ * LBM_F64, whose step is bound by arithmetic, not memory).  With 2 lbm_step advances
+ * pairs of steps with one kernel that keeps the intermediate state on chip (halving
+ * the memory traffic per step), with 3 triples, whenever the lattice stores FP32 / BF16 / FP16
  * populations (or moment-space deviations, with staged rows: lbm_set_staging),
  * omega = 2, there is no body load and no displacement tracking, and the
  * boundary is periodic or homogeneous Dirichlet; otherwise, and for an odd last
  * step, one kernel per step runs.  FP32 results are bit-identical to single
  * steps; 16-bit and moment-space results skip one rounding per pair and are more
- * accurate.  The moment-space formats also take steps_per_pass = 3, their default
- * (rows staged, lbm_set_staging 1): three steps per kernel, the deviations rounded
- * to 16 bits once per three steps; a remainder of one or two steps runs as a single
- * step or a pair.
+ * accurate.  Three steps per kernel need staged rows (lbm_set_staging 1; with 0 pairs
+ * run instead); a remainder of one or two steps runs as a single step or a pair.
  * rows_per_block sets the rows each thread block streams through (0 keeps the
- * format's default: 8 for LBM_F32, 32 for BF16 / FP16, 64 for moment space).
+ * format's default: 16 for LBM_F32, 64 for the others).
  * steps_per_pass = 1 always uses one kernel per step. */
 lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t rows_per_block);
 

@@ -421,11 +421,11 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
     ctx->a = p->cK / c;
     ctx->b = p->cmu / c;
     ctx->nwall = 2 * (p->nx + p->ny);
-    // several steps per pass for every reduced format (faster than single steps for each of them):
-    // two for the population formats, three for moment space (fewer 16-bit roundings and the
-    // decoding spread over three steps); rows per block measured best per format at 8192^2
-    ctx->fuse = (p->storage == LBM_F64) ? 1 : (p->storage >= LBM_MS_BF16) ? 3 : 2;
-    ctx->tb_rows = (p->storage == LBM_F32) ? 8 : (p->storage >= LBM_MS_BF16) ? 64 : 32;
+    // three steps per pass for every reduced format (measured faster than one or two steps for each
+    // of them at 8192^2, and fewer roundings to the storage format); rows per block measured best
+    // per format
+    ctx->fuse = (p->storage == LBM_F64) ? 1 : 3;
+    ctx->tb_rows = (p->storage == LBM_F32) ? 16 : 64;
     // symmetrizer blocks k_ij = g_ij^{-1}, g_ij = 1/4 I + (i A_x + j A_y)/(2c)  (Eq. stability_linear)
     const int VI[4] = {1, 0, -1, 0}, VJ[4] = {0, 1, 0, -1};
     for (int d = 0; d < 4; ++d) {
