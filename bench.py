@@ -49,23 +49,28 @@ STEPS_PER_PASS = {"f64": 1, "f32": 3, "bf16": 3, "f16": 3, "ms_bf16": 3, "ms_f16
 # scaling), valid only while the kernel sources hash to "sha256".  "<fmt>_fused" is one launch of
 # the two-step kernel (two steps), "<fmt>_fused3" of the three-step kernel, "f64_pipe" the FP64
 # step with every operation on the FP64 pipe.
-TRAFFIC_CAPTURE = {"sha256": "636853b3b8b5e11d5b731897d44f714d3ba3be4ee6225d876ead868eede7702e",
+TRAFFIC_CAPTURE = {"sha256": "c018f696a9fcf137e8fcfb661a3b3098bf456f4e5b171ed014172347c508741a",
                    "nodes": 8192 * 8192,
-                   "bytes_per_node": {"f64": 321.56, "f64_pipe": 319.25, "f32": 159.35, "f32_fused": 160.64,
-                                      "bf16": 79.29, "bf16_fused": 84.64, "f16": 79.29, "f16_fused": 84.64,
-                                      "ms_bf16_fused": 103.39, "ms_bf16_fused3": 103.96,
-                                      "ms_f16_fused": 103.41, "ms_f16_fused3": 103.94,
-                                      "ms_bfp_fused": 103.30, "ms_bfp_fused3": 103.87}}
+                   "bytes_per_node": {"f64": 322.39, "f64_pipe": 319.26,
+                                      "f32_fused": 170.22, "f32_fused3": 171.58,
+                                      "bf16_fused": 82.63, "bf16_fused3": 83.34,
+                                      "f16_fused": 82.65, "f16_fused3": 83.34,
+                                      "ms_bf16_fused": 103.39, "ms_bf16_fused3": 103.95,
+                                      "ms_f16_fused": 103.39, "ms_f16_fused3": 103.96,
+                                      "ms_bfp_fused": 103.29, "ms_bfp_fused3": 103.86}}
 KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_01081_gb300/csrc/lbm_kind.cu",
                   "paper_2408_01081_gb300/csrc/lbm_tb.cuh", "paper_2408_01081_gb300/csrc/lbm_ms.cuh",
-                  "paper_2408_01081_gb300/csrc/lbm_tbt.cuh", "paper_2408_01081_gb300/csrc/lbm_tma.cuh"]
-# Pipe instruction counts of the default FP64 step kernel per node (thread instructions:
-# 32 x smsp__inst_executed_pipe_{alu,fp64,fma}.sum / nodes from one ncu capture of 4096x2048),
+                  "paper_2408_01081_gb300/csrc/lbm_tbt.cuh", "paper_2408_01081_gb300/csrc/lbm_tma.cuh",
+                  "paper_2408_01081_gb300/csrc/lbm_f64emu.cuh", "paper_2408_01081_gb300/csrc/lbm_mscodec.cuh",
+                  "paper_2408_01081_gb300/csrc/lbm_f64stage.cuh"]
+# Pipe instruction counts of the default FP64 step kernel (step_f64_staged_kernel) per node
+# (thread instructions: 32 x smsp__inst_executed_pipe_{alu,fp64,fma}.sum / nodes from one ncu
+# capture of 4096x2048),
 # valid only while the kernel sources hash to "sha256".  Each SM issues 64 ALU-pipe and 2
 # FP64-pipe thread instructions per clock, so one node needs at least
 # max(alu / 64, fp64 / 2) SM clocks: the arithmetic roof of this kernel.
-PIPE_CAPTURE = {"sha256": "636853b3b8b5e11d5b731897d44f714d3ba3be4ee6225d876ead868eede7702e",
-                "alu_per_node": 1127.0, "fp64_per_node": 32.0, "fma_per_node": 260.0}
+PIPE_CAPTURE = {"sha256": "c018f696a9fcf137e8fcfb661a3b3098bf456f4e5b171ed014172347c508741a",
+                "alu_per_node": 1130.0, "fp64_per_node": 32.0, "fma_per_node": 192.0}
 ALU_LANES_PER_SM, FP64_LANES_PER_SM, N_SM = 64, 2, 152
 
 
@@ -540,7 +545,9 @@ def run_ours(args):
     else:
         roofline = dict(hbm_part)
     roofline.update({"traffic": args.traffic if args.traffic is not None else traffic_per_launch("f64", n_nodes),
-                "kernel": f"lbmk::step_kernel<F64,1,periodic,split level {SPLIT_LEVEL}>",
+                "kernel": (f"lbmk::step_f64_staged_kernel<periodic,split level {SPLIT_LEVEL}> (rows staged by "
+                           f"asynchronous copies)" if args.staging >= 1 else
+                           f"lbmk::step_kernel<F64,1,periodic,split level {SPLIT_LEVEL}>"),
                 "compute": {"limiter": "FP64 pipe and integer ALU pipe together (exact binary64 additions "
                                        "moved to the integer pipe); below the HBM roof",
                             "fp64_pipe_ops_per_node": fp64_pipe_ops,
@@ -623,7 +630,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-fusion", action="store_true", help="one kernel per step for every format")
     ap.add_argument("--fuse-formats", default="", help="formats advanced two steps per pass besides the default")
-    ap.add_argument("--staging", type=int, default=1, help="two-step kernel: 1 rows staged by tensor copies, 0 registers")
+    ap.add_argument("--staging", type=int, default=1,
+                    help="1: rows staged in shared memory (tensor copies for the multi-step kernels, asynchronous "
+                         "copies for the FP64 step), 0: register loads")
     ap.add_argument("--rows-per-block", type=int, default=0, help="two-step kernel rows per block (0: library default)")
     ap.add_argument("--batch-count", type=int, default=512, help="lattices in the batch leg")
     ap.add_argument("--no-surrogate", action="store_true")

@@ -107,15 +107,19 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const d
  * accurate.  Three steps per kernel need staged rows (lbm_set_staging 1; with 0 pairs
  * run instead); a remainder of one or two steps runs as a single step or a pair.
  * rows_per_block sets the rows each thread block streams through (0 keeps the
- * format's default: 16 for LBM_F32, 64 for the others).
+ * format's default: 16 for LBM_F32, 64 for the other reduced formats, 2 for the
+ * staged LBM_F64 step of lbm_set_staging).
  * steps_per_pass = 1 always uses one kernel per step. */
 lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t rows_per_block);
 
-/* How the two-step kernel of lbm_set_step_fusion reads its input (no counterpart in
- * the paper; results are identical either way).  1 (the default): each block's
- * input rows are copied into a ring of shared-memory stages by tensor copies
- * (TMA) issued by one producer warp, as far ahead as the ring allows.  0: each
- * thread prefetches the next row into registers.  A bounded wait of the staged
+/* How the multi-step kernels of lbm_set_step_fusion and the LBM_F64 step at split
+ * level 1 read their input (no counterpart in the paper; results are identical
+ * either way).  1 (the default): each multi-step block's input rows are copied into
+ * a ring of shared-memory stages by tensor copies (TMA) issued by one producer warp,
+ * as far ahead as the ring allows; each thread of the FP64 step copies the 20
+ * populations its node pulls into shared memory by asynchronous copies, one row
+ * ahead of the row it computes.  0: each thread loads into registers (the two-step
+ * kernel prefetches the next row there).  A bounded wait of the staged
  * kernel that runs out (about 2 s) makes the next lbm_synchronize return
  * LBM_ERR_TIMEOUT.  Mode 2 is a test hook: staged, but the producer withholds one
  * input row of every block, so that the compute warps' waits run out and the

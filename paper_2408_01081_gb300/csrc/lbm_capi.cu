@@ -197,9 +197,10 @@ struct lbm_ctx {
     double omega = 2.0;
     double neq_scale = 1.0;      // moment-space storage: scale of the stored deviations
     int fuse = 1;                // steps per pass over memory when the fused kernel applies
-    int tb_rows = 16;            // rows per block of the fused kernel
+    int tb_rows = 16;            // rows per block of the fused kernels and the staged FP64 step
     int split = 1;               // FP64: split level (which additions run on the integer pipes)
-    int staging = 1;             // fused kernel: 1 = rows staged by tensor copies, 0 = register prefetch
+    int staging = 1;             // 1 = rows staged in shared memory (tensor copies for the fused kernels,
+                                 // asynchronous copies for the FP64 step), 0 = register loads
     int l2_ahead = lbmk::TBT_L2_AHEAD;   // staged kernel: rows prefetched into L2 ahead of the ring
                                          // (environment LBM_TBT_L2_AHEAD, 0..64, read at lbm_create)
     int nyi = 0;                 // rows of the lattice's own (a slab: without its halo rows)
@@ -425,7 +426,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
     // of them at 8192^2, and fewer roundings to the storage format); rows per block measured best
     // per format
     ctx->fuse = (p->storage == LBM_F64) ? 1 : 3;
-    ctx->tb_rows = (p->storage == LBM_F32) ? 16 : 64;
+    ctx->tb_rows = (p->storage == LBM_F64) ? 2 : (p->storage == LBM_F32) ? 16 : 64;
     // symmetrizer blocks k_ij = g_ij^{-1}, g_ij = 1/4 I + (i A_x + j A_y)/(2c)  (Eq. stability_linear)
     const int VI[4] = {1, 0, -1, 0}, VJ[4] = {0, 1, 0, -1};
     for (int d = 0; d < 4; ++d) {
@@ -899,7 +900,10 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
         A.T = ctx->R > 0 ? ctx->fT + (m + 1) * 2 * ctx->R : nullptr;
         A.Tf = (ctx->R > 0 && ctx->fTf) ? ctx->fTf + (m + 1) * 2 * ctx->R : nullptr;
         A.g = ctx->g ? ctx->g + m * 2 * ctx->nwall : nullptr;
-        cudaError_t e = ops->step(A, variant, grid, block, ctx->s);
+        // FP64 at split level 1: rows staged by asynchronous copies unless staging is off
+        cudaError_t e = cudaErrorNotSupported;
+        if (split && ctx->split == 1 && ctx->staging >= 1) e = ops->step_staged(A, variant, ctx->tb_rows, ctx->s);
+        if (e == cudaErrorNotSupported) e = ops->step(A, variant, grid, block, ctx->s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step kernel");
         ctx->cur ^= 1;
         ctx->m = m + 1;

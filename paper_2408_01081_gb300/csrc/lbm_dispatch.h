@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "lbm_batch.cuh"
+#include "lbm_f64stage.cuh"
 #include "lbm_kernels.cuh"
 #include "lbm_ms.cuh"
 #include "lbm_tb.cuh"
@@ -73,6 +74,9 @@ struct KindOps {
     cudaError_t (*tbt_step)(const CUtensorMap* maps, const lbmk::TbtArgs&, bool dirichlet, dim3 grid, cudaStream_t s);
     // three fused steps (maps with box width Tbt3Geom::WIN, or Tbt3MsGeom::WIN for moment space)
     cudaError_t (*tbt3_step)(const CUtensorMap* maps, const lbmk::TbtArgs&, bool dirichlet, dim3 grid, cudaStream_t s);
+    // one FP64 step at split level 1 with the rows staged by asynchronous copies, `rows` rows
+    // per block (other formats and variants return cudaErrorNotSupported)
+    cudaError_t (*step_staged)(const lbmk::StepArgs&, int variant, int rows, cudaStream_t s);
     int vec_split;                 // nodes per thread of the FP64 split-level step kernels
     int batch_vec;                 // nodes per thread of the batch kernel
 };

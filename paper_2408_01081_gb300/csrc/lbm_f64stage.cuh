@@ -1,0 +1,184 @@
+// FP64 step (split collision, omega = 2, no body load) with each row's inputs staged
+// in shared memory by per-thread asynchronous copies (cp.async), issued one item ahead.
+//
+// The register step kernel loads the 20 inputs of a node and then waits for them:
+// with 80 registers and three 256-thread blocks per SM, about a sixth of its warp
+// cycles go to that wait (long scoreboard) while the integer pipe, which bounds the
+// split collision, idles.  Here a block of 128 threads computes one row segment of 128
+// columns (an item) at a time, thread t owning column t of the segment.  The copies of
+// the block's next item are issued as soon as the current one has been read out of
+// shared memory, so they are in flight during its whole collision and occupy no
+// registers; each thread copies exactly the 20 values its own node pulls
+// (f*_(1,0) from x - 1, f*_(-1,0) from x + 1, f*_(0,1) from y - 1, f*_(0,-1) from
+// y + 1, with the periodic wrap or the Dirichlet edge reflection in the source
+// address), so no value crosses threads and no barrier or wait loop is needed: a
+// thread's copies of an item complete by cp.async.wait_group.  The node arithmetic is the
+// split collision of step_kernel (lbm_kernels.cuh) on the same inputs, so results
+// are bit-identical to it.
+#pragma once
+
+#include "lbm_kernels.cuh"
+#include "lbm_tma.cuh"
+
+namespace lbmk {
+
+constexpr int SA_THREADS = 128;                       // columns per block, one per thread
+constexpr int SA_SLOTS = 20;                          // inputs per node
+#ifndef LBM_SA_MIN_BLOCKS
+#define LBM_SA_MIN_BLOCKS 6                           // 6 x 128 threads at <= 85 registers
+#endif
+#ifndef LBM_SA_DIRECT
+#define LBM_SA_DIRECT 0                               // 1: plain loads into registers instead of copies
+#endif
+#ifndef LBM_SA_AHEAD
+#define LBM_SA_AHEAD 1                                // rows whose copies are in flight (1 or 2)
+#endif
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ double lds_f64(uint32_t a)
+{
+    double v;
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+    return v;
+}
+
+// grid: (ceil(nx / SA_THREADS), ceil(ny / rows)), block SA_THREADS; block (cb, r) computes
+// the rows r * rows ... of column block cb, one item (row segment) after the other
+template <bool DIRICHLET, bool TRACK, unsigned long long SPLIT>
+__global__ void __launch_bounds__(SA_THREADS, LBM_SA_MIN_BLOCKS) step_f64_staged_kernel(StepArgs A, int rows)
+{
+    constexpr int NB = LBM_SA_AHEAD;
+    static_assert(NB == 1 || NB == 2, "one or two items in flight");
+    __shared__ __align__(16) double slot[NB][SA_SLOTS][SA_THREADS];
+    const int t = threadIdx.x;
+    const int nx = A.nx, ny = A.ny;
+    const int xg = blockIdx.x * SA_THREADS + t;
+    const bool active = xg < nx;
+    const int x = active ? xg : nx - 1;                // lanes past nx mirror column nx - 1
+    const int y0 = blockIdx.y * rows;
+    const int y1 = min(ny, y0 + rows);
+    const long long plane = A.plane, pitch = A.pitch;
+    const double* __restrict__ src = static_cast<const double*>(A.src);
+    double* __restrict__ dst = static_cast<double*>(A.dst);
+    const int xl = (x == 0) ? nx - 1 : x - 1, xr = (x == nx - 1) ? 0 : x + 1;
+    const bool le = DIRICHLET && x == 0, ri = DIRICHLET && x == nx - 1;
+    const uint32_t s0 = lbmt::smem_u32(&slot[0][0][t]);
+    constexpr uint32_t SL = SA_THREADS * 8;            // bytes from one slot to the next
+    constexpr uint32_t SB = SA_SLOTS * SL;             // bytes from one item buffer to the next
+
+    // source of slot d * 5 + k: the population of direction d, component k that node (x, y)
+    // pulls; on a Dirichlet edge the missing link's slot gets the node's own opposite population
+    auto sources = [&](int y, const double* (&p)[4]) {
+        const int ym = (y == 0) ? ny - 1 : y - 1, yp = (y == ny - 1) ? 0 : y + 1;
+        const bool bot = DIRICHLET && y == 0, top = DIRICHLET && y == ny - 1;
+        const long long r = (long long)y * pitch;
+        p[0] = src + (le ? 10 * plane + r + x : r + xl);
+        p[1] = src + (bot ? 15 * plane + r + x : 5 * plane + (long long)ym * pitch + x);
+        p[2] = src + (ri ? r + x : 10 * plane + r + xr);
+        p[3] = src + (top ? 5 * plane + r + x : 15 * plane + (long long)yp * pitch + x);
+    };
+    auto issue = [&](int y, uint32_t sb) {
+        const double* p[4];
+        sources(y, p);
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+#pragma unroll
+            for (int d = 0; d < 4; ++d) cp_async8(sb + (d * 5 + k) * SL, p[d] + k * plane);
+    };
+
+#if LBM_SA_DIRECT
+    for (int y = y0; y < y1; ++y) {
+        double f[4][5];
+        {
+            const double* p[4];
+            sources(y, p);
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+#pragma unroll
+                for (int d = 0; d < 4; ++d) f[d][k] = __ldg(p[d] + k * plane);
+        }
+#else
+    // one commit group per row (empty past the block's last row), NB groups in flight
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (y0 + j < y1) issue(y0 + j, s0 + j * SB);
+        cp_async_commit();
+    }
+    for (int y = y0; y < y1; ++y) {
+        const uint32_t sb = s0 + ((y - y0) % NB) * SB;
+        if constexpr (NB == 1) asm volatile("cp.async.wait_group 0;" ::: "memory");
+        else asm volatile("cp.async.wait_group 1;" ::: "memory");
+        double f[4][5];
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) f[d][k] = lds_f64(sb + (d * 5 + k) * SL);
+        // the slots have been read: the copies of row y + NB may overwrite them
+        __syncwarp();
+        if (y + NB < y1) issue(y + NB, sb);
+        cp_async_commit();
+#endif
+        if (DIRICHLET) {
+            // missing incoming links: f_ij = D f*_{-i,-j}(x) + S_ij(x_b, t + dt/2), as in step_kernel
+            const bool bot = y == 0, top = y == ny - 1;
+            if (le || ri || bot || top) {
+                const double Dk[5] = {-1.0, -1.0, 1.0, 1.0, 1.0};
+                double S[5];
+                if (le) {
+                    double gx = 0.0, gy = 0.0;
+                    if (A.g) { gx = A.g[y]; gy = A.g[A.nwall + y]; }
+                    wall_source(1, 0, gx, gy, A.a, A.b, S);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) f[0][k] = Dk[k] * f[0][k] + S[k];
+                }
+                if (ri) {
+                    double gx = 0.0, gy = 0.0;
+                    if (A.g) { gx = A.g[ny + y]; gy = A.g[A.nwall + ny + y]; }
+                    wall_source(-1, 0, gx, gy, A.a, A.b, S);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) f[2][k] = Dk[k] * f[2][k] + S[k];
+                }
+                if (bot) {
+                    double gx = 0.0, gy = 0.0;
+                    if (A.g) { gx = A.g[2 * ny + x]; gy = A.g[A.nwall + 2 * ny + x]; }
+                    wall_source(0, 1, gx, gy, A.a, A.b, S);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) f[1][k] = Dk[k] * f[1][k] + S[k];
+                }
+                if (top) {
+                    double gx = 0.0, gy = 0.0;
+                    if (A.g) { gx = A.g[2 * ny + nx + x]; gy = A.g[A.nwall + 2 * ny + nx + x]; }
+                    wall_source(0, -1, gx, gy, A.a, A.b, S);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) f[3][k] = Dk[k] * f[3][k] + S[k];
+                }
+            }
+        }
+        double U[5], o[4][5];
+        collide_split<SPLIT>(f, A.a, A.b, U, o);
+        if (active) {
+            const long long off = (long long)y * pitch + x;
+#pragma unroll
+            for (int d = 0; d < 4; ++d)
+#pragma unroll
+                for (int k = 0; k < 5; ++k) dst[(d * 5 + k) * plane + off] = o[d][k];
+            if (TRACK) {
+                // u*(t+2dt) = u*(t+dt) + dt v(t+dt)  (steps 1(b) and 2(c) of the summary, Sec. 3.6)
+                A.w[off] = fma(A.dt, U[0], A.w[off]);
+                A.w[plane + off] = fma(A.dt, U[1], A.w[plane + off]);
+            }
+        }
+    }
+    // no copy is left in flight: every group past the block's last row is empty
+}
+
+}  // namespace lbmk

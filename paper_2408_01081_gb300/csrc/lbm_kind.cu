@@ -65,6 +65,33 @@ cudaError_t step_split(const lbmk::StepArgs& a, int level, dim3 g, dim3 b, cudaS
     }
 }
 
+#ifndef LBM_SA_MASK
+#define LBM_SA_MASK lbmh::split_mask(1)   // the additions of split level 1 on the integer pipes
+#endif
+
+// FP64 at split level 1 with the rows staged by asynchronous copies (lbm_f64stage.cuh);
+// other formats, levels and variants return cudaErrorNotSupported
+template <bool D, bool T>
+cudaError_t step_staged_dt(const lbmk::StepArgs& a, int rows, cudaStream_t s)
+{
+    if constexpr (K != lbmk::K_F64) {
+        return cudaErrorNotSupported;
+    } else {
+        const dim3 g((a.nx + lbmk::SA_THREADS - 1) / lbmk::SA_THREADS, (a.ny + rows - 1) / rows);
+        lbmk::step_f64_staged_kernel<D, T, LBM_SA_MASK><<<g, lbmk::SA_THREADS, 0, s>>>(a, rows);
+        return cudaGetLastError();
+    }
+}
+
+cudaError_t step_staged(const lbmk::StepArgs& a, int variant, int rows, cudaStream_t s)
+{
+    const int level = (variant >> lbmh::STEP_SPLIT_SHIFT) & 15;
+    if (level != 1 || (variant & (lbmh::STEP_FORCING | lbmh::STEP_OMEGA)) || rows < 1) return cudaErrorNotSupported;
+    const bool d = variant & lbmh::STEP_DIRICHLET, t = variant & lbmh::STEP_TRACK;
+    return d ? (t ? step_staged_dt<true, true>(a, rows, s) : step_staged_dt<true, false>(a, rows, s))
+             : (t ? step_staged_dt<false, true>(a, rows, s) : step_staged_dt<false, false>(a, rows, s));
+}
+
 template <bool O>
 cudaError_t step_o(const lbmk::StepArgs& a, int variant, dim3 g, dim3 b, cudaStream_t s)
 {
@@ -264,7 +291,7 @@ namespace lbmh {
 const KindOps LBM_OPS_NAME(LBM_KIND) = {
     K, V, ELEM, NODE_BYTES,
     step, init, moments, get_pop, set_pop, energy, error, finite, batch_step, batch_occupancy, tb2_step, tbt_step,
-    tbt3_step,
+    tbt3_step, step_staged,
     LBM_VEC_SPLIT, VB,
 };
 

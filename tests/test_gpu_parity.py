@@ -336,12 +336,14 @@ def test_two_step_fusion_moment_space_against_oracle(lbm, storage, tol, dirichle
         assert errs[fuse] < tol and errs[fuse] <= 1.2 * errs[1], errs
 
 
-def _split_runs(lbm, nx, ny, f, us, steps, levels, dirichlet=False, wall=None, track=False):
+def _split_runs(lbm, nx, ny, f, us, steps, levels, dirichlet=False, wall=None, track=False, staging=1, rows=0):
     outs = {}
     for adds in levels:
         lat = lbm.Lattice(nx, ny, 0.1, 0.1 / 3.2, 1.0, 0.6, dirichlet=dirichlet, storage="f64",
                           track_displacement=track)
         lat.set_fp64_split(adds)
+        lat.set_staging(staging)
+        lat.set_step_fusion(1, rows)
         if wall is not None:
             lat.set_dirichlet(wall)
         lat.set_populations(f, us)
@@ -361,6 +363,24 @@ def test_fp64_split_is_bit_identical_periodic(lbm, nx, ny):
     for adds in (1, 2, 5, 7):
         np.testing.assert_array_equal(outs[adds][0].view(np.int64), outs[0][0].view(np.int64))
         np.testing.assert_array_equal(outs[adds][1].view(np.int64), outs[0][1].view(np.int64))
+
+
+@pytest.mark.parametrize("dirichlet", [False, True])
+@pytest.mark.parametrize("nx,ny,rows", [(3, 5, 64), (127, 9, 4), (129, 33, 7), (300, 17, 1), (1031, 7, 3)])
+def test_fp64_staged_step_equals_register_step(lbm, nx, ny, rows, dirichlet):
+    """The FP64 step with its rows staged by asynchronous copies (split level 1, the default)
+    gives the register kernel's populations and displacements bit for bit: ragged column
+    blocks, row counts that do not divide ny, one row per block, wall data on Dirichlet edges."""
+    steps = 9
+    rng = np.random.default_rng(3 * nx + ny + rows)
+    f = rng.standard_normal((4, 5, ny, nx))
+    us = rng.standard_normal((2, ny, nx))
+    wall = rng.standard_normal((steps, 2, 2 * (nx + ny))) * 1e-2 if dirichlet else None
+    kw = dict(dirichlet=dirichlet, wall=wall, track=True, rows=rows)
+    staged = _split_runs(lbm, nx, ny, f, us, steps, [1], staging=1, **kw)[1]
+    plain = _split_runs(lbm, nx, ny, f, us, steps, [1], staging=0, **kw)[1]
+    np.testing.assert_array_equal(staged[0].view(np.int64), plain[0].view(np.int64))
+    np.testing.assert_array_equal(staged[1].view(np.int64), plain[1].view(np.int64))
 
 
 def test_fp64_split_is_bit_identical_dirichlet_with_wall_data(lbm):
