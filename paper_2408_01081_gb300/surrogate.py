@@ -314,9 +314,12 @@ class Surrogate:
 
 
 def train(chunks_fn, n_chunks, batch=8, H=256, W=256, lr=1e-3, lr_min=1e-5, epochs_per_chunk=1, seed=0,
-          chans=(32, 64, 128, 256), k=32, log=None, scale=None, time_budget_s=None):
-    """Train on chunks produced by chunks_fn(i) (fresh trajectories per chunk).
-    Cosine learning-rate decay over all iterations.  Returns (Surrogate, history)."""
+          chans=(32, 64, 128, 256), k=32, log=None, scale=None, time_budget_s=None, eval_fn=None, eval_every=0,
+          curve=None):
+    """Train on chunks produced by chunks_fn(i) (fresh trajectories per chunk, or a fixed set
+    cycled over).  Cosine learning-rate decay over all iterations.  With eval_fn and
+    eval_every, after every eval_every chunks (and at the end) (iteration, seconds,
+    eval_fn(surrogate)) is appended to the list `curve`.  Returns (Surrogate, history)."""
     import torch
     net = UNet(chans, seed=seed)
     first = chunks_fn(0)
@@ -351,9 +354,17 @@ def train(chunks_fn, n_chunks, batch=8, H=256, W=256, lr=1e-3, lr_min=1e-5, epoc
                     if log:
                         log(f"iter {it}/{total} loss {lv:.3e} lr {lr_t:.2e} {time.time() - t0:.1f}s")
                 if time_budget_s and time.time() - t0 > time_budget_s:
+                    if eval_fn is not None and curve is not None:
+                        curve.append((it, round(time.time() - t0, 1), eval_fn(sur)))
                     return sur, hist
         del chunk
         torch.cuda.empty_cache()
+        if eval_fn is not None and curve is not None and eval_every and (ci + 1) % eval_every == 0:
+            curve.append((it, round(time.time() - t0, 1), eval_fn(sur)))
+            if log:
+                log(f"chunk {ci + 1}: held-out median {curve[-1][2]:.3e}")
+    if eval_fn is not None and curve is not None and (not curve or curve[-1][0] != it):
+        curve.append((it, round(time.time() - t0, 1), eval_fn(sur)))
     return sur, hist
 
 
@@ -574,18 +585,28 @@ def timing(sur, n=16, H=256, W=256, reps=5):
 
 
 def run(out_dir, n_chunks=20, lattices=256, H=256, W=256, k=32, J=4, batch=8, lr=1e-3, time_budget_s=None,
-        eval_lattices=64, chans=(32, 64, 128, 256), log=print):
-    """Generate trajectories, train, evaluate on held-out seeds, time; write report.json."""
+        eval_lattices=64, chans=(32, 64, 128, 256), log=print, distinct_chunks=0, eval_every=0):
+    """Generate trajectories, train, evaluate on held-out seeds, time; write report.json.
+    distinct_chunks > 0 trains on that many chunks of `lattices` trajectories (seeds
+    10000 + i), cycled over for n_chunks chunks (epochs); 0 draws fresh trajectories for
+    every chunk.  eval_every > 0 records the held-out error every eval_every chunks on the
+    first 16 held-out lattices (the learning curve)."""
     import json
     import os
     import torch
     os.makedirs(out_dir, exist_ok=True)
-    t0 = time.time()
-    chunks = lambda i: generate_chunk(lattices, 10_000 + i, H=H, W=W, k=k, J=J)
-    sur, hist = train(chunks, n_chunks, batch=batch, H=H, W=W, lr=lr, chans=chans, k=k, log=log,
-                      time_budget_s=time_budget_s)
-    t_train = time.time() - t0
+    if distinct_chunks > 0:
+        chunks = lambda i: generate_chunk(lattices, 10_000 + i % distinct_chunks, H=H, W=W, k=k, J=J)
+    else:
+        chunks = lambda i: generate_chunk(lattices, 10_000 + i, H=H, W=W, k=k, J=J)
     held = generate_chunk(eval_lattices, 900_000, H=H, W=W, k=k, J=J)
+    curve = []
+    probe = Chunk(held.U[:, :16], held.nu[:16], held.nu_norm[:16], 16, held.J)
+    eval_fn = (lambda s: float(np.median(evaluate(s, probe, batch=16)[0]))) if eval_every else None
+    t0 = time.time()
+    sur, hist = train(chunks, n_chunks, batch=batch, H=H, W=W, lr=lr, chans=chans, k=k, log=log,
+                      time_budget_s=time_budget_s, eval_fn=eval_fn, eval_every=eval_every, curve=curve)
+    t_train = time.time() - t0
     errs, pers = evaluate(sur, held, batch=16)
     errs_fast, _ = evaluate(sur, held, batch=16, act_bf16=True)
     tm = timing(sur, n=16, H=H, W=W)
@@ -601,6 +622,8 @@ def run(out_dir, n_chunks=20, lattices=256, H=256, W=256, k=32, J=4, batch=8, lr
         "fallback_tol": 1e-3, "fallback_fraction": drv.fallbacks / max(1, drv.checked),
         "check_errors_after_relift": [float(e) for e in derr],
         "timing": tm, "scale": sur.scale_np.tolist(), "history": hist[-50:],
+        "distinct_trajectories": (distinct_chunks * lattices) if distinct_chunks > 0 else None,
+        "curve": [{"iteration": c[0], "train_s": c[1], "heldout16_rel_l2_median": c[2]} for c in curve],
     }
     json.dump(report, open(os.path.join(out_dir, "report.json"), "w"), indent=1)
     np.savez(os.path.join(out_dir, "weights.npz"), **sur.net.state_dict(), scale=sur.scale_np)
@@ -734,6 +757,9 @@ if __name__ == "__main__":
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--budget", type=float, default=None, help="training time budget in seconds")
+    ap.add_argument("--distinct-chunks", type=int, default=0,
+                    help="train on this many chunks of trajectories, cycled over (0: fresh trajectories per chunk)")
+    ap.add_argument("--eval-every", type=int, default=0, help="record the held-out error every N chunks")
     ap.add_argument("--kernels", choices=["infer", "train"], default=None,
                     help="only run a fixed launch sequence of the layer kernels (for profiling)")
     ap.add_argument("--layer-timing", action="store_true",
@@ -747,6 +773,6 @@ if __name__ == "__main__":
         print("done")
     else:
         _, rep = run(a.out, a.chunks, a.lattices, a.size, a.size, a.k, batch=a.batch, lr=a.lr,
-                     time_budget_s=a.budget)
+                     time_budget_s=a.budget, distinct_chunks=a.distinct_chunks, eval_every=a.eval_every)
         import json
         print(json.dumps({k: v for k, v in rep.items() if k != "history"}, indent=1))
