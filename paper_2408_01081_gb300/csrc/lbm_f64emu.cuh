@@ -45,33 +45,43 @@ EMU_HD int clz64(u64 x)
 #endif
 }
 
+// significand of a magnitude x with its hidden bit (none for zero / subnormal) at bits
+// 62..10, from 32-bit halves: min(hi, 0x00100000) is the hidden bit exactly when the
+// exponent field is nonzero and otherwise lies within the fraction bits
+EMU_HD u64 sig_bits(u64 x)
+{
+    const unsigned hi = (unsigned)(x >> 32), lo = (unsigned)x;
+    const unsigned hid = hi < 0x00100000u ? hi : 0x00100000u;
+    return ((((u64)((hi & 0x000FFFFFu) | hid)) << 32) | lo) << 10;
+}
+
 EMU_HD u64 emu_add_bits(u64 ua, u64 ub, bool& ok)
 {
-    const u64 SIGN = 0x8000000000000000ull, FRAC = 0x000FFFFFFFFFFFFFull, HID = 0x0010000000000000ull;
+    const u64 SIGN = 0x8000000000000000ull;
     const u64 xa = ua & ~SIGN, xb = ub & ~SIGN;
     const bool sw = xb > xa;                        // order by magnitude: |h| >= |l|
     const u64 h = sw ? ub : ua, l = sw ? ua : ub;
-    const u64 xh = sw ? xb : xa, xl = sw ? xa : xb;
+    const u64 xh = h & ~SIGN, xl = l & ~SIGN;
     const int eh = (int)(xh >> 52), el = (int)(xl >> 52);
     const bool finite_in = eh < 2047;
-    // significands with the hidden bit (none for zero / subnormal, whose
-    // exponent acts as 1), placed at bits 62..10 to leave guard bits below
-    const u64 mh = ((xh & FRAC) | (eh ? HID : 0ull)) << 10;
-    const u64 ml = ((xl & FRAC) | (el ? HID : 0ull)) << 10;
-    const int e = eh + (eh == 0);
-    int d = e - (el + (el == 0));
-    d = d > 63 ? 63 : d;
+    // significands at bits 62..10, guard bits below (zero / subnormal: no hidden bit, and
+    // the exponent acts as 1)
+    const u64 mh = sig_bits(xh), ml = sig_bits(xl);
+    const int e = eh > 1 ? eh : 1;
+    int d = e - (el > 1 ? el : 1);
+    d = d < 63 ? d : 63;
     u64 al = ml >> d;
     al |= (u64)((al << d) != ml);                   // sticky bit of what was shifted out
-    const bool sub = ((h ^ l) & SIGN) != 0;
-    u64 s = sub ? mh - al : mh + al;
+    const u64 neg = (u64)0 - (u64)(((h ^ l) & SIGN) != 0);   // all ones for a subtraction
+    u64 s = mh + (al ^ neg) - neg;                  // mh + al or mh - al
     const bool zero = (s == 0);
     const int lz = clz64(s | 1ull);                 // leading one to bit 63
     s <<= lz;
     const int er = e + 1 - lz;                      // exponent field of the result
-    const u64 rem = s & 0x7FFull;
     u64 m = s >> 11;                                // 53-bit significand
-    m += (u64)((rem > 0x400ull) | ((rem == 0x400ull) & (unsigned)(m & 1ull)));
+    // round to nearest, ties to even: up when the 11 bits below exceed half, or equal half
+    // with m odd
+    m += (u64)(((unsigned)s & 0x7FFu) + ((unsigned)m & 1u) > 0x400u);
     const u64 r = ((u64)(er - 1) << 52) + m;        // a carry out of m bumps the exponent
     ok = ok && finite_in && (zero || (er >= 1 && (r >> 52) < 2047ull));
     // an exact zero is +0, except -0 + -0

@@ -702,13 +702,15 @@ __global__ void __launch_bounds__(TBT_THREADS, 2) tbt3_ms_kernel(const __grid_co
     const float Dk[5] = {-1.f, -1.f, 1.f, 1.f, 1.f};
 
     // S1 rows r-1 (p1, all directions) and r-2 (k1: (0,1)); S2 rows r-2 (p2) and r-3 (k2: (0,1));
-    // f*_(0,1)(t) of the own column in the staged row below the current one (d1)
-    float p1[4][5], k1[5], p2[4][5], k2[5], d1[5];
+    // f*_(0,1)(t) of the own column in the staged row below the current one (d1), and
+    // f*(t) of all four directions of the own column in the current staged row (ft), rebuilt
+    // from its moments once, as the row above of the previous S1 row
+    float p1[4][5], k1[5], p2[4][5], k2[5], d1[5], ft[4][5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         k1[k] = k2[k] = d1[k] = 0.f;
 #pragma unroll
-        for (int d = 0; d < 4; ++d) p1[d][k] = p2[d][k] = 0.f;
+        for (int d = 0; d < 4; ++d) p1[d][k] = p2[d][k] = ft[d][k] = 0.f;
     }
     auto row_of = [&](int r) { return (r < 0) ? r + ny : (r >= ny ? r - ny : r); };
     bool ok = lbmt::mbar_wait(lbmt::smem_u32(&full_bar[0]), 0, &abort_flag) &&
@@ -718,6 +720,11 @@ __global__ void __launch_bounds__(TBT_THREADS, 2) tbt3_ms_kernel(const __grid_co
         if (own_staged) ms3_node_smem<K>(sbase, idx, inv_s, n);
         else ms_node_global<K>(A.src, plane, (long long)row_of(y0 - 3) * A.pitch + xc, inv_s, n);
         ms_node_dir(n, 1, fa, fb, d1);
+        const uint32_t s1 = sbase + (1 % NST) * G::STAGE_BYTES;
+        if (own_staged) ms3_node_smem<K>(s1, idx, inv_s, n);
+        else ms_node_global<K>(A.src, plane, (long long)row_of(y0 - 2) * A.pitch + xc, inv_s, n);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) ms_node_dir(n, d, fa, fb, ft[d]);
     }
     for (int i = 0; i + 2 < nin; ++i) {
         const int r = y0 - 2 + i;                    // S1 row, from staged rows i, i+1, i+2
@@ -730,20 +737,23 @@ __global__ void __launch_bounds__(TBT_THREADS, 2) tbt3_ms_kernel(const __grid_co
         const uint32_t sp = sbase + ((i + 2) % NST) * G::STAGE_BYTES;   // row r+1
         float c1[4][5];
         {
-            MsNode n;
-            if (own_staged) ms3_node_smem<K>(sc, idx, inv_s, n);
-            else ms_node_global<K>(A.src, plane, (long long)row_of(r) * A.pitch + xc, inv_s, n);
-            float o0[5], o1[5], o2[5], o3[5], p3[5];
-            ms_node_dir(n, 0, fa, fb, o0);
-            ms_node_dir(n, 1, fa, fb, o1);
-            ms_node_dir(n, 2, fa, fb, o2);
-            ms_node_dir(n, 3, fa, fb, o3);
+            // own column: row r from the previous iteration, row r+1 rebuilt here (kept for the next)
+            float o0[5], o1[5], o2[5], o3[5], nt[4][5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                o0[k] = ft[0][k];
+                o1[k] = ft[1][k];
+                o2[k] = ft[2][k];
+                o3[k] = ft[3][k];
+            }
             {
                 MsNode np;
                 if (own_staged) ms3_node_smem<K>(sp, idx, inv_s, np);
                 else ms_node_global<K>(A.src, plane, (long long)row_of(r + 1) * A.pitch + xc, inv_s, np);
-                ms_node_dir(np, 3, fa, fb, p3);
+#pragma unroll
+                for (int d = 0; d < 4; ++d) ms_node_dir(np, d, fa, fb, nt[d]);
             }
+            const float (&p3)[5] = nt[3];
             float hl[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, hr[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
             if (lane == 0) {
                 MsNode h;
@@ -778,7 +788,11 @@ __global__ void __launch_bounds__(TBT_THREADS, 2) tbt3_ms_kernel(const __grid_co
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 5; ++k) d1[k] = o1[k];
+            for (int k = 0; k < 5; ++k) {
+                d1[k] = o1[k];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) ft[d][k] = nt[d][k];
+            }
             float U[5], rx[5], ry2[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
@@ -872,8 +886,12 @@ struct Tbt3Geom {
     static_assert((WIN * ES) % 16 == 0 && HL >= 3, "staged row geometry");
 };
 
+#ifndef LBM_TBT3_MIN_BLOCKS
+#define LBM_TBT3_MIN_BLOCKS 3       // 116-127 registers
+#endif
+
 template <int K, bool DIRICHLET>
-__global__ void __launch_bounds__(TBT_THREADS, 3) tbt3_kernel(const __grid_constant__ CUtensorMap map, TbtArgs A)
+__global__ void __launch_bounds__(TBT_THREADS, LBM_TBT3_MIN_BLOCKS) tbt3_kernel(const __grid_constant__ CUtensorMap map, TbtArgs A)
 {
     using E = typename Fmt<K>::E;
     using G = Tbt3Geom<(int)sizeof(E)>;

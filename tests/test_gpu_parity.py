@@ -241,15 +241,15 @@ def test_moment_space_storage_dirichlet_with_forcing(lbm, storage, tol):
 def test_two_step_fusion_fp32_is_bit_identical(lbm, dirichlet, nx, ny):
     """The fused kernels (two steps with rows staged by tensor copies or with register prefetch,
     three steps staged) equal single steps exactly in FP32 (tiles of 120 or 112 columns with a
-    ragged last tile, the lattice's wrap columns, blocks of 16 rows with a ragged last block,
-    step counts that leave remainders)."""
+    ragged last tile, the lattice's wrap columns, blocks of 16 rows or of the default 12 with a
+    ragged last block, step counts that leave remainders)."""
     rng = np.random.default_rng(nx + 1000 * ny)
     f = rng.standard_normal((4, 5, ny, nx)) * 1e-3
     outs = []
-    for fuse, staging in ((1, 1), (2, 0), (2, 1), (3, 1)):
+    for fuse, staging, rows in ((1, 1, 16), (2, 0, 16), (2, 1, 16), (3, 1, 16), (3, 1, 0)):
         lat = lbm.Lattice(nx, ny, 0.1, 0.1 / 3.2, 1.0, 0.6, dirichlet=dirichlet, storage="f32",
                           track_displacement=False)
-        lat.set_step_fusion(fuse, 16)
+        lat.set_step_fusion(fuse, rows)
         lat.set_staging(staging)
         lat.set_populations(f)
         lat.step(9)
