@@ -107,8 +107,8 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const d
  * accurate.  Three steps per kernel need staged rows (lbm_set_staging 1; with 0 pairs
  * run instead); a remainder of one or two steps runs as a single step or a pair.
  * rows_per_block sets the rows each thread block streams through (0 keeps the
- * format's default: 12 for LBM_F32, 64 for LBM_BF16 and LBM_F16, 128 for the
- * moment-space formats, 2 for the staged LBM_F64 step of lbm_set_staging).
+ * format's default: 12 for LBM_F32, 64 for the other reduced formats, 2 for the
+ * staged LBM_F64 step of lbm_set_staging).
  * steps_per_pass = 1 always uses one kernel per step. */
 lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t rows_per_block);
 

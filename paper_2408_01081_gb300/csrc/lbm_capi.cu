@@ -426,8 +426,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
     // of them at 8192^2, and fewer roundings to the storage format); rows per block measured best
     // per format
     ctx->fuse = (p->storage == LBM_F64) ? 1 : 3;
-    const bool ms_storage = p->storage == LBM_MS_BF16 || p->storage == LBM_MS_F16 || p->storage == LBM_MS_BFP;
-    ctx->tb_rows = (p->storage == LBM_F64) ? 2 : (p->storage == LBM_F32) ? 12 : ms_storage ? 128 : 64;
+    ctx->tb_rows = (p->storage == LBM_F64) ? 2 : (p->storage == LBM_F32) ? 12 : 64;
     // symmetrizer blocks k_ij = g_ij^{-1}, g_ij = 1/4 I + (i A_x + j A_y)/(2c)  (Eq. stability_linear)
     const int VI[4] = {1, 0, -1, 0}, VJ[4] = {0, 1, 0, -1};
     for (int d = 0; d < 4; ++d) {

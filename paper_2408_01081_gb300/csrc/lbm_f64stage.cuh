@@ -22,7 +22,10 @@
 
 namespace lbmk {
 
-constexpr int SA_THREADS = 128;                       // columns per block, one per thread
+#ifndef LBM_SA_THREADS
+#define LBM_SA_THREADS 128
+#endif
+constexpr int SA_THREADS = LBM_SA_THREADS;            // columns per block, one per thread
 constexpr int SA_SLOTS = 20;                          // inputs per node
 #ifndef LBM_SA_MIN_BLOCKS
 #define LBM_SA_MIN_BLOCKS 6                           // 6 x 128 threads at <= 85 registers

@@ -629,8 +629,13 @@ __device__ __forceinline__ void level_step(const float (&p)[4][5], const float (
     collide<float>(f, U, rx, ry2, fa, fb, o);
 }
 
+#ifndef LBM_TBT3MS_MIN_BLOCKS
+#define LBM_TBT3MS_MIN_BLOCKS 3     // 128 registers (a few values spilled): 3 blocks per SM measured
+                                    // faster than 2 at 164 registers
+#endif
+
 template <int K, bool DIRICHLET>
-__global__ void __launch_bounds__(TBT_THREADS, 2) tbt3_ms_kernel(const __grid_constant__ CUtensorMap map32,
+__global__ void __launch_bounds__(TBT_THREADS, LBM_TBT3MS_MIN_BLOCKS) tbt3_ms_kernel(const __grid_constant__ CUtensorMap map32,
                                                                  const __grid_constant__ CUtensorMap map16, TbtArgs A)
 {
     using Codec = typename Ms<K>::C;
