@@ -667,7 +667,8 @@ __device__ __forceinline__ void phiy(const double (&v)[5], double a, double b, d
 
 // Eq. ic_second written with the scaled fluxes (Phi/c), then the first collision.
 // Inputs are dense [5][ny][nx] (U0, dU0dx, dU0dy), [2][ny][nx] (B0, u0; may be null).
-template <int K>
+// HASB: B0 is given (without it every body-load term is zero and skipped).
+template <int K, bool HASB>
 __global__ void init_kernel(NodeArgs A, const double* __restrict__ U0, const double* __restrict__ Ux,
                             const double* __restrict__ Uy, const double* __restrict__ B0,
                             const double* __restrict__ u0)
@@ -683,43 +684,51 @@ __global__ void init_kernel(NodeArgs A, const double* __restrict__ U0, const dou
             ux[k] = Ux[k * n + id];
             uy[k] = Uy[k * n + id];
         }
-        if (B0) {
+        if (HASB) {
             bv[0] = B0[id];
             bv[1] = B0[n + id];
         }
         const double a = A.a, b = A.b, c = A.c;
-        double pxu[5], pyu[5], pxb[5], pyb[5], pxx[5], pyy[5], pxpxx[5], pypxx[5], pxpyy[5], pypyy[5];
+        // Phi/c is linear, so px(px u_x) + px(py u_y) = px(px u_x + py u_y), likewise py
+        double pxu[5], pyu[5], pxb[5], pyb[5], pxx[5], pyy[5], sxy[5], pxs[5], pys[5];
         phix(u, a, b, pxu);
         phiy(u, a, b, pyu);
-        phix(bv, a, b, pxb);
-        phiy(bv, a, b, pyb);
+        if (HASB) {
+            phix(bv, a, b, pxb);
+            phiy(bv, a, b, pyb);
+        }
         phix(ux, a, b, pxx);
         phiy(uy, a, b, pyy);
-        phix(pxx, a, b, pxpxx);
-        phiy(pxx, a, b, pypxx);
-        phix(pyy, a, b, pxpyy);
-        phiy(pyy, a, b, pypyy);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) sxy[k] = pxx[k] + pyy[k];
+        phix(sxy, a, b, pxs);
+        phiy(sxy, a, b, pys);
         // per velocity (i, j), with the zero and unit factors of i, j written out:
         //   f = 1/4 (u + 2 (i px u + j py u)) - dt/8 [ b + 2 (i px b + j py b)
         //       + c (i u_x + (2 i^2 - 1) px u_x - 2 (i px + j py) px u_x)
         //       + c (j u_y + (2 j^2 - 1) py u_y - 2 (i px + j py) py u_y) ]
+        // so for (+-1, 0): 1/4 u +- 1/2 px u - dt/8 [ b +- 2 px b + c (px u_x - py u_y)
+        //                  +- c (u_x - 2 px (px u_x + py u_y)) ], and (0, +-1) with x, y exchanged
         double f[4][5];
         const double h = 0.125 * A.dt;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            const double q = bv[k];
-            // (1,0) and (-1,0)
-            const double ex = 0.5 * pxu[k], bx2 = 2.0 * pxb[k];
-            const double sx = c * (pxx[k] - pyy[k]);                     // parts common to +/- x
-            const double dxp = c * (ux[k] - 2.0 * pxpxx[k] - 2.0 * pxpyy[k]);
-            f[0][k] = (0.25 * u[k] + ex) - h * ((q + bx2) + (sx + dxp));
-            f[2][k] = (0.25 * u[k] - ex) - h * ((q - bx2) + (sx - dxp));
-            // (0,1) and (0,-1)
-            const double ey = 0.5 * pyu[k], by2 = 2.0 * pyb[k];
-            const double sy = c * (pyy[k] - pxx[k]);
-            const double dyp = c * (uy[k] - 2.0 * pypxx[k] - 2.0 * pypyy[k]);
-            f[1][k] = (0.25 * u[k] + ey) - h * ((q + by2) + (sy + dyp));
-            f[3][k] = (0.25 * u[k] - ey) - h * ((q - by2) + (sy - dyp));
+            const double qu = 0.25 * u[k];
+            const double sx = c * (pxx[k] - pyy[k]);                     // the y rows carry -sx
+            const double ex = 0.5 * pxu[k], ey = 0.5 * pyu[k];
+            const double dxp = c * fma(-2.0, pxs[k], ux[k]);
+            const double dyp = c * fma(-2.0, pys[k], uy[k]);
+            double gxp = sx + dxp, gxm = sx - dxp, gyp = dyp - sx, gym = -sx - dyp;
+            if (HASB) {
+                gxp += bv[k] + 2.0 * pxb[k];
+                gxm += bv[k] - 2.0 * pxb[k];
+                gyp += bv[k] + 2.0 * pyb[k];
+                gym += bv[k] - 2.0 * pyb[k];
+            }
+            f[0][k] = fma(-h, gxp, qu + ex);
+            f[2][k] = fma(-h, gxm, qu - ex);
+            f[1][k] = fma(-h, gyp, qu + ey);
+            f[3][k] = fma(-h, gym, qu - ey);
         }
         double S[4][5], U[5];
         collide_node(f, bv[0], bv[1], A.dt, A.omega, a, b, S, U);

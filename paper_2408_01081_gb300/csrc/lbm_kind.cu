@@ -121,7 +121,8 @@ cudaError_t step(const lbmk::StepArgs& a, int variant, dim3 g, dim3 b, cudaStrea
 cudaError_t init(const lbmk::NodeArgs& a, const double* U0, const double* Ux, const double* Uy,
                  const double* B0, const double* u0, dim3 g, dim3 b, cudaStream_t s)
 {
-    lbmk::init_kernel<K><<<g, b, 0, s>>>(a, U0, Ux, Uy, B0, u0);
+    if (B0) lbmk::init_kernel<K, true><<<g, b, 0, s>>>(a, U0, Ux, Uy, B0, u0);
+    else lbmk::init_kernel<K, false><<<g, b, 0, s>>>(a, U0, Ux, Uy, B0, u0);
     return cudaGetLastError();
 }
 

@@ -414,13 +414,15 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
     const float fa = A.af, fb = A.bf;
     const float Dk[5] = {-1.f, -1.f, 1.f, 1.f, 1.f};
 
-    float keep_py[5], prev[4][5], d1_prev[5];        // S1 rows r-2 (direction (0,1)), r-1; f*_(0,1)(t) of row r-1
+    // S1 rows r-2 (direction (0,1)), r-1; f*_(0,1)(t) of row r-1; f*(t) of all four directions of
+    // the own column in row r, rebuilt from its moments once, as the row above of row r-1
+    float keep_py[5], prev[4][5], d1_prev[5], ft[4][5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         keep_py[k] = 0.f;
         d1_prev[k] = 0.f;
 #pragma unroll
-        for (int d = 0; d < 4; ++d) prev[d][k] = 0.f;
+        for (int d = 0; d < 4; ++d) prev[d][k] = ft[d][k] = 0.f;
     }
     auto row_of = [&](int r) { return (r < 0) ? r + ny : (r >= ny ? r - ny : r); };
     bool ok = lbmt::mbar_wait(lbmt::smem_u32(&full_bar[0]), 0, &abort_flag) &&
@@ -431,6 +433,11 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
         if (own_staged) ms_node_smem<K>(sbase, idx, inv_s, n);
         else ms_node_global<K>(A.src, plane, (long long)row_of(y0 - 2) * A.pitch + xc, inv_s, n);
         ms_node_dir(n, 1, fa, fb, d1_prev);
+        const uint32_t s1 = sbase + (1 % NST) * G::STAGE_BYTES;
+        if (own_staged) ms_node_smem<K>(s1, idx, inv_s, n);
+        else ms_node_global<K>(A.src, plane, (long long)row_of(y0 - 1) * A.pitch + xc, inv_s, n);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) ms_node_dir(n, d, fa, fb, ft[d]);
     }
     for (int i = 0; i + 2 < nin; ++i) {
         const int r = y0 - 1 + i;
@@ -444,21 +451,24 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
         float cur[4][5];
         const bool row_ok = DIRICHLET ? (r >= 0 && r < ny) : true;
         {
-            // own node of row r (all four directions) and (0,-1) of row r+1
-            MsNode n;
-            if (own_staged) ms_node_smem<K>(sc, idx, inv_s, n);
-            else ms_node_global<K>(A.src, plane, (long long)row_of(r) * A.pitch + xc, inv_s, n);
-            float o0[5], o1[5], o2[5], o3[5], p3[5];
-            ms_node_dir(n, 0, fa, fb, o0);
-            ms_node_dir(n, 1, fa, fb, o1);
-            ms_node_dir(n, 2, fa, fb, o2);
-            ms_node_dir(n, 3, fa, fb, o3);
+            // own node of row r (all four directions, from the previous iteration) and row r+1
+            // (rebuilt here, kept for the next)
+            float o0[5], o1[5], o2[5], o3[5], nt[4][5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                o0[k] = ft[0][k];
+                o1[k] = ft[1][k];
+                o2[k] = ft[2][k];
+                o3[k] = ft[3][k];
+            }
             {
                 MsNode np;
                 if (own_staged) ms_node_smem<K>(sp, idx, inv_s, np);
                 else ms_node_global<K>(A.src, plane, (long long)row_of(r + 1) * A.pitch + xc, inv_s, np);
-                ms_node_dir(np, 3, fa, fb, p3);
+#pragma unroll
+                for (int d = 0; d < 4; ++d) ms_node_dir(np, d, fa, fb, nt[d]);
             }
+            const float (&p3)[5] = nt[3];
             float hl[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, hr[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
             if (lane == 0) {
                 MsNode h;
@@ -493,7 +503,11 @@ __global__ void __launch_bounds__(TBT_THREADS, 3) tbt_ms_kernel(const __grid_con
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 5; ++k) d1_prev[k] = o1[k];
+            for (int k = 0; k < 5; ++k) {
+                d1_prev[k] = o1[k];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) ft[d][k] = nt[d][k];
+            }
             float U[5], rx[5], ry2[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
