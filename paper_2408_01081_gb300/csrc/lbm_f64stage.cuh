@@ -1,20 +1,20 @@
-// FP64 step (split collision, omega = 2, no body load) with each row's inputs staged
-// in shared memory by per-thread asynchronous copies (cp.async), issued one item ahead.
+// FP64 step (split collision, omega = 2, no body load) with each node's inputs staged
+// in shared memory by per-thread asynchronous copies (cp.async), one row ahead.
 //
 // The register step kernel loads the 20 inputs of a node and then waits for them:
 // with 80 registers and three 256-thread blocks per SM, about a sixth of its warp
-// cycles go to that wait (long scoreboard) while the integer pipe, which bounds the
-// split collision, idles.  Here a block of 128 threads computes one row segment of 128
-// columns (an item) at a time, thread t owning column t of the segment.  The copies of
-// the block's next item are issued as soon as the current one has been read out of
-// shared memory, so they are in flight during its whole collision and occupy no
-// registers; each thread copies exactly the 20 values its own node pulls
-// (f*_(1,0) from x - 1, f*_(-1,0) from x + 1, f*_(0,1) from y - 1, f*_(0,-1) from
-// y + 1, with the periodic wrap or the Dirichlet edge reflection in the source
-// address), so no value crosses threads and no barrier or wait loop is needed: a
-// thread's copies of an item complete by cp.async.wait_group.  The node arithmetic is the
-// split collision of step_kernel (lbm_kernels.cuh) on the same inputs, so results
-// are bit-identical to it.
+// cycles go to that wait (long scoreboard) while the integer pipe, which shares the
+// bound of the split collision with the FP64 pipe, idles.  Here a block of 128 threads
+// owns 128 consecutive columns and walks down `rows` rows (2 by default), thread t
+// computing column t of each row.  The copies of the next row are issued as soon as
+// the current row has been read out of shared memory, so they are in flight during its
+// whole collision and occupy no registers.  Each thread copies exactly the 20 values its
+// own node pulls (f*_(1,0) from x - 1, f*_(-1,0) from x + 1, f*_(0,1) from y - 1,
+// f*_(0,-1) from y + 1, with the periodic wrap or the Dirichlet edge reflection in the
+// source address), so no value crosses threads and no barrier or wait loop is needed: a
+// thread's copies of a row complete by cp.async.wait_group.  The node arithmetic is the
+// split collision of step_kernel (lbm_kernels.cuh) on the same inputs, so results are
+// bit-identical to it.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -29,12 +29,6 @@ constexpr int SA_THREADS = LBM_SA_THREADS;            // columns per block, one 
 constexpr int SA_SLOTS = 20;                          // inputs per node
 #ifndef LBM_SA_MIN_BLOCKS
 #define LBM_SA_MIN_BLOCKS 6                           // 6 x 128 threads at <= 85 registers
-#endif
-#ifndef LBM_SA_DIRECT
-#define LBM_SA_DIRECT 0                               // 1: plain loads into registers instead of copies
-#endif
-#ifndef LBM_SA_AHEAD
-#define LBM_SA_AHEAD 1                                // rows whose copies are in flight (1 or 2)
 #endif
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src)
@@ -55,13 +49,11 @@ __device__ __forceinline__ double lds_f64(uint32_t a)
 }
 
 // grid: (ceil(nx / SA_THREADS), ceil(ny / rows)), block SA_THREADS; block (cb, r) computes
-// the rows r * rows ... of column block cb, one item (row segment) after the other
+// the rows r * rows ... of column block cb, one after the other
 template <bool DIRICHLET, bool TRACK, unsigned long long SPLIT>
 __global__ void __launch_bounds__(SA_THREADS, LBM_SA_MIN_BLOCKS) step_f64_staged_kernel(StepArgs A, int rows)
 {
-    constexpr int NB = LBM_SA_AHEAD;
-    static_assert(NB == 1 || NB == 2, "one or two items in flight");
-    __shared__ __align__(16) double slot[NB][SA_SLOTS][SA_THREADS];
+    __shared__ __align__(16) double slot[SA_SLOTS][SA_THREADS];
     const int t = threadIdx.x;
     const int nx = A.nx, ny = A.ny;
     const int xg = blockIdx.x * SA_THREADS + t;
@@ -74,9 +66,8 @@ __global__ void __launch_bounds__(SA_THREADS, LBM_SA_MIN_BLOCKS) step_f64_staged
     double* __restrict__ dst = static_cast<double*>(A.dst);
     const int xl = (x == 0) ? nx - 1 : x - 1, xr = (x == nx - 1) ? 0 : x + 1;
     const bool le = DIRICHLET && x == 0, ri = DIRICHLET && x == nx - 1;
-    const uint32_t s0 = lbmt::smem_u32(&slot[0][0][t]);
+    const uint32_t s0 = lbmt::smem_u32(&slot[0][t]);
     constexpr uint32_t SL = SA_THREADS * 8;            // bytes from one slot to the next
-    constexpr uint32_t SB = SA_SLOTS * SL;             // bytes from one item buffer to the next
 
     // source of slot d * 5 + k: the population of direction d, component k that node (x, y)
     // pulls; on a Dirichlet edge the missing link's slot gets the node's own opposite population
@@ -98,38 +89,20 @@ __global__ void __launch_bounds__(SA_THREADS, LBM_SA_MIN_BLOCKS) step_f64_staged
             for (int d = 0; d < 4; ++d) cp_async8(sb + (d * 5 + k) * SL, p[d] + k * plane);
     };
 
-#if LBM_SA_DIRECT
+    // one commit group per row
+    if (y0 < y1) issue(y0, s0);
+    cp_async_commit();
     for (int y = y0; y < y1; ++y) {
-        double f[4][5];
-        {
-            const double* p[4];
-            sources(y, p);
-#pragma unroll
-            for (int k = 0; k < 5; ++k)
-#pragma unroll
-                for (int d = 0; d < 4; ++d) f[d][k] = __ldg(p[d] + k * plane);
-        }
-#else
-    // one commit group per row (empty past the block's last row), NB groups in flight
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-        if (y0 + j < y1) issue(y0 + j, s0 + j * SB);
-        cp_async_commit();
-    }
-    for (int y = y0; y < y1; ++y) {
-        const uint32_t sb = s0 + ((y - y0) % NB) * SB;
-        if constexpr (NB == 1) asm volatile("cp.async.wait_group 0;" ::: "memory");
-        else asm volatile("cp.async.wait_group 1;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         double f[4][5];
 #pragma unroll
         for (int d = 0; d < 4; ++d)
 #pragma unroll
-            for (int k = 0; k < 5; ++k) f[d][k] = lds_f64(sb + (d * 5 + k) * SL);
-        // the slots have been read: the copies of row y + NB may overwrite them
+            for (int k = 0; k < 5; ++k) f[d][k] = lds_f64(s0 + (d * 5 + k) * SL);
+        // the slots have been read: the copies of row y + 1 may overwrite them
         __syncwarp();
-        if (y + NB < y1) issue(y + NB, sb);
+        if (y + 1 < y1) issue(y + 1, s0);
         cp_async_commit();
-#endif
         if (DIRICHLET) {
             // missing incoming links: f_ij = D f*_{-i,-j}(x) + S_ij(x_b, t + dt/2), as in step_kernel
             const bool bot = y == 0, top = y == ny - 1;
@@ -181,7 +154,7 @@ __global__ void __launch_bounds__(SA_THREADS, LBM_SA_MIN_BLOCKS) step_f64_staged
             }
         }
     }
-    // no copy is left in flight: every group past the block's last row is empty
+    // no copy is left in flight: the group committed after the last row is empty
 }
 
 }  // namespace lbmk
