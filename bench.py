@@ -49,12 +49,12 @@ STEPS_PER_PASS = {"f64": 1, "f32": 3, "bf16": 3, "f16": 3, "ms_bf16": 3, "ms_f16
 # scaling), valid only while the kernel sources hash to "sha256".  "<fmt>_fused" is one launch of
 # the two-step kernel (two steps), "<fmt>_fused3" of the three-step kernel, "f64_pipe" the FP64
 # step with every operation on the FP64 pipe.
-TRAFFIC_CAPTURE = {"sha256": "4cd6575dca6adf5a1091531a347c243070dedc849c0ed47e12b0882a4abda224",
+TRAFFIC_CAPTURE = {"sha256": "d5c460ed088b0e2ce7563d9ea0521f1a53fc76b8c74124bae267d3a21becda8c",
                    "nodes": 8192 * 8192,
-                   "bytes_per_node": {"f64": 322.73, "f64_pipe": 319.26, "f32_fused": 165.22, "f32_fused3": 164.6,
-                                      "bf16_fused": 82.65, "bf16_fused3": 83.34, "f16_fused": 82.64,
-                                      "f16_fused3": 83.34, "ms_bf16_fused": 103.21, "ms_bf16_fused3": 105.14,
-                                      "ms_f16_fused": 103.2, "ms_f16_fused3": 105.15, "ms_bfp_fused": 103.2,
+                   "bytes_per_node": {"f64": 322.74, "f64_pipe": 319.25, "f32_fused": 165.22, "f32_fused3": 164.62,
+                                      "bf16_fused": 82.65, "bf16_fused3": 83.34, "f16_fused": 82.65,
+                                      "f16_fused3": 83.34, "ms_bf16_fused": 103.19, "ms_bf16_fused3": 105.14,
+                                      "ms_f16_fused": 103.19, "ms_f16_fused3": 105.15, "ms_bfp_fused": 103.2,
                                       "ms_bfp_fused3": 105.15}}
 KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_01081_gb300/csrc/lbm_kind.cu",
                   "paper_2408_01081_gb300/csrc/lbm_tb.cuh", "paper_2408_01081_gb300/csrc/lbm_ms.cuh",
@@ -67,7 +67,7 @@ KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_010
 # valid only while the kernel sources hash to "sha256".  Each SM issues 64 ALU-pipe and 2
 # FP64-pipe thread instructions per clock, so one node needs at least
 # max(alu / 64, fp64 / 2) SM clocks: the arithmetic roof of this kernel.
-PIPE_CAPTURE = {"sha256": "4cd6575dca6adf5a1091531a347c243070dedc849c0ed47e12b0882a4abda224",
+PIPE_CAPTURE = {"sha256": "d5c460ed088b0e2ce7563d9ea0521f1a53fc76b8c74124bae267d3a21becda8c",
                 "alu_per_node": 1025.0, "fp64_per_node": 32.0, "fma_per_node": 201.0}
 ALU_LANES_PER_SM, FP64_LANES_PER_SM, N_SM = 64, 2, 152
 
