@@ -138,6 +138,22 @@ def test_error_sums_match_host_reduction(lbm):
     np.testing.assert_allclose(s[2], np.max(np.abs(e), axis=(1, 2)), rtol=1e-12)
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32", "ms_bfp"])
+def test_init_without_body_load_equals_zero_body_load(lbm, storage):
+    """The initialisation skips every body-load term when no body load is given; with an
+    explicit zero body load it evaluates them: the populations must agree exactly."""
+    nx, ny = 133, 47
+    rng = np.random.default_rng(17)
+    U0, Ux, Uy = (rng.standard_normal((5, ny, nx)) * 1e-3 for _ in range(3))
+    out = []
+    for B0 in (None, np.zeros((2, ny, nx))):
+        lat = lbm.Lattice(nx, ny, 0.1, 0.1 / 3.2, 1.0, 0.6, storage=storage, track_displacement=False)
+        lat.init(U0, Ux, Uy, B0)
+        out.append(lat.populations()[0])
+        lat.close()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
 def test_checkpoint_resume_is_bit_exact(lbm):
     wl = _config1(steps=40)
     a = gpu_lattice(lbm, wl)
