@@ -103,7 +103,8 @@ def test_dirichlet_2048x1024_against_full_oracle(lbm, storage, tol):
 def test_batch_512_lattices_sampled_against_single_lattices(lbm, tmp_path):
     """The benchmark's batch workload at full size and in its launch configuration (autotuned
     tiles and mode, graphs of 100 steps): the smallest, the largest and a spread of other
-    lattices, periodic and Dirichlet, equal single-lattice runs bit for bit after 200 steps."""
+    lattices, periodic and Dirichlet, equal single-lattice runs bit for bit after 200 steps,
+    and the smallest periodic and Dirichlet lattices equal the FP64 oracle within 1e-5."""
     import torch
     from workloads.grf import batch_lattice_inputs_torch
     spec = W.batch_spec(count=512)
@@ -140,4 +141,21 @@ def test_batch_512_lattices_sampled_against_single_lattices(lbm, tmp_path):
         torch.cuda.synchronize()
         lat.close()
         assert torch.equal(got[0:5], ref[0:5]), (i, nx, ny, bc)
+    # anchored to the FP64 oracle: the smallest periodic and the smallest Dirichlet lattice of the
+    # batch, run by the oracle from the same inputs, agree with the batch's FP32 fields within the
+    # FP32 storage bound
+    for bc_want in (0, 1):
+        i = min((j for j in range(512) if descs[j][2] == bc_want), key=lambda j: nodes[j])
+        sp, (nx, ny, bc, dx, dt, cK, cmu) = spec[i], descs[i]
+        got = torch.empty((10, ny, nx), dtype=torch.float64, device="cuda")
+        lbm.lbm_batch_moments(b, i, got)
+        lbm.lbm_batch_synchronize(b)
+        U0, Ux, Uy = (t.cpu().numpy() for t in batch_lattice_inputs_torch(sp, dx, device="cuda"))
+        o = Oracle(Params(nx, ny, dx, dt, cK, cmu, bool(bc)))
+        o.init(U0, Ux, Uy)
+        for _ in range(200):
+            o.step(track_displacement=False)
+        ref = o.outputs()
+        errs = field_errors(got.cpu().numpy(), ref, range(5))
+        assert max(errs) < 1e-5, (i, nx, ny, bc, errs)
     lbm.lbm_batch_destroy(b)
