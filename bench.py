@@ -388,6 +388,9 @@ def run_ours(args):
         lat.close()
         mlups_rank = n_nodes * args.steps / (ms * 1e-3) / 1e6
         spp = 1 if args.no_fusion else (2 if storage in args.fuse_formats else STEPS_PER_PASS[storage])
+        if args.staging == 0 and spp > 1:
+            # without staged rows the population formats pair steps in registers; moment space steps singly
+            spp = 1 if storage.startswith("ms_") else 2
         results[storage] = {"ms_per_step": ms / args.steps, "mlups": mlups_rank * ws, "steps_per_pass": spp,
                             "launches": args.steps // spp + (1 if args.steps % spp else 0)}
 
@@ -520,7 +523,8 @@ def run_ours(args):
     hbm_part = {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(hbm_ach / hbm_peak, 4), "bytes_per_node": BYTES_PER_NODE["f64"],
                 "peak_source": peak_src}
-    pc = pipe_counts()
+    # the captured counts and traffic describe the default (staged) FP64 step kernel only
+    pc = pipe_counts() if args.staging >= 1 else None
     if pc is not None:
         # arithmetic roof: SM clocks per node = max(ALU-pipe / 64, FP64-pipe / 2) thread instructions
         alu_pn, fp64_pn, fma_pn = pc
@@ -542,7 +546,8 @@ def run_ours(args):
                     "hbm": hbm_part}
     else:
         roofline = dict(hbm_part)
-    roofline.update({"traffic": args.traffic if args.traffic is not None else traffic_per_launch("f64", n_nodes),
+    roofline.update({"traffic": args.traffic if args.traffic is not None else
+                     (traffic_per_launch("f64", n_nodes) if args.staging >= 1 else None),
                 "kernel": (f"lbmk::step_f64_staged_kernel<periodic,split level {SPLIT_LEVEL}> (rows staged by "
                            f"asynchronous copies)" if args.staging >= 1 else
                            f"lbmk::step_kernel<F64,1,periodic,split level {SPLIT_LEVEL}>"),
