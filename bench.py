@@ -574,8 +574,8 @@ def run_ours(args):
                     "launches": r["launches"],
                     "hbm": {"achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                             "frac": round(ach / hbm_peak, 4), "bytes_per_node_step": bpn,
-                            "traffic": traffic_per_launch({1: s, 2: s + "_fused", 3: s + "_fused3"}[r["steps_per_pass"]],
-                                                          n_nodes)},
+                            "traffic": (traffic_per_launch({1: s, 2: s + "_fused", 3: s + "_fused3"}[r["steps_per_pass"]],
+                                                           n_nodes) if args.staging >= 1 else None)},
                     "rel_l2_vs_f64_after_timed_run": {k: float(f"{v:.3e}") for k, v in r["rel_l2_vs_f64"].items()},
                     "timed_run_error_at_step": args.warmup + args.steps}
         if precision is not None and s in precision["formats"]:
