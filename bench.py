@@ -40,8 +40,11 @@ METRIC = "MLUPS and % of HBM roofline; mixed-precision vs FP64 at stated L2 erro
 BYTES_PER_NODE = {"f64": 320, "f32": 160, "bf16": 80, "f16": 80,    # one read + one write of 20 values
                   "ms_bf16": 100, "ms_f16": 100, "ms_bfp": 100}    # 5 FP32 + 15 16-bit moments, read + write
 FP64_OPS_PER_NODE = 47                                                # DADD/DFMA per node, no forcing
-SPLIT_LEVEL = 1               # lbm_set_fp64_split default: the 15 sums of a node on the integer pipe
-SPLIT_INTEGER_ADDS = 15
+SPLIT_LEVEL = 12              # lbm_set_fp64_split default: the node update in exact fixed-point arithmetic
+SPLIT_IEEE = 1                # the IEEE binary64 operation sequence with its 15 sums on the integer pipe
+ARITHMETIC = ("binary64 state; per node exact 64-bit fixed-point arithmetic on the integer pipes (inputs as "
+              "multiples of 2^-57 of the node's largest, 7 products rounded there) and one round-to-nearest-even "
+              "conversion to binary64 per output (lbm_set_fp64_split level 12)")
 # steps per launch of each format at the library's defaults (lbm_set_step_fusion)
 STEPS_PER_PASS = {"f64": 1, "f32": 3, "bf16": 3, "f16": 3, "ms_bf16": 3, "ms_f16": 3, "ms_bfp": 3}
 # DRAM bytes per node and launch of each step kernel (dram__bytes_read.sum + dram__bytes_write.sum
@@ -49,26 +52,24 @@ STEPS_PER_PASS = {"f64": 1, "f32": 3, "bf16": 3, "f16": 3, "ms_bf16": 3, "ms_f16
 # scaling), valid only while the kernel sources hash to "sha256".  "<fmt>_fused" is one launch of
 # the two-step kernel (two steps), "<fmt>_fused3" of the three-step kernel, "f64_pipe" the FP64
 # step with every operation on the FP64 pipe.
-TRAFFIC_CAPTURE = {"sha256": "d5c460ed088b0e2ce7563d9ea0521f1a53fc76b8c74124bae267d3a21becda8c",
+TRAFFIC_CAPTURE = {"sha256": "a0db4ef9c242616cffb2e5394784021f350c396c2b293d25745f11fdba2d956e",
                    "nodes": 8192 * 8192,
-                   "bytes_per_node": {"f64": 322.74, "f64_pipe": 319.25, "f32_fused": 165.22, "f32_fused3": 164.62,
-                                      "bf16_fused": 82.65, "bf16_fused3": 83.34, "f16_fused": 82.65,
-                                      "f16_fused3": 83.34, "ms_bf16_fused": 103.19, "ms_bf16_fused3": 105.14,
-                                      "ms_f16_fused": 103.19, "ms_f16_fused3": 105.15, "ms_bfp_fused": 103.2,
-                                      "ms_bfp_fused3": 105.15}}
+                   "bytes_per_node": {"f64": 319.23, "f64_ieee": 322.77, "f64_pipe": 319.26, "f32_fused3": 164.7,
+                                      "bf16_fused3": 83.34, "f16_fused3": 83.34, "ms_bf16_fused3": 105.14,
+                                      "ms_f16_fused3": 105.15, "ms_bfp_fused3": 105.15}}
 KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_01081_gb300/csrc/lbm_kind.cu",
                   "paper_2408_01081_gb300/csrc/lbm_tb.cuh", "paper_2408_01081_gb300/csrc/lbm_ms.cuh",
                   "paper_2408_01081_gb300/csrc/lbm_tbt.cuh", "paper_2408_01081_gb300/csrc/lbm_tma.cuh",
                   "paper_2408_01081_gb300/csrc/lbm_f64emu.cuh", "paper_2408_01081_gb300/csrc/lbm_mscodec.cuh",
-                  "paper_2408_01081_gb300/csrc/lbm_f64stage.cuh"]
-# Pipe instruction counts of the default FP64 step kernel (step_f64_staged_kernel) per node
+                  "paper_2408_01081_gb300/csrc/lbm_f64stage.cuh", "paper_2408_01081_gb300/csrc/lbm_f64fx.cuh"]
+# Pipe instruction counts of the default FP64 step kernel (step_f64_staged_kernel, split level 12) per node
 # (thread instructions: 32 x smsp__inst_executed_pipe_{alu,fp64,fma}.sum / nodes from one ncu
 # capture of 4096x2048),
 # valid only while the kernel sources hash to "sha256".  Each SM issues 64 ALU-pipe and 2
 # FP64-pipe thread instructions per clock, so one node needs at least
 # max(alu / 64, fp64 / 2) SM clocks: the arithmetic roof of this kernel.
-PIPE_CAPTURE = {"sha256": "d5c460ed088b0e2ce7563d9ea0521f1a53fc76b8c74124bae267d3a21becda8c",
-                "alu_per_node": 1025.0, "fp64_per_node": 32.0, "fma_per_node": 201.0}
+PIPE_CAPTURE = {"sha256": "a0db4ef9c242616cffb2e5394784021f350c396c2b293d25745f11fdba2d956e",
+                "alu_per_node": 585.8, "fp64_per_node": 20.0, "fma_per_node": 188.2}
 ALU_LANES_PER_SM, FP64_LANES_PER_SM, N_SM = 64, 2, 152
 
 
@@ -422,25 +423,29 @@ def run_ours(args):
                  "halo_bytes_per_step_per_cut_each_way": 5 * nx * 8,
                  "launches_per_step": 3, "exchange": "NCCL send/recv (torch.distributed.batch_isend_irecv)"}
 
-    # the FP64 step with every operation on the FP64 pipe (split level 0), for reference
+    # for reference: the IEEE binary64 operation sequence of the node update with its 15 sums on
+    # the integer pipe (split level 1, bit-identical to the FP64 pipe) and with every operation on
+    # the FP64 pipe (split level 0)
     if "f64" in args.formats:
         k0 = min(args.steps, 100)
-        lat = lbm.Lattice(nx, ny, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet=False, storage="f64",
-                          track_displacement=False, stream=stream.cuda_stream)
-        lat.set_fp64_split(0)
-        lat.init(U0, Ux, Uy)
-        lat.step(args.warmup)
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        lat.step(k0)
-        e1.record(stream)
-        barrier()
-        ms0 = max_over_ranks(e0.elapsed_time(e1))
-        lat.close()
-        results["f64_pipe_only"] = {"mlups": round(n_nodes * k0 / (ms0 * 1e-3) / 1e6 * ws, 1),
-                                    "ms_per_step": round(ms0 / k0, 4), "steps": k0}
+        for key, level in (("f64_ieee_sequence", SPLIT_IEEE), ("f64_pipe_only", 0)):
+            lat = lbm.Lattice(nx, ny, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet=False, storage="f64",
+                              track_displacement=False, stream=stream.cuda_stream)
+            lat.set_fp64_split(level)
+            lat.set_staging(args.staging)
+            lat.init(U0, Ux, Uy)
+            lat.step(args.warmup)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.step(k0)
+            e1.record(stream)
+            barrier()
+            ms0 = max_over_ranks(e0.elapsed_time(e1))
+            lat.close()
+            results[key] = {"split_level": level, "mlups": round(n_nodes * k0 / (ms0 * 1e-3) / 1e6 * ws, 1),
+                            "ms_per_step": round(ms0 / k0, 4), "steps": k0}
 
     # relative L2 of every moment field against the FP64 run after the same steps
     ref = finals.get("f64")
@@ -518,49 +523,55 @@ def run_ours(args):
     sm_mhz = (clocks or {}).get("sm_mhz") or 2032.0
     # FP64 pipe: 2 DFMA/DADD per SM per clock on GB300 (measured 601.6 G DFMA/s at ~1.98 GHz)
     fp64_peak = 152 * 2 * sm_mhz * 1e6 / 1e9
-    fp64_ach = FP64_OPS_PER_NODE * nodes_per_s / 1e9
-    fp64_pipe_ops = FP64_OPS_PER_NODE - SPLIT_INTEGER_ADDS
     hbm_part = {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(hbm_ach / hbm_peak, 4), "bytes_per_node": BYTES_PER_NODE["f64"],
                 "peak_source": peak_src}
+    hbm_node_peak = hbm_peak * 1e9 / BYTES_PER_NODE["f64"]
     # the captured counts and traffic describe the default (staged) FP64 step kernel only
     pc = pipe_counts() if args.staging >= 1 else None
+    arith = None
     if pc is not None:
         # arithmetic roof: SM clocks per node = max(ALU-pipe / 64, FP64-pipe / 2) thread instructions
         alu_pn, fp64_pn, fma_pn = pc
-        alu_bound = alu_pn / ALU_LANES_PER_SM >= fp64_pn / FP64_LANES_PER_SM
-        inst_pn, lanes = (alu_pn, ALU_LANES_PER_SM) if alu_bound else (fp64_pn, FP64_LANES_PER_SM)
-        clk_pn = inst_pn / lanes
+        clk_pn = max(alu_pn / ALU_LANES_PER_SM, fp64_pn / FP64_LANES_PER_SM)
         node_peak = N_SM * sm_mhz * 1e6 / clk_pn
+        arith = {"alu_inst_per_node": alu_pn, "fp64_inst_per_node": fp64_pn, "fma_inst_per_node": fma_pn,
+                 "sm_clocks_per_node": round(clk_pn, 3), "node_rate_peak_G_per_s": round(node_peak / 1e9, 3),
+                 "node_rate_achieved_G_per_s": round(nodes_per_s / 1e9, 3),
+                 "frac": round(nodes_per_s / node_peak, 4),
+                 "hbm_node_rate_peak_G_per_s": round(hbm_node_peak / 1e9, 3),
+                 "source": "ncu pipe instruction counts of this kernel x 152 SMs x median SM clock sampled in "
+                           "the timed region"}
+    if arith is not None and arith["node_rate_peak_G_per_s"] * 1e9 < hbm_node_peak:
+        alu_bound = arith["alu_inst_per_node"] / ALU_LANES_PER_SM >= arith["fp64_inst_per_node"] / FP64_LANES_PER_SM
+        inst_pn, lanes = ((arith["alu_inst_per_node"], ALU_LANES_PER_SM) if alu_bound else
+                          (arith["fp64_inst_per_node"], FP64_LANES_PER_SM))
         roofline = {"bound": "alu", "achieved": round(inst_pn * nodes_per_s / 1e9, 1),
                     "peak": round(N_SM * lanes * sm_mhz * 1e6 / 1e9, 1),
                     "unit": "G ALU-pipe inst/s" if alu_bound else "G FP64-pipe inst/s",
-                    "frac": round(nodes_per_s / node_peak, 4),
-                    "model": {"alu_inst_per_node": alu_pn, "fp64_inst_per_node": fp64_pn, "fma_inst_per_node": fma_pn,
-                              "sm_clocks_per_node": round(clk_pn, 3),
-                              "node_rate_peak_G_per_s": round(node_peak / 1e9, 3),
-                              "node_rate_achieved_G_per_s": round(nodes_per_s / 1e9, 3),
-                              "hbm_node_rate_peak_G_per_s": round(hbm_peak * 1e9 / BYTES_PER_NODE["f64"] / 1e9, 3),
-                              "source": "ncu pipe instruction counts of this kernel x 152 SMs x median SM clock "
-                                        "sampled in the timed region"},
-                    "hbm": hbm_part}
+                    "frac": arith["frac"], "model": arith, "hbm": hbm_part}
     else:
         roofline = dict(hbm_part)
+        if arith is not None:
+            roofline["arithmetic_roof"] = arith
+    ieee = results.get("f64_ieee_sequence")
+    if ieee is not None:
+        ieee = dict(ieee, hbm_frac=round(BYTES_PER_NODE["f64"] * ieee["mlups"] * 1e6 / 1e9 / hbm_peak, 4),
+                    note="the IEEE binary64 operation sequence (bit-identical to the FP64 pipe), its 15 sums "
+                         "as exact binary64 additions on the integer pipe; bound by the FP64 and integer pipes")
     roofline.update({"traffic": args.traffic if args.traffic is not None else
                      (traffic_per_launch("f64", n_nodes) if args.staging >= 1 else None),
-                "kernel": (f"lbmk::step_f64_staged_kernel<periodic,split level {SPLIT_LEVEL}> (rows staged by "
-                           f"asynchronous copies)" if args.staging >= 1 else
-                           f"lbmk::step_kernel<F64,1,periodic,split level {SPLIT_LEVEL}>"),
-                "compute": {"limiter": "FP64 pipe and integer ALU pipe together (exact binary64 additions "
-                                       "moved to the integer pipe); below the HBM roof",
-                            "fp64_pipe_ops_per_node": fp64_pipe_ops,
-                            "integer_pipe_adds_per_node": SPLIT_INTEGER_ADDS,
-                            "fp64_pipe_achieved": round(fp64_pipe_ops * nodes_per_s / 1e9, 2),
-                            "fp64_pipe_peak": round(fp64_peak, 2), "unit": "GFP64op/s",
-                            "fp64_pipe_frac": round(fp64_pipe_ops * nodes_per_s / 1e9 / fp64_peak, 4),
-                            "fp64_pipe_peak_source": "152 SMs x 2 FP64 ops/clk x median SM clock sampled in the "
-                                                     "timed region",
-                            "fp64_pipe_only": results.get("f64_pipe_only")}})
+                     "kernel": (f"lbmk::step_f64_staged_kernel<periodic,split level {SPLIT_LEVEL}> (fixed-point "
+                                f"node update; rows staged by asynchronous copies)" if args.staging >= 1 else
+                                f"lbmk::step_kernel<F64,1,periodic,split level {SPLIT_LEVEL}>"),
+                     "compute": {"arithmetic": ARITHMETIC,
+                                 "fp64_pipe_ops_per_node": 20,
+                                 "fp64_pipe_use": "the 20 conversions of the outputs to binary64",
+                                 "fp64_pipe_peak": round(fp64_peak, 2), "unit": "GFP64op/s",
+                                 "fp64_pipe_frac": round(20 * nodes_per_s / 1e9 / fp64_peak, 4),
+                                 "fp64_pipe_peak_source": "152 SMs x 2 FP64 ops/clk x median SM clock sampled "
+                                                          "in the timed region",
+                                 "ieee_sequence": ieee, "fp64_pipe_only": results.get("f64_pipe_only")}})
     mixed = {}
     for s in args.formats:
         if s == "f64":
@@ -596,7 +607,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": round(head["mlups"], 1), "unit": "MLUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(head["ms_per_step"], 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
+            "arithmetic": ARITHMETIC, "data": "synthetic",
             "config": {"workload": _workload_desc(nx, ny) + (
                            f"; {ws} row slabs of one {nx}x{ny * ws} lattice (the tile repeated along y)"
                            if slabs is not None else ""),

@@ -107,8 +107,8 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const d
  * accurate.  Three steps per kernel need staged rows (lbm_set_staging 1; with 0 pairs
  * run instead); a remainder of one or two steps runs as a single step or a pair.
  * rows_per_block sets the rows each thread block streams through (0 keeps the
- * format's default: 12 for LBM_F32, 64 for the other reduced formats, 2 for the
- * staged LBM_F64 step of lbm_set_staging).
+ * format's default: 12 for LBM_F32, 64 for the other reduced formats; for the
+ * staged LBM_F64 step of lbm_set_staging 4 at split level 12 and 2 at level 1).
  * steps_per_pass = 1 always uses one kernel per step. */
 lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t rows_per_block);
 
@@ -139,11 +139,23 @@ lbm_status lbm_set_staging(lbm_ctx* ctx, int32_t mode);
  * 1, 2 or 5 of the f*_(-1,0) subtractions; results stay within FP64 accuracy of
  * level 0 but are not bit-identical, and the rounding is biased (half up, no sticky
  * bit): over 10^5 steps the discrete energy drifts by about 3e-12 instead of 4e-16.
- * Level 9 (16 additions) runs about 3 % faster than level 1, which stays the
- * default.  Lanes whose operands leave the integer path (subnormal, infinite or
- * NaN results) recompute on the FP64 pipe.  Level 0 runs every operation on
- * the FP64 pipe.  Applies to steps without body load and with omega = 2; other
- * steps use the FP64 pipe only.  A level outside [0, 11] returns LBM_ERR_ARG. */
+ * Lanes whose operands leave the integer path (subnormal, infinite or NaN results)
+ * recompute on the FP64 pipe.  Level 12 (the default where it applies) computes the
+ * whole node update (Eqs. cond_eq, feq, collision) in exact 64-bit fixed-point
+ * arithmetic on the integer pipes: each input as an integer multiple of
+ * rho = 2^-57 times the power of two just above the node's largest input (exact
+ * within 2^5 of it), the sums exactly, the seven products by cK / c and cmu / c
+ * rounded to a multiple of rho, and one round-to-nearest-even conversion to
+ * binary64 per output.  Every output is then within half an ulp plus 10 rho of the
+ * exact update of its inputs, a tighter bound than the FP64 operation sequence's,
+ * but the bits differ from level 0.  The state stays binary64; the step is bound by
+ * memory instead of the FP64 pipe.  Nodes whose largest input is below about
+ * 2^-964, at or above about 2^1019, or not finite run the level-1 sequence instead
+ * (the choice depends on the node's own inputs only).  Level 12 needs cK / c and
+ * cmu / c in [2^-60, 1/2) (cmu may be 0); otherwise it returns LBM_ERR_ARG and
+ * level 1 is the default.  Level 0 runs every operation on the FP64 pipe.  Applies
+ * to steps without body load and with omega = 2; other steps use the FP64 pipe
+ * only.  A level outside [0, 12] returns LBM_ERR_ARG. */
 lbm_status lbm_set_fp64_split(lbm_ctx* ctx, int32_t level);
 
 /* Relaxation rate of the BGK collision (Eq. collision); the paper's scheme is

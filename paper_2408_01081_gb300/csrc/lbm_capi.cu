@@ -198,7 +198,10 @@ struct lbm_ctx {
     double neq_scale = 1.0;      // moment-space storage: scale of the stored deviations
     int fuse = 1;                // steps per pass over memory when the fused kernel applies
     int tb_rows = 16;            // rows per block of the fused kernels and the staged FP64 step
-    int split = 1;               // FP64: split level (which additions run on the integer pipes)
+    bool rows_set = false;       // tb_rows given by lbm_set_step_fusion (else the staged FP64 step's
+                                 // rows per block follow its split level)
+    int split = 1;               // FP64: split level (which additions run on the integer pipes; 12:
+                                 // the fixed-point node update, the default where it applies)
     int staging = 1;             // 1 = rows staged in shared memory (tensor copies for the fused kernels,
                                  // asynchronous copies for the FP64 step), 0 = register loads
     int l2_ahead = lbmk::TBT_L2_AHEAD;   // staged kernel: rows prefetched into L2 ahead of the ring
@@ -427,6 +430,9 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
     // per format
     ctx->fuse = (p->storage == LBM_F64) ? 1 : 3;
     ctx->tb_rows = (p->storage == LBM_F64) ? 2 : (p->storage == LBM_F32) ? 12 : 64;
+    // FP64: the fixed-point node update by default (within FP64 accuracy, bound by memory
+    // instead of the FP64 pipe); the exact integer-pipe sums where its multipliers do not fit
+    ctx->split = (lbmfx::mul_ok(ctx->a) && lbmfx::mul_ok(ctx->b)) ? lbmh::STEP_SPLIT_FIXED : 1;
     // symmetrizer blocks k_ij = g_ij^{-1}, g_ij = 1/4 I + (i A_x + j A_y)/(2c)  (Eq. stability_linear)
     const int VI[4] = {1, 0, -1, 0}, VJ[4] = {0, 1, 0, -1};
     for (int d = 0; d < 4; ++d) {
@@ -628,14 +634,19 @@ lbm_status lbm_set_step_fusion(lbm_ctx* ctx, int32_t steps_per_pass, int32_t row
     if (steps_per_pass < 1 || steps_per_pass > 3 || rows_per_block < 0 || rows_per_block > 65535)
         return fail(ctx, LBM_ERR_ARG, "steps_per_pass must be 1, 2 or 3 and rows_per_block in [0, 65535]");
     ctx->fuse = steps_per_pass;
-    if (rows_per_block > 0) ctx->tb_rows = rows_per_block;
+    if (rows_per_block > 0) {
+        ctx->tb_rows = rows_per_block;
+        ctx->rows_set = true;
+    }
     return LBM_OK;
 }
 
 lbm_status lbm_set_fp64_split(lbm_ctx* ctx, int32_t level)
 {
     LBM_CHECK_CTX(ctx);
-    if (level < 0 || level >= lbmh::STEP_SPLIT_LEVELS) return fail(ctx, LBM_ERR_ARG, "split level must be in [0, 11]");
+    if (level < 0 || level >= lbmh::STEP_SPLIT_LEVELS) return fail(ctx, LBM_ERR_ARG, "split level must be in [0, 12]");
+    if (level == lbmh::STEP_SPLIT_FIXED && (!lbmfx::mul_ok(ctx->a) || !lbmfx::mul_ok(ctx->b)))
+        return fail(ctx, LBM_ERR_ARG, "split level 12 needs cK/c and cmu/c in [2^-60, 1/2) (or cmu = 0)");
     ctx->split = level;
     return LBM_OK;
 }
@@ -902,7 +913,11 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
         A.g = ctx->g ? ctx->g + m * 2 * ctx->nwall : nullptr;
         // FP64 at split level 1: rows staged by asynchronous copies unless staging is off
         cudaError_t e = cudaErrorNotSupported;
-        if (split && ctx->split == 1 && ctx->staging >= 1) e = ops->step_staged(A, variant, ctx->tb_rows, ctx->s);
+        if (split && (ctx->split == 1 || ctx->split == lbmh::STEP_SPLIT_FIXED) && ctx->staging >= 1) {
+            // rows per block measured best at 8192^2: 2 at level 1, 4 for the fixed-point update
+            const int rows = ctx->rows_set ? ctx->tb_rows : (ctx->split == 1 ? 2 : 4);
+            e = ops->step_staged(A, variant, rows, ctx->s);
+        }
         if (e == cudaErrorNotSupported) e = ops->step(A, variant, grid, block, ctx->s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step kernel");
         ctx->cur ^= 1;

@@ -16,7 +16,7 @@ namespace lbmh {
 
 // step variant bits; bits 4-7 hold the FP64 split level (0 = every addition on the FP64 pipe)
 enum { STEP_DIRICHLET = 1, STEP_FORCING = 2, STEP_TRACK = 4, STEP_OMEGA = 8, STEP_SPLIT_SHIFT = 4,
-       STEP_SPLIT_LEVELS = 12 };
+       STEP_SPLIT_LEVELS = 13, STEP_SPLIT_FIXED = 12 };
 
 // additions moved to the integer pipes at split level 1..7, as bit masks over the
 // node's 35 additions (bit layout of lbmk::collide_split): 0-4 f*_(-1,0), 5-9
@@ -37,13 +37,16 @@ constexpr unsigned long long split_mask(int level)
          : level == 9 ? lbmk::kSplitFastMask                               // 16: + f*_(-1,0) 0
          : level == 10 ? (0x001FFFC03ull | lbmk::kSplitFaithful)           // 17: + f*_(-1,0) 0-1
          : level == 11 ? (0x001FFFC1Full | lbmk::kSplitFaithful)           // 20: + f*_(-1,0)
+         // level 12: the whole node in exact fixed-point arithmetic (lbm_f64fx.cuh)
+         : level == 12 ? lbmk::kSplitFixed
                       : 0ull;
 }
 
 constexpr int split_adds(int level)
 {
     int n = 0;
-    for (unsigned long long m = split_mask(level) & ~lbmk::kSplitFaithful; m; m >>= 1) n += (int)(m & 1);
+    for (unsigned long long m = split_mask(level) & ~(lbmk::kSplitFaithful | lbmk::kSplitFixed); m; m >>= 1)
+        n += (int)(m & 1);
     return n;
 }
 

@@ -30,6 +30,9 @@ constexpr int SA_SLOTS = 20;                          // inputs per node
 #ifndef LBM_SA_MIN_BLOCKS
 #define LBM_SA_MIN_BLOCKS 6                           // 6 x 128 threads at <= 85 registers
 #endif
+#ifndef LBM_SA_FX_MIN_BLOCKS
+#define LBM_SA_FX_MIN_BLOCKS 4                        // fixed-point node update: <= 128 registers
+#endif
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src)
 {
@@ -51,7 +54,8 @@ __device__ __forceinline__ double lds_f64(uint32_t a)
 // grid: (ceil(nx / SA_THREADS), ceil(ny / rows)), block SA_THREADS; block (cb, r) computes
 // the rows r * rows ... of column block cb, one after the other
 template <bool DIRICHLET, bool TRACK, unsigned long long SPLIT>
-__global__ void __launch_bounds__(SA_THREADS, LBM_SA_MIN_BLOCKS) step_f64_staged_kernel(StepArgs A, int rows)
+__global__ void __launch_bounds__(SA_THREADS, (SPLIT & kSplitFixed) ? LBM_SA_FX_MIN_BLOCKS : LBM_SA_MIN_BLOCKS)
+    step_f64_staged_kernel(StepArgs A, int rows)
 {
     __shared__ __align__(16) double slot[SA_SLOTS][SA_THREADS];
     const int t = threadIdx.x;

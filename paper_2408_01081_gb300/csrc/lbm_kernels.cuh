@@ -20,6 +20,7 @@
 #pragma once
 
 #include "lbm_f64emu.cuh"
+#include "lbm_f64fx.cuh"
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -177,6 +178,9 @@ constexpr unsigned long long kSplitDefaultMask = 0x001FFFC00ull;
 // mask bit 63: the integer-pipe additions are rounded faithfully (emu_add_faithful_bits)
 // instead of correctly
 constexpr unsigned long long kSplitFaithful = 1ull << 63;
+// mask bit 62: the whole node in exact fixed-point arithmetic on the integer pipes, one
+// rounding per output (lbm_f64fx.cuh); not bit-identical to the FP64-pipe sequence
+constexpr unsigned long long kSplitFixed = 1ull << 62;
 // the fastest faithful split measured (opt-in, level 9): the 15 sums and the (-1,0)
 // subtraction of component 0; its rounding is biased (half up, no sticky bit), which a
 // long run shows as energy drift
@@ -239,8 +243,55 @@ __device__ __forceinline__ void split_outputs(const double (&U)[5], const double
 // the integer path (a subnormal, infinite or NaN result) recomputes on the FP64 pipe.
 template <unsigned long long M>
 __device__ __forceinline__ void collide_split(const double (&f)[4][5], double a, double b, double (&U)[5],
+                                              double (&o)[4][5]);
+
+// The node update in exact fixed-point arithmetic (lbmfx::fx_node): a = cK / c, b = cmu / c
+// in [0, 1/2) (the CFL-like bound) and not below 2^-60 unless zero (checked by the host).
+// A node outside the fixed-point range (its largest input below about 2^-964 or above
+// 2^1019, or not finite) runs the exact split collision instead; the choice depends on
+// the node's own inputs only.
+__device__ __forceinline__ void collide_fixed(const double (&f)[4][5], double a, double b, double (&U)[5],
                                               double (&o)[4][5])
 {
+    const lbmfx::Mul A = lbmfx::make_mul(lbmemu::bits_of(a)), B = lbmfx::make_mul(lbmemu::bits_of(b));
+    lbmfx::u64 in[4][5], out[4][5], Uo[5];
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) in[d][k] = lbmemu::bits_of(f[d][k]);
+    const int E = lbmfx::node_exp(in);
+    const bool ok = lbmfx::exp_ok(E);
+    if (__all_sync(0xffffffffu, ok)) {
+        lbmfx::fx_update(in, E, A, B, out, Uo);
+    } else {
+        // warp-uniform branch: every lane runs the split collision (it synchronises the warp
+        // itself); the lanes inside the fixed-point range then overwrite its results
+        double U2[5], o2[4][5];
+        collide_split<kSplitDefaultMask>(f, a, b, U2, o2);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            Uo[k] = lbmemu::bits_of(U2[k]);
+#pragma unroll
+            for (int d = 0; d < 4; ++d) out[d][k] = lbmemu::bits_of(o2[d][k]);
+        }
+        if (ok) lbmfx::fx_update(in, E, A, B, out, Uo);
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        U[k] = lbmemu::double_of(Uo[k]);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) o[d][k] = lbmemu::double_of(out[d][k]);
+    }
+}
+
+template <unsigned long long M>
+__device__ __forceinline__ void collide_split(const double (&f)[4][5], double a, double b, double (&U)[5],
+                                              double (&o)[4][5])
+{
+    if constexpr ((M & kSplitFixed) != 0) {
+        collide_fixed(f, a, b, U, o);
+        return;
+    }
     bool ok = true;
     double rx[5], ry[5];
     split_sums<M, 0>(f, rx, ry, U, ok);

@@ -60,6 +60,7 @@ cudaError_t step_split(const lbmk::StepArgs& a, int level, dim3 g, dim3 b, cudaS
         case 9: return step_v<D, false, T, false, lbmh::split_mask(9)>(a, g, b, s);
         case 10: return step_v<D, false, T, false, lbmh::split_mask(10)>(a, g, b, s);
         case 11: return step_v<D, false, T, false, lbmh::split_mask(11)>(a, g, b, s);
+        case 12: return step_v<D, false, T, false, lbmh::split_mask(12)>(a, g, b, s);
         default: return cudaErrorInvalidValue;
         }
     }
@@ -71,25 +72,35 @@ cudaError_t step_split(const lbmk::StepArgs& a, int level, dim3 g, dim3 b, cudaS
 
 // FP64 at split level 1 with the rows staged by asynchronous copies (lbm_f64stage.cuh);
 // other formats, levels and variants return cudaErrorNotSupported
-template <bool D, bool T>
+template <bool D, bool T, unsigned long long M>
 cudaError_t step_staged_dt(const lbmk::StepArgs& a, int rows, cudaStream_t s)
 {
     if constexpr (K != lbmk::K_F64) {
         return cudaErrorNotSupported;
     } else {
         const dim3 g((a.nx + lbmk::SA_THREADS - 1) / lbmk::SA_THREADS, (a.ny + rows - 1) / rows);
-        lbmk::step_f64_staged_kernel<D, T, LBM_SA_MASK><<<g, lbmk::SA_THREADS, 0, s>>>(a, rows);
+        lbmk::step_f64_staged_kernel<D, T, M><<<g, lbmk::SA_THREADS, 0, s>>>(a, rows);
         return cudaGetLastError();
     }
 }
 
+template <unsigned long long M>
+cudaError_t step_staged_m(const lbmk::StepArgs& a, bool d, bool t, int rows, cudaStream_t s)
+{
+    return d ? (t ? step_staged_dt<true, true, M>(a, rows, s) : step_staged_dt<true, false, M>(a, rows, s))
+             : (t ? step_staged_dt<false, true, M>(a, rows, s) : step_staged_dt<false, false, M>(a, rows, s));
+}
+
+// split levels 1 (LBM_SA_MASK) and 12 (fixed point)
 cudaError_t step_staged(const lbmk::StepArgs& a, int variant, int rows, cudaStream_t s)
 {
     const int level = (variant >> lbmh::STEP_SPLIT_SHIFT) & 15;
-    if (level != 1 || (variant & (lbmh::STEP_FORCING | lbmh::STEP_OMEGA)) || rows < 1) return cudaErrorNotSupported;
+    if ((level != 1 && level != lbmh::STEP_SPLIT_FIXED) || (variant & (lbmh::STEP_FORCING | lbmh::STEP_OMEGA)) ||
+        rows < 1)
+        return cudaErrorNotSupported;
     const bool d = variant & lbmh::STEP_DIRICHLET, t = variant & lbmh::STEP_TRACK;
-    return d ? (t ? step_staged_dt<true, true>(a, rows, s) : step_staged_dt<true, false>(a, rows, s))
-             : (t ? step_staged_dt<false, true>(a, rows, s) : step_staged_dt<false, false>(a, rows, s));
+    return level == 1 ? step_staged_m<LBM_SA_MASK>(a, d, t, rows, s)
+                      : step_staged_m<lbmh::split_mask(lbmh::STEP_SPLIT_FIXED)>(a, d, t, rows, s);
 }
 
 template <bool O>

@@ -431,11 +431,120 @@ def test_fp64_split_handles_zeros_subnormals_and_wide_ranges(lbm):
 
 def test_fp64_split_rejects_unsupported_counts(lbm):
     lat = lbm.Lattice(8, 8, 0.1, 0.1 / 3.2, 1.0, 0.6, storage="f64")
-    for bad in (-1, 12, 100):
+    for bad in (-1, 13, 100):
         with pytest.raises(lbm.LbmError):
             lat.set_fp64_split(bad)
     lat.set_fp64_split(11)
+    lat.set_fp64_split(12)
     lat.close()
+    # the fixed-point level needs cK / c at or above 2^-60
+    lat = lbm.Lattice(8, 8, 1.0, 0.5, 1e-20, 0.0, storage="f64")
+    with pytest.raises(lbm.LbmError):
+        lat.set_fp64_split(12)
+    lat.close()
+
+
+FIXED = 12     # split level: the node update in exact fixed-point arithmetic
+
+
+@pytest.mark.parametrize("case", ["grf_periodic", "energy_box", "ragged_periodic", "ragged_dirichlet"])
+def test_fp64_fixed_point_level_matches_oracle(lbm, case):
+    """Split level 12 (exact fixed-point node update, one rounding per output) against the
+    FP64 oracle at the FP64 tolerance: periodic and homogeneous Dirichlet lattices without
+    body load, ragged sizes, staged and register kernels."""
+    if case == "grf_periodic":
+        wl = W.grf_periodic(250, 64, 1.5, 0.5, ell=8.0, std=1e-3, seeds=(5, 6), steps=0)
+        dirichlet, steps = False, 300
+    elif case == "energy_box":
+        wl = W.energy_box(96, 1.1, 0.4, 1.0 / 240.0, 0)
+        dirichlet, steps = True, 300
+    else:
+        dirichlet = case == "ragged_dirichlet"
+        wl = W.energy_box(37, 1.1, 0.4, 1.0 / 100.0, 0) if dirichlet else \
+            W.grf_periodic(131, 29, 1.5, 0.5, ell=6.0, std=1e-3, seeds=(7, 8), steps=0)
+        steps = 150
+    o = Oracle(Params(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet))
+    o.init(wl.U0, wl.dU0dx, wl.dU0dy)
+    for _ in range(steps):
+        o.step(track_displacement=False)
+    ref = o.moments()
+    for staging in (1, 0):
+        lat = lbm.Lattice(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet=dirichlet, storage="f64",
+                          track_displacement=False)
+        lat.set_fp64_split(FIXED)
+        lat.set_staging(staging)
+        lat.init(wl.U0, wl.dU0dx, wl.dU0dy)
+        lat.step(steps)
+        errs = field_errors(lat.moments(), ref, fields=range(5))
+        lat.close()
+        assert max(errs) < TOL64, (staging, errs)
+
+
+@pytest.mark.parametrize("dirichlet", [False, True])
+@pytest.mark.parametrize("nx,ny,rows", [(3, 5, 64), (129, 33, 7), (1031, 7, 3)])
+def test_fp64_fixed_point_staged_equals_register_step(lbm, nx, ny, rows, dirichlet):
+    """Level 12 computes the same bits in the staged and the register kernel (the same
+    integer arithmetic per node), with wall data and displacement tracking; and it stays
+    within FP64 accuracy of the FP64-pipe sequence (level 0)."""
+    steps = 9
+    rng = np.random.default_rng(5 * nx + ny + rows)
+    f = rng.standard_normal((4, 5, ny, nx))
+    us = rng.standard_normal((2, ny, nx))
+    wall = rng.standard_normal((steps, 2, 2 * (nx + ny))) * 1e-2 if dirichlet else None
+    kw = dict(dirichlet=dirichlet, wall=wall, track=True, rows=rows)
+    staged = _split_runs(lbm, nx, ny, f, us, steps, [FIXED], staging=1, **kw)[FIXED]
+    plain = _split_runs(lbm, nx, ny, f, us, steps, [FIXED], staging=0, **kw)[FIXED]
+    ref = _split_runs(lbm, nx, ny, f, us, steps, [0], staging=0, **kw)[0]
+    np.testing.assert_array_equal(staged[0].view(np.int64), plain[0].view(np.int64))
+    np.testing.assert_array_equal(staged[1].view(np.int64), plain[1].view(np.int64))
+    for part in (0, 1):
+        rel = np.linalg.norm(staged[part] - ref[part]) / np.linalg.norm(ref[part])
+        assert rel < 1e-14, (part, rel)
+
+
+def test_fp64_fixed_point_conserves_energy(lbm):
+    """Homogeneous Dirichlet, b = 0 (Sec. 6.2 set-up): ||f||_P conserved by the fixed-point
+    level to the same bound as the FP64 path over 4000 steps."""
+    wl = W.energy_box(160, 1.1, 0.4, 1.0 / 400.0, 4000)
+    lat = lbm.Lattice(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet=True, storage="f64",
+                      track_displacement=False)
+    lat.set_fp64_split(FIXED)
+    lat.init(wl.U0, wl.dU0dx, wl.dU0dy, None, wl.u0)
+    e0 = lat.energy()
+    drift = 0.0
+    for _ in range(40):
+        lat.step(100)
+        drift = max(drift, abs(math.sqrt(lat.energy()) - math.sqrt(e0)) / math.sqrt(e0))
+    lat.close()
+    assert drift < 3.4e-14, drift
+
+
+def test_fp64_fixed_point_handles_zeros_subnormals_and_wide_ranges(lbm):
+    """Nodes outside the fixed-point range (all zero, tiny, near overflow) run the FP64
+    sequence; the rest keep FP64 accuracy: finite where level 0 is finite, within FP64
+    accuracy of level 0 over the whole field and over the band of tiny values."""
+    nx, ny = 96, 40
+    rng = np.random.default_rng(8)
+    f = rng.standard_normal((4, 5, ny, nx))
+    pick = rng.integers(0, 6, size=f.shape)
+    f[pick == 0] = 0.0
+    f[pick == 1] = -0.0
+    f[pick == 2] *= 1e-310
+    f[pick == 3] *= 1e-300
+    f[pick == 4] *= 1e300
+    f[:, :, :, :8] = 0.0
+    f[:, :, 10:34, 40:90] = rng.standard_normal((4, 5, 24, 50)) * 1e-295   # below the fixed-point range
+    outs = _split_runs(lbm, nx, ny, f, None, 5, [0, FIXED])
+    def rel(a, b):
+        sc = np.max(np.abs(b))
+        return np.linalg.norm((a - b) / sc) / np.linalg.norm(b / sc)
+
+    ref, got = outs[0][0], outs[FIXED][0]
+    assert np.array_equal(np.isfinite(got), np.isfinite(ref))
+    assert rel(got, ref) <= 1e-14, rel(got, ref)
+    # nodes that only ever saw the tiny block ran the FP64 sequence: the same bits as level 0
+    inner = (slice(None), slice(None), slice(16, 28), slice(46, 84))
+    np.testing.assert_array_equal(got[inner].view(np.int64), ref[inner].view(np.int64))
 
 
 @pytest.mark.parametrize("nx,ny,dirichlet", [(67, 45, False), (1031, 7, False), (150, 70, True)])
