@@ -39,6 +39,24 @@ def test_config1_periodic_64_fp64_matches_oracle(lbm):
     assert rel_l2(out[5:7], ex[5:7]) < 2e-2
 
 
+@pytest.mark.parametrize("kind", ["P", "S"])
+def test_config1_force_free_plane_waves_fp64(lbm, kind):
+    """Config 1's forcing-free check on the periodic 64^2 lattice, 1000 steps: a standing P or S
+    wave with b = 0, so the default FP64 step (fixed-point node update) runs every step; it equals
+    the oracle within the FP64 tolerance, and u stays within the scheme's second-order error of
+    the exact wave."""
+    wl = W.plane_wave_periodic(64, 1.5, 0.5, kind, steps=1000)
+    _, ref = oracle_run(wl)
+    lat = gpu_lattice(lbm, wl)
+    lat.step(wl.steps)
+    out = lat.moments()
+    lat.close()
+    errs = field_errors(out, ref)
+    assert max(errs) < TOL64, errs
+    ex = wl.exact_outputs(wl.steps * wl.dt)
+    assert rel_l2(out[5:7], ex[5:7]) < 2e-3          # the oracle: 6.7e-4 (P wave)
+
+
 @pytest.mark.parametrize("nx,ny", [(48, 24), (37, 23), (1100, 9)])
 def test_dirichlet_mms_fp64_matches_oracle(lbm, nx, ny):
     wl = W.dirichlet_mms(nx, ny, 1.1, 0.4, cfl=0.9, steps=60, height=1.0)

@@ -1,7 +1,7 @@
 """Pins of the FP64 oracle against the paper's numerical results (no GPU).
 
 * second-order convergence on the moving manufactured solution, periodic
-  (u and sigma, L2 and Linf) and Dirichlet (u in both norms, sigma in L2), with
+  (u and sigma, L2 and Linf), on force-free standing P and S waves, and Dirichlet (u in both norms, sigma in L2), with
   sigma in Linf degrading towards first order under Dirichlet (Sec. 6.1);
 * conservation of ||f||_P to round-off on the energy set-up of Sec. 6.2
   (paper: max relative drift about 3.4e-15);
@@ -38,6 +38,21 @@ def _slopes(a, b):
 @pytest.mark.parametrize("mat", [(1.1, 0.4), (1.4, 0.1), (0.75, 0.75)])
 def test_periodic_second_order(mat):
     errs = [_run_mms(W.periodic_mms(n, *mat, c=2.5, t_final=0.5)) for n in (40, 80)]
+    for s in _slopes(*errs):
+        assert 1.85 < s < 2.2, (errs, s)
+
+
+@pytest.mark.parametrize("kind", ["P", "S"])
+def test_plane_waves_are_force_free_and_converge_at_second_order(kind):
+    """Config 1's forcing-free check: a standing P wave (c_P^2 = cK^2 + cmu^2) or S wave (cmu^2)
+    along x solves Eq. teq with b = 0 (the Navier body load of the workload vanishes), and the
+    oracle converges to it at second order in u and sigma, L2 and Linf, without any body load."""
+    wl = W.plane_wave_periodic(32, 1.5, 0.5, kind, t_final=0.5)
+    assert wl.forcing is None
+    for t in (0.0, 0.3, 0.77):
+        b = W.mms.dense_stack(wl.exact.body_load(), 32, 32, wl.dx, t)
+        assert np.abs(b).max() < 1e-13, (t, np.abs(b).max())
+    errs = [_run_mms(W.plane_wave_periodic(n, 1.5, 0.5, kind, t_final=0.5)) for n in (32, 64)]
     for s in _slopes(*errs):
         assert 1.85 < s < 2.2, (errs, s)
 

@@ -9,6 +9,7 @@ Workloads
 * ``periodic_mms``   -- periodic square with the moving manufactured solution of
   Eq. periodic_moving (any amplitude / wavenumbers), body load from the Navier form.
 * ``dirichlet_mms``  -- same solution on a rectangle with u = u_hat on all edges.
+* ``plane_wave_periodic`` -- periodic square with a body-force-free standing P or S wave.
 * ``energy_box``     -- homogeneous Dirichlet, b = 0, the initial data of Sec. 6.2.
 * ``grf_periodic``   -- periodic lattice at rest (u0 = 0) with a Gaussian random
   initial velocity (correlation length ell cells, given std), b = 0.
@@ -110,6 +111,19 @@ def dirichlet_mms(nx: int, ny: int, cK2: float, cmu2: float, *, c: Optional[floa
         steps = int(round(t_final / dt))
     sol = _mms.paper_moving_solution(math.sqrt(cK2), math.sqrt(cmu2), amp, kx, ky, w)
     return _from_solution(f"dirichlet_mms_{nx}x{ny}", sol, nx, ny, dx, dt, True, steps)
+
+
+def plane_wave_periodic(n: int, cK2: float, cmu2: float, kind: str, *, cfl: float = 0.9,
+                        steps: Optional[int] = None, t_final: float = 1.0, amp: float = 1e-2,
+                        k: float = 2 * math.pi) -> Workload:
+    """Periodic unit square with a body-force-free standing P wave (kind "P": u_x) or S wave
+    (kind "S": u_y) along x, one wavelength per side for k = 2 pi; b = 0, so no forcing tables."""
+    dx = 1.0 / n
+    dt = dx / lattice_speed(cK2, cmu2, cfl)
+    if steps is None:
+        steps = int(round(t_final / dt))
+    sol = _mms.plane_wave(math.sqrt(cK2), math.sqrt(cmu2), kind, amp, k)
+    return _from_solution(f"plane_wave_{kind}_{n}", sol, n, n, dx, dt, False, steps, with_forcing=False)
 
 
 def energy_box(n: int, cK2: float, cmu2: float, dt: float, steps: int) -> Workload:
