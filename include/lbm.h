@@ -230,8 +230,28 @@ lbm_status lbm_check_finite(lbm_ctx* ctx);
 /* Current step counter m (t = m dt). */
 lbm_status lbm_time_step(const lbm_ctx* ctx, int64_t* m);
 
+/* Energy monitor (failure detection; Sec. 6.2 takes growth of ||f||_P, Definition
+ * grid_norm, as the sign of instability).  With every > 0, lbm_step evaluates the
+ * discrete energy ||f||_P^2 on the device after each `every` steps (counted from this
+ * call) and compares it with growth times its value at this call; a larger or
+ * non-finite energy sets a device flag that the next lbm_synchronize reports as
+ * LBM_ERR_UNSTABLE (and clears).  Nothing waits on the host: the check is two
+ * small kernels on the context's stream.  Without body load or wall data the energy
+ * is conserved up to the storage format's rounding (FP64: 4e-16 relative over 10^5
+ * steps on 512 x 256; the reduced formats round the state every pass), so a growth
+ * just above 1 plus that drift detects an instability; with data the energy may grow
+ * legitimately and growth is the caller's bound.  The steps run
+ * in chunks that end where a check is due, which changes how steps group into the
+ * multi-step kernels of lbm_set_step_fusion (FP32 and FP64 results are unchanged;
+ * 16-bit formats round once per pass, so choose every as a multiple of 3 there).
+ * every = 0 turns it off.  Errors: LBM_ERR_ARG for every < 0 or a growth that is not
+ * positive and finite; LBM_ERR_STATE before lbm_init. */
+lbm_status lbm_set_energy_check(lbm_ctx* ctx, int32_t every, double growth);
+
 /* Wait until all work enqueued by this context has finished; LBM_ERR_TIMEOUT if a
- * bounded device-side wait of the staged two-step kernel ran out since the last call. */
+ * bounded device-side wait of the staged two-step kernel ran out since the last call,
+ * else LBM_ERR_UNSTABLE if the energy monitor (lbm_set_energy_check) found the energy
+ * above its bound since the last call. */
 lbm_status lbm_synchronize(lbm_ctx* ctx);
 
 /* Release all device memory of the context; NULL is accepted. */

@@ -2,6 +2,7 @@
 // memory, data tables and kernel launches for one lattice.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -101,6 +102,8 @@ constexpr int kRedBlocks = 152 * 4;   // blocks of the FP64 reductions (one part
 constexpr int kMaxR = 16;
 constexpr int kTimeoutSlot = kRedBlocks * 30 + 56;   // scratch double index of the staged kernel's timeout flag
 constexpr int kSatSlot = kRedBlocks * 30 + 58;       // scratch double index of the block-floating-point saturation flag
+constexpr int kEnergyThrSlot = kRedBlocks * 30 + 60; // energy monitor: growth x the energy when it was armed
+constexpr int kUnstableSlot = kRedBlocks * 30 + 62;  // energy monitor: set when the energy exceeded it
 
 // cuTensorMapEncodeTiled, reached through the runtime's driver entry point (no link to libcuda)
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -202,6 +205,8 @@ struct lbm_ctx {
                                  // rows per block follow its split level)
     int split = 1;               // FP64: split level (which additions run on the integer pipes; 12:
                                  // the fixed-point node update, the default where it applies)
+    int echeck_every = 0;        // energy monitor (lbm_set_energy_check): steps between checks, 0 = off
+    int echeck_since = 0;        // steps since the last check
     int staging = 1;             // 1 = rows staged in shared memory (tensor copies for the fused kernels,
                                  // asynchronous copies for the FP64 step), 0 = register loads
     int l2_ahead = lbmk::TBT_L2_AHEAD;   // staged kernel: rows prefetched into L2 ahead of the ring
@@ -617,6 +622,17 @@ lbm_status lbm_synchronize(lbm_ctx* ctx)
         return fail(ctx, LBM_ERR_TIMEOUT, "a bounded wait of the staged two-step kernel ran out; the state is "
                                           "undefined until re-initialised");
     }
+    if (ctx->echeck_every > 0) {
+        int* uflag = reinterpret_cast<int*>(ctx->scratch + kUnstableSlot);
+        LBM_CUDA(ctx, cudaMemcpyAsync(&h, uflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+        LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+        if (h) {
+            LBM_CUDA(ctx, cudaMemsetAsync(uflag, 0, sizeof(int), ctx->s));
+            LBM_CUDA(ctx, cudaStreamSynchronize(ctx->s));
+            return fail(ctx, LBM_ERR_UNSTABLE, "the energy ||f||_P exceeded the growth bound of lbm_set_energy_check "
+                                               "(or is not finite)");
+        }
+    }
     return LBM_OK;
 }
 
@@ -788,17 +804,9 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const d
     return LBM_OK;
 }
 
-lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
+// n > 0 steps, arguments checked by lbm_step
+static lbm_status step_n(lbm_ctx* ctx, int64_t n)
 {
-    LBM_CHECK_CTX(ctx);
-    if (n < 0) return fail(ctx, LBM_ERR_ARG, "n < 0");
-    if (n == 0) return LBM_OK;
-    lbm_status st = check_ready(ctx);
-    if (st != LBM_OK) return st;
-    if (ctx->R > 0 && ctx->m + n >= ctx->fnt)
-        return fail(ctx, LBM_ERR_STATE, "body-load table has no row for the requested time");
-    if (ctx->g && ctx->m + n > ctx->gnt)
-        return fail(ctx, LBM_ERR_STATE, "Dirichlet table has no row for the requested step");
     const KindOps* ops = ctx->ops;
     const bool split = ctx->p.storage == LBM_F64 && ctx->split > 0 && ctx->R == 0 && ctx->omega == 2.0;
     const int vec = split ? ops->vec_split : ops->vec;
@@ -923,6 +931,72 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
         ctx->cur ^= 1;
         ctx->m = m + 1;
     }
+    return LBM_OK;
+}
+
+__global__ void energy_threshold_kernel(const double* e, double growth, double* thr) { *thr = growth * e[0]; }
+
+// sets the flag when the energy exceeds the threshold or is not finite
+__global__ void energy_guard_kernel(const double* e, const double* thr, int* flag)
+{
+    if (!(e[0] <= thr[0])) *flag = 1;
+}
+
+// ||f||_P of the current state into the scratch result slot, on the stream, no host wait
+static lbm_status energy_on_device(lbm_ctx* ctx)
+{
+    double* partial = ctx->scratch;
+    double* result = ctx->scratch + kRedBlocks * 30;
+    LBM_CUDA(ctx, ctx->ops->energy(node_args(ctx, ctx->m), partial, dim3(kRedBlocks), dim3(256), ctx->s));
+    LBM_CUDA(ctx, lbmh::finish_sum1(partial, kRedBlocks, result, ctx->s));
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* ctx, int64_t n)
+{
+    LBM_CHECK_CTX(ctx);
+    if (n < 0) return fail(ctx, LBM_ERR_ARG, "n < 0");
+    if (n == 0) return LBM_OK;
+    lbm_status st = check_ready(ctx);
+    if (st != LBM_OK) return st;
+    if (ctx->R > 0 && ctx->m + n >= ctx->fnt)
+        return fail(ctx, LBM_ERR_STATE, "body-load table has no row for the requested time");
+    if (ctx->g && ctx->m + n > ctx->gnt)
+        return fail(ctx, LBM_ERR_STATE, "Dirichlet table has no row for the requested step");
+    if (ctx->echeck_every <= 0) return step_n(ctx, n);
+    // energy monitor: the steps run in chunks that end where a check is due
+    while (n > 0) {
+        const int64_t m = std::min<int64_t>(n, ctx->echeck_every - ctx->echeck_since);
+        if ((st = step_n(ctx, m)) != LBM_OK) return st;
+        n -= m;
+        ctx->echeck_since += (int)m;
+        if (ctx->echeck_since == ctx->echeck_every) {
+            ctx->echeck_since = 0;
+            if ((st = energy_on_device(ctx)) != LBM_OK) return st;
+            energy_guard_kernel<<<1, 1, 0, ctx->s>>>(ctx->scratch + kRedBlocks * 30, ctx->scratch + kEnergyThrSlot,
+                                                     reinterpret_cast<int*>(ctx->scratch + kUnstableSlot));
+            LBM_CUDA(ctx, cudaGetLastError());
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_energy_check(lbm_ctx* ctx, int32_t every, double growth)
+{
+    LBM_CHECK_CTX(ctx);
+    if (every < 0) return fail(ctx, LBM_ERR_ARG, "every must be >= 0");
+    if (every > 0 && !(growth > 0.0 && std::isfinite(growth)))
+        return fail(ctx, LBM_ERR_ARG, "growth must be positive and finite");
+    ctx->echeck_every = 0;
+    ctx->echeck_since = 0;
+    if (every == 0) return LBM_OK;
+    lbm_status st = check_ready(ctx);
+    if (st != LBM_OK) return st;
+    if ((st = energy_on_device(ctx)) != LBM_OK) return st;
+    energy_threshold_kernel<<<1, 1, 0, ctx->s>>>(ctx->scratch + kRedBlocks * 30, growth, ctx->scratch + kEnergyThrSlot);
+    LBM_CUDA(ctx, cudaGetLastError());
+    LBM_CUDA(ctx, cudaMemsetAsync(ctx->scratch + kUnstableSlot, 0, sizeof(int), ctx->s));
+    ctx->echeck_every = every;
     return LBM_OK;
 }
 

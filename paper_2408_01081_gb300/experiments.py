@@ -107,9 +107,10 @@ def dirichlet_convergence(ny_list=(128, 256, 512, 1024, 2048, 4096), nus=(0.0, 0
 
 
 def long_run(steps=100_000, nx=512, ny=256, cK2=1.1, cmu2=0.4, cfl=None, dt=None, storage="f64", every=1000,
-             device="cuda"):
+             device="cuda", split=None):
     """Homogeneous Dirichlet, b = 0, u0 = sin(4 pi x) sin(2 pi y) [sin(-0.4 pi), sin(1.6 pi)] on
-    (0, nx dx) x (0, 1) with dx = 1/ny; max relative drift of ||f||_P over the run."""
+    (0, nx dx) x (0, 1) with dx = 1/ny; max relative drift of ||f||_P over the run (FP64 at the
+    library's default arithmetic, or at lbm_set_fp64_split level `split`)."""
     import torch
     from workloads import material, mms
     dx = 1.0 / ny
@@ -123,6 +124,8 @@ def long_run(steps=100_000, nx=512, ny=256, cK2=1.1, cmu2=0.4, cfl=None, dt=None
     lat = L.Lattice(nx, ny, dx, dt, math.sqrt(cK2), math.sqrt(cmu2), dirichlet=True, storage=storage,
                     track_displacement=False, stream=torch.cuda.current_stream().cuda_stream)
     try:
+        if split is not None:
+            lat.set_fp64_split(split)
         lat.init(U0, Ux, Uy)
         e0 = math.sqrt(lat.energy())
         drift, done = 0.0, 0

@@ -25,7 +25,7 @@ STATUS_NAMES = ["LBM_OK", "LBM_ERR_ARG", "LBM_ERR_CFL", "LBM_ERR_OOM", "LBM_ERR_
                 "LBM_ERR_TIMEOUT", "LBM_ERR_STATE"]
 
 # every symbol declared in include/lbm.h
-EXPORTS = ["lbm_create", "lbm_init", "lbm_set_relaxation", "lbm_set_step_fusion", "lbm_set_staging", "lbm_set_fp64_split", "lbm_set_forcing", "lbm_set_dirichlet", "lbm_set_dirichlet_separable", "lbm_step", "lbm_moments",
+EXPORTS = ["lbm_create", "lbm_init", "lbm_set_relaxation", "lbm_set_step_fusion", "lbm_set_staging", "lbm_set_fp64_split", "lbm_set_energy_check", "lbm_set_forcing", "lbm_set_dirichlet", "lbm_set_dirichlet_separable", "lbm_step", "lbm_moments",
            "lbm_energy", "lbm_error_sums", "lbm_get_populations", "lbm_set_populations", "lbm_check_finite",
            "lbm_time_step", "lbm_synchronize", "lbm_destroy", "lbm_last_error", "lbm_state_bytes",
            "lbm_save_state", "lbm_load_state", "lbm_energy_noalloc", "lbm_create_slab", "lbm_halo_bytes",
@@ -80,6 +80,7 @@ def load(path: Optional[str] = None):
         "lbm_set_step_fusion": ([vp, i32, i32], i32),
         "lbm_set_staging": ([vp, i32], i32),
         "lbm_set_fp64_split": ([vp, i32], i32),
+        "lbm_set_energy_check": ([vp, i32, ctypes.c_double], i32),
         "lbm_set_dirichlet": ([vp, dp, i64, i32], i32),
         "lbm_set_dirichlet_separable": ([vp, i32, dp, dp, dp, dp, dp, i64, i32], i32),
         "lbm_step": ([vp, i64], i32),
@@ -217,6 +218,10 @@ def lbm_set_staging(ctx, mode=1):
 
 def lbm_set_fp64_split(ctx, level):
     _check(ctx, load().lbm_set_fp64_split(ctx, int(level)))
+
+
+def lbm_set_energy_check(ctx, every, growth=1.0 + 1e-9):
+    _check(ctx, load().lbm_set_energy_check(ctx, int(every), float(growth)))
 
 
 def lbm_set_relaxation(ctx, omega):
@@ -477,6 +482,9 @@ class Lattice:
 
     def set_fp64_split(self, level):
         lbm_set_fp64_split(self.ctx, level)
+
+    def set_energy_check(self, every, growth=1.0 + 1e-9):
+        lbm_set_energy_check(self.ctx, every, growth)
 
     def set_relaxation(self, omega):
         lbm_set_relaxation(self.ctx, omega)

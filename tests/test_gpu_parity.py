@@ -735,3 +735,55 @@ def test_pinned_host_buffers_are_used_in_place(lbm):
         lat.close()
     np.testing.assert_array_equal(outs[0], outs[1])
     np.testing.assert_array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_energy_monitor_is_quiet_and_changes_nothing_on_a_conserving_run(lbm, storage):
+    """Homogeneous Dirichlet, b = 0: ||f||_P is conserved up to the storage format's rounding,
+    so a monitor with growth 1 + 1e-9 (FP64) or 1 + 1e-5 (FP32), checked every 50 steps with the
+    last check mid-run, reports nothing, and the state equals that of the same run without it
+    bit for bit."""
+    wl = W.energy_box(96, 1.1, 0.4, 1.0 / 240.0, 0)
+    outs = []
+    for every in (0, 50):
+        lat = lbm.Lattice(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet=True, storage=storage,
+                          track_displacement=False)
+        lat.init(wl.U0, wl.dU0dx, wl.dU0dy)
+        lat.set_energy_check(every, 1.0 + (1e-9 if storage == "f64" else 1e-5))
+        lat.step(130)
+        lat.step(290)
+        lat.synchronize()
+        outs.append(lat.moments())
+        lat.close()
+    np.testing.assert_array_equal(outs[0].view(np.int64), outs[1].view(np.int64))
+
+
+def test_energy_monitor_reports_growth_beyond_its_bound(lbm):
+    """A bound below the (conserved) energy: the first check sets the flag, the next
+    lbm_synchronize reports LBM_ERR_UNSTABLE once and clears it; the context stays usable
+    and turning the monitor off stops the reports.  Bad arguments and an uninitialised
+    context are refused."""
+    wl = W.energy_box(64, 1.1, 0.4, 1.0 / 170.0, 0)
+    lat = lbm.Lattice(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet=True, storage="f64",
+                      track_displacement=False)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.set_energy_check(10, 2.0)                  # before lbm_init
+    assert e.value.status == lbm.LBM_ERR_STATE
+    lat.init(wl.U0, wl.dU0dx, wl.dU0dy)
+    for every, growth in ((-1, 2.0), (10, 0.0), (10, float("nan")), (10, float("inf"))):
+        with pytest.raises(lbm.LbmError) as e:
+            lat.set_energy_check(every, growth)
+        assert e.value.status == lbm.LBM_ERR_ARG
+    lat.set_energy_check(10, 0.5)
+    lat.step(9)
+    lat.synchronize()                                  # no check has run yet
+    lat.step(2)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.synchronize()
+    assert e.value.status == lbm.LBM_ERR_UNSTABLE
+    lat.synchronize()                                  # reported once
+    lat.set_energy_check(0, 0.5)
+    lat.step(30)
+    lat.synchronize()
+    assert np.all(np.isfinite(lat.moments()))
+    lat.close()
