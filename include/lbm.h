@@ -42,16 +42,20 @@ typedef enum {
     LBM_OK = 0,
     LBM_ERR_ARG = 1,       /* invalid argument: NULL pointer, size, enum, table too short  */
     LBM_ERR_CFL = 2,       /* 2 sqrt(cK^2 + cmu^2) >= c: some g_ij is not SPD (Eq. stab_cond) */
-    LBM_ERR_OOM = 3,       /* device allocation failed                                      */
+    LBM_ERR_OOM = 3,       /* a device allocation was refused (not sticky: the context and
+                              the device stay usable)                                       */
     LBM_ERR_CUDA = 4,      /* a CUDA runtime call or launch failed (sticky)                 */
-    LBM_ERR_UNSTABLE = 5,  /* a non-finite value was found by lbm_check_finite              */
+    LBM_ERR_UNSTABLE = 5,  /* lbm_check_finite found a non-finite value, or the energy
+                              monitor of lbm_set_energy_check found growth beyond its bound */
     LBM_ERR_TIMEOUT = 6,   /* a bounded device-side wait ran out                            */
     LBM_ERR_STATE = 7      /* call order: stepping before lbm_init, data for step m missing */
 } lbm_status;
 
 typedef enum { LBM_PERIODIC = 0, LBM_DIRICHLET = 1 } lbm_bc;
 
-/* Storage of the state.  LBM_F64 stores and computes in FP64; LBM_F32 / BF16 /
+/* Storage of the state.  LBM_F64 stores in FP64 and computes to FP64 accuracy (by
+ * default the node update in exact fixed point with one binary64 rounding per output,
+ * lbm_set_fp64_split); LBM_F32 / BF16 /
  * F16 store the populations in that format and compute in FP32.  LBM_MS_BF16 /
  * LBM_MS_F16 store per node the zeroth moment U (FP32) and the 15 deviations of
  * the other moments from their local-equilibrium values (Eq. cond_eq) in BF16 /

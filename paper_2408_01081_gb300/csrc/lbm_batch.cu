@@ -413,6 +413,9 @@ lbm_status lbm_batch_create(int32_t count, const lbm_lattice_desc* lats, int32_t
     if (e != cudaSuccess) {
         g_batch_create_error = std::string("device allocation or query failed: ") + cudaGetErrorString(e);
         lbm_batch_destroy(b);
+        // a refused allocation is not sticky; clear the runtime's last error so that later launch
+        // checks do not report it as theirs
+        if (e == cudaErrorMemoryAllocation) cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
     }
     b->persistent_grid = std::max(1, occ) * sms;

@@ -234,6 +234,12 @@ lbm_status fail(lbm_ctx* ctx, lbm_status st, const std::string& msg)
 
 lbm_status cuda_fail(lbm_ctx* ctx, cudaError_t e, const char* what)
 {
+    if (e == cudaErrorMemoryAllocation) {
+        // a refused allocation leaves the context usable (not sticky); the runtime keeps it as
+        // its last error, which the launch checks of later calls would otherwise report as theirs
+        cudaGetLastError();
+        return fail(ctx, LBM_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+    }
     return fail(ctx, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
@@ -496,6 +502,9 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out)
     if (e != cudaSuccess) {
         g_create_error = std::string("device allocation failed: ") + cudaGetErrorString(e);
         lbm_destroy(ctx);
+        // a refused allocation is not sticky, but the runtime keeps it as its last error, which
+        // the launch checks of later calls (cudaGetLastError) would otherwise report as theirs
+        if (e == cudaErrorMemoryAllocation) cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
     }
     *out = ctx;

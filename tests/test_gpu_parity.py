@@ -787,3 +787,23 @@ def test_energy_monitor_reports_growth_beyond_its_bound(lbm):
     lat.synchronize()
     assert np.all(np.isfinite(lat.moments()))
     lat.close()
+
+
+def test_refused_allocation_reports_oom_and_leaves_the_device_usable(lbm):
+    """A lattice far beyond the GPU's memory (60000^2 FP64: two 576 GB state buffers, refused by
+    the first allocation, before any launch): lbm_create returns LBM_ERR_OOM, and a lattice
+    created next runs normally (the refused allocation does not leak into the launch checks
+    of later calls)."""
+    n = 60000
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Lattice(n, n, 1.0 / n, 1.0 / n / 3.2, 1.0, 0.6, storage="f64", track_displacement=False)
+    assert e.value.status == lbm.LBM_ERR_OOM
+    wl = W.energy_box(64, 1.1, 0.4, 1.0 / 170.0, 0)
+    lat = lbm.Lattice(wl.nx, wl.ny, wl.dx, wl.dt, wl.cK, wl.cmu, dirichlet=True, storage="f64",
+                      track_displacement=False)
+    lat.init(wl.U0, wl.dU0dx, wl.dU0dy)
+    e0 = lat.energy()
+    lat.step(50)
+    lat.synchronize()
+    assert abs(lat.energy() - e0) <= 1e-13 * e0
+    lat.close()
