@@ -108,6 +108,13 @@ struct lbm_batch {
     unsigned long long timeout_ns = 2000000000ull;
     unsigned int extra_arrivals = 0;
     bool own_stream = false;              // created here because the caller gave the legacy stream
+    // mode 2: three steps per pass with staged rows (FP32 / BF16 / FP16)
+    bool t3_ok = false;                   // row maps encoded and tile lists built
+    int t3_rows = 0;                      // output rows per tile
+    lbmk::BatchLatT3* d_lat3 = nullptr;
+    CUtensorMap* d_maps = nullptr;        // [lattice][arena]
+    int4* d_t3 = nullptr;                 // periodic tiles, then Dirichlet tiles
+    int nt3[2] = {0, 0};                  // tile counts: periodic, Dirichlet
     cudaGraphExec_t graph = nullptr;
     bool graph_valid = false;
     bool initialised = false;
@@ -172,6 +179,52 @@ lbm_status build_tiles(lbm_batch* b)
     return LBM_OK;
 }
 
+// Row maps (box width Tbt3Geom::WIN, both arenas) and tile lists of mode 2, for the
+// population formats FP32 / BF16 / FP16 and lattices of at least 2 x 2 nodes; leaves
+// t3_ok false (mode 2 unavailable) where a map cannot be encoded
+lbm_status setup_t3(lbm_batch* b)
+{
+    if (b->storage != LBM_F32 && b->storage != LBM_BF16 && b->storage != LBM_F16) return LBM_OK;
+    const int es = b->ops->elem_bytes;
+    const int win = es == 4 ? lbmk::Tbt3Geom<4>::WIN : lbmk::Tbt3Geom<2>::WIN;
+    b->t3_rows = es == 4 ? 12 : 64;          // the single-lattice defaults (lbm_set_step_fusion)
+    std::vector<CUtensorMap> maps((size_t)2 * b->count);
+    std::vector<lbmk::BatchLatT3> l3((size_t)b->count);
+    std::vector<int4> tiles[2];
+    for (int i = 0; i < b->count; ++i) {
+        const lbmk::LatDesc& L = b->lat[i];
+        for (int a = 0; a < 2; ++a) {
+            void* base = static_cast<char*>(b->arena[a]) + (size_t)L.off * es;
+            if (!lbmh::encode_rows_map(&maps[(size_t)2 * i + a], base, es, L.nx, L.ny, L.pitch, L.plane, 20, win))
+                return LBM_OK;
+        }
+        lbmk::BatchLatT3& q = l3[i];
+        q.off = L.off;
+        q.plane = L.plane;
+        q.nx = L.nx;
+        q.ny = L.ny;
+        q.pitch = L.pitch;
+        q.af = (float)L.a;
+        q.bf = (float)L.b;
+        q.pad_ = 0;
+        for (int y = 0; y < L.ny; y += b->t3_rows)
+            for (int x = 0; x < L.nx; x += lbmk::TBT3_OUT) tiles[L.bc ? 1 : 0].push_back(make_int4(i, x, y, 0));
+    }
+    b->nt3[0] = (int)tiles[0].size();
+    b->nt3[1] = (int)tiles[1].size();
+    std::vector<int4> all(tiles[0]);
+    all.insert(all.end(), tiles[1].begin(), tiles[1].end());
+    B_CUDA(b, cudaMalloc((void**)&b->d_lat3, l3.size() * sizeof(lbmk::BatchLatT3)));
+    B_CUDA(b, cudaMalloc((void**)&b->d_maps, maps.size() * sizeof(CUtensorMap)));
+    B_CUDA(b, cudaMalloc((void**)&b->d_t3, std::max<size_t>(1, all.size()) * sizeof(int4)));
+    B_CUDA(b, cudaMemcpy(b->d_lat3, l3.data(), l3.size() * sizeof(lbmk::BatchLatT3), cudaMemcpyHostToDevice));
+    B_CUDA(b, cudaMemcpy(b->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    if (!all.empty())
+        B_CUDA(b, cudaMemcpy(b->d_t3, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    b->t3_ok = true;
+    return LBM_OK;
+}
+
 lbmk::BatchArgs batch_args(const lbm_batch* b, int steps, int parity)
 {
     lbmk::BatchArgs A;
@@ -190,15 +243,43 @@ lbmk::BatchArgs batch_args(const lbm_batch* b, int steps, int parity)
     return A;
 }
 
+// arena swaps of `steps` steps: one per launch (a three-step pass of mode 2 is one launch pair)
+int swaps_of(const lbm_batch* b, long long steps)
+{
+    return (int)((b->mode == 2 ? steps / 3 + steps % 3 : steps) & 1);
+}
+
 // enqueue `steps` steps starting from arena `parity` (no graph)
 cudaError_t enqueue_steps(lbm_batch* b, int steps, int parity)
 {
     if (b->mode == 1) {
         return b->ops->batch_step(batch_args(b, steps, parity), true, b->persistent_grid, b->s);
     }
-    for (int i = 0; i < steps; ++i) {
-        cudaError_t e = b->ops->batch_step(batch_args(b, 1, (parity + i) & 1), false, b->ntiles, b->s);
+    int i = 0;
+    if (b->mode == 2) {
+        // three steps per pass: the periodic tiles and the Dirichlet tiles, one launch each
+        lbmk::BatchTbtArgs T;
+        T.lat = b->d_lat3;
+        T.maps = b->d_maps;
+        T.arenaA = b->arena[0];
+        T.arenaB = b->arena[1];
+        T.rows = b->t3_rows;
+        T.timeout = reinterpret_cast<int*>(b->d_bar + 2);
+        for (; i + 3 <= steps; i += 3) {
+            T.parity = parity;
+            T.tiles = b->d_t3;
+            cudaError_t e = b->ops->batch_tbt3_step(T, false, b->nt3[0], b->s);
+            if (e != cudaSuccess) return e;
+            T.tiles = b->d_t3 + b->nt3[0];
+            e = b->ops->batch_tbt3_step(T, true, b->nt3[1], b->s);
+            if (e != cudaSuccess) return e;
+            parity ^= 1;
+        }
+    }
+    for (; i < steps; ++i) {
+        cudaError_t e = b->ops->batch_step(batch_args(b, 1, parity), false, b->ntiles, b->s);
         if (e != cudaSuccess) return e;
+        parity ^= 1;
     }
     return cudaSuccess;
 }
@@ -235,13 +316,13 @@ lbm_status run_steps(lbm_batch* b, long long n)
             lbm_status st = ensure_graph(b);
             if (st != LBM_OK) return st;
             B_CUDA(b, cudaGraphLaunch(b->graph, b->s));
-            n -= b->graph_steps;           // graph_steps is even: the state returns to arena 0
+            n -= b->graph_steps;           // an even number of swaps: the state returns to arena 0
             continue;
         }
         const int k = (int)std::min<long long>(n, b->cur == 0 ? (n % b->graph_steps) : 1);
         const int kk = std::max(1, k);
         B_CUDA(b, enqueue_steps(b, kk, b->cur));
-        b->cur = (b->cur + kk) & 1;
+        b->cur = (b->cur + swaps_of(b, kk)) & 1;
         n -= kk;
     }
     return LBM_OK;
@@ -419,7 +500,7 @@ lbm_status lbm_batch_create(int32_t count, const lbm_lattice_desc* lats, int32_t
         return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
     }
     b->persistent_grid = std::max(1, occ) * sms;
-    if (build_tiles(b) != LBM_OK) {
+    if (build_tiles(b) != LBM_OK || setup_t3(b) != LBM_OK) {
         g_batch_create_error = b->err;
         lbm_batch_destroy(b);
         return LBM_ERR_CUDA;
@@ -439,6 +520,9 @@ lbm_status lbm_batch_destroy(lbm_batch* b)
     cudaFree(b->d_tile);
     cudaFree(b->d_bar);
     cudaFree(b->scratch);
+    cudaFree(b->d_lat3);
+    cudaFree(b->d_maps);
+    cudaFree(b->d_t3);
     if (b->own_stream) cudaStreamDestroy(b->s);
     delete b;
     return LBM_OK;
@@ -453,8 +537,12 @@ lbm_status lbm_batch_set_mode(lbm_batch* b, int32_t mode, int32_t graph_steps)
 {
     if (!b) return LBM_ERR_ARG;
     if (b->sticky) return LBM_ERR_CUDA;
-    if ((mode != 0 && mode != 1) || graph_steps < 2 || graph_steps > 10000 || (graph_steps & 1))
-        return bfail(b, LBM_ERR_ARG, "mode must be 0 or 1 and graph_steps even in [2, 10000]");
+    // a graph must return the state to arena 0, an even number of arena swaps: graph_steps even
+    // (in mode 2, 3q + r steps swap q + r times, even exactly when 3q + r is)
+    if (mode < 0 || mode > 2 || graph_steps < 2 || graph_steps > 10000 || (graph_steps & 1))
+        return bfail(b, LBM_ERR_ARG, "mode must be 0, 1 or 2 and graph_steps even in [2, 10000]");
+    if (mode == 2 && !b->t3_ok)
+        return bfail(b, LBM_ERR_ARG, "mode 2 needs FP32, BF16 or FP16 storage");
     b->mode = mode;
     b->graph_steps = graph_steps;
     drop_graph(b);
@@ -612,6 +700,7 @@ lbm_status lbm_batch_tune(lbm_batch* b, const char* cache_path)
     }
     if (all_cached) {
         b->mode = cache[key + "mode"];
+        if (b->mode < 0 || b->mode > 2 || (b->mode == 2 && !b->t3_ok)) b->mode = 0;
         return build_tiles(b);
     }
     const int V = b->ops->batch_vec;
@@ -619,8 +708,8 @@ lbm_status lbm_batch_tune(lbm_batch* b, const char* cache_path)
     const int saved_graph = b->graph_steps;
     b->graph_steps = 2;
     const std::map<int, int> start = b->tpr_of_class;
-    std::map<int, int> tpr_mode[2];
-    float mode_ms[2] = {1e30f, 1e30f};
+    std::map<int, int> tpr_mode[3];
+    float mode_ms[3] = {1e30f, 1e30f, 1e30f};
     for (int mode = 0; mode < 2; ++mode) {
         b->mode = mode;
         b->tpr_of_class = start;
@@ -669,7 +758,26 @@ lbm_status lbm_batch_tune(lbm_batch* b, const char* cache_path)
         b->graph_steps = 2;
         tpr_mode[mode] = b->tpr_of_class;
     }
-    const int best_mode = (mode_ms[1] < mode_ms[0]) ? 1 : 0;
+    if (b->t3_ok) {
+        // mode 2: three steps per pass over fixed tiles; its remainder steps use mode 0's widths
+        b->mode = 2;
+        b->tpr_of_class = tpr_mode[0];
+        b->graph_steps = saved_graph;
+        for (int rep = 0; rep < 2; ++rep) {
+            float ms = 0.f;
+            lbm_status st = time_config(b, 2 * saved_graph, &ms);
+            if (st != LBM_OK) {
+                b->graph_steps = saved_graph;
+                return st;
+            }
+            mode_ms[2] = std::min(mode_ms[2], ms);
+        }
+        b->graph_steps = 2;
+        tpr_mode[2] = tpr_mode[0];
+    }
+    int best_mode = 0;
+    for (int m = 1; m < 3; ++m)
+        if (mode_ms[m] < mode_ms[best_mode]) best_mode = m;
     b->tpr_of_class = tpr_mode[best_mode];
     b->graph_steps = saved_graph;
     b->mode = best_mode;

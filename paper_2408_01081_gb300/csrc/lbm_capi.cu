@@ -15,6 +15,7 @@
 #include "lbm_dispatch.h"
 
 using lbmh::KindOps;
+using lbmh::encode_rows_map;
 
 namespace {
 
@@ -125,6 +126,10 @@ EncodeTiledFn encode_tiled()
     return fn;
 }
 
+}  // namespace
+
+namespace lbmh {
+
 // 3D map of a lattice buffer: x = column (extent nx), y = row (extent ny), z = plane
 // (extent nplanes); box {box_w, 1, nplanes}, out-of-range elements read as zero
 bool encode_rows_map(CUtensorMap* m, void* base, int esize, int nx, int ny, int pitch, long long plane,
@@ -140,6 +145,10 @@ bool encode_rows_map(CUtensorMap* m, void* base, int esize, int nx, int ny, int 
     return fn(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+}  // namespace lbmh
+
+namespace {
 
 // 5x5 inverse by Gauss-Jordan elimination with partial pivoting (FP64)
 bool invert5(const double (&a_in)[25], double (&inv)[25])

@@ -80,6 +80,9 @@ struct KindOps {
     // one FP64 step at split level 1 with the rows staged by asynchronous copies, `rows` rows
     // per block (other formats and variants return cudaErrorNotSupported)
     cudaError_t (*step_staged)(const lbmk::StepArgs&, int variant, int rows, cudaStream_t s);
+    // three fused steps over the tiles of a batch (FP32 / BF16 / FP16; others return
+    // cudaErrorNotSupported): `ntiles` blocks, all of periodic or all of Dirichlet lattices
+    cudaError_t (*batch_tbt3_step)(const lbmk::BatchTbtArgs&, bool dirichlet, int ntiles, cudaStream_t s);
     int vec_split;                 // nodes per thread of the FP64 split-level step kernels
     int batch_vec;                 // nodes per thread of the batch kernel
 };
@@ -91,6 +94,11 @@ extern const KindOps kind_ops_3;  // FP16
 extern const KindOps kind_ops_4;  // moment space, BF16 deviations
 extern const KindOps kind_ops_5;  // moment space, FP16 deviations
 extern const KindOps kind_ops_6;  // moment space, block-floating-point deviations
+
+// 3D row map of a lattice buffer (x = column, y = row, z = plane; box {box_w, 1, nplanes},
+// out-of-range elements read as zero), defined in lbm_capi.cu
+bool encode_rows_map(CUtensorMap* m, void* base, int esize, int nx, int ny, int pitch, long long plane,
+                     int nplanes, int box_w);
 
 // reduction tails (format independent), defined in lbm_capi.cu
 cudaError_t finish_sum1(const double* partial, int nblk, double* out, cudaStream_t s);

@@ -288,6 +288,28 @@ cudaError_t tbt3_step(const CUtensorMap* maps, const lbmk::TbtArgs& a, bool diri
     return tbt3_t<K>(maps, a, dirichlet, g, s);
 }
 
+template <int KK>
+cudaError_t batch_tbt3_t(const lbmk::BatchTbtArgs& a, bool dirichlet, int ntiles, cudaStream_t s)
+{
+    if constexpr (KK == lbmk::K_F32 || KK == lbmk::K_BF16 || KK == lbmk::K_F16) {
+        using G = lbmk::Tbt3Geom<(int)sizeof(typename lbmk::Fmt<KK>::E)>;
+        if (ntiles <= 0) return cudaSuccess;
+        void (*kern)(lbmk::BatchTbtArgs) =
+            dirichlet ? lbmk::batch_tbt3_kernel<KK, true> : lbmk::batch_tbt3_kernel<KK, false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        kern<<<ntiles, lbmk::TBT_THREADS, G::SMEM, s>>>(a);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
+cudaError_t batch_tbt3_step(const lbmk::BatchTbtArgs& a, bool dirichlet, int ntiles, cudaStream_t s)
+{
+    return batch_tbt3_t<K>(a, dirichlet, ntiles, s);
+}
+
 cudaError_t batch_occupancy(int* n)
 {
     return batch_occupancy_t<K>(n);
@@ -303,7 +325,7 @@ namespace lbmh {
 const KindOps LBM_OPS_NAME(LBM_KIND) = {
     K, V, ELEM, NODE_BYTES,
     step, init, moments, get_pop, set_pop, energy, error, finite, batch_step, batch_occupancy, tb2_step, tbt_step,
-    tbt3_step, step_staged,
+    tbt3_step, step_staged, batch_tbt3_step,
     LBM_VEC_SPLIT, VB,
 };
 

@@ -29,6 +29,14 @@
 
 namespace lbmk {
 
+// r modulo ny in [0, ny) for any r (the staged rows of the three-step kernels reach three rows
+// beyond the lattice, more than one period when ny = 2)
+__device__ __forceinline__ int wrap_row(int r, int ny)
+{
+    const int q = r % ny;
+    return q < 0 ? q + ny : q;
+}
+
 struct TbtArgs {
     const void* src;       // f*(t) planes (wrapped edge columns are read here)
     void* dst;             // f*(t+2dt) planes
@@ -695,7 +703,7 @@ __global__ void __launch_bounds__(TBT_THREADS, LBM_TBT3MS_MIN_BLOCKS) tbt3_ms_ke
                     lbmt::mbar_arrive(fb);
                     continue;
                 }
-                if (!DIRICHLET) y = (y < 0) ? y + ny : (y >= ny ? y - ny : y);
+                if (!DIRICHLET) y = wrap_row(y, ny);   // rows y0 - 3 .. y1 + 2: more than one wrap when ny = 2
                 const uint32_t st = sbase + s * G::STAGE_BYTES;
                 lbmt::mbar_arrive_expect_tx(fb, G::ROW_BYTES);
                 lbmt::tma_load_3d(st, &map32, X0 - HL, y, 0, fb);
@@ -731,7 +739,7 @@ __global__ void __launch_bounds__(TBT_THREADS, LBM_TBT3MS_MIN_BLOCKS) tbt3_ms_ke
 #pragma unroll
         for (int d = 0; d < 4; ++d) p1[d][k] = p2[d][k] = ft[d][k] = 0.f;
     }
-    auto row_of = [&](int r) { return (r < 0) ? r + ny : (r >= ny ? r - ny : r); };
+    auto row_of = [&](int r) { return wrap_row(r, ny); };   // r in y0 - 3 .. y1 + 2
     bool ok = lbmt::mbar_wait(lbmt::smem_u32(&full_bar[0]), 0, &abort_flag) &&
               lbmt::mbar_wait(lbmt::smem_u32(&full_bar[1 % NST]), (1 / NST) & 1, &abort_flag);
     if (__all_sync(0xffffffffu, ok)) {
@@ -909,8 +917,11 @@ struct Tbt3Geom {
 #define LBM_TBT3_MIN_BLOCKS 3       // 116-127 registers
 #endif
 
+// One block's work: output columns X0 .. X0 + TBT3_OUT - 1 and rows y0 .. y0 + A.rows - 1 of
+// the lattice A describes, its rows staged through `map` (a generic address: a kernel
+// parameter or a map in global memory).
 template <int K, bool DIRICHLET>
-__global__ void __launch_bounds__(TBT_THREADS, LBM_TBT3_MIN_BLOCKS) tbt3_kernel(const __grid_constant__ CUtensorMap map, TbtArgs A)
+__device__ __forceinline__ void tbt3_body(const CUtensorMap* mapp, const TbtArgs& A, int X0, int y0)
 {
     using E = typename Fmt<K>::E;
     using G = Tbt3Geom<(int)sizeof(E)>;
@@ -921,8 +932,6 @@ __global__ void __launch_bounds__(TBT_THREADS, LBM_TBT3_MIN_BLOCKS) tbt3_kernel(
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nx = A.nx, ny = A.ny;
-    const int X0 = blockIdx.x * TBT3_OUT;
-    const int y0 = blockIdx.y * A.rows;
     const int y1 = min(ny, y0 + A.rows);
     const int nin = (y1 - y0) + 6;                   // staged input rows y0-3 .. y1+2
     const uint32_t raw = lbmt::smem_u32(tbt_smem_raw);
@@ -940,7 +949,7 @@ __global__ void __launch_bounds__(TBT_THREADS, LBM_TBT3_MIN_BLOCKS) tbt3_kernel(
 
     if (warp == TBT_WARPS) {
         if (lane == 0) {
-            lbmt::prefetch_map(&map);
+            lbmt::prefetch_map(mapp);
             int j = 0;
             for (; j < nin; ++j) {
                 const int s = j % NST;
@@ -953,9 +962,9 @@ __global__ void __launch_bounds__(TBT_THREADS, LBM_TBT3_MIN_BLOCKS) tbt3_kernel(
                     lbmt::mbar_arrive(fb);
                     continue;
                 }
-                if (!DIRICHLET) y = (y < 0) ? y + ny : (y >= ny ? y - ny : y);
+                if (!DIRICHLET) y = wrap_row(y, ny);   // rows y0 - 3 .. y1 + 2: more than one wrap when ny = 2
                 lbmt::mbar_arrive_expect_tx(fb, G::ROW_BYTES);
-                lbmt::tma_load_3d(sbase + s * G::STAGE_BYTES, &map, X0 - HL, y, 0, fb);
+                lbmt::tma_load_3d(sbase + s * G::STAGE_BYTES, mapp, X0 - HL, y, 0, fb);
             }
             for (int q = (j > NST ? j - NST : 0); q < j; ++q)
                 if (q != A.withhold) lbmt::mbar_drain(lbmt::smem_u32(&full_bar[q % NST]), (q / NST) & 1);
@@ -1081,6 +1090,64 @@ __global__ void __launch_bounds__(TBT_THREADS, LBM_TBT3_MIN_BLOCKS) tbt3_kernel(
         }
     }
     if (lane == 0 && abort_flag) atomicExch(A.timeout, 1);
+}
+
+template <int K, bool DIRICHLET>
+__global__ void __launch_bounds__(TBT_THREADS, LBM_TBT3_MIN_BLOCKS) tbt3_kernel(const __grid_constant__ CUtensorMap map, TbtArgs A)
+{
+    tbt3_body<K, DIRICHLET>(&map, A, blockIdx.x * TBT3_OUT, blockIdx.y * A.rows);
+}
+
+// ---------------------------------------------------------------------------
+// Batches of lattices, three steps per pass (lbm_batch.cu, mode 2): one block per tile
+// {lattice, X0, y0} of a flat list, each running tbt3_body on its lattice with that
+// lattice's row map of the source arena.  The maps live in global memory, written by the
+// host before the launch; a lattice's planes sit at its element offset in each arena.
+// ---------------------------------------------------------------------------
+struct BatchLatT3 {
+    long long off;         // element offset of plane 0 in each arena
+    long long plane;       // elements per plane = ny * pitch
+    int nx, ny, pitch;
+    float af, bf;          // cK / c, cmu / c in FP32
+    int pad_;
+};
+
+struct BatchTbtArgs {
+    const int4* tiles;          // {lattice, X0, y0, 0} per block
+    const BatchLatT3* lat;
+    const CUtensorMap* maps;    // [lattice][arena]: row maps (box width Tbt3Geom::WIN)
+    void* arenaA;
+    void* arenaB;
+    int parity;                 // 0: read arena A, write arena B
+    int rows;                   // output rows per tile
+    int* timeout;               // set when a bounded wait ran out
+};
+
+template <int K, bool DIRICHLET>
+__global__ void __launch_bounds__(TBT_THREADS, LBM_TBT3_MIN_BLOCKS) batch_tbt3_kernel(BatchTbtArgs B)
+{
+    using E = typename Fmt<K>::E;
+    const int4 t = B.tiles[blockIdx.x];
+    const BatchLatT3 L = B.lat[t.x];
+    E* a = static_cast<E*>(B.arenaA) + L.off;
+    E* b = static_cast<E*>(B.arenaB) + L.off;
+    TbtArgs A;
+    A.src = B.parity ? b : a;
+    A.dst = B.parity ? a : b;
+    A.nx = L.nx;
+    A.ny = L.ny;
+    A.pitch = L.pitch;
+    A.plane = L.plane;
+    A.af = L.af;
+    A.bf = L.bf;
+    A.rows = B.rows;
+    A.timeout = B.timeout;
+    A.withhold = -1;
+    A.scale = 1.f;
+    A.inv_s = 1.f;
+    A.sat = nullptr;
+    A.l2_ahead = 0;
+    tbt3_body<K, DIRICHLET>(B.maps + 2 * t.x + B.parity, A, t.y, t.z);
 }
 
 }  // namespace lbmk

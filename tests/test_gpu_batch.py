@@ -150,3 +150,42 @@ def test_torch_grf_inputs_match_numpy_recipe(lbm):
         np.testing.assert_allclose(U0, ref.U0, atol=1e-15)
         np.testing.assert_allclose(Ux, ref.dU0dx, atol=1e-12 * np.max(np.abs(ref.dU0dx)))
         np.testing.assert_allclose(Uy, ref.dU0dy, atol=1e-12 * np.max(np.abs(ref.dU0dy)))
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_three_step_mode_equals_the_other_modes_and_single_lattices(lbm, storage):
+    """Mode 2 (three steps per pass over staged-row tiles of every lattice; steps beyond a
+    multiple of three as single steps): in FP32 it equals mode 0 bit for bit at a step count
+    that leaves remainders, inside and outside graphs; in BF16, after a multiple of three
+    steps, it equals single-lattice runs (which also advance three steps per pass)."""
+    descs = _descs(4)
+    if storage == "f32":
+        a, ea = _run_batch(lbm, descs, "f32", 0, 37, graph_steps=8)
+        b, eb = _run_batch(lbm, descs, "f32", 2, 37, graph_steps=8)
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
+        assert ea == eb
+        return
+    outs, _ = _run_batch(lbm, descs, "bf16", 2, 24, graph_steps=6)
+    for i, d in enumerate(descs):
+        nx, ny, bc, dx, dt, cK, cmu = d
+        lat = lbm.Lattice(nx, ny, dx, dt, cK, cmu, dirichlet=bool(bc), storage="bf16", track_displacement=False)
+        lat.init(*_inputs(d, 100 + i))
+        lat.step(24)
+        np.testing.assert_array_equal(outs[i][0:5], lat.moments()[0:5])
+        lat.close()
+
+
+def test_three_step_mode_is_refused_for_fp64_and_odd_graphs(lbm):
+    descs = _descs(5)
+    b = lbm.lbm_batch_create(descs, storage=lbm.LBM_F64)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_set_mode(b, 2, 10)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    lbm.lbm_batch_destroy(b)
+    b = lbm.lbm_batch_create(descs, storage=lbm.LBM_F32)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_set_mode(b, 2, 7)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    lbm.lbm_batch_set_mode(b, 2, 10)
+    lbm.lbm_batch_destroy(b)
