@@ -179,6 +179,13 @@ lbm_status build_tiles(lbm_batch* b)
     return LBM_OK;
 }
 
+#ifndef LBM_BATCH_T3_ROWS4
+#define LBM_BATCH_T3_ROWS4 12     // output rows per mode-2 tile, FP32 (the single-lattice default)
+#endif
+#ifndef LBM_BATCH_T3_ROWS2
+#define LBM_BATCH_T3_ROWS2 64     // the same for BF16 / FP16
+#endif
+
 // Row maps (box width Tbt3Geom::WIN, both arenas) and tile lists of mode 2, for the
 // population formats FP32 / BF16 / FP16 and lattices of at least 2 x 2 nodes; leaves
 // t3_ok false (mode 2 unavailable) where a map cannot be encoded
@@ -187,7 +194,7 @@ lbm_status setup_t3(lbm_batch* b)
     if (b->storage != LBM_F32 && b->storage != LBM_BF16 && b->storage != LBM_F16) return LBM_OK;
     const int es = b->ops->elem_bytes;
     const int win = es == 4 ? lbmk::Tbt3Geom<4>::WIN : lbmk::Tbt3Geom<2>::WIN;
-    b->t3_rows = es == 4 ? 12 : 64;          // the single-lattice defaults (lbm_set_step_fusion)
+    b->t3_rows = es == 4 ? LBM_BATCH_T3_ROWS4 : LBM_BATCH_T3_ROWS2;
     std::vector<CUtensorMap> maps((size_t)2 * b->count);
     std::vector<lbmk::BatchLatT3> l3((size_t)b->count);
     std::vector<int4> tiles[2];
