@@ -19,6 +19,10 @@
 
 namespace lbmk {
 
+#ifndef LBM_BATCH_F64_FIXED
+#define LBM_BATCH_F64_FIXED 1     // FP64 batches: 1 = fixed-point node update, 0 = split level 1
+#endif
+
 struct LatDesc {
     long long off;        // element offset of plane 0 of this lattice in each arena
     long long plane;      // elements per plane = ny * pitch
@@ -185,8 +189,12 @@ __device__ __forceinline__ void batch_tile(const LatDesc& L, int local_tile, con
         M U[5], rx[5], ry[5];
         M o[4][5];
         if constexpr (K == K_F64) {
-            // FP64: the default split (bit-identical to the FP64-pipe collision)
-            collide_split<kSplitDefaultMask>(f, a, b, U, o);
+            // FP64: the fixed-point node update, the single-lattice default, where the lattice's
+            // multipliers allow it (uniform over the tile: one lattice per tile), else the exact
+            // integer-pipe sums of split level 1
+            if (LBM_BATCH_F64_FIXED && lbmfx::mul_ok(L.a) && lbmfx::mul_ok(L.b))
+                collide_split<kSplitFixed>(f, a, b, U, o);
+            else collide_split<kSplitDefaultMask>(f, a, b, U, o);
         } else {
 #pragma unroll
             for (int k = 0; k < 5; ++k) {

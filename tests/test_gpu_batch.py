@@ -64,8 +64,6 @@ def test_batch_equals_single_lattices_bitwise(lbm, storage):
     for i, d in enumerate(descs):
         nx, ny, bc, dx, dt, cK, cmu = d
         lat = lbm.Lattice(nx, ny, dx, dt, cK, cmu, dirichlet=bool(bc), storage=storage, track_displacement=False)
-        if storage == "f64":
-            lat.set_fp64_split(1)       # FP64 batches run the level-1 arithmetic (exact integer-pipe sums)
         lat.init(*_inputs(d, 100 + i))
         lat.step(25)
         ref = lat.moments()
