@@ -240,13 +240,15 @@ def run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws):
     b = lbm.lbm_batch_create(descs, storage=lbm.LBM_F32, stream=stream.cuda_stream)
     cache = os.path.join(ROOT, "paper_2408_01081_gb300", "_build", "tune_cache.txt")
     t0 = time.perf_counter()
-    lbm.lbm_batch_tune(b, cache)
+    if args.batch_mode < 0:
+        lbm.lbm_batch_tune(b, cache)
     tune_s = time.perf_counter() - t0
     for i, (sp, d) in enumerate(zip(spec, descs)):
         U0, Ux, Uy = batch_lattice_inputs_torch(sp, d[3], device=dev)
         lbm.lbm_batch_init(b, i, U0, Ux, Uy)
     del U0, Ux, Uy
-    lbm.lbm_batch_set_mode(b, _batch_mode(cache), 100)
+    mode = _batch_mode(cache) if args.batch_mode < 0 else args.batch_mode
+    lbm.lbm_batch_set_mode(b, mode, 100)
     lbm.lbm_batch_step(b, 100)
     lbm.lbm_batch_synchronize(b)
     barrier()
@@ -260,7 +262,6 @@ def run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws):
     barrier()
     ms = max_over_ranks(e0.elapsed_time(e1)) / steps
     info = lbm.lbm_batch_info(b, 0)
-    mode = _batch_mode(cache)
     lbm.lbm_batch_destroy(b)
     peaks = _peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
@@ -657,6 +658,8 @@ def main():
                          "copies for the FP64 step), 0: register loads")
     ap.add_argument("--rows-per-block", type=int, default=0, help="two-step kernel rows per block (0: library default)")
     ap.add_argument("--batch-count", type=int, default=512, help="lattices in the batch leg")
+    ap.add_argument("--batch-mode", type=int, default=-1,
+                    help="batch launch mode (0, 1, 2); -1: the autotuner's choice")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-budget", type=float, default=60.0, help="surrogate training seconds")
     ap.add_argument("--cpu-steps", type=int, default=100)
