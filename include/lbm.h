@@ -157,9 +157,11 @@ lbm_status lbm_set_staging(lbm_ctx* ctx, int32_t mode);
  * 2^-964, at or above about 2^1019, or not finite run the level-1 sequence instead
  * (the choice depends on the node's own inputs only).  Level 12 needs cK / c and
  * cmu / c in [2^-60, 1/2) (cmu may be 0); otherwise it returns LBM_ERR_ARG and
- * level 1 is the default.  Level 0 runs every operation on the FP64 pipe.  Applies
- * to steps without body load and with omega = 2; other steps use the FP64 pipe
- * only.  A level outside [0, 12] returns LBM_ERR_ARG. */
+ * level 1 is the default.  Level 0 runs every operation on the FP64 pipe.  Levels
+ * 1..11 apply to steps without body load, level 12 also to steps with one (U of the
+ * two velocity components gains dt/2 b, rounded once in FP64, as another input of the
+ * exact update); all need omega = 2, and other steps use the FP64 pipe only.  A
+ * level outside [0, 12] returns LBM_ERR_ARG. */
 lbm_status lbm_set_fp64_split(lbm_ctx* ctx, int32_t level);
 
 /* Relaxation rate of the BGK collision (Eq. collision); the paper's scheme is

@@ -826,7 +826,9 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* U0, const double* dU0dx, const d
 static lbm_status step_n(lbm_ctx* ctx, int64_t n)
 {
     const KindOps* ops = ctx->ops;
-    const bool split = ctx->p.storage == LBM_F64 && ctx->split > 0 && ctx->R == 0 && ctx->omega == 2.0;
+    // the split levels apply without body load; the fixed-point update (level 12) with one too
+    const bool split = ctx->p.storage == LBM_F64 && ctx->split > 0 &&
+                       (ctx->R == 0 || ctx->split == lbmh::STEP_SPLIT_FIXED) && ctx->omega == 2.0;
     const int vec = split ? ops->vec_split : ops->vec;
     const int nchunk = (ctx->p.nx + vec - 1) / vec;
     int bx = (nchunk + 31) / 32 * 32;

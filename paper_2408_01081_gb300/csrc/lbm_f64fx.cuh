@@ -143,13 +143,31 @@ FX_HD int node_exp(const u64 (&in)[4][5])
     return (int)(mx >> 20);
 }
 
+// the same over the 20 inputs and the two body-load terms h
+FX_HD int node_exp_h(const u64 (&in)[4][5], const u64 (&h)[2])
+{
+    const int e0 = node_exp(in);
+    const int e1 = (int)((h[0] >> 52) & 0x7FFu), e2 = (int)((h[1] >> 52) & 0x7FFu);
+    const int e12 = e1 > e2 ? e1 : e2;
+    return e0 > e12 ? e0 : e12;
+}
+
 // nodes the fixed-point update takes (see above)
 FX_HD bool exp_ok(int E) { return E >= 59 && E <= 2042; }
 
 // The node update on bit patterns for a node with exp_ok(E): in[d][k] the pulled f*_(d)
 // component k (d: (1,0), (0,1), (-1,0), (0,-1)), out the post-collision populations in the
 // same order, Uout the moments U (rounded once each; only for the displacement helper).
-FX_HD void fx_update(const u64 (&in)[4][5], int E, const Mul& A, const Mul& B, u64 (&out)[4][5], u64 (&Uout)[5])
+// With HASH, h = [dt/2 b_x, dt/2 b_y] (binary64, E taken over them too) enters U's two
+// velocity components (Eq. cond_eq with a body load); at omega = 2 the collision has no
+// other body-load term, and f*_(1,0) + f*_(-1,0) = U - f_(1,0) - f_(-1,0) = rx + h, so the
+// pair sums used for the opposite directions carry h too.  Every intermediate then stays
+// below 46 * 2^(E - 1023) (U below 10, the doubled outputs below 46 times that), inside the
+// 2^63 rho range, and each output is within half an ulp plus 13 rho of the exact update of
+// its inputs (five floors in U, three in a pair sum with h).
+template <bool HASH>
+FX_HD void fx_update_h(const u64 (&in)[4][5], const u64 (&h)[2], int E, const Mul& A, const Mul& B,
+                       u64 (&out)[4][5], u64 (&Uout)[5])
 {
     i64 X[4][5];
 #pragma unroll
@@ -162,6 +180,15 @@ FX_HD void fx_update(const u64 (&in)[4][5], int E, const Mul& A, const Mul& B, u
         rx[k] = X[1][k] + X[3][k];
         ry[k] = X[0][k] + X[2][k];
         U[k] = rx[k] + ry[k];
+    }
+    if (HASH) {
+        const i64 h0 = to_fixed(h[0], E), h1 = to_fixed(h[1], E);
+        U[0] += h0;
+        U[1] += h1;
+        rx[0] += h0;
+        rx[1] += h1;
+        ry[0] += h0;
+        ry[1] += h1;
     }
     // Phi_x = [cK js + cmu jd, cmu jxy, cK vx, cmu vx, cmu vy],
     // Phi_y = [cmu jxy, cK js - cmu jd, cK vy, -cmu vy, cmu vx]  (U = [vx, vy, js, jd, jxy])
@@ -191,12 +218,28 @@ FX_HD void fx_update(const u64 (&in)[4][5], int E, const Mul& A, const Mul& B, u
     }
 }
 
+FX_HD void fx_update(const u64 (&in)[4][5], int E, const Mul& A, const Mul& B, u64 (&out)[4][5], u64 (&Uout)[5])
+{
+    const u64 h[2] = {0ull, 0ull};
+    fx_update_h<false>(in, h, E, A, B, out, Uout);
+}
+
 // fx_update() where exp_ok(node_exp(in)); false (nothing written) otherwise
 FX_HD bool fx_node(const u64 (&in)[4][5], const Mul& A, const Mul& B, u64 (&out)[4][5], u64 (&Uout)[5])
 {
     const int E = node_exp(in);
     if (!exp_ok(E)) return false;
     fx_update(in, E, A, B, out, Uout);
+    return true;
+}
+
+// the same with the body-load terms h (fx_update_h)
+FX_HD bool fx_node_h(const u64 (&in)[4][5], const u64 (&h)[2], const Mul& A, const Mul& B, u64 (&out)[4][5],
+                     u64 (&Uout)[5])
+{
+    const int E = node_exp_h(in, h);
+    if (!exp_ok(E)) return false;
+    fx_update_h<true>(in, h, E, A, B, out, Uout);
     return true;
 }
 

@@ -284,6 +284,56 @@ __device__ __forceinline__ void collide_fixed(const double (&f)[4][5], double a,
     }
 }
 
+// The fixed-point node update with a body load (b_x, b_y at the node, hdt = dt/2): U of the two
+// velocity components gains h = hdt b (Eq. cond_eq).  Nodes outside the fixed-point range run
+// the FP64 sequence of step_kernel's body-load path (the body load folded into the pair sums
+// by fused multiply-adds, then the 47-operation collision).
+__device__ __forceinline__ void collide_fixed_forced(const double (&f)[4][5], double bx, double by, double hdt,
+                                                     double a, double b, double (&U)[5], double (&o)[4][5])
+{
+    const lbmfx::Mul A = lbmfx::make_mul(lbmemu::bits_of(a)), B = lbmfx::make_mul(lbmemu::bits_of(b));
+    lbmfx::u64 in[4][5], out[4][5], Uo[5];
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) in[d][k] = lbmemu::bits_of(f[d][k]);
+    const lbmfx::u64 h[2] = {lbmemu::bits_of(hdt * bx), lbmemu::bits_of(hdt * by)};
+    const int E = lbmfx::node_exp_h(in, h);
+    const bool ok = lbmfx::exp_ok(E);
+    if (__all_sync(0xffffffffu, ok)) {
+        lbmfx::fx_update_h<true>(in, h, E, A, B, out, Uo);
+    } else {
+        double rx[5], ry[5], U2[5], o2[4][5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            rx[k] = f[1][k] + f[3][k];
+            ry[k] = f[0][k] + f[2][k];
+        }
+        rx[0] = fma(hdt, bx, rx[0]);
+        rx[1] = fma(hdt, by, rx[1]);
+        ry[0] = fma(hdt, bx, ry[0]);
+        ry[1] = fma(hdt, by, ry[1]);
+        U2[0] = rx[0] + (f[0][0] + f[2][0]);
+        U2[1] = rx[1] + (f[0][1] + f[2][1]);
+#pragma unroll
+        for (int k = 2; k < 5; ++k) U2[k] = rx[k] + ry[k];
+        collide<double>(f, U2, rx, ry, a, b, o2);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            Uo[k] = lbmemu::bits_of(U2[k]);
+#pragma unroll
+            for (int d = 0; d < 4; ++d) out[d][k] = lbmemu::bits_of(o2[d][k]);
+        }
+        if (ok) lbmfx::fx_update_h<true>(in, h, E, A, B, out, Uo);
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        U[k] = lbmemu::double_of(Uo[k]);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) o[d][k] = lbmemu::double_of(out[d][k]);
+    }
+}
+
 template <unsigned long long M>
 __device__ __forceinline__ void collide_split(const double (&f)[4][5], double a, double b, double (&U)[5],
                                               double (&o)[4][5])
@@ -481,6 +531,17 @@ step_kernel(StepArgs A)
         M o[4][5];
         if constexpr (SPLIT > 0 && sizeof(M) == 8 && !FORCING && !OMEGA) {
             collide_split<SPLIT>(f, a, b, U, o);
+        } else if constexpr ((SPLIT & kSplitFixed) != 0 && sizeof(M) == 8 && FORCING && !OMEGA) {
+            // body load in FP64 as below, then the fixed-point node update with it
+            double bx = 0.0, by = 0.0;
+            if (x < nx) {
+                for (int r = 0; r < A.R; ++r) {
+                    const double xy = A.X[(long long)r * nx + x] * A.Y[(long long)r * ny + y];
+                    bx = fma(xy, A.T[r], bx);
+                    by = fma(xy, A.T[A.R + r], by);
+                }
+            }
+            collide_fixed_forced(f, bx, by, 0.5 * A.dt, a, b, U, o);
         } else {
 #pragma unroll
             for (int k = 0; k < 5; ++k) {

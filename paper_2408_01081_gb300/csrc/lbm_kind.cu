@@ -118,9 +118,25 @@ cudaError_t step_o(const lbmk::StepArgs& a, int variant, dim3 g, dim3 b, cudaStr
     }
 }
 
+// FP64 with a body load at split level 12 (omega = 2): the fixed-point node update with it
+template <bool D, bool T>
+cudaError_t step_fixed_forced(const lbmk::StepArgs& a, dim3 g, dim3 b, cudaStream_t s)
+{
+    if constexpr (K != lbmk::K_F64) {
+        return cudaErrorNotSupported;
+    } else {
+        return step_v<D, true, T, false, lbmh::split_mask(lbmh::STEP_SPLIT_FIXED)>(a, g, b, s);
+    }
+}
+
 cudaError_t step(const lbmk::StepArgs& a, int variant, dim3 g, dim3 b, cudaStream_t s)
 {
     const int level = (variant >> lbmh::STEP_SPLIT_SHIFT) & 15;
+    if (level == lbmh::STEP_SPLIT_FIXED && (variant & lbmh::STEP_FORCING) && !(variant & lbmh::STEP_OMEGA)) {
+        const bool d = variant & lbmh::STEP_DIRICHLET, t = variant & lbmh::STEP_TRACK;
+        return d ? (t ? step_fixed_forced<true, true>(a, g, b, s) : step_fixed_forced<true, false>(a, g, b, s))
+                 : (t ? step_fixed_forced<false, true>(a, g, b, s) : step_fixed_forced<false, false>(a, g, b, s));
+    }
     if (level && !(variant & (lbmh::STEP_FORCING | lbmh::STEP_OMEGA))) {
         const bool d = variant & lbmh::STEP_DIRICHLET, t = variant & lbmh::STEP_TRACK;
         return d ? (t ? step_split<true, true>(a, level, g, b, s) : step_split<true, false>(a, level, g, b, s))
