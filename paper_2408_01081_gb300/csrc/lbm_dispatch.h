@@ -77,8 +77,8 @@ struct KindOps {
     cudaError_t (*tbt_step)(const CUtensorMap* maps, const lbmk::TbtArgs&, bool dirichlet, dim3 grid, cudaStream_t s);
     // three fused steps (maps with box width Tbt3Geom::WIN, or Tbt3MsGeom::WIN for moment space)
     cudaError_t (*tbt3_step)(const CUtensorMap* maps, const lbmk::TbtArgs&, bool dirichlet, dim3 grid, cudaStream_t s);
-    // one FP64 step at split level 1 with the rows staged by asynchronous copies, `rows` rows
-    // per block (other formats and variants return cudaErrorNotSupported)
+    // one FP64 step at split level 1 or 12 with the rows staged by asynchronous copies, `rows`
+    // rows per block (other formats and variants return cudaErrorNotSupported)
     cudaError_t (*step_staged)(const lbmk::StepArgs&, int variant, int rows, cudaStream_t s);
     // three fused steps over the tiles of a batch (FP32 / BF16 / FP16; others return
     // cudaErrorNotSupported): `ntiles` blocks, all of periodic or all of Dirichlet lattices

@@ -1,20 +1,21 @@
-// FP64 step (split collision, omega = 2, no body load) with each node's inputs staged
-// in shared memory by per-thread asynchronous copies (cp.async), one row ahead.
+// FP64 step (omega = 2, no body load; the node update of split level 1, the IEEE operation
+// sequence, or 12, the fixed-point update) with each node's inputs staged in shared memory
+// by per-thread asynchronous copies (cp.async), one row ahead.
 //
 // The register step kernel loads the 20 inputs of a node and then waits for them:
 // with 80 registers and three 256-thread blocks per SM, about a sixth of its warp
 // cycles go to that wait (long scoreboard) while the integer pipe, which shares the
 // bound of the split collision with the FP64 pipe, idles.  Here a block of 128 threads
-// owns 128 consecutive columns and walks down `rows` rows (2 by default), thread t
-// computing column t of each row.  The copies of the next row are issued as soon as
+// owns 128 consecutive columns and walks down `rows` rows (the library passes 2 at level 1
+// and 4 at level 12), thread t computing column t of each row.  The copies of the next row are issued as soon as
 // the current row has been read out of shared memory, so they are in flight during its
 // whole collision and occupy no registers.  Each thread copies exactly the 20 values its
 // own node pulls (f*_(1,0) from x - 1, f*_(-1,0) from x + 1, f*_(0,1) from y - 1,
 // f*_(0,-1) from y + 1, with the periodic wrap or the Dirichlet edge reflection in the
 // source address), so no value crosses threads and no barrier or wait loop is needed: a
-// thread's copies of a row complete by cp.async.wait_group.  The node arithmetic is the
-// split collision of step_kernel (lbm_kernels.cuh) on the same inputs, so results are
-// bit-identical to it.
+// thread's copies of a row complete by cp.async.wait_group.  The node arithmetic is
+// collide_split of the same level as in step_kernel (lbm_kernels.cuh) on the same inputs,
+// so results are bit-identical to it.
 #pragma once
 
 #include "lbm_kernels.cuh"

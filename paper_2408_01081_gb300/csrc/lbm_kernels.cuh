@@ -16,7 +16,10 @@
 //     f*_{0,-1} = (U - f_{0,1} - f_{0,-1}) - f*_{0,1}.
 // That is 47 FP64 operations per node without forcing (35 additions, 12 fused
 // multiply-adds), the FP64 ALU bound on GB300; the SPLIT variants compute part of
-// the additions on the integer pipes (collide_split), exactly or faithfully rounded.
+// the additions on the integer pipes (collide_split), exactly or faithfully rounded,
+// or (split level 12, collide_fixed) the whole node update in exact 64-bit fixed point
+// with one binary64 rounding per output (lbm_f64fx.cuh), which leaves only the output
+// conversions on the FP64 pipe.
 #pragma once
 
 #include "lbm_f64emu.cuh"

@@ -70,7 +70,7 @@ cudaError_t step_split(const lbmk::StepArgs& a, int level, dim3 g, dim3 b, cudaS
 #define LBM_SA_MASK lbmh::split_mask(1)   // the additions of split level 1 on the integer pipes
 #endif
 
-// FP64 at split level 1 with the rows staged by asynchronous copies (lbm_f64stage.cuh);
+// FP64 at split level 1 or 12 with the rows staged by asynchronous copies (lbm_f64stage.cuh);
 // other formats, levels and variants return cudaErrorNotSupported
 template <bool D, bool T, unsigned long long M>
 cudaError_t step_staged_dt(const lbmk::StepArgs& a, int rows, cudaStream_t s)

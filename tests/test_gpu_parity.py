@@ -402,7 +402,7 @@ def test_fp64_split_is_bit_identical_periodic(lbm, nx, ny):
 @pytest.mark.parametrize("dirichlet", [False, True])
 @pytest.mark.parametrize("nx,ny,rows", [(3, 5, 64), (127, 9, 4), (129, 33, 7), (300, 17, 1), (1031, 7, 3)])
 def test_fp64_staged_step_equals_register_step(lbm, nx, ny, rows, dirichlet):
-    """The FP64 step with its rows staged by asynchronous copies (split level 1, the default)
+    """The FP64 step with its rows staged by asynchronous copies (split level 1, the IEEE sequence)
     gives the register kernel's populations and displacements bit for bit: ragged column
     blocks, row counts that do not divide ny, one row per block, wall data on Dirichlet edges."""
     steps = 9
