@@ -29,12 +29,17 @@
 
 namespace lbmk {
 
-// r modulo ny in [0, ny) for any r (the staged rows of the three-step kernels reach three rows
-// beyond the lattice, more than one period when ny = 2)
+// r modulo ny in [0, ny) for r within three rows of the lattice (the staged rows of the
+// three-step kernels): one wrap suffices unless ny = 2, where the remainder is taken
 __device__ __forceinline__ int wrap_row(int r, int ny)
 {
-    const int q = r % ny;
-    return q < 0 ? q + ny : q;
+    if (r < 0) r += ny;
+    else if (r >= ny) r -= ny;
+    if ((unsigned)r >= (unsigned)ny) {
+        const int q = r % ny;
+        r = q < 0 ? q + ny : q;
+    }
+    return r;
 }
 
 struct TbtArgs {
