@@ -52,11 +52,11 @@ STEPS_PER_PASS = {"f64": 1, "f32": 3, "bf16": 3, "f16": 3, "ms_bf16": 3, "ms_f16
 # scaling), valid only while the kernel sources hash to "sha256".  "<fmt>_fused" is one launch of
 # the two-step kernel (two steps), "<fmt>_fused3" of the three-step kernel, "f64_pipe" the FP64
 # step with every operation on the FP64 pipe.
-TRAFFIC_CAPTURE = {"sha256": "023d8f9ca9cd9f87baa3be17c5cd40dab12cdb9350186221d740cdc9bbd4a459",
+TRAFFIC_CAPTURE = {"sha256": "427275c0b852342612482484dcd6605f8b9ba6a8e2209f6534469d96ebb1a946",
                    "nodes": 8192 * 8192,
-                   "bytes_per_node": {"f64": 319.23, "f64_ieee": 322.71, "f64_pipe": 319.25, "f32_fused3": 164.39,
-                                      "bf16_fused3": 83.3, "f16_fused3": 83.31, "ms_bf16_fused3": 105.17,
-                                      "ms_f16_fused3": 105.2, "ms_bfp_fused3": 105.22}}
+                   "bytes_per_node": {"f64": 319.23, "f64_ieee": 322.79, "f64_pipe": 319.26, "f32_fused3": 164.66,
+                                      "bf16_fused3": 83.32, "f16_fused3": 83.33, "ms_bf16_fused3": 105.1,
+                                      "ms_f16_fused3": 105.11, "ms_bfp_fused3": 105.2}}
 KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_01081_gb300/csrc/lbm_kind.cu",
                   "paper_2408_01081_gb300/csrc/lbm_tb.cuh", "paper_2408_01081_gb300/csrc/lbm_ms.cuh",
                   "paper_2408_01081_gb300/csrc/lbm_tbt.cuh", "paper_2408_01081_gb300/csrc/lbm_tma.cuh",
@@ -68,8 +68,8 @@ KERNEL_SOURCES = ["paper_2408_01081_gb300/csrc/lbm_kernels.cuh", "paper_2408_010
 # valid only while the kernel sources hash to "sha256".  Each SM issues 64 ALU-pipe and 2
 # FP64-pipe thread instructions per clock, so one node needs at least
 # max(alu / 64, fp64 / 2) SM clocks: the arithmetic roof of this kernel.
-PIPE_CAPTURE = {"sha256": "023d8f9ca9cd9f87baa3be17c5cd40dab12cdb9350186221d740cdc9bbd4a459",
-                "alu_per_node": 586.0, "fp64_per_node": 20.0, "fma_per_node": 188.3}
+PIPE_CAPTURE = {"sha256": "427275c0b852342612482484dcd6605f8b9ba6a8e2209f6534469d96ebb1a946",
+                "alu_per_node": 586.3, "fp64_per_node": 20.0, "fma_per_node": 188.4}
 ALU_LANES_PER_SM, FP64_LANES_PER_SM, N_SM = 64, 2, 152
 
 
