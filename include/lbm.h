@@ -346,8 +346,8 @@ lbm_status lbm_batch_create(int32_t count, const lbm_lattice_desc* lattices, int
 lbm_status lbm_batch_init(lbm_batch* b, int32_t index, const double* U0, const double* dU0dx,
                           const double* dU0dy, int32_t on_device);
 
-/* Choose the tile width of every size class and the launch mode (0, 1, or 2 where
- * the storage allows) by timing them on this GPU, before any lbm_batch_init
+/* Choose the tile width of every size class and the launch mode (0, 1, and 2 or 3
+ * where the storage allows) by timing them on this GPU, before any lbm_batch_init
  * (tuning steps the zero state; returns
  * LBM_ERR_STATE afterwards).  cache_path (or NULL): a text file of earlier
  * results keyed by GPU name, storage format and size class; found entries are
@@ -361,10 +361,15 @@ lbm_status lbm_batch_tune(lbm_batch* b, const char* cache_path);
  * one block per tile stages the tile's input rows with tensor copies and keeps the
  * two intermediate steps on chip (the single-lattice three-step kernel of
  * lbm_set_step_fusion), one launch for the periodic and one for the Dirichlet
- * tiles per pass; steps beyond a multiple of three run as mode 0.  FP32 results
- * are bit-identical in every mode; 16-bit formats round the state once per pass in
- * mode 2.  graph_steps (even, 2..10000): steps captured in one CUDA graph and
- * replayed. */
+ * tiles per pass; steps beyond a multiple of three run as mode 0;
+ * 3 = one step per launch on staged rows (FP64 storage only, LBM_ERR_ARG otherwise):
+ * tiles of 128 columns and 4 rows (2 for a lattice on the level-1 sequence), one
+ * block per tile copying each node's 20 inputs into shared memory one row ahead
+ * (the single-lattice FP64 staged step), one launch per non-empty list of periodic
+ * and Dirichlet lattices on the fixed-point update and on the level-1 sequence.
+ * FP32 and FP64 results are bit-identical in every mode; 16-bit formats round the
+ * state once per pass in mode 2.  graph_steps (even, 2..10000): steps captured in
+ * one CUDA graph and replayed. */
 lbm_status lbm_batch_set_mode(lbm_batch* b, int32_t mode, int32_t graph_steps);
 
 /* Advance every lattice n >= 0 steps, asynchronously.  Barrier time-outs of the

@@ -115,6 +115,10 @@ struct lbm_batch {
     CUtensorMap* d_maps = nullptr;        // [lattice][arena]
     int4* d_t3 = nullptr;                 // periodic tiles, then Dirichlet tiles
     int nt3[2] = {0, 0};                  // tile counts: periodic, Dirichlet
+    // mode 3: FP64 on staged rows, one step per launch (lbm_batch_f64.cu)
+    bool f64s_ok = false;                 // tile lists built (FP64 storage)
+    int4* d_f64s = nullptr;               // the four lists, one after the other
+    int nf64s[4] = {0, 0, 0, 0};          // periodic / Dirichlet x fixed point / split level 1
     cudaGraphExec_t graph = nullptr;
     bool graph_valid = false;
     bool initialised = false;
@@ -232,6 +236,45 @@ lbm_status setup_t3(lbm_batch* b)
     return LBM_OK;
 }
 
+#ifndef LBM_BATCH_F64S_ROWS_FX
+#define LBM_BATCH_F64S_ROWS_FX 4     // rows per mode-3 tile on the fixed-point update (single-lattice default)
+#endif
+#ifndef LBM_BATCH_F64S_ROWS_L1
+#define LBM_BATCH_F64S_ROWS_L1 2     // the same on the IEEE sequence of split level 1
+#endif
+
+int f64s_rows(int list)
+{
+    return list < 2 ? LBM_BATCH_F64S_ROWS_FX : LBM_BATCH_F64S_ROWS_L1;
+}
+
+// Tile lists of mode 3 for FP64 storage: 128 columns x f64s_rows(list) rows, row bands of a
+// lattice one after the other, each lattice in the list of its boundary and node update
+// (the fixed-point update where both multipliers allow it, as batch_tile decides per lattice)
+lbm_status setup_f64s(lbm_batch* b)
+{
+    if (b->storage != LBM_F64) return LBM_OK;
+    std::vector<int4> tiles[4];
+    for (int i = 0; i < b->count; ++i) {
+        const lbmk::LatDesc& L = b->lat[i];
+        const bool fixed = LBM_BATCH_F64_FIXED && lbmfx::mul_ok(L.a) && lbmfx::mul_ok(L.b);
+        const int list = (fixed ? 0 : 2) + (L.bc ? 1 : 0);
+        const int rows = f64s_rows(list);
+        for (int y = 0; y < L.ny; y += rows)
+            for (int x = 0; x < L.nx; x += lbmk::SA_THREADS) tiles[list].push_back(make_int4(i, x, y, 0));
+    }
+    std::vector<int4> all;
+    for (int l = 0; l < 4; ++l) {
+        b->nf64s[l] = (int)tiles[l].size();
+        all.insert(all.end(), tiles[l].begin(), tiles[l].end());
+    }
+    B_CUDA(b, cudaMalloc((void**)&b->d_f64s, std::max<size_t>(1, all.size()) * sizeof(int4)));
+    if (!all.empty())
+        B_CUDA(b, cudaMemcpy(b->d_f64s, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    b->f64s_ok = true;
+    return LBM_OK;
+}
+
 lbmk::BatchArgs batch_args(const lbm_batch* b, int steps, int parity)
 {
     lbmk::BatchArgs A;
@@ -261,6 +304,25 @@ cudaError_t enqueue_steps(lbm_batch* b, int steps, int parity)
 {
     if (b->mode == 1) {
         return b->ops->batch_step(batch_args(b, steps, parity), true, b->persistent_grid, b->s);
+    }
+    if (b->mode == 3) {
+        // one launch per non-empty tile list and step
+        lbmk::BatchF64Args F;
+        F.lat = b->d_lat;
+        for (int i = 0; i < steps; ++i) {
+            F.src = static_cast<const double*>(b->arena[parity]);
+            F.dst = static_cast<double*>(b->arena[parity ^ 1]);
+            const int4* t = b->d_f64s;
+            for (int l = 0; l < 4; ++l) {
+                F.tiles = t;
+                F.rows = f64s_rows(l);
+                cudaError_t e = lbmh::batch_f64_staged_step(F, l, b->nf64s[l], b->s);
+                if (e != cudaSuccess) return e;
+                t += b->nf64s[l];
+            }
+            parity ^= 1;
+        }
+        return cudaSuccess;
     }
     int i = 0;
     if (b->mode == 2) {
@@ -507,7 +569,7 @@ lbm_status lbm_batch_create(int32_t count, const lbm_lattice_desc* lats, int32_t
         return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
     }
     b->persistent_grid = std::max(1, occ) * sms;
-    if (build_tiles(b) != LBM_OK || setup_t3(b) != LBM_OK) {
+    if (build_tiles(b) != LBM_OK || setup_t3(b) != LBM_OK || setup_f64s(b) != LBM_OK) {
         g_batch_create_error = b->err;
         lbm_batch_destroy(b);
         return LBM_ERR_CUDA;
@@ -530,6 +592,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b)
     cudaFree(b->d_lat3);
     cudaFree(b->d_maps);
     cudaFree(b->d_t3);
+    cudaFree(b->d_f64s);
     if (b->own_stream) cudaStreamDestroy(b->s);
     delete b;
     return LBM_OK;
@@ -546,10 +609,12 @@ lbm_status lbm_batch_set_mode(lbm_batch* b, int32_t mode, int32_t graph_steps)
     if (b->sticky) return LBM_ERR_CUDA;
     // a graph must return the state to arena 0, an even number of arena swaps: graph_steps even
     // (in mode 2, 3q + r steps swap q + r times, even exactly when 3q + r is)
-    if (mode < 0 || mode > 2 || graph_steps < 2 || graph_steps > 10000 || (graph_steps & 1))
-        return bfail(b, LBM_ERR_ARG, "mode must be 0, 1 or 2 and graph_steps even in [2, 10000]");
+    if (mode < 0 || mode > 3 || graph_steps < 2 || graph_steps > 10000 || (graph_steps & 1))
+        return bfail(b, LBM_ERR_ARG, "mode must be 0, 1, 2 or 3 and graph_steps even in [2, 10000]");
     if (mode == 2 && !b->t3_ok)
         return bfail(b, LBM_ERR_ARG, "mode 2 needs FP32, BF16 or FP16 storage");
+    if (mode == 3 && !b->f64s_ok)
+        return bfail(b, LBM_ERR_ARG, "mode 3 needs FP64 storage");
     b->mode = mode;
     b->graph_steps = graph_steps;
     drop_graph(b);
@@ -707,7 +772,7 @@ lbm_status lbm_batch_tune(lbm_batch* b, const char* cache_path)
     }
     if (all_cached) {
         b->mode = cache[key + "mode"];
-        if (b->mode < 0 || b->mode > 2 || (b->mode == 2 && !b->t3_ok)) b->mode = 0;
+        if (b->mode < 0 || b->mode > 3 || (b->mode == 2 && !b->t3_ok) || (b->mode == 3 && !b->f64s_ok)) b->mode = 0;
         return build_tiles(b);
     }
     const int V = b->ops->batch_vec;
@@ -715,8 +780,8 @@ lbm_status lbm_batch_tune(lbm_batch* b, const char* cache_path)
     const int saved_graph = b->graph_steps;
     b->graph_steps = 2;
     const std::map<int, int> start = b->tpr_of_class;
-    std::map<int, int> tpr_mode[3];
-    float mode_ms[3] = {1e30f, 1e30f, 1e30f};
+    std::map<int, int> tpr_mode[4];
+    float mode_ms[4] = {1e30f, 1e30f, 1e30f, 1e30f};
     for (int mode = 0; mode < 2; ++mode) {
         b->mode = mode;
         b->tpr_of_class = start;
@@ -765,9 +830,11 @@ lbm_status lbm_batch_tune(lbm_batch* b, const char* cache_path)
         b->graph_steps = 2;
         tpr_mode[mode] = b->tpr_of_class;
     }
-    if (b->t3_ok) {
-        // mode 2: three steps per pass over fixed tiles; its remainder steps use mode 0's widths
-        b->mode = 2;
+    // mode 2 (three steps per pass, FP32 / 16 bits) and mode 3 (FP64 on staged rows) run over
+    // fixed tiles; mode 2's remainder steps use mode 0's widths
+    for (int m = 2; m < 4; ++m) {
+        if (!(m == 2 ? b->t3_ok : b->f64s_ok)) continue;
+        b->mode = m;
         b->tpr_of_class = tpr_mode[0];
         b->graph_steps = saved_graph;
         for (int rep = 0; rep < 2; ++rep) {
@@ -777,13 +844,13 @@ lbm_status lbm_batch_tune(lbm_batch* b, const char* cache_path)
                 b->graph_steps = saved_graph;
                 return st;
             }
-            mode_ms[2] = std::min(mode_ms[2], ms);
+            mode_ms[m] = std::min(mode_ms[m], ms);
         }
         b->graph_steps = 2;
-        tpr_mode[2] = tpr_mode[0];
+        tpr_mode[m] = tpr_mode[0];
     }
     int best_mode = 0;
-    for (int m = 1; m < 3; ++m)
+    for (int m = 1; m < 4; ++m)
         if (mode_ms[m] < mode_ms[best_mode]) best_mode = m;
     b->tpr_of_class = tpr_mode[best_mode];
     b->graph_steps = saved_graph;

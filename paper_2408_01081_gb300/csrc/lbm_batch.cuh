@@ -216,6 +216,15 @@ __device__ __forceinline__ void batch_tile(const LatDesc& L, int local_tile, con
         for (int k = 0; k < 5; ++k) vstore<K, V>(dst + (d * 5 + k) * plane + row, out[d][k]);
 }
 
+// batch mode 3 (FP64, staged rows, lbm_batch_f64.cu): one step over one tile list
+struct BatchF64Args {
+    const LatDesc* lat;
+    const int4* tiles;            // {lattice, first column (a multiple of 128), first row, 0}
+    const double* src;            // arena read by this step
+    double* dst;                  // arena written
+    int rows;                     // rows per tile
+};
+
 template <int K, int V, bool PERSISTENT>
 __global__ void __launch_bounds__(256, K == K_F64 ? LBM_SPLIT_MIN_BLOCKS : 2) batch_step_kernel(BatchArgs A)
 {
@@ -237,3 +246,11 @@ __global__ void __launch_bounds__(256, K == K_F64 ? LBM_SPLIT_MIN_BLOCKS : 2) ba
 }
 
 }  // namespace lbmk
+
+namespace lbmh {
+
+// list 0 / 1: periodic / Dirichlet lattices on the fixed-point node update; 2 / 3: the same on
+// the IEEE sequence of split level 1.  ntiles == 0 launches nothing.
+cudaError_t batch_f64_staged_step(const lbmk::BatchF64Args& A, int list, int ntiles, cudaStream_t s);
+
+}  // namespace lbmh

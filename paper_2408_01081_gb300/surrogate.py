@@ -412,9 +412,9 @@ def evaluate(sur, chunk, batch=16, act_bf16=False):
 
 def _solver_mode(storage):
     """The fastest batch mode of a storage format: three steps per pass (mode 2) for the
-    population formats in FP32 / 16 bits (bit-identical to single steps in FP32), one launch
-    per step for FP64."""
-    return 2 if storage in ("f32", "bf16", "f16") else 0
+    population formats in FP32 / 16 bits (bit-identical to single steps in FP32), one step per
+    launch on staged rows (mode 3) for FP64."""
+    return 2 if storage in ("f32", "bf16", "f16") else 3 if storage == "f64" else 0
 
 
 def _descs_for(nu, H, W, cfl=0.9):
@@ -554,7 +554,9 @@ def driver_timing(sur, chunk, check_every=(1, 4, 16), tol=1e-3, storage="f32", n
 
 def timing(sur, n=16, H=256, W=256, reps=5):
     """ms per lattice for one jump: surrogate inference (batch n; hi/lo activations and
-    single-BF16 activations) vs k solver steps on a batch of n lattices (FP64, FP32 storage)."""
+    single-BF16 activations) vs k solver steps on a batch of n lattices (FP64, FP32 storage),
+    the solver started from the same random moment fields (populations of zero would send the
+    FP64 fixed-point update to its fallback for every node)."""
     import torch
     k = sur.k
     stride = 10 * H * W
@@ -581,6 +583,9 @@ def timing(sur, n=16, H=256, W=256, reps=5):
     for storage in ("f64", "f32"):
         b = L.lbm_batch_create(_descs_for(nu, H, W), storage=L.STORAGE[storage],
                                stream=torch.cuda.current_stream().cuda_stream)
+        zero = torch.zeros((5, H, W), dtype=torch.float64, device=sur.net.dev)
+        for i in range(n):
+            L.lbm_batch_init(b, i, U[i, :5].contiguous(), zero, zero)
         L.lbm_batch_set_mode(b, _solver_mode(storage), 2 * k)
         L.lbm_batch_step(b, 2 * k)
         L.lbm_batch_synchronize(b)

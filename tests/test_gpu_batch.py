@@ -72,9 +72,10 @@ def test_batch_equals_single_lattices_bitwise(lbm, storage):
         lat.close()
 
 
-def test_batch_matches_oracle_fp64(lbm):
+@pytest.mark.parametrize("mode", [0, 3])
+def test_batch_matches_oracle_fp64(lbm, mode):
     descs = _descs()
-    outs, _ = _run_batch(lbm, descs, "f64", 0, 25)
+    outs, _ = _run_batch(lbm, descs, "f64", mode, 25)
     for i, d in enumerate(descs):
         nx, ny, bc, dx, dt, cK, cmu = d
         o = Oracle(Params(nx, ny, dx, dt, cK, cmu, bool(bc)))
@@ -186,4 +187,61 @@ def test_three_step_mode_is_refused_for_fp64_and_odd_graphs(lbm):
         lbm.lbm_batch_set_mode(b, 2, 7)
     assert e.value.status == lbm.LBM_ERR_ARG
     lbm.lbm_batch_set_mode(b, 2, 10)
+    lbm.lbm_batch_destroy(b)
+
+
+def _descs_with_level1_lattices():
+    """_descs(6) plus a periodic and a Dirichlet lattice whose cmu/c lies below 2^-60: the
+    fixed-point update cannot take that multiplier, so these two run the IEEE sequence of split
+    level 1 (a list of their own in mode 3)."""
+    out = _descs(6)
+    for nx, ny, bc in ((200, 13, 0), (131, 10, 1)):
+        cK = 1.0
+        c = W.material.lattice_speed(cK * cK, 0.0, 0.9)
+        dx = 1.0 / max(nx, ny)
+        out.append((nx, ny, bc, dx, dx / c, cK, 1e-25))
+    return out
+
+
+def test_staged_fp64_mode_equals_launch_per_step(lbm):
+    """Mode 3 (FP64 on staged rows, 128 x 4 tiles on the fixed-point update and 128 x 2 on the
+    level-1 sequence) equals mode 0 bit for bit, inside graphs (8 steps) and in the remainder
+    steps (37 = 4 x 8 + 5), for ragged periodic and Dirichlet lattices of both node updates."""
+    descs = _descs_with_level1_lattices()
+    a, ea = _run_batch(lbm, descs, "f64", 0, 37, graph_steps=8)
+    b, eb = _run_batch(lbm, descs, "f64", 3, 37, graph_steps=8)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    assert ea == eb
+
+
+def test_staged_fp64_mode_is_refused_for_other_formats(lbm):
+    descs = _descs(7)
+    b = lbm.lbm_batch_create(descs, storage=lbm.LBM_F32)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_set_mode(b, 3, 10)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_set_mode(b, 4, 10)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    lbm.lbm_batch_destroy(b)
+
+
+def test_tuned_fp64_batch_equals_launch_per_step(lbm, tmp_path):
+    """The tuner times modes 0, 1 and 3 for an FP64 batch and keeps the fastest; whichever it
+    keeps, the trajectory equals mode 0's bit for bit."""
+    descs = _descs_with_level1_lattices()
+    ref, _ = _run_batch(lbm, descs, "f64", 0, 12, graph_steps=4)
+    cache = tmp_path / "tune.txt"
+    b = lbm.lbm_batch_create(descs, storage=lbm.LBM_F64)
+    lbm.lbm_batch_tune(b, cache)
+    assert "|f64|mode|" in cache.read_text()
+    for i, d in enumerate(descs):
+        lbm.lbm_batch_init(b, i, *_inputs(d, 100 + i))
+    lbm.lbm_batch_step(b, 12)
+    lbm.lbm_batch_synchronize(b)
+    for i, d in enumerate(descs):
+        o = np.empty((10, d[1], d[0]))
+        lbm.lbm_batch_moments(b, i, o)
+        np.testing.assert_array_equal(o, ref[i])
     lbm.lbm_batch_destroy(b)
