@@ -227,7 +227,7 @@ def run_reference(args):
 
 
 def run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws):
-    """512 ragged lattices (config 4 of the workload set), FP32, graph of 100 steps per replay."""
+    """512 ragged lattices (config 4 of the workload set), FP32 (or FP64), graph of 100 steps per replay."""
     import workloads as W
     from workloads.grf import batch_lattice_inputs_torch
     spec = W.batch_spec(count=args.batch_count)
@@ -237,7 +237,8 @@ def run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws):
         dx = 1.0 / max(sp.nx, sp.ny)
         descs.append((sp.nx, sp.ny, int(sp.dirichlet), dx, dx / c, sp.cK2 ** 0.5, sp.cmu2 ** 0.5))
     nodes = sum(d[0] * d[1] for d in descs)
-    b = lbm.lbm_batch_create(descs, storage=lbm.LBM_F32, stream=stream.cuda_stream)
+    storage = args.batch_storage
+    b = lbm.lbm_batch_create(descs, storage=lbm.STORAGE[storage], stream=stream.cuda_stream)
     cache = os.path.join(ROOT, "paper_2408_01081_gb300", "_build", "tune_cache.txt")
     t0 = time.perf_counter()
     if args.batch_mode < 0:
@@ -247,7 +248,7 @@ def run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws):
         U0, Ux, Uy = batch_lattice_inputs_torch(sp, d[3], device=dev)
         lbm.lbm_batch_init(b, i, U0, Ux, Uy)
     del U0, Ux, Uy
-    mode = _batch_mode(cache) if args.batch_mode < 0 else args.batch_mode
+    mode = _batch_mode(cache, storage) if args.batch_mode < 0 else args.batch_mode
     lbm.lbm_batch_set_mode(b, mode, 100)
     lbm.lbm_batch_step(b, 100)
     lbm.lbm_batch_synchronize(b)
@@ -268,17 +269,23 @@ def run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws):
     # algorithmic bytes per node and step: one read and one write of the state per launch; mode 2
     # runs 33 three-step passes and one single step per 100 steps
     passes, singles = (steps // 3, steps % 3) if mode == 2 else (0, steps)
-    bpn = 160 * (passes + singles) / steps
+    bpn = (320 if storage == "f64" else 160) * (passes + singles) / steps
     ach = bpn * nodes / (ms * 1e-3) / 1e9
-    launches = (steps // 100) if mode == 1 else (2 * passes + singles if mode == 2 else steps)
+    # mode 3: one launch per step for each boundary kind present (every lattice of this workload
+    # has cK/c and cmu/c in [2^-60, 1/2), so all of them take the fixed-point node update)
+    kinds = len({d[2] for d in descs})
+    label = {"f32": "FP32", "f64": "FP64"}[storage]
+    launches = {1: steps // 100, 2: 2 * passes + singles, 3: kinds * steps}.get(mode, steps)
     return {"workload": f"{args.batch_count} lattices, short side log-uniform [64,1024], aspect U[1,4], nu U[0,0.49], "
                         "even periodic / odd homogeneous Dirichlet, GRF v0 (ell = short side/16, std 1e-3), "
-                        "FP32 storage, CUDA graph of 100 steps per replay",
+                        f"{label} storage, CUDA graph of 100 steps per replay",
             "nodes": nodes, "steps": steps, "ms_per_step": round(ms, 4),
             "mlups": round(nodes * ws / (ms * 1e-3) / 1e6, 1),
             "mode": {0: "launch per step", 1: "persistent",
                      2: "three steps per pass (tiles with staged rows), one launch each for periodic and "
-                        "Dirichlet tiles"}[mode],
+                        "Dirichlet tiles",
+                     3: "FP64 tiles with staged rows, one launch per step each for periodic and Dirichlet "
+                        "tiles"}[mode],
             "graph_replays": steps // 100, "gpu_launches": launches,
             "tiles": info["ntiles"], "tune_s": round(tune_s, 2),
             "hbm": {"achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
@@ -324,11 +331,11 @@ def run_surrogate(args):
                                  "gain_vs_f32": round(tm["gain_bf16_act_vs_f32"], 3)}}
 
 
-def _batch_mode(cache):
-    """Launch mode the tuner stored for FP32 on this GPU (0 if unknown)."""
+def _batch_mode(cache, storage="f32"):
+    """Launch mode the tuner stored for this storage format on this GPU (0 if unknown)."""
     try:
         for line in open(cache):
-            if "|f32|mode|" in line:
+            if f"|{storage}|mode|" in line:
                 mode = int(line.rsplit("|", 1)[1])
         return mode
     except Exception:
@@ -659,7 +666,9 @@ def main():
     ap.add_argument("--rows-per-block", type=int, default=0, help="two-step kernel rows per block (0: library default)")
     ap.add_argument("--batch-count", type=int, default=512, help="lattices in the batch leg")
     ap.add_argument("--batch-mode", type=int, default=-1,
-                    help="batch launch mode (0, 1, 2); -1: the autotuner's choice")
+                    help="batch launch mode (0, 1, 2 for FP32, 3 for FP64); -1: the autotuner's choice")
+    ap.add_argument("--batch-storage", default="f32", choices=["f32", "f64"],
+                    help="storage of the batch leg (the workload's figure is FP32)")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-budget", type=float, default=60.0, help="surrogate training seconds")
     ap.add_argument("--cpu-steps", type=int, default=100)

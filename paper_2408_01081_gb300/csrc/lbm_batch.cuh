@@ -9,6 +9,9 @@
 // step's (pull, Dirichlet reflection, omega = 2 collision): results are
 // bit-identical to stepping each lattice alone.
 //
+// FP64 batches can also run on staged rows, one block per tile of 128 columns
+// (batch mode 3, lbm_batch_f64.cu).
+//
 // Persistent mode runs `steps` steps in one launch with a grid barrier between
 // steps.  The barrier waits with a time limit: on expiry it sets an error flag
 // and every block returns, so a launch that cannot make progress ends instead
