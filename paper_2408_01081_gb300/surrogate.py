@@ -260,6 +260,8 @@ def generate_chunk(n, seed, H=256, W=256, k=32, J=4, storage="f64", device="cuda
     stream = torch.cuda.current_stream().cuda_stream
     b = L.lbm_batch_create(descs, storage=L.STORAGE[storage], stream=stream)
     try:
+        if storage == "f64":
+            L.lbm_batch_set_mode(b, 3)      # staged rows: the same bits as one launch per step
         for i, sp in enumerate(specs):
             U0, Ux, Uy = batch_lattice_inputs_torch(sp, descs[i][3], std=std, device=dev)
             L.lbm_batch_init(b, i, U0, Ux, Uy)

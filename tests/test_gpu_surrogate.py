@@ -41,8 +41,9 @@ def test_surrogate_trains_beats_persistence_and_falls_back(lbm):
 def test_jump_costs_less_than_the_fp64_solver_at_the_workload_size(lbm):
     """At the learned workload's size (256^2 lattices, jumps of 32 steps, the 1.96 M-parameter
     U-Net, batches of 16) one network jump takes less GPU time than 32 FP64 solver steps of the
-    same lattices (measured about 1.25x with hi/lo activations and 1.7x with single-BF16
-    activations); against FP32 storage the solver is faster (about 0.37x / 0.5x)."""
+    same lattices, the solver on staged rows (batch mode 3) from the same random fields
+    (measured 1.25x with hi/lo activations and 1.35x with single-BF16 activations); against FP32
+    storage at three steps per pass the solver is faster (about 0.37x / 0.40x)."""
     import numpy as np
     from paper_2408_01081_gb300 import surrogate as S
     net = S.UNet((32, 64, 128, 256), seed=0)
