@@ -226,6 +226,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batch_accounting(mode, storage, descs, steps, ntiles_one_step):
+    """(algorithmic bytes per node and step, launches, tiles) of `steps` batch steps in `mode`
+    for lattices descs = [(nx, ny, bc, ...)], graphs of 100 steps.
+
+    Bytes: one read and one write of the state per launch (FP32 160 B per node, FP64 320); mode 2
+    runs 33 three-step passes and one single step per 100 steps.  Launches: mode 1 one per graph,
+    mode 2 two per pass (periodic and Dirichlet tiles) and one per single step, mode 3 one per step
+    and boundary kind present (every lattice of the benchmark's workload has cK/c and cmu/c in
+    [2^-60, 1/2), so all take the fixed-point update, whose lists are the two used).  Tiles: the
+    library's one-step work-list (modes 0 and 1, `ntiles_one_step`), else the mode's own tiles,
+    112 x 12 in mode 2 (FP32) and 128 x 4 in mode 3."""
+    passes, singles = (steps // 3, steps % 3) if mode == 2 else (0, steps)
+    bpn = (320 if storage == "f64" else 160) * (passes + singles) / steps
+    kinds = len({d[2] for d in descs})
+    launches = {1: steps // 100, 2: 2 * passes + singles, 3: kinds * steps}.get(mode, steps)
+    tile_shape = {2: (112, 12), 3: (128, 4)}.get(mode)
+    tiles = ntiles_one_step if tile_shape is None else sum(
+        math.ceil(d[0] / tile_shape[0]) * math.ceil(d[1] / tile_shape[1]) for d in descs)
+    return bpn, launches, tiles
+
+
 def run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws):
     """512 ragged lattices (config 4 of the workload set), FP32 (or FP64), graph of 100 steps per replay."""
     import workloads as W
@@ -266,21 +287,9 @@ def run_batch(args, lbm, torch, stream, dev, max_over_ranks, barrier, ws):
     lbm.lbm_batch_destroy(b)
     peaks = _peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
-    # algorithmic bytes per node and step: one read and one write of the state per launch; mode 2
-    # runs 33 three-step passes and one single step per 100 steps
-    passes, singles = (steps // 3, steps % 3) if mode == 2 else (0, steps)
-    bpn = (320 if storage == "f64" else 160) * (passes + singles) / steps
+    bpn, launches, tiles = batch_accounting(mode, storage, descs, steps, info["ntiles"])
     ach = bpn * nodes / (ms * 1e-3) / 1e9
-    # mode 3: one launch per step for each boundary kind present (every lattice of this workload
-    # has cK/c and cmu/c in [2^-60, 1/2), so all of them take the fixed-point node update)
-    kinds = len({d[2] for d in descs})
     label = {"f32": "FP32", "f64": "FP64"}[storage]
-    launches = {1: steps // 100, 2: 2 * passes + singles, 3: kinds * steps}.get(mode, steps)
-    # tiles of the mode that ran: the library reports its one-step work-list (modes 0 and 1);
-    # mode 2 cuts lattices into 112 x 12 tiles (FP32), mode 3 into 128 x 4 (fixed-point update)
-    tile_shape = {2: (112, 12), 3: (128, 4)}.get(mode)
-    tiles = info["ntiles"] if tile_shape is None else sum(
-        -(-d[0] // tile_shape[0]) * -(-d[1] // tile_shape[1]) for d in descs)
     return {"workload": f"{args.batch_count} lattices, short side log-uniform [64,1024], aspect U[1,4], nu U[0,0.49], "
                         "even periodic / odd homogeneous Dirichlet, GRF v0 (ell = short side/16, std 1e-3), "
                         f"{label} storage, CUDA graph of 100 steps per replay",

@@ -36,3 +36,20 @@ def test_traffic_figure_only_for_the_captured_sources():
     else:
         assert t is None and bench.pipe_counts() is None
     assert bench.traffic_per_launch("f64", 1000) is None      # captured size only, never scaled
+
+
+def test_batch_accounting_of_each_mode():
+    """Algorithmic bytes per node and step, launches and tiles that the batch leg reports, for a
+    periodic 200 x 13 and a Dirichlet 113 x 25 lattice over 200 steps (graphs of 100)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    descs = [(200, 13, 0), (113, 25, 1)]
+    # one launch per step, or one per graph; the library's own work-list
+    assert bench.batch_accounting(0, "f32", descs, 200, 77) == (160.0, 200, 77)
+    assert bench.batch_accounting(1, "f32", descs, 200, 77) == (160.0, 2, 77)
+    # three steps per pass: 66 passes of two launches and 2 single steps; 112 x 12 tiles: 2 x 2 + 2 x 3
+    bpn, launches, tiles = bench.batch_accounting(2, "f32", descs, 200, 77)
+    assert bpn == 160 * 68 / 200 and launches == 134 and tiles == 10
+    # FP64 on staged rows: 320 B, one launch per step and boundary kind; 128 x 4 tiles: 2 x 4 + 1 x 7
+    assert bench.batch_accounting(3, "f64", descs, 200, 77) == (320.0, 400, 15)
+    assert bench.batch_accounting(3, "f64", descs[:1], 200, 77) == (320.0, 200, 8)
